@@ -1,0 +1,855 @@
+"""Plain, slow FP64 CPU oracle for the octree-block multigrid method of arXiv 2403.08063.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call or execute this module; only the tests,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it.  It shares no code with the CUDA
+path: its forest tables, interpolation weights, transfer operators and solver are written here from the paper.
+
+What it computes
+----------------
+* Discretisation (Sec. 5, Eq. 1-2): -div(k grad u) = f on [0,1]^3, cell-centred finite volumes on a forest of
+  octree blocks (Sec. 2), every block holding n^3 cells plus one ghost layer (Sec. 3.3: "half of the ghost layers").
+  Point form: (A u)_i = (1/h_i^2) sum_faces T_f (u_i - u_f), u_f the neighbour or ghost value.
+  T_f = 1 for constant k, else the harmonic mean 2 k_i k_g / (k_i + k_g) (variable coefficients are future work
+  in Sec. 8; harmonic mean is the standard finite-volume reading).
+* Ghost exchange (Sec. 3.1): same-level copy; domain boundary Dirichlet reflection ghost = 2 g - u_i (g = 0);
+  coarse-to-fine (Sec. 3.3.2) quadratic Lagrange extrapolation: first along the normal through the current coarse
+  cell and two cells inward, then along each orthogonal axis through {-1, 0, +1}, with any base that falls in the
+  coarse block's ghost region remapped by -2o, targets at -h/4 (downwind) and +h/4 (upwind); fine-to-coarse
+  (Sec. 3.3.1) mean of the 2x2x2 fine inner cells overlapping a coarse ghost cell (weight 0.125).
+* Interface variants: 'P' is the paper's ghost-only scheme (coarse ghosts from the F2C mean).  'C' replaces the
+  coarse cell's interface flux by the sum of the four fine sub-face fluxes (coarse ghost written so that
+  T_C (u_C - G) = 1/2 sum_j T_j (g_j - u_j)), which makes the composite operator conservative.  The paper states
+  no conservation property; 'C' is this project's reading, 'P' reproduces the paper.
+* Multigrid (Sec. 5: block-local coarsening down to 4^3 cells per block): V(nu1, nu2) with red-black Gauss-Seidel,
+  colour (x+y+z) mod 2 of the block-local cell index (blocks have even n, so this is the global parity), red
+  first, an exchange before every half-sweep; residual restricted by the mean of the 8 children; prolongation
+  e_f = 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) with s_d towards the child's side; coarse levels rediscretised
+  with homogeneous Dirichlet data and k averaged over the 8 children; when the 4^3 level has more than
+  ``max_coarse`` unknowns, complete sibling octets at the deepest level are merged into their parent (a
+  coarsening step the paper does not need, since it smooths on the coarsest level); the coarsest level is solved
+  by a dense LU factorisation.
+* Stopping: volume-weighted L2 norm sqrt(sum h^3 r^2) of the residual relative to that of f (Sec. 5 says only
+  "L2 residual norm"; a normalised norm is the reading that gives the printed kappa near 0.25).
+* Adjoint: A^T applied matrix-free as the transposed stencil followed by the transposed ghost exchange; dL/df =
+  lambda and dL/dk = -lambda^T (dA/dk) u for L = 1/2 sum (u - u_t)^2.
+
+User layout: leaf-major in the order of the leaf list, each leaf n^3 interior cells with x fastest.
+"""
+from __future__ import annotations
+
+import functools
+from fractions import Fraction
+
+import numpy as np
+import scipy.linalg
+
+# ----------------------------------------------------------------------------------------------------------
+# Lagrange weights (Sec. 3.3.2: w_i(x) = prod_{j != i} (x - x_j) / (x_i - x_j))
+# ----------------------------------------------------------------------------------------------------------
+
+
+def lagrange_weights(nodes, x):
+    """Exact Lagrange basis weights at x for the given nodes (Sec. 3.3.2 weight formula)."""
+    nodes = [Fraction(v) for v in nodes]
+    x = Fraction(x)
+    out = []
+    for i, xi in enumerate(nodes):
+        w = Fraction(1)
+        for j, xj in enumerate(nodes):
+            if j != i:
+                w *= (x - xj) / (xi - xj)
+        out.append(w)
+    return out
+
+
+# Normal step: bases at the current coarse cell and the two cells inward (the -d_comm direction), measured in
+# coarse cells inward; the fine ghost centre lies h_c/4 outward of the current coarse centre.
+NORMAL_NODES = (0, 1, 2)
+NORMAL_TARGET = Fraction(-1, 4)
+NORMAL_W = [float(w) for w in lagrange_weights(NORMAL_NODES, NORMAL_TARGET)]
+
+
+def tangential_nodes(yc, n):
+    """Bases along an orthogonal axis for coarse cell yc of a block with n cells on that axis (Sec. 3.3.2).
+
+    Start from {-1, 0, +1}; a neighbour o in {-1, +1} lying in the ghost region (outside 0..n-1) is remapped to
+    the inner cell at -2o.
+    """
+    nodes = []
+    for o in (-1, 0, 1):
+        if o != 0 and not (0 <= yc + o <= n - 1):
+            nodes.append(-2 * o)
+        else:
+            nodes.append(o)
+    return nodes
+
+
+@functools.lru_cache(maxsize=None)
+def _tangential_matrix_cached(n, offset):
+    M = tangential_matrix_uncached(n, offset)
+    M.setflags(write=False)
+    return M
+
+
+def tangential_matrix(n, offset):
+    return _tangential_matrix_cached(n, offset)
+
+
+def tangential_matrix_uncached(n, offset):
+    """(n x n) map from the coarse cells of one tangential axis to the n fine ghost cells of a segment.
+
+    Fine index yf belongs to coarse cell yc = offset + yf // 2; even yf sits at -1/4 (downwind), odd at +1/4.
+    """
+    M = np.zeros((n, n))
+    for yf in range(n):
+        yc = offset + yf // 2
+        target = Fraction(-1, 4) if yf % 2 == 0 else Fraction(1, 4)
+        nodes = tangential_nodes(yc, n)
+        for node, w in zip(nodes, lagrange_weights(nodes, target)):
+            M[yf, yc + node] += float(w)
+    return M
+
+
+def harmonic(a, b):
+    return 2.0 * a * b / (a + b)
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Forest geometry and neighbour tables (Sec. 2, Sec. 3.1: N_neigh = 4 finer neighbours per face in 3D)
+# ----------------------------------------------------------------------------------------------------------
+
+
+def face_view(a, axis, side):
+    """View of a padded block array a[z, y, x] as [depth, t1, t2] for face (axis, side).
+
+    depth 0 is the ghost layer of that face, depth 1 the first interior layer, and so on; t1 < t2 are the two
+    other spatial axes in increasing order, in their original orientation.
+    """
+    t1, t2 = [d for d in range(3) if d != axis]
+    v = np.moveaxis(a, (2 - axis, 2 - t1, 2 - t2), (0, 1, 2))
+    return v[::-1] if side == 1 else v
+
+
+class Level:
+    """One multigrid level: a list of blocks (level, i, j, k) all holding n^3 cells."""
+
+    def __init__(self, R, n, keys):
+        self.R, self.n, self.keys = R, n, list(keys)
+        self.index = {key: b for b, key in enumerate(self.keys)}
+        self.nb = len(self.keys)
+        self.h = np.array([1.0 / (R * 2.0 ** key[0] * n) for key in self.keys])
+        self.faces = [[self._face(key, f // 2, f % 2) for f in range(6)] for key in self.keys]
+        self.kpad = None
+        self.T = None  # cached face coefficients (6 arrays (nb, n, n, n)) for variable k
+
+    def blocks_per_axis(self, lev):
+        m = self.R * 2.0 ** lev
+        assert m == int(m) and m >= 1, "level below the root grid"
+        return int(m)
+
+    def _face(self, key, axis, side):
+        lev = key[0]
+        idx = list(key[1:])
+        m = self.blocks_per_axis(lev)
+        p = idx.copy()
+        p[axis] += 1 if side == 1 else -1
+        if not (0 <= p[axis] < m):
+            return ("bnd",)
+        same = (lev, *p)
+        if same in self.index:
+            return ("same", self.index[same])
+        t1, t2 = [d for d in range(3) if d != axis]
+        parent = (lev - 1, p[0] // 2, p[1] // 2, p[2] // 2)
+        if parent in self.index:
+            return ("c2f", self.index[parent], (idx[t1] % 2, idx[t2] % 2))
+        segs = []
+        for s2 in (0, 1):
+            for s1 in (0, 1):
+                c = [0, 0, 0]
+                c[axis] = 2 * p[axis] + (1 if side == 0 else 0)
+                c[t1] = 2 * p[t1] + s1
+                c[t2] = 2 * p[t2] + s2
+                ck = (lev + 1, *c)
+                if ck not in self.index:
+                    raise ValueError(f"block {key} face {(axis, side)}: neighbourhood is not 2:1 balanced or has holes")
+                segs.append((self.index[ck], s1, s2))
+        return ("f2c", segs)
+
+    def zeros(self):
+        n = self.n
+        return np.zeros((self.nb, n + 2, n + 2, n + 2))
+
+    def colour_mask(self, c):
+        n = self.n
+        z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        return ((x + y + z) % 2) == c
+
+
+def check_forest(R, keys):
+    """The leaves tile the unit cube: no leaf is an ancestor of another and the volumes sum to 1."""
+    keyset = set(keys)
+    if len(keyset) != len(keys):
+        raise ValueError("duplicate leaves")
+    vol = Fraction(0)
+    for (l, i, j, k) in keys:
+        m = R * 2 ** l
+        if not (0 <= i < m and 0 <= j < m and 0 <= k < m):
+            raise ValueError("leaf outside the domain")
+        vol += Fraction(1, m ** 3)
+        a = (l, i, j, k)
+        while a[0] > 0:
+            a = (a[0] - 1, a[1] // 2, a[2] // 2, a[3] // 2)
+            if a in keyset:
+                raise ValueError("overlapping leaves")
+    if vol != 1:
+        raise ValueError("leaves do not cover the domain")
+
+
+# ----------------------------------------------------------------------------------------------------------
+# The solver
+# ----------------------------------------------------------------------------------------------------------
+
+
+class OracleMG:
+    """FP64 octree-block multigrid on one forest.
+
+    R: root blocks per axis; n: cells per block edge on the finest level (power of two, >= 4);
+    keys: leaf list (level, i, j, k); k_user: None for -Laplace, else (n_leaves, n^3) coefficient values.
+    """
+
+    def __init__(self, R, n, keys, k_user=None, variant="C", nu1=2, nu2=2, max_coarse=512, operator_only=False,
+                 bc=None):
+        """operator_only builds the finest level alone (for applying A, A^T and dA/dk; no solver).
+
+        bc: None for homogeneous Dirichlet data, else a vectorised g(x, y, z) giving the Dirichlet value at
+        boundary face centres of the finest level (Sec. 5, Eq. 2); coarse levels always use g = 0.
+        """
+        if n < 4 or n & (n - 1):
+            raise ValueError("n must be a power of two >= 4")
+        check_forest(R, list(keys))
+        self.R, self.n, self.variant = R, n, variant
+        self.nu1, self.nu2 = nu1, nu2
+        self.levels = [Level(R, n, keys)]
+        self.transfer = []  # transfer[l]: per coarse block of level l+1, ('halve', b) | ('copy', b) | ('merge', [8 b])
+        while self.levels[-1].n > 4 and not operator_only:
+            L = self.levels[-1]
+            self.levels.append(Level(R, L.n // 2, L.keys))
+            self.transfer.append([("halve", b) for b in range(L.nb)])
+        while self.levels[-1].nb * self.levels[-1].n ** 3 > max_coarse and not operator_only:
+            nxt = self._merge_deepest(self.levels[-1])
+            if nxt is None:
+                break
+            self.levels.append(nxt[0])
+            self.transfer.append(nxt[1])
+        self.gface = {}
+        if bc is not None:
+            L0 = self.levels[0]
+            for b, key in enumerate(L0.keys):
+                for f in range(6):
+                    if L0.faces[b][f][0] == "bnd":
+                        self.gface[(b, f)] = _boundary_face_values(R, n, key, f // 2, f % 2, bc)
+        self.coeff = k_user is not None
+        if self.coeff:
+            L0 = self.levels[0]
+            L0.kpad = self.to_pad(np.asarray(k_user, dtype=np.float64))
+            self.exchange_k(0)
+            for l in range(len(self.levels) - 1):
+                kc = self.levels[l + 1].zeros()
+                self._restrict_into(l, self.levels[l].kpad, kc)
+                self.levels[l + 1].kpad = kc
+                self.exchange_k(l + 1)
+            for l in range(len(self.levels)):
+                self._cache_T(l)
+        if not operator_only:
+            self._factor_coarsest()
+
+    # -- hierarchy -------------------------------------------------------------------------------------
+    def _merge_deepest(self, L):
+        deepest = max(key[0] for key in L.keys)
+        m_parent = L.R * 2.0 ** (deepest - 1)
+        if m_parent != int(m_parent) or m_parent < 1:
+            return None
+        groups = {}
+        for key in L.keys:
+            if key[0] == deepest:
+                groups.setdefault((deepest - 1, key[1] // 2, key[2] // 2, key[3] // 2), []).append(key)
+        parents = {p for p, ch in groups.items() if len(ch) == 8}
+        if not parents:
+            return None
+        merged = set()
+        for p in parents:
+            merged.update(groups[p])
+        keys = [k for k in L.keys if k not in merged] + sorted(parents, key=lambda t: (t[3], t[2], t[1]))
+        C = Level(L.R, L.n, keys)
+        tr = []
+        for key in C.keys:
+            if key in parents:
+                l, i, j, k = key
+                ch = [L.index[(l + 1, 2 * i + a, 2 * j + b, 2 * k + c)] for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+                tr.append(("merge", ch))
+            else:
+                tr.append(("copy", L.index[key]))
+        return C, tr
+
+    # -- layout ----------------------------------------------------------------------------------------
+    def to_pad(self, x_user, level=0):
+        L = self.levels[level]
+        n = L.n
+        U = L.zeros()
+        U[:, 1:-1, 1:-1, 1:-1] = np.asarray(x_user, dtype=np.float64).reshape(L.nb, n, n, n)
+        return U
+
+    def from_pad(self, U):
+        return U[:, 1:-1, 1:-1, 1:-1].reshape(U.shape[0], -1).copy()
+
+    # -- ghost exchange --------------------------------------------------------------------------------
+    def _c2f_values(self, Vc, n, seg):
+        """Fine ghost face (n x n, [t1, t2]) from the coarse view Vc (Sec. 3.3.2, 3D scheme)."""
+        E = NORMAL_W[0] * Vc[1, 1:-1, 1:-1] + NORMAL_W[1] * Vc[2, 1:-1, 1:-1] + NORMAL_W[2] * Vc[3, 1:-1, 1:-1]
+        M1 = tangential_matrix(n, seg[0] * n // 2)
+        M2 = tangential_matrix(n, seg[1] * n // 2)
+        return M1 @ E @ M2.T
+
+    def exchange(self, l, U):
+        """Fill every ghost face of level l's field U (homogeneous Dirichlet on the domain boundary)."""
+        L = self.levels[l]
+        n, h2 = L.n, n_half(L.n)
+        for b in range(L.nb):
+            for f in range(6):
+                axis, side = f // 2, f % 2
+                fc = L.faces[b][f]
+                V = face_view(U[b], axis, side)
+                if fc[0] == "bnd":
+                    g = self.gface.get((b, f)) if l == 0 else None
+                    V[0, 1:-1, 1:-1] = -V[1, 1:-1, 1:-1] if g is None else 2.0 * g - V[1, 1:-1, 1:-1]
+                elif fc[0] == "same":
+                    W = face_view(U[fc[1]], axis, 1 - side)
+                    V[0, 1:-1, 1:-1] = W[1, 1:-1, 1:-1]
+                elif fc[0] == "c2f":
+                    Vc = face_view(U[fc[1]], axis, 1 - side)
+                    V[0, 1:-1, 1:-1] = self._c2f_values(Vc, n, fc[2])
+                elif fc[0] == "f2c" and self.variant == "P":
+                    for (fb, s1, s2) in fc[1]:
+                        Vf = face_view(U[fb], axis, 1 - side)
+                        o1, o2 = s1 * h2, s2 * h2
+                        V[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2] = \
+                            Vf[1:3, 1:-1, 1:-1].reshape(2, h2, 2, h2, 2).mean(axis=(0, 2, 4))
+        if self.variant == "C":
+            for b in range(L.nb):
+                for f in range(6):
+                    fc = L.faces[b][f]
+                    if fc[0] == "f2c":
+                        self._f2c_flux(l, U, b, f // 2, f % 2, fc[1])
+
+    def _f2c_flux(self, l, U, b, axis, side, segs):
+        """Coarse ghost G with T_C (u_C - G) = 1/2 sum_j T_j (g_j - u_j) over the 4 fine cells j of each coarse face."""
+        L = self.levels[l]
+        h2 = n_half(L.n)
+        V = face_view(U[b], axis, side)
+        for (fb, s1, s2) in segs:
+            Vf = face_view(U[fb], axis, 1 - side)
+            o1, o2 = s1 * h2, s2 * h2
+            g = Vf[0, 1:-1, 1:-1]
+            u = Vf[1, 1:-1, 1:-1]
+            uc = V[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2]
+            if self.coeff:
+                Kf = face_view(L.kpad[fb], axis, 1 - side)
+                Tj = harmonic(Kf[1, 1:-1, 1:-1], Kf[0, 1:-1, 1:-1])
+                Kc = face_view(L.kpad[b], axis, side)
+                Tc = harmonic(Kc[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2], Kc[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2])
+            else:
+                Tj = np.ones_like(g)
+                Tc = np.ones_like(uc)
+            flux = (Tj * (g - u)).reshape(h2, 2, h2, 2).sum(axis=(1, 3))
+            V[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2] = uc - flux / (2.0 * Tc)
+
+    def exchange_k(self, l):
+        """Ghost k: boundary k_g = k_i; same level copy; fine ghosts inject the overlapping coarse cell's k;
+        coarse ghosts take the mean of the 8 overlapping fine k."""
+        L = self.levels[l]
+        K = L.kpad
+        h2 = n_half(L.n)
+        for b in range(L.nb):
+            for f in range(6):
+                axis, side = f // 2, f % 2
+                fc = L.faces[b][f]
+                V = face_view(K[b], axis, side)
+                if fc[0] == "bnd":
+                    V[0, 1:-1, 1:-1] = V[1, 1:-1, 1:-1]
+                elif fc[0] == "same":
+                    V[0, 1:-1, 1:-1] = face_view(K[fc[1]], axis, 1 - side)[1, 1:-1, 1:-1]
+                elif fc[0] == "c2f":
+                    Vc = face_view(K[fc[1]], axis, 1 - side)
+            # injection: fine ghost (yf, zf) lies in coarse cell (o1 + yf//2, o2 + zf//2) of the first layer
+                    o1, o2 = fc[2][0] * h2, fc[2][1] * h2
+                    seg = Vc[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2]
+                    V[0, 1:-1, 1:-1] = np.repeat(np.repeat(seg, 2, axis=0), 2, axis=1)
+                elif fc[0] == "f2c":
+                    for (fb, s1, s2) in fc[1]:
+                        Vf = face_view(K[fb], axis, 1 - side)
+                        o1, o2 = s1 * h2, s2 * h2
+                        V[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2] = \
+                            Vf[1:3, 1:-1, 1:-1].reshape(2, h2, 2, h2, 2).mean(axis=(0, 2, 4))
+
+    def _cache_T(self, l):
+        L = self.levels[l]
+        K = L.kpad
+        kc = K[:, 1:-1, 1:-1, 1:-1]
+        L.T = [harmonic(kc, nb) for nb in _neighbours(K)]
+
+    # -- stencil ---------------------------------------------------------------------------------------
+    def _T(self, l):
+        return self.levels[l].T if self.coeff else [1.0] * 6
+
+    def apply_padded(self, l, U):
+        """(A u) on the interior of level l, ghosts of U already filled."""
+        L = self.levels[l]
+        T = self._T(l)
+        uc = U[:, 1:-1, 1:-1, 1:-1]
+        acc = np.zeros_like(uc)
+        for Tf, nb in zip(T, _neighbours(U)):
+            acc += Tf * (uc - nb)
+        return acc / (L.h ** 2)[:, None, None, None]
+
+    def residual(self, l, U, F):
+        self.exchange(l, U)
+        return F - self.apply_padded(l, U)
+
+    def half_sweep(self, l, U, F, colour):
+        """Gauss-Seidel update of one colour: u_i = (h^2 f_i + sum_f T_f u_f) / sum_f T_f."""
+        L = self.levels[l]
+        self.exchange(l, U)
+        T = self._T(l)
+        num = (L.h ** 2)[:, None, None, None] * F
+        den = 0.0
+        for Tf, nb in zip(T, _neighbours(U)):
+            num = num + Tf * nb
+            den = den + Tf
+        new = num / den
+        mask = L.colour_mask(colour)[None]
+        uc = U[:, 1:-1, 1:-1, 1:-1]
+        U[:, 1:-1, 1:-1, 1:-1] = np.where(mask, new, uc)
+
+    def smooth(self, l, U, F, iters):
+        for _ in range(iters):
+            self.half_sweep(l, U, F, 0)
+            self.half_sweep(l, U, F, 1)
+
+    # -- transfers -------------------------------------------------------------------------------------
+    def _restrict_into(self, l, Xf, Xc_pad):
+        """Mean of the 8 children (8:1 restriction) from level l (padded or interior) into level l+1's interior."""
+        Lf, Lc = self.levels[l], self.levels[l + 1]
+        nf, nc = Lf.n, Lc.n
+        Xi = Xf[:, 1:-1, 1:-1, 1:-1] if Xf.shape[1] == nf + 2 else Xf
+        for B, tr in enumerate(self.transfer[l]):
+            if tr[0] == "copy":
+                Xc_pad[B, 1:-1, 1:-1, 1:-1] = Xi[tr[1]]
+                continue
+            fine = Xi[tr[1]] if tr[0] == "halve" else _assemble_octets([Xi[c] for c in tr[1]])
+            Xc_pad[B, 1:-1, 1:-1, 1:-1] = fine.reshape(nc, 2, nc, 2, nc, 2).mean(axis=(1, 3, 5))
+
+    def _prolong_add(self, l, Ec_pad, Uf):
+        """u_f += P e_c, P the face-neighbour linear cell-centred interpolation; Ec_pad has its ghosts filled."""
+        Lf, Lc = self.levels[l], self.levels[l + 1]
+        nc = Lc.n
+        for B, tr in enumerate(self.transfer[l]):
+            E = Ec_pad[B]
+            if tr[0] == "copy":
+                Uf[tr[1], 1:-1, 1:-1, 1:-1] += E[1:-1, 1:-1, 1:-1]
+                continue
+            P = np.zeros((2 * nc,) * 3)
+            c = E[1:-1, 1:-1, 1:-1]
+            for sz in (0, 1):
+                for sy in (0, 1):
+                    for sx in (0, 1):
+                        ex = E[1:-1, 1:-1, 2:] if sx else E[1:-1, 1:-1, :-2]
+                        ey = E[1:-1, 2:, 1:-1] if sy else E[1:-1, :-2, 1:-1]
+                        ez = E[2:, 1:-1, 1:-1] if sz else E[:-2, 1:-1, 1:-1]
+                        P[sz::2, sy::2, sx::2] = 0.25 * (c + ex + ey + ez)
+            if tr[0] == "halve":
+                Uf[tr[1], 1:-1, 1:-1, 1:-1] += P
+            else:
+                for o, cb in enumerate(tr[1]):
+                    a, bb, cc = o % 2, (o // 2) % 2, o // 4
+                    Uf[cb, 1:-1, 1:-1, 1:-1] += P[cc * nc:(cc + 1) * nc, bb * nc:(bb + 1) * nc, a * nc:(a + 1) * nc]
+
+    # -- coarsest solve --------------------------------------------------------------------------------
+    def _factor_coarsest(self):
+        l = len(self.levels) - 1
+        L = self.levels[l]
+        N = L.nb * L.n ** 3
+        A = np.zeros((N, N))
+        for m in range(N):
+            X = np.zeros(N)
+            X[m] = 1.0
+            U = L.zeros()
+            U[:, 1:-1, 1:-1, 1:-1] = X.reshape(L.nb, L.n, L.n, L.n)
+            self.exchange(l, U)
+            A[:, m] = self.apply_padded(l, U).reshape(-1)
+        self.A_coarse = A
+        self.lu = scipy.linalg.lu_factor(A)
+
+    def coarse_solve(self, F):
+        l = len(self.levels) - 1
+        L = self.levels[l]
+        U = L.zeros()
+        U[:, 1:-1, 1:-1, 1:-1] = scipy.linalg.lu_solve(self.lu, F.reshape(-1)).reshape(F.shape)
+        return U
+
+    # -- cycle -----------------------------------------------------------------------------------------
+    def vcycle(self, l, U, F):
+        if l == len(self.levels) - 1:
+            U[...] = self.coarse_solve(F)
+            return
+        self.smooth(l, U, F, self.nu1)
+        r = self.residual(l, U, F)
+        Fc = self.levels[l + 1].zeros()
+        self._restrict_into(l, r, Fc)
+        Fc = Fc[:, 1:-1, 1:-1, 1:-1].copy()
+        Ec = self.levels[l + 1].zeros()
+        self.vcycle(l + 1, Ec, Fc)
+        self.exchange(l + 1, Ec)
+        self._prolong_add(l, Ec, U)
+        self.smooth(l, U, F, self.nu2)
+
+    def norm(self, l, X):
+        L = self.levels[l]
+        return float(np.sqrt(np.sum((L.h ** 3)[:, None, None, None] * X ** 2)))
+
+    def solve(self, f_user, u0_user=None, cycles=None, rtol=None, max_cycles=100):
+        """V-cycles from u0 (default 0): exactly ``cycles`` of them, or until ||r|| / ||r_0|| <= rtol.
+
+        r_0 is the residual of the zero guess, i.e. f itself under homogeneous Dirichlet data.
+        Returns (u_user, list of relative residuals after each cycle).
+        """
+        F = self.to_pad(f_user)[:, 1:-1, 1:-1, 1:-1].copy()
+        U = self.to_pad(u0_user) if u0_user is not None else self.levels[0].zeros()
+        fn = self.norm(0, self.residual(0, self.levels[0].zeros(), F))
+        hist = []
+        ncyc = cycles if cycles is not None else max_cycles
+        for _ in range(ncyc):
+            self.vcycle(0, U, F)
+            rel = self.norm(0, self.residual(0, U, F)) / fn
+            hist.append(rel)
+            if rtol is not None and rel <= rtol:
+                break
+        return self.from_pad(U), hist
+
+    # -- plain operator in user layout -----------------------------------------------------------------
+    def apply_A(self, u_user, level=0):
+        U = self.to_pad(u_user, level)
+        self.exchange(level, U)
+        return self.apply_padded(level, U).reshape(U.shape[0], -1)
+
+    def rel_residual(self, u_user, f_user):
+        F = self.to_pad(f_user)[:, 1:-1, 1:-1, 1:-1]
+        U = self.to_pad(u_user)
+        return self.norm(0, self.residual(0, U, F)) / self.norm(0, F)
+
+    # -- adjoint ---------------------------------------------------------------------------------------
+    def apply_AT(self, y_user):
+        """A^T y on the finest level, in user layout."""
+        L = self.levels[0]
+        return self.apply_AT_level(0, y_user.reshape(L.nb, L.n, L.n, L.n)).reshape(L.nb, -1)
+
+    def apply_AT_level(self, l, Y_int):
+        """A^T y on level l (interior arrays): transposed stencil into a padded adjoint array, then the transposed
+        ghost exchange."""
+        L = self.levels[l]
+        Y = Y_int / (L.h ** 2)[:, None, None, None]
+        T = self._T(l)
+        G = L.zeros()
+        for Tf, sl in zip(T, _neighbour_slices()):
+            G[:, 1:-1, 1:-1, 1:-1] += Tf * Y
+            G[(slice(None),) + sl] -= Tf * Y
+        self.exchange_T(l, G)
+        return G[:, 1:-1, 1:-1, 1:-1].copy()
+
+    def exchange_T(self, l, G):
+        """Transpose of the (linear part of the) ghost exchange, in place on a padded adjoint array G: every ghost
+        adjoint is added into the interior cells its ghost value was computed from.  Reverse order of the forward
+        exchange: the flux-carrying coarse ghosts (variant C) first, then copies, reflections, C2F and F2C."""
+        L = self.levels[l]
+        n = L.n
+        h2 = n_half(n)
+        if self.variant == "C":
+            for b in range(L.nb):
+                for f in range(6):
+                    fc = L.faces[b][f]
+                    if fc[0] != "f2c":
+                        continue
+                    axis, side = f // 2, f % 2
+                    V = face_view(G[b], axis, side)
+                    for (fb, s1, s2) in fc[1]:
+                        o1, o2 = s1 * h2, s2 * h2
+                        Gg = V[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2]
+                        if self.coeff:
+                            Kf = face_view(L.kpad[fb], axis, 1 - side)
+                            Tj = harmonic(Kf[1, 1:-1, 1:-1], Kf[0, 1:-1, 1:-1])
+                            Kc = face_view(L.kpad[b], axis, side)
+                            Tc = harmonic(Kc[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2],
+                                          Kc[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2])
+                        else:
+                            Tj, Tc = np.ones((n, n)), np.ones((h2, h2))
+                        V[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2] += Gg
+                        cj = Tj / (2.0 * np.repeat(np.repeat(Tc, 2, axis=0), 2, axis=1))
+                        Gj = np.repeat(np.repeat(Gg, 2, axis=0), 2, axis=1)
+                        Vf = face_view(G[fb], axis, 1 - side)
+                        Vf[0, 1:-1, 1:-1] -= cj * Gj
+                        Vf[1, 1:-1, 1:-1] += cj * Gj
+        for b in range(L.nb):
+            for f in range(6):
+                axis, side = f // 2, f % 2
+                fc = L.faces[b][f]
+                V = face_view(G[b], axis, side)
+                gadj = V[0, 1:-1, 1:-1]
+                if fc[0] == "bnd":
+                    V[1, 1:-1, 1:-1] -= gadj
+                elif fc[0] == "same":
+                    face_view(G[fc[1]], axis, 1 - side)[1, 1:-1, 1:-1] += gadj
+                elif fc[0] == "c2f":
+                    seg = fc[2]
+                    M1 = tangential_matrix(n, seg[0] * n // 2)
+                    M2 = tangential_matrix(n, seg[1] * n // 2)
+                    back = M1.T @ gadj @ M2
+                    Vc = face_view(G[fc[1]], axis, 1 - side)
+                    for a in range(3):
+                        Vc[1 + a, 1:-1, 1:-1] += NORMAL_W[a] * back
+                elif fc[0] == "f2c" and self.variant == "P":
+                    for (fb, s1, s2) in fc[1]:
+                        o1, o2 = s1 * h2, s2 * h2
+                        Gg = V[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2]
+                        Vf = face_view(G[fb], axis, 1 - side)
+                        Vf[1:3, 1:-1, 1:-1] += np.repeat(np.repeat(Gg, 2, axis=0), 2, axis=1)[None] / 8.0
+
+    def _diag_lagged(self, l):
+        """sum_f T_f / h^2: the diagonal the ghost-lagged smoother divides by."""
+        L = self.levels[l]
+        T = self._T(l)
+        D = sum(np.broadcast_to(Tf, (L.nb, L.n, L.n, L.n)) for Tf in T)
+        return D / (L.h ** 2)[:, None, None, None]
+
+    def _restrict_T(self, l, Fc_bar):
+        """Transpose of the 8:1 mean restriction: each fine cell receives 1/8 of its parent's adjoint."""
+        Lf, Lc = self.levels[l], self.levels[l + 1]
+        nc = Lc.n
+        out = np.zeros((Lf.nb, Lf.n, Lf.n, Lf.n))
+        for B, tr in enumerate(self.transfer[l]):
+            x = Fc_bar[B]
+            if tr[0] == "copy":
+                out[tr[1]] += x
+                continue
+            big = np.repeat(np.repeat(np.repeat(x, 2, 0), 2, 1), 2, 2) / 8.0
+            if tr[0] == "halve":
+                out[tr[1]] += big
+            else:
+                for o, cb in enumerate(tr[1]):
+                    a, bb, cc = o % 2, (o // 2) % 2, o // 4
+                    out[cb] += big[cc * nc:(cc + 1) * nc, bb * nc:(bb + 1) * nc, a * nc:(a + 1) * nc]
+        return out
+
+    def _prolong_T(self, l, Ubar_int):
+        """Transpose of u_f += P e_c: the padded coarse adjoint of the interpolation stencil, then the transposed
+        coarse exchange (P reads coarse ghosts).  Returns the coarse interior adjoint."""
+        Lf, Lc = self.levels[l], self.levels[l + 1]
+        nc = Lc.n
+        Eb = Lc.zeros()
+        for B, tr in enumerate(self.transfer[l]):
+            if tr[0] == "copy":
+                Eb[B, 1:-1, 1:-1, 1:-1] += Ubar_int[tr[1]]
+                continue
+            Q = Ubar_int[tr[1]] if tr[0] == "halve" else _assemble_octets([Ubar_int[c] for c in tr[1]])
+            E = Eb[B]
+            for sz in (0, 1):
+                for sy in (0, 1):
+                    for sx in (0, 1):
+                        q = 0.25 * Q[sz::2, sy::2, sx::2]
+                        E[1:-1, 1:-1, 1:-1] += q
+                        E[1:-1, 1:-1, (slice(2, None) if sx else slice(0, -2))] += q
+                        E[1:-1, (slice(2, None) if sy else slice(0, -2)), 1:-1] += q
+                        E[(slice(2, None) if sz else slice(0, -2)), 1:-1, 1:-1] += q
+        self.exchange_T(l + 1, Eb)
+        return Eb[:, 1:-1, 1:-1, 1:-1].copy()
+
+    def _smooth_steps(self, nu):
+        return [c for _ in range(nu) for c in (0, 1)]
+
+    def vcycle_transposed(self, l, Ubar):
+        """M_l^T: the exact transpose of the forward V-cycle map f -> u (zero initial guess) on level l.
+
+        The forward cycle is a sequence of linear steps (half-sweeps u += Pi_c D^-1 (f - A u), residual,
+        restriction, coarse cycle, prolongation); its transpose runs them in reverse with each step transposed.
+        A half-sweep's transpose is: z = Pi_c D^-1 ubar; fbar += z; ubar -= A^T z.
+        Returns fbar (interior array of level l)."""
+        L = self.levels[l]
+        if l == len(self.levels) - 1:
+            return scipy.linalg.lu_solve(self.lu, Ubar.reshape(-1), trans=1).reshape(Ubar.shape)
+        D = self._diag_lagged(l)
+        masks = [L.colour_mask(0)[None], L.colour_mask(1)[None]]
+        ub = Ubar.copy()
+        fb = np.zeros_like(ub)
+
+        def smooth_T(steps):
+            nonlocal ub, fb
+            for c in reversed(steps):
+                z = np.where(masks[c], ub / D, 0.0)
+                fb += z
+                ub = ub - self.apply_AT_level(l, z)
+
+        smooth_T(self._smooth_steps(self.nu2))
+        ecb = self._prolong_T(l, ub)
+        fcb = self.vcycle_transposed(l + 1, ecb)
+        rb = self._restrict_T(l, fcb)
+        fb += rb
+        ub = ub - self.apply_AT_level(l, rb)
+        smooth_T(self._smooth_steps(self.nu1))
+        return fb
+
+    def adjoint_solve(self, g_user, rtol=1e-13, max_cycles=100, return_history=False):
+        """lambda with A^T lambda = g, by defect correction lambda += M^T (g - A^T lambda), M the forward V-cycle.
+
+        The error propagator is (I - M A)^T, so it converges at the forward cycle's rate.
+        """
+        L = self.levels[0]
+        n = L.n
+        G = np.asarray(g_user, dtype=np.float64).reshape(L.nb, n, n, n)
+        lam = np.zeros_like(G)
+        gn = self.norm(0, G)
+        hist = []
+        for _ in range(max_cycles):
+            lam = lam + self.vcycle_transposed(0, G - self.apply_AT_level(0, lam))
+            rel = self.norm(0, G - self.apply_AT_level(0, lam)) / gn
+            hist.append(rel)
+            if rel <= rtol:
+                break
+        else:
+            raise RuntimeError(f"adjoint multigrid did not reach {rtol} in {max_cycles} cycles: {hist[-3:]}")
+        lam = lam.reshape(L.nb, -1)
+        return (lam, hist) if return_history else lam
+
+    def grad_k(self, u_user, lam_user):
+        """dL/dk = -lambda^T (dA/dk) u, face by face through the harmonic-mean coefficients and ghost k maps."""
+        if not self.coeff:
+            raise ValueError("constant-coefficient problem has no k")
+        L = self.levels[0]
+        n = L.n
+        h2 = n_half(n)
+        U = self.to_pad(u_user)
+        self.exchange(0, U)
+        K = L.kpad
+        kc = K[:, 1:-1, 1:-1, 1:-1]
+        lam = lam_user.reshape(L.nb, n, n, n) / (L.h ** 2)[:, None, None, None]
+        uc = U[:, 1:-1, 1:-1, 1:-1]
+        grad = np.zeros_like(kc)
+        gadj = L.zeros()  # adjoint of the k value at neighbour/ghost positions
+        # mask out coarse-side interface faces in variant C (their row term is handled below)
+        skip = np.zeros((6,) + kc.shape, dtype=bool)
+        if self.variant == "C":
+            for b in range(L.nb):
+                for f in range(6):
+                    if L.faces[b][f][0] == "f2c":
+                        m = np.zeros((n + 2,) * 3, dtype=bool)
+                        face_view(m, f // 2, f % 2)[1, 1:-1, 1:-1] = True
+                        skip[f, b] = m[1:-1, 1:-1, 1:-1]
+        for f, (nb, sl) in enumerate(zip(_neighbours(K), _neighbour_slices())):
+            unb = _neighbours(U)[f]
+            d = uc - unb
+            dTa = 2.0 * nb ** 2 / (kc + nb) ** 2
+            dTb = 2.0 * kc ** 2 / (kc + nb) ** 2
+            w = np.where(skip[f], 0.0, -lam * d)
+            grad += w * dTa
+            gadj[(slice(None),) + sl] += w * dTb
+        grad += gadj[:, 1:-1, 1:-1, 1:-1]  # neighbours inside the block: their own k
+        for b in range(L.nb):
+            for f in range(6):
+                axis, side = f // 2, f % 2
+                fc = L.faces[b][f]
+                Vg = face_view(gadj[b], axis, side)
+                gr = _interior_view(grad[b], axis, side)
+                if fc[0] == "bnd":
+                    gr[0] += Vg[0, 1:-1, 1:-1]
+                elif fc[0] == "same":
+                    _interior_view(grad[fc[1]], axis, 1 - side)[0] += Vg[0, 1:-1, 1:-1]
+                elif fc[0] == "c2f":
+                    o1, o2 = fc[2][0] * h2, fc[2][1] * h2
+                    s = Vg[0, 1:-1, 1:-1].reshape(h2, 2, h2, 2).sum(axis=(1, 3))
+                    _interior_view(grad[fc[1]], axis, 1 - side)[0, o1:o1 + h2, o2:o2 + h2] += s
+                elif fc[0] == "f2c" and self.variant == "P":
+                    for (fb, s1, s2) in fc[1]:
+                        o1, o2 = s1 * h2, s2 * h2
+                        a = Vg[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2] / 8.0
+                        gi = _interior_view(grad[fb], axis, 1 - side)
+                        gi[0:2] += np.repeat(np.repeat(a, 2, axis=0), 2, axis=1)[None]
+                elif fc[0] == "f2c" and self.variant == "C":
+                    # row C term: (1/h_c^2) 1/2 sum_j T_j (g_j - u_j), T_j = harmonic(k_j, k_C)
+                    for (fb, s1, s2) in fc[1]:
+                        o1, o2 = s1 * h2, s2 * h2
+                        Vf = face_view(U[fb], axis, 1 - side)
+                        Kf = face_view(K[fb], axis, 1 - side)
+                        kj = Kf[1, 1:-1, 1:-1]
+                        kC = np.repeat(np.repeat(face_view(K[b], axis, side)[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2],
+                                                 2, axis=0), 2, axis=1)
+                        lC = np.repeat(np.repeat(_interior_view(lam[b], axis, side, padded=False)[0, o1:o1 + h2, o2:o2 + h2],
+                                                 2, axis=0), 2, axis=1)
+                        dd = 0.5 * (Vf[0, 1:-1, 1:-1] - Vf[1, 1:-1, 1:-1])
+                        w = -lC * dd
+                        _interior_view(grad[fb], axis, 1 - side)[0] += w * 2.0 * kC ** 2 / (kj + kC) ** 2
+                        s = (w * 2.0 * kj ** 2 / (kj + kC) ** 2).reshape(h2, 2, h2, 2).sum(axis=(1, 3))
+                        _interior_view(grad[b], axis, side)[0, o1:o1 + h2, o2:o2 + h2] += s
+        return grad.reshape(L.nb, -1)
+
+
+# ----------------------------------------------------------------------------------------------------------
+# small helpers
+# ----------------------------------------------------------------------------------------------------------
+
+
+def n_half(n):
+    return n // 2
+
+
+def _boundary_face_values(R, n, key, axis, side, g):
+    """g at the n x n face centres of a block's boundary face, in face_view order [t1, t2]."""
+    lev = key[0]
+    ext = 1.0 / (R * 2.0 ** lev)
+    h = ext / n
+    org = np.array(key[1:], dtype=np.float64) * ext
+    t1, t2 = [d for d in range(3) if d != axis]
+    c1 = org[t1] + (np.arange(n) + 0.5) * h
+    c2 = org[t2] + (np.arange(n) + 0.5) * h
+    A, B = np.meshgrid(c1, c2, indexing="ij")
+    X = [None, None, None]
+    X[axis] = np.full_like(A, org[axis] + (ext if side == 1 else 0.0))
+    X[t1], X[t2] = A, B
+    return g(X[0], X[1], X[2])
+
+
+def _neighbour_slices():
+    """Padded-array slices of the 6 face neighbours of every interior cell, order x-, x+, y-, y+, z-, z+."""
+    I = slice(1, -1)
+    return [
+        (I, I, slice(0, -2)), (I, I, slice(2, None)),
+        (I, slice(0, -2), I), (I, slice(2, None), I),
+        (slice(0, -2), I, I), (slice(2, None), I, I),
+    ]
+
+
+def _neighbours(U):
+    return [U[(slice(None),) + sl] for sl in _neighbour_slices()]
+
+
+def _interior_view(a, axis, side, padded=False):
+    """View [depth, t1, t2] of an interior-only block array (n, n, n) for face (axis, side); depth 0 = first layer."""
+    t1, t2 = [d for d in range(3) if d != axis]
+    v = np.moveaxis(a, (2 - axis, 2 - t1, 2 - t2), (0, 1, 2))
+    return v[::-1] if side == 1 else v
+
+
+def _assemble_octets(children):
+    """8 child blocks (n^3 each, octant order x fastest) -> one (2n)^3 array."""
+    n = children[0].shape[0]
+    out = np.zeros((2 * n,) * 3)
+    for o, c in enumerate(children):
+        a, b, cc = o % 2, (o // 2) % 2, o // 4
+        out[cc * n:(cc + 1) * n, b * n:(b + 1) * n, a * n:(a + 1) * n] = c
+    return out

@@ -1,0 +1,409 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics, not by the oracle itself.
+
+(a) 7-point exactness on polynomials; (b) O(h^2) convergence (kappa -> 0.25, Sec. 5 Eq. 3); (c) symmetry on
+uniform forests; (d) a uniformly refined forest reproduces the exact single-grid solve (DST-II); (e) flux
+conservation of the conservative interface variant; (f) dense direct solve on tiny forests; plus C2F
+triquadratic exactness in all nine remap cases (Sec. 3.3.2), F2C multilinear exactness (Sec. 3.3.1), transfer
+operators on linear functions, the transposed operator (dot-product test), and the adjoint gradients against
+finite differences of dense solves.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.fft
+
+import synthetic as syn
+from oracle.octree_mg import OracleMG, face_view
+from tests.helpers import (padded_centres, one_refined_root, poly3, neg_laplace_poly3, vw_norm, leaf_h)
+
+
+def _fill_exact(mg, level, p):
+    L = mg.levels[level]
+    U = L.zeros()
+    for b, key in enumerate(L.keys):
+        U[b] = p(*padded_centres(L.R, L.n, key))
+    return U
+
+
+# ---------------------------------------------------------------- interpolation at refinement interfaces
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_c2f_reproduces_triquadratic_all_nine_cases(n):
+    R = 2
+    keys = one_refined_root(R)
+    mg = OracleMG(R, n, keys, operator_only=True)
+    L = mg.levels[0]
+    rng = np.random.default_rng(1)
+    p = poly3(rng.normal(size=(3, 3, 3)))
+    Ue = _fill_exact(mg, 0, p)
+    U = Ue.copy()
+    mg.exchange(0, U)
+    cases = set()
+    checked = 0
+    for b in range(L.nb):
+        for f in range(6):
+            fc = L.faces[b][f]
+            if fc[0] not in ("c2f", "same"):
+                continue
+            got = face_view(U[b], f // 2, f % 2)[0, 1:-1, 1:-1]
+            want = face_view(Ue[b], f // 2, f % 2)[0, 1:-1, 1:-1]
+            np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(Ue).max())
+            if fc[0] == "c2f":
+                checked += 1
+                for yf in range(n):
+                    for zf in range(n):
+                        yc, zc = fc[2][0] * n // 2 + yf // 2, fc[2][1] * n // 2 + zf // 2
+                        cy = 1 if yc == 0 else (2 if yc == n - 1 else 0)
+                        cz = 1 if zc == 0 else (2 if zc == n - 1 else 0)
+                        cases.add((cy, cz))
+    assert checked == 12  # 3 fine-block faces x 4 coarse neighbours... each of 3 coarse faces holds 4 segments
+    assert cases == {(a, b) for a in range(3) for b in range(3)}
+
+
+def test_c2f_is_not_exact_for_cubics():
+    """Control: the scheme is quadratic, so a cubic in the normal direction is not reproduced."""
+    R, n = 2, 8
+    mg = OracleMG(R, n, one_refined_root(R), operator_only=True)
+    coef = np.zeros((4, 1, 1))
+    coef[3, 0, 0] = 1.0
+    Ue = _fill_exact(mg, 0, poly3(coef))
+    U = Ue.copy()
+    mg.exchange(0, U)
+    L = mg.levels[0]
+    err = 0.0
+    for b in range(L.nb):
+        for f in (0, 1):
+            if L.faces[b][f][0] == "c2f":
+                err = max(err, np.abs(face_view(U[b], 0, f)[0] - face_view(Ue[b], 0, f)[0]).max())
+    assert err > 1e-6
+
+
+def test_f2c_mean_exact_for_multilinear():
+    R, n = 2, 8
+    mg = OracleMG(R, n, one_refined_root(R), variant="P", operator_only=True)
+    L = mg.levels[0]
+    rng = np.random.default_rng(2)
+    p = poly3(rng.normal(size=(2, 2, 2)))
+    Ue = _fill_exact(mg, 0, p)
+    U = Ue.copy()
+    mg.exchange(0, U)
+    hits = 0
+    for b in range(L.nb):
+        for f in range(6):
+            if L.faces[b][f][0] == "f2c":
+                got = face_view(U[b], f // 2, f % 2)[0, 1:-1, 1:-1]
+                want = face_view(Ue[b], f // 2, f % 2)[0, 1:-1, 1:-1]
+                np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * np.abs(Ue).max())
+                hits += 1
+    assert hits == 3
+
+
+# ---------------------------------------------------------------- (a) stencil exactness
+
+
+@pytest.mark.parametrize("forest", ["uniform", "refined"])
+def test_a_operator_exact_on_triquadratics(forest):
+    R, n = 2, 8
+    keys = syn.uniform_leaves(R) if forest == "uniform" else one_refined_root(R)
+    mg = OracleMG(R, n, keys, operator_only=True)
+    rng = np.random.default_rng(3)
+    coef = rng.normal(size=(3, 3, 3))
+    U = _fill_exact(mg, 0, poly3(coef))
+    got = mg.apply_padded(0, U)
+    want = np.stack([neg_laplace_poly3(coef)(*[c[1:-1, 1:-1, 1:-1] for c in padded_centres(R, n, key)])
+                     for key in keys])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
+# ---------------------------------------------------------------- (b) second-order convergence
+
+
+def _manufactured_error(R, n, keys, variant="C"):
+    mg = OracleMG(R, n, keys, variant=variant)
+    f = syn.sin_product_rhs(R, n, keys).numpy()
+    ue = syn.sin_product(R, n, keys).numpy()
+    u, hist = mg.solve(f, rtol=1e-12, max_cycles=40)
+    assert hist[-1] <= 1e-12
+    return vw_norm(leaf_h(R, n, keys), u - ue)
+
+
+def test_b_kappa_uniform():
+    R = 2
+    keys = syn.uniform_leaves(R)
+    e = [_manufactured_error(R, n, keys) for n in (4, 8, 16)]
+    kap = [e[i + 1] / e[i] for i in range(2)]
+    assert 0.23 < kap[1] < 0.27, kap
+
+
+def test_b_kappa_refined():
+    R, _, keys = syn.workload_forest("sphere_2x4")
+    e = [_manufactured_error(R, n, keys, "C") for n in (4, 8, 16)]
+    kap = [e[i + 1] / e[i] for i in range(2)]
+    assert 0.2 < kap[1] < 0.3, kap
+
+
+def _golden_table():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_table_err_analysis.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].split()
+            if line:
+                rows[int(line[0])] = [float(v) for v in line[1:]]
+    return rows
+
+
+def test_b_paper_error_table_second_order():
+    """The paper's own accuracy problem with its ghost-only interface scheme (variant P), block sizes 16 and 32.
+
+    Loose pin: the paper leaves the Dirichlet discretisation and norm unstated; with the reflection ghost
+    2 g - u_i and the volume-weighted L2 norm the errors land within 12 % of the printed values and kappa near
+    0.25, while a wrong interpolation order would give kappa near 0.5 or 1 (the table's other columns).
+    """
+    table = _golden_table()
+    R, _, keys = syn.workload_forest("sphere_2x4")
+    g = lambda x, y, z: np.sin(np.pi * x) * np.sin(np.pi * y) * np.sinh(np.sqrt(2) * np.pi * z)  # noqa: E731
+    errs = {}
+    for n in (16, 32):
+        mg = OracleMG(R, n, keys, variant="P", bc=g)
+        u, hist = mg.solve(np.zeros((len(keys), n ** 3)), rtol=1e-12, max_cycles=40)
+        c = syn.cell_centres(R, n, keys).numpy().reshape(len(keys), -1, 3)
+        errs[n] = vw_norm(leaf_h(R, n, keys), u - g(c[..., 0], c[..., 1], c[..., 2]))
+        assert abs(errs[n] / table[n][2] - 1.0) < 0.12, (n, errs[n], table[n][2])
+    assert 0.23 < errs[32] / errs[16] < 0.26
+
+
+def test_b_kappa_variable_coefficient():
+    """k = 1 + 1/2 sin(2 pi x) sin(2 pi y) sin(2 pi z), u = sin pi x sin pi y sin pi z, f = -div(k grad u)."""
+    R, _, keys = syn.workload_forest("sphere_2x4")
+    errs = []
+    for n in (4, 8, 16):
+        c = syn.cell_centres(R, n, keys).numpy().reshape(len(keys), -1, 3)
+        x, y, z = c[..., 0], c[..., 1], c[..., 2]
+        pi = math.pi
+        k = 1 + 0.5 * np.sin(2 * pi * x) * np.sin(2 * pi * y) * np.sin(2 * pi * z)
+        u = np.sin(pi * x) * np.sin(pi * y) * np.sin(pi * z)
+        kx = pi * np.cos(2 * pi * x) * np.sin(2 * pi * y) * np.sin(2 * pi * z)
+        ky = pi * np.sin(2 * pi * x) * np.cos(2 * pi * y) * np.sin(2 * pi * z)
+        kz = pi * np.sin(2 * pi * x) * np.sin(2 * pi * y) * np.cos(2 * pi * z)
+        ux = pi * np.cos(pi * x) * np.sin(pi * y) * np.sin(pi * z)
+        uy = pi * np.sin(pi * x) * np.cos(pi * y) * np.sin(pi * z)
+        uz = pi * np.sin(pi * x) * np.sin(pi * y) * np.cos(pi * z)
+        f = 3 * pi ** 2 * k * u - (kx * ux + ky * uy + kz * uz)
+        mg = OracleMG(R, n, keys, k_user=k)
+        us, hist = mg.solve(f, rtol=1e-12, max_cycles=60)
+        assert hist[-1] <= 1e-12
+        errs.append(vw_norm(leaf_h(R, n, keys), us - u))
+    kap = errs[2] / errs[1]
+    assert 0.2 < kap < 0.3, errs
+
+
+# ---------------------------------------------------------------- (c) symmetry on uniform forests
+
+
+@pytest.mark.parametrize("coeff", [False, True])
+def test_c_symmetric_on_uniform_forest(coeff):
+    R, n = 2, 8
+    keys = syn.uniform_leaves(R)
+    k = syn.lognormal_k_rff(R, n, keys, seed=4).numpy() if coeff else None
+    mg = OracleMG(R, n, keys, k_user=k, operator_only=True)
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(len(keys), n ** 3))
+    y = rng.normal(size=(len(keys), n ** 3))
+    a, b = np.sum(x * mg.apply_A(y)), np.sum(y * mg.apply_A(x))
+    assert abs(a - b) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(mg.apply_A(y))
+
+
+# ---------------------------------------------------------------- (d) uniformly refined forest vs single grid
+
+
+def _dst_poisson(fgrid, N):
+    """Exact inverse of the cell-centred 7-point Laplacian with Dirichlet reflection on an N^3 grid, h = 1/N."""
+    m = np.arange(1, N + 1)
+    lam1 = (2.0 - 2.0 * np.cos(np.pi * m / N)) * N ** 2
+    lam = lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :]
+    return scipy.fft.idstn(scipy.fft.dstn(fgrid, type=2) / lam, type=2)
+
+
+def test_d_uniformly_refined_forest_matches_single_grid():
+    R, n = 2, 8
+    keys = syn.uniform_leaves(R, level=1)  # 64 blocks of 8^3 = a 32^3 grid
+    N = R * 2 * n
+    rng = np.random.default_rng(6)
+    f = rng.uniform(-1, 1, size=(len(keys), n ** 3))
+    mg = OracleMG(R, n, keys)
+    u, hist = mg.solve(f, rtol=1e-13, max_cycles=60)
+    fg = np.zeros((N, N, N))
+    for b, (_, i, j, k) in enumerate(keys):
+        fg[k * n:(k + 1) * n, j * n:(j + 1) * n, i * n:(i + 1) * n] = f[b].reshape(n, n, n)
+    ug = _dst_poisson(fg, N)
+    ub = np.stack([ug[k * n:(k + 1) * n, j * n:(j + 1) * n, i * n:(i + 1) * n].reshape(-1) for (_, i, j, k) in keys])
+    assert np.linalg.norm(u - ub) <= 1e-11 * np.linalg.norm(ub)
+
+
+# ---------------------------------------------------------------- (e) conservation
+
+
+def _boundary_flux(mg, u_user, k_user=None):
+    """sum over domain-boundary faces of h T (u_i - ghost) with ghost = -u_i: 2 h T u_i, T = k_i (or 1)."""
+    L = mg.levels[0]
+    n = L.n
+    U = mg.to_pad(u_user)
+    K = mg.to_pad(k_user) if k_user is not None else None
+    tot = 0.0
+    for b in range(L.nb):
+        for f in range(6):
+            if L.faces[b][f][0] == "bnd":
+                ui = face_view(U[b], f // 2, f % 2)[1, 1:-1, 1:-1]
+                T = face_view(K[b], f // 2, f % 2)[1, 1:-1, 1:-1] if K is not None else 1.0
+                tot += float(np.sum(2.0 * L.h[b] * T * ui))
+    return tot
+
+
+@pytest.mark.parametrize("coeff", [False, True])
+def test_e_conservative_variant_telescopes(coeff):
+    R, n, keys = syn.workload_forest("sphere_2x4")
+    k = syn.lognormal_k_rff(R, n, keys, seed=7).numpy() if coeff else None
+    rng = np.random.default_rng(8)
+    u = rng.normal(size=(len(keys), n ** 3))
+    h = leaf_h(R, n, keys)
+    mgC = OracleMG(R, n, keys, k_user=k, variant="C", operator_only=True)
+    total = float(np.sum(h[:, None] ** 3 * mgC.apply_A(u)))
+    bnd = _boundary_flux(mgC, u, k)
+    scale = float(np.sum(np.abs(h[:, None] ** 3 * mgC.apply_A(u))))
+    assert abs(total - bnd) <= 1e-13 * scale
+    mgP = OracleMG(R, n, keys, k_user=k, variant="P", operator_only=True)
+    totalP = float(np.sum(h[:, None] ** 3 * mgP.apply_A(u)))
+    assert abs(totalP - bnd) > 1e-6 * scale  # the paper's ghost-only scheme is not conservative
+
+
+# ---------------------------------------------------------------- (f) dense direct solve on a tiny forest
+
+
+def _dense(mg):
+    L = mg.levels[0]
+    N = L.nb * L.n ** 3
+    A = np.zeros((N, N))
+    for m in range(N):
+        e = np.zeros(N)
+        e[m] = 1.0
+        A[:, m] = mg.apply_A(e.reshape(L.nb, -1)).reshape(-1)
+    return A
+
+
+@pytest.mark.parametrize("coeff", [False, True])
+@pytest.mark.parametrize("variant", ["C", "P"])
+def test_f_multigrid_matches_dense_solve(coeff, variant):
+    R, n = 2, 4
+    keys = one_refined_root(R)
+    k = syn.lognormal_k_rff(R, n, keys, seed=9).numpy() if coeff else None
+    mg = OracleMG(R, n, keys, k_user=k, variant=variant)
+    assert [lv.nb for lv in mg.levels] == [15, 8]  # 8 children merged into their parent
+    f = np.random.default_rng(10).uniform(-1, 1, size=(len(keys), n ** 3))
+    u, hist = mg.solve(f, rtol=1e-14, max_cycles=80)
+    A = _dense(mg)
+    ud = np.linalg.solve(A, f.reshape(-1)).reshape(f.shape)
+    assert np.linalg.norm(u - ud) <= 1e-11 * np.linalg.norm(ud)
+
+
+# ---------------------------------------------------------------- transfer operators
+
+
+def test_transfers_exact_on_linear_functions():
+    R, _, keys = syn.workload_forest("sphere_2x4")
+    mg = OracleMG(R, 8, keys)
+    rng = np.random.default_rng(11)
+    a = rng.normal(size=4)
+    lin = lambda x, y, z: a[0] + a[1] * x + a[2] * y + a[3] * z  # noqa: E731
+    kinds = set()
+    for l in range(len(mg.levels) - 1):
+        Lf, Lc = mg.levels[l], mg.levels[l + 1]
+        kinds.update(t[0] for t in mg.transfer[l])
+        Ec = _fill_exact(mg, l + 1, lin)
+        Uf = Lf.zeros()
+        mg._prolong_add(l, Ec, Uf)
+        want = _fill_exact(mg, l, lin)[:, 1:-1, 1:-1, 1:-1]
+        np.testing.assert_allclose(Uf[:, 1:-1, 1:-1, 1:-1], want, atol=1e-13)
+        Xc = Lc.zeros()
+        mg._restrict_into(l, _fill_exact(mg, l, lin), Xc)
+        np.testing.assert_allclose(Xc[:, 1:-1, 1:-1, 1:-1], Ec[:, 1:-1, 1:-1, 1:-1], atol=1e-13)
+    assert kinds == {"halve", "merge", "copy"}
+
+
+def test_vcycle_convergence_factor():
+    R, n, keys = syn.workload_forest("uniform_2x16")
+    mg = OracleMG(R, n, keys)
+    f = syn.sin_product_rhs(R, n, keys).numpy()
+    _, hist = mg.solve(f, cycles=8)
+    rates = [hist[i + 1] / hist[i] for i in range(len(hist) - 1)]
+    assert max(rates) < 0.15, rates
+
+
+# ---------------------------------------------------------------- adjoint
+
+
+@pytest.mark.parametrize("variant", ["C", "P"])
+@pytest.mark.parametrize("coeff", [False, True])
+def test_transposed_operator_dot_product(variant, coeff):
+    R, n, keys = syn.workload_forest("sphere_2x4")
+    k = syn.lognormal_k_rff(R, n, keys, seed=12).numpy() if coeff else None
+    mg = OracleMG(R, n, keys, k_user=k, variant=variant, operator_only=True)
+    rng = np.random.default_rng(13)
+    x = rng.normal(size=(len(keys), n ** 3))
+    y = rng.normal(size=(len(keys), n ** 3))
+    Ay = mg.apply_A(y)
+    ATx = mg.apply_AT(x)
+    lhs, rhs = np.sum(x * Ay), np.sum(ATx * y)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(Ay)
+    if variant == "C" or coeff:
+        assert np.linalg.norm(ATx - mg.apply_A(x)) > 1e-6 * np.linalg.norm(ATx)  # refined: A is not symmetric
+
+
+@pytest.mark.parametrize("variant", ["C", "P"])
+def test_adjoint_solve_and_gradients_match_dense(variant):
+    R, n = 2, 4
+    keys = one_refined_root(R)
+    rng = np.random.default_rng(14)
+    k = syn.lognormal_k_rff(R, n, keys, seed=15).numpy()
+    f = rng.uniform(-1, 1, size=(len(keys), n ** 3))
+    ut = syn.sin_target(R, n, keys, seed=16).numpy()
+    mg = OracleMG(R, n, keys, k_user=k, variant=variant)
+    A = _dense(mg)
+    u = np.linalg.solve(A, f.reshape(-1)).reshape(f.shape)
+    g = u - ut
+    lam = mg.adjoint_solve(g, rtol=1e-13)
+    lam_d = np.linalg.solve(A.T, g.reshape(-1)).reshape(f.shape)
+    assert np.linalg.norm(lam - lam_d) <= 1e-10 * np.linalg.norm(lam_d)
+    grad = mg.grad_k(u, lam_d)
+
+    def loss(kk):
+        Ak = _dense(OracleMG(R, n, keys, k_user=kk, variant=variant, operator_only=True))
+        uu = np.linalg.solve(Ak, f.reshape(-1))
+        return 0.5 * np.sum((uu - ut.reshape(-1)) ** 2)
+
+    # directional derivatives along random directions (relative perturbation of k), central differences
+    for s in range(2):
+        d = np.random.default_rng(100 + s).normal(size=k.shape) * k
+        eps = 1e-6
+        fd = (loss(k + eps * d) - loss(k - eps * d)) / (2 * eps)
+        an = float(np.sum(grad * d))
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+@pytest.mark.parametrize("variant", ["C", "P"])
+def test_transposed_vcycle_is_the_transpose(variant):
+    """<x, M y> = <M^T x, y> for the forward V-cycle map M (zero initial guess) and its reverse sweep."""
+    R, n, keys = syn.workload_forest("sphere_2x4")
+    k = syn.lognormal_k_rff(R, n, keys, seed=17).numpy()
+    mg = OracleMG(R, n, keys, k_user=k, variant=variant)
+    L = mg.levels[0]
+    rng = np.random.default_rng(18)
+    x = rng.normal(size=(L.nb, n, n, n))
+    y = rng.normal(size=(L.nb, n, n, n))
+    U = L.zeros()
+    mg.vcycle(0, U, y.copy())
+    My = U[:, 1:-1, 1:-1, 1:-1]
+    MTx = mg.vcycle_transposed(0, x)
+    assert abs(np.sum(x * My) - np.sum(MTx * y)) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(My)
