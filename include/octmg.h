@@ -1,0 +1,117 @@
+/*
+ * octmg.h -- C ABI of the GB300 octree-block multigrid library (libocmg.so).
+ *
+ * The method is the matrix-free multigrid of arXiv 2403.08063 ("Towards Code Generation for Octree-Based
+ * Multigrid Solvers"): a forest of octree blocks over the unit cube (Sec. 2), every block holding n^3
+ * cell-centred unknowns plus one ghost layer (Sec. 3.3), with same-level, coarse-to-fine (quadratic, Sec. 3.3.2)
+ * and fine-to-coarse (linear, Sec. 3.3.1) ghost exchange, solving -div(k grad u) = f with Dirichlet data
+ * (Sec. 5, Eq. 1-2) by V-cycles whose coarse levels halve every block down to 4^3 cells (Sec. 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Field layout ("user layout"): leaf-major in the order of mg_config.leaves; each leaf holds its n^3 interior
+ *    cells with x fastest, i.e. element [leaf * n^3 + (z * n + y) * n + x].  FP64.
+ *  - Pointers named *_dev are CUDA device pointers, caller-owned; pointers named *_host are host pointers.
+ *    Device work is ordered on mg_config.stream; a call returns after its work is enqueued unless it returns a
+ *    host-visible result (residual norms, cycle counts), in which case it synchronises that stream.
+ *  - The library never keeps a caller pointer beyond the call.  mg_set_rhs copies f and k into the forest.
+ *  - Errors: every call returns mg_status; nothing is thrown across the ABI and no error traps the GPU.
+ *    mg_last_error() returns a thread-local description of the last failure.  CUDA errors map to MG_ERR_CUDA.
+ *  - Thread safety: a forest may be used by one host thread at a time.
+ */
+#ifndef OCTMG_H
+#define OCTMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_forest mg_forest; /* opaque, library-owned */
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum value */
+    MG_ERR_UNBALANCED = 2,    /* leaves do not tile the domain, overlap, or violate 2:1 face balance (Sec. 2) */
+    MG_ERR_BLOCK_SIZE = 3,    /* n not a power of two >= 4 (C2F needs 3 cells per axis, Sec. 3.3.2) */
+    MG_ERR_OOM = 4,           /* device or host allocation failed */
+    MG_ERR_CUDA = 5,          /* a CUDA call failed */
+    MG_ERR_NOT_CONVERGED = 6, /* residual did not reach rtol within max_cycles, or became non-finite */
+    MG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up (batched persistent kernel) */
+    MG_ERR_NONFINITE = 8,     /* NaN/Inf in an input field, or k <= 0 */
+    MG_ERR_STATE = 9          /* call out of order (e.g. solve before mg_set_rhs) */
+} mg_status;
+
+typedef struct {
+    int32_t roots;            /* R: root blocks per axis; the roots are R^3 cubes of edge 1/R over [0,1]^3 (Sec. 2) */
+    int32_t n;                /* cells per block edge on the finest level; power of two, >= 4 */
+    int32_t n_leaves;
+    const int32_t *leaves;    /* host, 5 * n_leaves int32: (problem, level, i, j, k); problem must be 0 here.
+                                 Leaf (level, i, j, k) covers [i, i+1] x [j, j+1] x [k, k+1] / (R 2^level). */
+    int32_t coeff;            /* 0: -Laplace(u) = f;  1: -div(k grad u) = f with per-cell k > 0 */
+    int32_t interface_flux;   /* 1 (default): conservative coarse-fine faces (the coarse flux is the sum of the four
+                                 fine sub-face fluxes); 0: the paper's ghost-only scheme (coarse ghost = F2C mean) */
+    int32_t precision;        /* 0: FP64 V-cycles; 1: FP32 V-cycles inside FP64 defect correction */
+    int32_t nu1, nu2;         /* pre/post red-black Gauss-Seidel iterations (2, 2) */
+    int32_t max_coarse;       /* octets are merged below 4^3 blocks until the coarsest level has at most this many
+                                 unknowns (default 512 when <= 0); that level is solved by a dense FP64 inverse */
+    void *stream;             /* cudaStream_t, or NULL for the legacy default stream */
+} mg_config;
+
+/* Build the forest: validate the leaves, build neighbour and segment tables for every multigrid level, allocate
+ * device pools.  For coeff == 0 the coarsest-level inverse is assembled here; for coeff == 1 in mg_set_rhs.
+ * Errors: MG_ERR_INVALID_ARG, MG_ERR_BLOCK_SIZE, MG_ERR_UNBALANCED, MG_ERR_OOM, MG_ERR_CUDA.  On error *out = NULL. */
+mg_status mg_forest_create(const mg_config *cfg, mg_forest **out);
+
+/* Free every device and host buffer of the forest (synchronises its stream).  NULL is a no-op. */
+void mg_forest_destroy(mg_forest *forest);
+
+/* Number of multigrid levels, and (optionally) per level the block count and block edge (host arrays of
+ * n_levels entries, either may be NULL).  Level 0 is the finest. */
+mg_status mg_forest_levels(const mg_forest *forest, int32_t *n_levels, int32_t *nb_per_level, int32_t *n_per_level);
+
+/* Block keys (level, i, j, k) of multigrid level `level`, in the level's block order (keys_host: 4 * nb int32). */
+mg_status mg_level_keys(const mg_forest *forest, int32_t level, int32_t *keys_host);
+
+/* Copy the right-hand side f (and, for coeff == 1, the coefficient k) into the forest; for coeff == 1 also build
+ * the coefficient pyramid (k of a coarse cell = mean of its 8 children) and the coarsest-level inverse.
+ * f_dev: n_leaves * n^3 doubles; k_dev: same size, every entry finite and > 0, or NULL when coeff == 0.
+ * Errors: MG_ERR_INVALID_ARG, MG_ERR_NONFINITE, MG_ERR_CUDA. */
+mg_status mg_set_rhs(mg_forest *forest, const double *f_dev, const double *k_dev);
+
+/* Run exactly ncycles V(nu1, nu2) cycles on u_dev (initial guess on entry, iterate on exit; FP64 cycles, or FP32
+ * cycles inside FP64 defect correction when precision == 1).  If rel_res_out is not NULL it receives
+ * ||f - A u|| / ||f|| after the last cycle (volume-weighted L2 norm sqrt(sum h^3 r^2)).  Requires mg_set_rhs. */
+mg_status mg_vcycle(mg_forest *forest, double *u_dev, int32_t ncycles, double *rel_res_out);
+
+/* Cycle from the initial guess in u_dev until ||f - A u|| / ||f|| <= rtol or max_cycles cycles ran.
+ * cycles_out / rel_res_out (host, may be NULL) receive the cycle count and final relative residual.
+ * Returns MG_ERR_NOT_CONVERGED (u_dev still holds the last iterate) when rtol is not reached. */
+mg_status mg_solve(mg_forest *forest, double *u_dev, double rtol, int32_t max_cycles, int32_t *cycles_out,
+                   double *rel_res_out);
+
+/* Adjoint of the converged solve for L = 1/2 sum_i (u_i - u_t,i)^2: given u_dev (the forward solution) and
+ * dLdu_dev = u - u_t, solve A^T lambda = dL/du by defect correction with the transposed V-cycle, write lambda
+ * (= dL/df) to lambda_dev and, when dLdk_dev is not NULL and coeff == 1, dL/dk = -lambda^T (dA/dk) u.
+ * All arrays n_leaves * n^3 doubles on the device.  Returns MG_ERR_NOT_CONVERGED if rtol is not reached. */
+mg_status mg_adjoint_solve(mg_forest *forest, const double *u_dev, const double *dLdu_dev, double *lambda_dev,
+                           double *dLdk_dev, double rtol, int32_t max_cycles);
+
+/* The finest-level operator: Au_dev = A u_dev (ghosts filled by the full exchange, homogeneous Dirichlet data),
+ * and its transpose ATy_dev = A^T y_dev.  Requires mg_set_rhs when coeff == 1. */
+mg_status mg_apply(mg_forest *forest, const double *u_dev, double *Au_dev);
+mg_status mg_apply_transpose(mg_forest *forest, const double *y_dev, double *ATy_dev);
+
+/* Debug view of one exchange: copy u_dev (user layout of level `level`, nb_level * n_level^3 doubles) into the
+ * level's FP64 pool, run that level's ghost exchange, and copy the whole padded pool (nb_level * (n_level+2)^3
+ * doubles, block-major, x fastest) to padded_dev. */
+mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
+
+/* Thread-local description of the last error (empty string if none). */
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCTMG_H */

@@ -1,0 +1,132 @@
+"""Python front end of the C ABI: torch tensors in, device pointers and the current stream out."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+F64 = torch.float64
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev_f64(t, numel, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != F64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with {numel} elements")
+    return t
+
+
+class Forest:
+    """A forest of octree blocks with its multigrid hierarchy (wraps mg_forest_create / mg_forest_destroy).
+
+    R: root blocks per axis; n: cells per block edge; leaves: (n_leaves, 5) int32 rows (problem, level, i, j, k)
+    or a list of (level, i, j, k) keys.  Fields are (n_leaves, n^3) float64 CUDA tensors in leaf order, x fastest.
+    """
+
+    def __init__(self, R, n, leaves, coeff=False, interface_flux=True, precision=0, nu1=2, nu2=2, max_coarse=512,
+                 stream=None):
+        self.lib = _lib.load()
+        arr = np.asarray(leaves, dtype=np.int32)
+        if arr.ndim == 2 and arr.shape[1] == 4:
+            arr = np.concatenate([np.zeros((arr.shape[0], 1), np.int32), arr], axis=1)
+        self._leaves = np.ascontiguousarray(arr, dtype=np.int32)
+        self.R, self.n, self.n_leaves = int(R), int(n), int(self._leaves.shape[0])
+        self.coeff = bool(coeff)
+        self.precision = int(precision)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = _lib.MGConfig()
+        cfg.roots, cfg.n, cfg.n_leaves = self.R, self.n, self.n_leaves
+        cfg.leaves = self._leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        cfg.coeff, cfg.interface_flux, cfg.precision = int(coeff), int(interface_flux), int(precision)
+        cfg.nu1, cfg.nu2, cfg.max_coarse = int(nu1), int(nu2), int(max_coarse)
+        cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.mg_forest_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self.numel = self.n_leaves * self.n ** 3
+
+    # -- lifetime ----------------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.mg_forest_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- structure ---------------------------------------------------------------------------------------
+    def levels(self):
+        nl = ctypes.c_int32()
+        _lib.check(self.lib.mg_forest_levels(self.h, ctypes.byref(nl), None, None))
+        nb = (ctypes.c_int32 * nl.value)()
+        nn = (ctypes.c_int32 * nl.value)()
+        _lib.check(self.lib.mg_forest_levels(self.h, ctypes.byref(nl), nb, nn))
+        return [(nb[i], nn[i]) for i in range(nl.value)]
+
+    def level_keys(self, level):
+        nb = self.levels()[level][0]
+        keys = np.zeros((nb, 4), dtype=np.int32)
+        _lib.check(self.lib.mg_level_keys(self.h, level, keys.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return [tuple(int(v) for v in r) for r in keys]
+
+    # -- solver ------------------------------------------------------------------------------------------
+    def set_rhs(self, f, k=None):
+        _dev_f64(f, self.numel, "f")
+        if self.coeff:
+            _dev_f64(k, self.numel, "k")
+        _lib.check(self.lib.mg_set_rhs(self.h, _ptr(f), _ptr(k) if self.coeff else None))
+
+    def vcycle(self, u, ncycles=1):
+        _dev_f64(u, self.numel, "u")
+        rel = ctypes.c_double()
+        _lib.check(self.lib.mg_vcycle(self.h, _ptr(u), int(ncycles), ctypes.byref(rel)))
+        return rel.value
+
+    def solve(self, u, rtol=1e-10, max_cycles=100, raise_on_failure=True):
+        """Cycle on u (initial guess in place) until ||f - A u|| / ||f|| <= rtol.  Returns (cycles, rel)."""
+        _dev_f64(u, self.numel, "u")
+        cyc = ctypes.c_int32()
+        rel = ctypes.c_double()
+        st = self.lib.mg_solve(self.h, _ptr(u), float(rtol), int(max_cycles), ctypes.byref(cyc), ctypes.byref(rel))
+        if st != 0 and (raise_on_failure or st != 6):
+            _lib.check(st)
+        return cyc.value, rel.value
+
+    def apply(self, u):
+        _dev_f64(u, self.numel, "u")
+        out = torch.empty_like(u)
+        _lib.check(self.lib.mg_apply(self.h, _ptr(u), _ptr(out)))
+        return out
+
+    def apply_transpose(self, y):
+        _dev_f64(y, self.numel, "y")
+        out = torch.empty_like(y)
+        _lib.check(self.lib.mg_apply_transpose(self.h, _ptr(y), _ptr(out)))
+        return out
+
+    def adjoint(self, u, dLdu, want_k=True, rtol=1e-12, max_cycles=100):
+        """lambda = A^-T dL/du (= dL/df) and, for coeff problems, dL/dk.  Returns (lambda, dLdk or None)."""
+        _dev_f64(u, self.numel, "u")
+        _dev_f64(dLdu, self.numel, "dLdu")
+        lam = torch.empty_like(u)
+        gk = torch.empty_like(u) if (want_k and self.coeff) else None
+        _lib.check(self.lib.mg_adjoint_solve(self.h, _ptr(u), _ptr(dLdu), _ptr(lam), _ptr(gk), float(rtol),
+                                             int(max_cycles)))
+        return lam, gk
+
+    def exchange_level(self, level, u):
+        nb, n = self.levels()[level]
+        _dev_f64(u, nb * n ** 3, "u")
+        out = torch.empty(nb * (n + 2) ** 3, dtype=F64, device=u.device)
+        _lib.check(self.lib.mg_exchange_level(self.h, int(level), _ptr(u), _ptr(out)))
+        return out.view(nb, n + 2, n + 2, n + 2)

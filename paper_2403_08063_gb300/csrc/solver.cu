@@ -1,0 +1,650 @@
+// The forest object, the V-cycle driver and the C-ABI entry points (include/octmg.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "octmg_internal.h"
+
+namespace octmg {
+
+thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+#define MG_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+            return MG_ERR_CUDA;                                                                \
+        }                                                                                      \
+    } while (0)
+
+#define MG_TRY(expr)                      \
+    do {                                  \
+        mg_status s_ = (expr);            \
+        if (s_ != MG_OK) return s_;       \
+    } while (0)
+
+constexpr int kMaxGrid = 152 * 32;  // grid-stride loops: at most 32 CTAs of 256 threads per SM
+
+inline int grid_for(int64_t total) {
+    int64_t g = (total + kThreads - 1) / kThreads;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, kMaxGrid)));
+}
+
+struct DevLevel {
+    LevelGeom g{};
+    FaceItem *faces = nullptr;
+    int nfaces = 0;
+    SegItem *segs = nullptr;
+    int nsegs = 0;
+    XferItem *xfer = nullptr;  // from this level to the next (per block of the next level)
+    double *h2 = nullptr;      // per block h^2
+    double *u64 = nullptr, *f64 = nullptr;
+    float *u32 = nullptr, *f32 = nullptr;
+    double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dinv = nullptr;
+    float *kap = nullptr;
+    Coef c64() const { return Coef{tx, ty, tz, dinv, nullptr}; }
+    Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, kap}; }
+    int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }
+    int64_t cells() const { return static_cast<int64_t>(g.nb) << (3 * g.lg); }
+};
+
+}  // namespace octmg
+
+struct mg_forest {
+    mg_config cfg{};
+    cudaStream_t st = nullptr;
+    octmg::HostHierarchy H;
+    std::vector<octmg::DevLevel> L;
+    std::vector<void *> allocs;
+    double *Ainv = nullptr;
+    int64_t *cmap = nullptr;
+    int Nc = 0;
+    double *partial = nullptr;  // 2 * kMaxGrid
+    double *sums = nullptr;     // 2 doubles on the device
+    double *pinned = nullptr;   // 2 doubles, host pinned
+    double *s64a = nullptr, *s64b = nullptr;  // level-0 FP64 scratch pools
+    double *coarse_r = nullptr;               // coarsest-level scratch pool (operator assembly)
+    int *flag = nullptr;                      // input-check flag
+    bool rhs_set = false;
+    double fnorm = 0.0;
+};
+
+namespace octmg {
+
+template <typename T>
+mg_status dalloc(mg_forest *F, T **p, int64_t count, bool zero = true) {
+    void *q = nullptr;
+    const size_t bytes = static_cast<size_t>(std::max<int64_t>(count, 1)) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
+    F->allocs.push_back(q);
+    if (zero) MG_CUDA(cudaMemsetAsync(q, 0, bytes, F->st));
+    *p = static_cast<T *>(q);
+    return MG_OK;
+}
+
+template <typename T>
+mg_status upload(mg_forest *F, T **p, const std::vector<T> &v) {
+    MG_TRY(dalloc(F, p, static_cast<int64_t>(v.size()), false));
+    if (!v.empty()) MG_CUDA(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));  // host vectors may die after return
+    return MG_OK;
+}
+
+int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Level operations
+// ---------------------------------------------------------------------------------------------------------------
+template <typename T> T *ufield(DevLevel &d);
+template <> double *ufield<double>(DevLevel &d) { return d.u64; }
+template <> float *ufield<float>(DevLevel &d) { return d.u32; }
+template <typename T> T *ffield(DevLevel &d);
+template <> double *ffield<double>(DevLevel &d) { return d.f64; }
+template <> float *ffield<float>(DevLevel &d) { return d.f32; }
+template <typename T> Coef coef_of(const DevLevel &d);
+template <> Coef coef_of<double>(const DevLevel &d) { return d.c64(); }
+template <> Coef coef_of<float>(const DevLevel &d) { return d.c32(); }
+
+template <typename T, int MODE>
+void exchange(mg_forest *F, DevLevel &d, T *u) {
+    if (d.nfaces)
+        k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(d.nfaces) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
+            u, d.faces, d.nfaces, d.g);
+    if (d.nsegs) {
+        const int64_t tot = static_cast<int64_t>(d.nsegs) * (d.g.n / 2) * (d.g.n / 2);
+        if (F->cfg.interface_flux)
+            k_exchange_segs<T, MODE, true><<<grid_for(tot), kThreads, 0, F->st>>>(u, coef_of<T>(d), d.segs, d.nsegs, d.g);
+        else
+            k_exchange_segs<T, MODE, false><<<grid_for(tot), kThreads, 0, F->st>>>(u, coef_of<T>(d), d.segs, d.nsegs, d.g);
+    }
+}
+
+void exchange_any64(mg_forest *F, DevLevel &d, double *u) {
+    if (F->cfg.coeff) exchange<double, 1>(F, d, u);
+    else exchange<double, 0>(F, d, u);
+}
+
+// Coefficient exchange: boundary copy, same-level copy, C2F injection, F2C mean (either interface variant).
+void exchange_k(mg_forest *F, DevLevel &d) {
+    if (d.nfaces)
+        k_exchange_faces<double, true><<<grid_for(static_cast<int64_t>(d.nfaces) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
+            d.k64, d.faces, d.nfaces, d.g);
+    if (d.nsegs)
+        k_exchange_segs<double, 0, false><<<grid_for(static_cast<int64_t>(d.nsegs) * (d.g.n / 2) * (d.g.n / 2)), kThreads, 0,
+                                             F->st>>>(d.k64, Coef{}, d.segs, d.nsegs, d.g);
+}
+
+template <typename T, int MODE>
+void smooth(mg_forest *F, DevLevel &d, int colour) {
+    k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2,
+                                                                       d.g, colour);
+}
+
+template <typename T, int MODE>
+void vcycle(mg_forest *F, int l) {
+    DevLevel &d = F->L[l];
+    const int last = static_cast<int>(F->L.size()) - 1;
+    if (l == last) {
+        k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d),
+                                                                                          F->Ainv, F->cmap, F->Nc);
+        return;
+    }
+    for (int i = 0; i < F->cfg.nu1; ++i) {
+        exchange<T, MODE>(F, d, ufield<T>(d));
+        smooth<T, MODE>(F, d, 0);
+        exchange<T, MODE>(F, d, ufield<T>(d));
+        smooth<T, MODE>(F, d, 1);
+    }
+    exchange<T, MODE>(F, d, ufield<T>(d));
+    DevLevel &c = F->L[l + 1];
+    k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
+        ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2, d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
+    vcycle<T, MODE>(F, l + 1);
+    exchange<T, MODE>(F, c, ufield<T>(c));
+    k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
+    for (int i = 0; i < F->cfg.nu2; ++i) {
+        exchange<T, MODE>(F, d, ufield<T>(d));
+        smooth<T, MODE>(F, d, 0);
+        exchange<T, MODE>(F, d, ufield<T>(d));
+        smooth<T, MODE>(F, d, 1);
+    }
+}
+
+// Level-0 FP64 residual r = f - A u (exchange first), optional output (scaled, cast) and zeroing; returns
+// ||r||^2 and ||f||^2 (volume-weighted) to the host.
+template <int MODE, typename TO>
+mg_status residual64(mg_forest *F, double *u, const double *f, TO *out, double scale, TO *zero_out, double *rr,
+                     double *ff) {
+    DevLevel &d = F->L[0];
+    exchange<double, MODE>(F, d, u);
+    const int grid = grid_for(d.cells());
+    k_residual_full<double, MODE, TO><<<grid, kThreads, 0, F->st>>>(u, f, d.c64(), d.h2, d.g, out, scale, F->partial,
+                                                                     zero_out);
+    k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
+    if (rr || ff) {
+        MG_CUDA(cudaMemcpyAsync(F->pinned, F->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, F->st));
+        MG_CUDA(cudaStreamSynchronize(F->st));
+        if (rr) *rr = F->pinned[0];
+        if (ff) *ff = F->pinned[1];
+    }
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status residual64_any(mg_forest *F, double *u, const double *f, double *rr, double *ff) {
+    if (F->cfg.coeff) return residual64<1, double>(F, u, f, nullptr, 1.0, nullptr, rr, ff);
+    return residual64<0, double>(F, u, f, nullptr, 1.0, nullptr, rr, ff);
+}
+
+// Coarsest-level dense operator (FP64 kernels on unit vectors), inverted on the host, uploaded.
+mg_status assemble_coarse(mg_forest *F) {
+    const int l = static_cast<int>(F->L.size()) - 1;
+    DevLevel &d = F->L[l];
+    const int N = static_cast<int>(d.cells());
+    F->Nc = N;
+    if (!F->cmap) {
+        std::vector<int64_t> cmap(N);
+        const int n = d.g.n;
+        for (int b = 0, m = 0; b < d.g.nb; ++b)
+            for (int z = 0; z < n; ++z)
+                for (int y = 0; y < n; ++y)
+                    for (int x = 0; x < n; ++x) cmap[m++] = b * d.g.bs + off3(x + 1, y + 1, z + 1, d.g.P);
+        MG_TRY(upload(F, &F->cmap, cmap));
+        MG_TRY(dalloc(F, &F->Ainv, static_cast<int64_t>(N) * N));
+    }
+    if (!F->coarse_r) MG_TRY(dalloc(F, &F->coarse_r, d.pool_elems()));
+    double *r = F->coarse_r, *Adev = F->Ainv;
+    for (int m = 0; m < N; ++m) {
+        MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
+        k_set_unit<<<1, 32, 0, F->st>>>(d.u64, F->cmap, m);
+        if (F->cfg.coeff) {
+            exchange<double, 1>(F, d, d.u64);
+            k_residual_full<double, 1, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
+                d.u64, nullptr, d.c64(), d.h2, d.g, r, 1.0, nullptr, nullptr);
+        } else {
+            exchange<double, 0>(F, d, d.u64);
+            k_residual_full<double, 0, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
+                d.u64, nullptr, d.c64(), d.h2, d.g, r, 1.0, nullptr, nullptr);
+        }
+        k_gather_column<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, N, Adev, m);
+    }
+    MG_CUDA(cudaGetLastError());
+    std::vector<double> A(static_cast<size_t>(N) * N);
+    MG_CUDA(cudaMemcpyAsync(A.data(), Adev, A.size() * sizeof(double), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (!invert_dense(A, N)) {
+        set_error("coarsest-level operator is singular");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaMemcpyAsync(Adev, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
+    MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    return MG_OK;
+}
+
+// Coefficient pyramid: k with ghosts on every level, face coefficients (FP64) and 1/k (FP32).
+mg_status build_coefficients(mg_forest *F) {
+    for (size_t l = 0; l < F->L.size(); ++l) {
+        DevLevel &d = F->L[l];
+        if (l > 0) {
+            DevLevel &p = F->L[l - 1];
+            k_restrict_field<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(p.k64, p.g, d.k64, p.xfer, d.g);
+        }
+        exchange_k(F, d);
+        k_face_coefs<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.k64, d.g, d.tx, d.ty, d.tz, d.kap);
+        k_diag_inv<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.g, d.dinv);
+    }
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename T>
+mg_status pack_user(mg_forest *F, DevLevel &d, T *pool, const double *user) {
+    k_pack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(pool, user, d.g);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename T>
+mg_status unpack_user(mg_forest *F, DevLevel &d, double *user, const T *pool) {
+    k_unpack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(user, pool, d.g);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+// One FP64 V-cycle on level 0.
+void vcycle64(mg_forest *F) {
+    if (F->cfg.coeff) vcycle<double, 1>(F, 0);
+    else vcycle<double, 0>(F, 0);
+}
+void vcycle32(mg_forest *F) {
+    if (F->cfg.coeff) vcycle<float, 2>(F, 0);
+    else vcycle<float, 0>(F, 0);
+}
+
+double pow2_near(double x) {
+    if (!(x > 0.0) || !std::isfinite(x)) return 1.0;
+    return std::ldexp(1.0, static_cast<int>(std::lround(std::log2(x))));
+}
+
+// Mixed precision: r64 = f - A u (FP64), written as FP32 r / s; FP32 V-cycle; u += s e.  `iters` outer steps;
+// returns the relative residual measured before the last update when `final_rel` is requested afterwards.
+mg_status mixed_step(mg_forest *F, double scale, double *rr) {
+    DevLevel &d = F->L[0];
+    if (F->cfg.coeff)
+        MG_TRY((residual64<1, float>(F, d.u64, d.f64, d.f32, 1.0 / scale, d.u32, rr, nullptr)));
+    else
+        MG_TRY((residual64<0, float>(F, d.u64, d.f64, d.f32, 1.0 / scale, d.u32, rr, nullptr)));
+    return MG_OK;
+}
+
+mg_status finish_mixed_cycle(mg_forest *F, double scale) {
+    DevLevel &d = F->L[0];
+    vcycle32(F);
+    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, scale, d.g);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status check_ready(mg_forest *F) {
+    if (!F) {
+        set_error("null forest");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (!F->rhs_set) {
+        set_error("mg_set_rhs has not been called");
+        return MG_ERR_STATE;
+    }
+    return MG_OK;
+}
+
+// Runs cycles until rel <= rtol (rtol < 0: exactly max_cycles).  u_dev in/out.
+mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, int *cycles_out, double *rel_out) {
+    MG_TRY(check_ready(F));
+    DevLevel &d = F->L[0];
+    MG_TRY(pack_user<double>(F, d, d.u64, u_dev));
+    const double fn = F->fnorm > 0.0 ? F->fnorm : 1.0;
+    int done = 0;
+    double rel = -1.0;
+    if (F->cfg.precision == 0) {
+        for (; done < max_cycles; ++done) {
+            if (rtol >= 0.0 && done > 0 && rel <= rtol) break;
+            vcycle64(F);
+            double rr = 0.0;
+            if (rtol >= 0.0 || rel_out || done + 1 == max_cycles) {
+                MG_TRY(residual64_any(F, d.u64, d.f64, &rr, nullptr));
+                rel = std::sqrt(rr) / fn;
+                if (!std::isfinite(rel)) {
+                    set_error("residual is not finite");
+                    ++done;
+                    break;
+                }
+            }
+        }
+    } else {
+        double rr = 0.0;
+        double scale = pow2_near(F->fnorm);
+        MG_TRY(mixed_step(F, scale, &rr));
+        rel = std::sqrt(rr) / fn;
+        for (; done < max_cycles; ++done) {
+            if (rtol >= 0.0 && rel <= rtol) break;
+            MG_TRY(finish_mixed_cycle(F, scale));
+            scale = pow2_near(std::sqrt(rr));
+            MG_TRY(mixed_step(F, scale, &rr));
+            rel = std::sqrt(rr) / fn;
+            if (!std::isfinite(rel)) {
+                set_error("residual is not finite");
+                ++done;
+                break;
+            }
+        }
+    }
+    MG_TRY(unpack_user<double>(F, d, u_dev, d.u64));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (cycles_out) *cycles_out = done;
+    if (rel_out) *rel_out = rel;
+    if (!std::isfinite(rel)) return MG_ERR_NOT_CONVERGED;
+    if (rtol >= 0.0 && !(rel <= rtol)) {
+        set_error("relative residual " + std::to_string(rel) + " above rtol after " + std::to_string(done) + " cycles");
+        return MG_ERR_NOT_CONVERGED;
+    }
+    return MG_OK;
+}
+
+mg_status create(const mg_config *cfg, mg_forest **out) {
+    if (!cfg || !out || !cfg->leaves || cfg->n_leaves <= 0) {
+        set_error("null config, output or leaves");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (cfg->coeff < 0 || cfg->coeff > 1 || cfg->precision < 0 || cfg->precision > 1 || cfg->nu1 < 0 || cfg->nu2 < 0 ||
+        cfg->nu1 + cfg->nu2 == 0 || cfg->interface_flux < 0 || cfg->interface_flux > 1) {
+        set_error("bad coeff / precision / nu1 / nu2 / interface_flux");
+        return MG_ERR_INVALID_ARG;
+    }
+    std::vector<Key> leaves(cfg->n_leaves);
+    for (int i = 0; i < cfg->n_leaves; ++i) {
+        const int32_t *r = cfg->leaves + 5 * static_cast<int64_t>(i);
+        if (r[0] != 0) {
+            set_error("leaf problem index must be 0 for a single forest");
+            return MG_ERR_INVALID_ARG;
+        }
+        leaves[i] = Key{r[1], r[2], r[3], r[4]};
+    }
+    mg_forest *F = new (std::nothrow) mg_forest();
+    if (!F) return MG_ERR_OOM;
+    F->cfg = *cfg;
+    F->cfg.leaves = nullptr;
+    if (F->cfg.max_coarse <= 0) F->cfg.max_coarse = 512;
+    F->st = static_cast<cudaStream_t>(cfg->stream);
+    std::string err;
+    mg_status st = build_hierarchy(cfg->roots, cfg->n, leaves, F->cfg.max_coarse, F->H, err);
+    if (st != MG_OK) {
+        set_error(err);
+        delete F;
+        return st;
+    }
+    auto fail = [&](mg_status s) {
+        mg_forest_destroy(F);
+        return s;
+    };
+    const size_t nl = F->H.levels.size();
+    F->L.resize(nl);
+    for (size_t l = 0; l < nl; ++l) {
+        const HostLevel &h = F->H.levels[l];
+        DevLevel &d = F->L[l];
+        d.g.nb = static_cast<int32_t>(h.keys.size());
+        d.g.n = h.n;
+        d.g.lg = ilog2(h.n);
+        d.g.P = h.n + 2;
+        const int64_t per = static_cast<int64_t>(d.g.P) * d.g.P * d.g.P;
+        d.g.bs = (per + 31) / 32 * 32;
+        d.nfaces = static_cast<int>(h.faces.size());
+        d.nsegs = static_cast<int>(h.segs.size());
+        if ((st = upload(F, &d.faces, h.faces)) != MG_OK) return fail(st);
+        if ((st = upload(F, &d.segs, h.segs)) != MG_OK) return fail(st);
+        if (!h.to_next.empty() && (st = upload(F, &d.xfer, h.to_next)) != MG_OK) return fail(st);
+        std::vector<double> h2(h.h.size());
+        for (size_t b = 0; b < h2.size(); ++b) h2[b] = h.h[b] * h.h[b];
+        if ((st = upload(F, &d.h2, h2)) != MG_OK) return fail(st);
+        const int64_t pe = d.pool_elems();
+        if ((st = dalloc(F, &d.u64, pe)) != MG_OK) return fail(st);
+        if ((st = dalloc(F, &d.f64, pe)) != MG_OK) return fail(st);
+        if (cfg->precision == 1) {
+            if ((st = dalloc(F, &d.u32, pe)) != MG_OK) return fail(st);
+            if ((st = dalloc(F, &d.f32, pe)) != MG_OK) return fail(st);
+        }
+        if (cfg->coeff) {
+            if ((st = dalloc(F, &d.k64, pe)) != MG_OK) return fail(st);
+            if ((st = dalloc(F, &d.tx, pe)) != MG_OK) return fail(st);
+            if ((st = dalloc(F, &d.ty, pe)) != MG_OK) return fail(st);
+            if ((st = dalloc(F, &d.tz, pe)) != MG_OK) return fail(st);
+            if ((st = dalloc(F, &d.dinv, pe)) != MG_OK) return fail(st);
+            if (cfg->precision == 1 && (st = dalloc(F, &d.kap, pe)) != MG_OK) return fail(st);
+        }
+    }
+    if ((st = dalloc(F, &F->partial, 2 * kMaxGrid)) != MG_OK) return fail(st);
+    if ((st = dalloc(F, &F->sums, 2)) != MG_OK) return fail(st);
+    if ((st = dalloc(F, &F->flag, 1)) != MG_OK) return fail(st);
+    if ((st = dalloc(F, &F->s64a, F->L[0].pool_elems())) != MG_OK) return fail(st);
+    if ((st = dalloc(F, &F->s64b, F->L[0].pool_elems())) != MG_OK) return fail(st);
+    if (cudaMallocHost(&F->pinned, 2 * sizeof(double)) != cudaSuccess) return fail(MG_ERR_OOM);
+    if (!cfg->coeff && (st = assemble_coarse(F)) != MG_OK) return fail(st);
+    if (cudaStreamSynchronize(F->st) != cudaSuccess) {
+        set_error("stream error during forest creation");
+        return fail(MG_ERR_CUDA);
+    }
+    *out = F;
+    return MG_OK;
+}
+
+__global__ void k_check_inputs(const double *__restrict__ f, const double *__restrict__ k, int64_t n,
+                               int *__restrict__ bad) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (!isfinite(f[i])) atomicOr(bad, 1);
+        if (k && !(isfinite(k[i]) && k[i] > 0.0)) atomicOr(bad, 2);
+    }
+}
+
+mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
+    if (!F || !f_dev) {
+        set_error("null forest or f");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (F->cfg.coeff && !k_dev) {
+        set_error("coeff == 1 needs k");
+        return MG_ERR_INVALID_ARG;
+    }
+    DevLevel &d = F->L[0];
+    int *bad = F->flag;
+    MG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), F->st));
+    k_check_inputs<<<grid_for(d.cells()), kThreads, 0, F->st>>>(f_dev, F->cfg.coeff ? k_dev : nullptr, d.cells(), bad);
+    int hbad = 0;
+    MG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (hbad) {
+        set_error(hbad & 2 ? "k must be finite and > 0" : "f has a non-finite entry");
+        return MG_ERR_NONFINITE;
+    }
+    MG_TRY(pack_user<double>(F, d, d.f64, f_dev));
+    if (F->cfg.coeff) {
+        MG_TRY(pack_user<double>(F, d, d.k64, k_dev));
+        MG_TRY(build_coefficients(F));
+        MG_TRY(assemble_coarse(F));
+    }
+    double ff = 0.0;
+    MG_CUDA(cudaMemsetAsync(F->s64a, 0, d.pool_elems() * sizeof(double), F->st));
+    MG_TRY(residual64_any(F, F->s64a, d.f64, nullptr, &ff));
+    F->fnorm = std::sqrt(ff);
+    F->rhs_set = true;
+    return MG_OK;
+}
+
+mg_status apply_op(mg_forest *F, const double *u_dev, double *Au_dev) {
+    if (!F || !u_dev || !Au_dev) {
+        set_error("null argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (F->cfg.coeff && !F->rhs_set) {
+        set_error("mg_set_rhs (k) has not been called");
+        return MG_ERR_STATE;
+    }
+    DevLevel &d = F->L[0];
+    MG_TRY(pack_user<double>(F, d, F->s64a, u_dev));
+    exchange_any64(F, d, F->s64a);
+    if (F->cfg.coeff)
+        k_residual_full<double, 1, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
+            F->s64a, nullptr, d.c64(), d.h2, d.g, F->s64b, -1.0, nullptr, nullptr);
+    else
+        k_residual_full<double, 0, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
+            F->s64a, nullptr, d.c64(), d.h2, d.g, F->s64b, -1.0, nullptr, nullptr);
+    MG_TRY(unpack_user<double>(F, d, Au_dev, F->s64b));
+    return MG_OK;
+}
+
+}  // namespace octmg
+
+using namespace octmg;
+
+extern "C" {
+
+mg_status mg_forest_create(const mg_config *cfg, mg_forest **out) {
+    if (out) *out = nullptr;
+    return create(cfg, out);
+}
+
+void mg_forest_destroy(mg_forest *F) {
+    if (!F) return;
+    cudaStreamSynchronize(F->st);
+    for (void *p : F->allocs) cudaFree(p);
+    if (F->pinned) cudaFreeHost(F->pinned);
+    delete F;
+}
+
+mg_status mg_forest_levels(const mg_forest *F, int32_t *n_levels, int32_t *nb_per_level, int32_t *n_per_level) {
+    if (!F || !n_levels) {
+        set_error("null argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    *n_levels = static_cast<int32_t>(F->L.size());
+    for (size_t l = 0; l < F->L.size(); ++l) {
+        if (nb_per_level) nb_per_level[l] = F->L[l].g.nb;
+        if (n_per_level) n_per_level[l] = F->L[l].g.n;
+    }
+    return MG_OK;
+}
+
+mg_status mg_level_keys(const mg_forest *F, int32_t level, int32_t *keys_host) {
+    if (!F || !keys_host || level < 0 || level >= static_cast<int32_t>(F->L.size())) {
+        set_error("bad argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    const HostLevel &h = F->H.levels[level];
+    for (size_t b = 0; b < h.keys.size(); ++b) {
+        keys_host[4 * b + 0] = h.keys[b].lev;
+        keys_host[4 * b + 1] = h.keys[b].i;
+        keys_host[4 * b + 2] = h.keys[b].j;
+        keys_host[4 * b + 3] = h.keys[b].k;
+    }
+    return MG_OK;
+}
+
+mg_status mg_set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) { return set_rhs(F, f_dev, k_dev); }
+
+mg_status mg_vcycle(mg_forest *F, double *u_dev, int32_t ncycles, double *rel_res_out) {
+    if (!F || !u_dev || ncycles < 0) {
+        set_error("bad argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    return run_cycles(F, u_dev, -1.0, ncycles, nullptr, rel_res_out);
+}
+
+mg_status mg_solve(mg_forest *F, double *u_dev, double rtol, int32_t max_cycles, int32_t *cycles_out,
+                   double *rel_res_out) {
+    if (!F || !u_dev || max_cycles < 0 || !(rtol >= 0.0)) {
+        set_error("bad argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    return run_cycles(F, u_dev, rtol, max_cycles, cycles_out, rel_res_out);
+}
+
+mg_status mg_apply(mg_forest *F, const double *u_dev, double *Au_dev) { return apply_op(F, u_dev, Au_dev); }
+
+mg_status mg_exchange_level(mg_forest *F, int32_t level, const double *u_dev, double *padded_dev) {
+    if (!F || !u_dev || !padded_dev || level < 0 || level >= static_cast<int32_t>(F->L.size())) {
+        set_error("bad argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (F->cfg.coeff && !F->rhs_set) {
+        set_error("mg_set_rhs (k) has not been called");
+        return MG_ERR_STATE;
+    }
+    DevLevel &d = F->L[level];
+    double *pool = nullptr;
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    MG_CUDA(cudaMalloc(&pool, d.pool_elems() * sizeof(double)));
+    cudaMemsetAsync(pool, 0, d.pool_elems() * sizeof(double), F->st);
+    k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(pool, u_dev, d.g);
+    exchange_any64(F, d, pool);
+    const size_t per = static_cast<size_t>(d.g.P) * d.g.P * d.g.P;
+    cudaMemcpy2DAsync(padded_dev, per * sizeof(double), pool, d.g.bs * sizeof(double), per * sizeof(double), d.g.nb,
+                      cudaMemcpyDeviceToDevice, F->st);
+    cudaError_t e = cudaStreamSynchronize(F->st);
+    cudaFree(pool);
+    if (e != cudaSuccess) {
+        set_error(std::string("exchange_level: ") + cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+const char *mg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+extern "C" {
+// Placeholders until the adjoint translation unit lands; they report MG_ERR_STATE.
+mg_status mg_apply_transpose(mg_forest *F, const double *, double *) {
+    (void)F;
+    octmg::set_error("mg_apply_transpose: not available in this build");
+    return MG_ERR_STATE;
+}
+mg_status mg_adjoint_solve(mg_forest *F, const double *, const double *, double *, double *, double, int32_t) {
+    (void)F;
+    octmg::set_error("mg_adjoint_solve: not available in this build");
+    return MG_ERR_STATE;
+}
+}
