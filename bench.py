@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the octree-block multigrid solve on GB300 (one JSON line on stdout, rank 0).
+
+Workload (default 'uniform_8x64_k'): 8^3 root blocks of 64^3 cells (512^3 = 134,217,728 cells) on the unit cube,
+-div(k grad u) = f with k = exp(g), g a seeded Gaussian random field (sigma 1, correlation length 0.1, random
+Fourier features), f ~ U(-1, 1) seeded, homogeneous Dirichlet data.  One step = one solve from u = 0 to a 1e-10
+relative residual with FP32 V(2,2) cycles inside FP64 defect correction (every kernel of the path runs: ghost
+exchange, red-black Gauss-Seidel, residual + restriction, prolongation, dense coarsest solve, FP64 outer residual
+and update).  The plain FP64 V-cycle solve of the same problem is timed in the same run.
+
+Metric: GLUPS per V(2,2) cycle = cells x cycles / time / 1e9, summed over ranks (independent replicas: the
+solver does not shard across GPUs).  Inputs (~4 GB per replica) exceed the 129 MB L2, so no flush is needed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "GLUPS per V(2,2) cycle (FP32-in-FP64 solve to 1e-10 relative residual)"
+UNIT = "GLUPS"
+
+WORKLOADS = {
+    # name: (forest, coefficient, rhs)
+    "uniform_8x64_k": ("uniform_8x64", True, "uniform"),
+    "sphere_2x32": ("sphere_2x32", False, "bump"),
+    "uniform_4x64_k": ("uniform_4x64", True, "uniform"),
+}
+
+
+def _inputs(workload, device, seed=0):
+    import synthetic as syn
+    forest, coeff, rhs = WORKLOADS[workload]
+    R, n, keys = syn.workload_forest(forest)
+    k = syn.lognormal_k_rff(R, n, keys, seed=seed, device=device) if coeff else None
+    if rhs == "uniform":
+        f = syn.uniform_rhs(len(keys), n, seed=seed + 1).to(device)
+    else:
+        f = syn.gaussian_bump_with_noise(R, n, keys, seed=seed + 1, device=device)
+    return R, n, keys, k, f
+
+
+# ------------------------------------------------------------------------------------------------------------
+# byte and flop models of the kernel families (per cell of the level a launch covers)
+# ------------------------------------------------------------------------------------------------------------
+def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total):
+    """Algorithmic bytes and FP64 flops of one family over the timed region.
+
+    Per cell of the level a launch sweeps:
+      smooth_f32       8 B   (one colour of the 16 B/cell RBGS iteration: u read, f read, 1/k read, u write, FP32)
+      smooth_f64      12 B   (24 B/cell RBGS iteration for -Laplace in FP64: u, f, u)
+      residual_f64    32 B   (u, f, k read as FP64; r written as FP32; FP32 correction zeroed) and 27 FP64 flops
+                             (stencil 11, diagonal 5, residual 4, scaling 1, two volume-weighted norms 6)
+      update_mixed    20 B   (u64 read + write, e32 read)
+    """
+    cells = [nb * n ** 3 for nb, n in levels]
+    sweeps = 2 * (nu1 + nu2)
+    if fam == "smooth_f32":
+        b = sum(c for c in cells[:-1]) * sweeps * 8 * cycles_total
+        return b, 0.0
+    if fam == "smooth_f64":
+        per = 16 if coeff else 12
+        b = sum(c for c in cells[:-1]) * sweeps * per * cycles_total
+        return b, 0.0
+    if fam == "residual_f64":
+        return cells[0] * 32 * outer_total, cells[0] * 27.0 * outer_total
+    if fam == "update_mixed":
+        return cells[0] * 20 * cycles_total, 0.0
+    return None, None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mp = json.load(fh)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            bus = torch.cuda.get_device_properties(self.dev).pci_bus_id if hasattr(
+                torch.cuda.get_device_properties(self.dev), "pci_bus_id") else None
+        except Exception:
+            bus = None
+        sel = ["-i", bus] if bus else []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", *sel], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist, rank, ws, local
+    return None, 0, 1, 0
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline): bounded sample of the same recipe
+# ------------------------------------------------------------------------------------------------------------
+ORACLE_SAMPLE = ("uniform_2x64", "2^3 roots of 64^3 cells (2,097,152 cells) of the same recipe (log-normal k, "
+                 "U(-1,1) f), FP64 V(2,2) cycles of the numpy oracle on one host core")
+
+
+def _oracle_setup():
+    import synthetic as syn
+    from oracle.octree_mg import OracleMG
+    R, n = 2, 64
+    keys = syn.uniform_leaves(R)
+    k = syn.lognormal_k_rff(R, n, keys, seed=0).numpy()
+    f = syn.uniform_rhs(len(keys), n, seed=1).numpy()
+    mg = OracleMG(R, n, keys, k_user=k)
+    return mg, f, len(keys) * n ** 3
+
+
+def _oracle_cycle(mg, f, U, F):
+    mg.vcycle(0, U, F)
+
+
+def run_reference(args):
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return
+    mg, f, cells = _oracle_setup()
+    F = mg.to_pad(f)[:, 1:-1, 1:-1, 1:-1].copy()
+    U = mg.levels[0].zeros()
+    for _ in range(args.warmup):
+        mg.vcycle(0, U, F)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mg.vcycle(0, U, F)
+    dt = time.perf_counter() - t0
+    value = cells * args.steps / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": ORACLE_SAMPLE[0]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE[1]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(budget_s=20.0):
+    mg, f, cells = _oracle_setup()
+    F = mg.to_pad(f)[:, 1:-1, 1:-1, 1:-1].copy()
+    U = mg.levels[0].zeros()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        mg.vcycle(0, U, F)
+        n += 1
+        if time.perf_counter() - t0 > budget_s / 2 or n >= 4:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cells * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ORACLE_SAMPLE[1]}; {n} cycles in {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------------------
+def run_ours(args):
+    from paper_2403_08063_gb300 import Forest
+    dist, rank, ws, local = _dist()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    R, n, keys, k, f = _inputs(args.workload, dev)
+    coeff = k is not None
+    cells = len(keys) * n ** 3
+    F = Forest(R, n, keys, coeff=coeff, precision=1)
+    F.set_rhs(f, k)
+    levels = F.levels()
+    u = torch.zeros_like(f)
+
+    def step(forest):
+        u.zero_()
+        cyc, rel = forest.solve(u, rtol=args.rtol, max_cycles=60)
+        return cyc, rel
+
+    for _ in range(args.warmup):
+        step(F)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    F.profile(True)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cycles = []
+    rels = []
+    for _ in range(args.steps):
+        c, r = step(F)
+        cycles.append(c)
+        rels.append(r)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clocks = sampler.stop()
+    prof = F.profile_read()
+    F.profile(False)
+    t = _max_over_ranks(dist, e0.elapsed_time(e1) / 1e3)
+    tot_cycles = sum(cycles)
+    value = cells * tot_cycles / t / 1e9 * ws
+    launches = sum(v[1] for v in prof.values())
+
+    # roofline of the dominant family
+    fam = max((k_ for k_ in prof if prof[k_][1] > 0), key=lambda k_: prof[k_][0])
+    outer = tot_cycles + args.steps  # one FP64 residual per cycle plus the initial one
+    bytes_, flops = _family_work(fam, levels, 2, 2, coeff, tot_cycles, outer)
+    hbm, src = _peaks()
+    fam_s = prof[fam][0] / 1e3
+    roof = None
+    if bytes_ is not None:
+        if fam == "residual_f64":
+            fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+            ach = flops / fam_s / 1e12
+            roof = {"kernel": fam, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak, "traffic": None, "peak_source": "derived FP64 FMA issue rate",
+                    "hbm_achieved_gbs": bytes_ / fam_s / 1e9}
+        else:
+            ach = bytes_ / fam_s / 1e9
+            roof = {"kernel": fam, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "peak_source": src}
+        roof["launches"] = prof[fam][1]
+        roof["avg_launch_ms"] = prof[fam][0] / max(1, prof[fam][1])
+
+    # plain FP64 V-cycles on the same problem (time to 1e-10)
+    F64 = Forest(R, n, keys, coeff=coeff, precision=0)
+    F64.set_rhs(f, k)
+    step(F64)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps64 = 2
+    s0.record(stream)
+    cyc64 = []
+    for _ in range(reps64):
+        c, _r = step(F64)
+        cyc64.append(c)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    t64 = s0.elapsed_time(s1) / 1e3 / reps64
+    F64.close()
+
+    # end to end through host buffers: H2D of f and k, set_rhs, solve, D2H of u
+    fh = f.cpu().pin_memory()
+    kh = k.cpu().pin_memory() if coeff else None
+    uh = torch.empty_like(fh).pin_memory()
+    fd, kd = torch.empty_like(f), (torch.empty_like(k) if coeff else None)
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_cycles = 0
+    h0.record(stream)
+    for _ in range(e2e_steps):
+        fd.copy_(fh, non_blocking=True)
+        if coeff:
+            kd.copy_(kh, non_blocking=True)
+        F.set_rhs(fd, kd)
+        c, _r = step(F)
+        e2e_cycles += c
+        uh.copy_(u, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    te2e = _max_over_ranks(dist, h0.elapsed_time(h1) / 1e3)
+
+    out = None
+    if rank == 0:
+        tmix = t / args.steps
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 outer", "data": "synthetic",
+            "config": {"workload": args.workload, "cells": cells, "blocks": len(keys), "block": f"{n}^3",
+                       "levels": levels, "coefficient": "log-normal k (sigma 1, ell 0.1)" if coeff else "1",
+                       "rhs": WORKLOADS[args.workload][2], "rtol": args.rtol, "cycle": "V(2,2) red-black GS",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"{ws} independent replicas"},
+            "cycles_per_solve": cycles, "final_rel_residual": rels[-1],
+            "time_to_rtol_s": {"fp32_in_fp64": tmix, "fp64": t64, "speedup": t64 / tmix},
+            "fp64_cycles_per_solve": cyc64, "fp64_glups_per_cycle": cells * statistics.mean(cyc64) / t64 / 1e9,
+            "roofline": roof,
+            "kernel_families_ms": {k_: round(v[0], 3) for k_, v in prof.items() if v[1]},
+            "kernel_families_launches": {k_: v[1] for k_, v in prof.items() if v[1]},
+            "gpu_launches": launches,
+            "e2e": {"value": cells * e2e_cycles / te2e / 1e9 * ws, "unit": UNIT,
+                    "h2d_bytes_per_step": int(fh.numel() * 8 * (2 if coeff else 1)),
+                    "d2h_bytes_per_step": int(uh.numel() * 8),
+                    "includes": "H2D f,k + mg_set_rhs (coefficient pyramid, coarsest inverse) + solve + D2H u"},
+            "clocks": clocks,
+        }
+    F.close()
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform_8x64_k")
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

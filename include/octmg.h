@@ -108,6 +108,15 @@ mg_status mg_apply_transpose(mg_forest *forest, const double *y_dev, double *ATy
  * doubles, block-major, x fastest) to padded_dev. */
 mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
 
+/* Kernel accounting.  Launch counters per kernel family always run; mg_profile(forest, 1) clears them and starts
+ * recording a CUDA-event pair on the forest's stream around every family's launches, mg_profile(forest, 0) stops.
+ * mg_profile_read synchronises the stream and, for up to max_families families, writes the family name (32 bytes
+ * each, NUL-terminated) into names, the summed event time in milliseconds into ms and the launch count into
+ * launches (each output may be NULL); *n_families receives the number of families. */
+mg_status mg_profile(mg_forest *forest, int32_t enable);
+mg_status mg_profile_read(mg_forest *forest, int32_t max_families, char *names, double *ms, int64_t *launches,
+                          int32_t *n_families);
+
 /* Thread-local description of the last error (empty string if none). */
 const char *mg_last_error(void);
 

@@ -130,3 +130,22 @@ class Forest:
         out = torch.empty(nb * (n + 2) ** 3, dtype=F64, device=u.device)
         _lib.check(self.lib.mg_exchange_level(self.h, int(level), _ptr(u), _ptr(out)))
         return out.view(nb, n + 2, n + 2, n + 2)
+
+    # -- accounting --------------------------------------------------------------------------------------
+    def profile(self, enable=True):
+        _lib.check(self.lib.mg_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """{family: (milliseconds, launches)} of the kernel families since the last profile(True)."""
+        nf = ctypes.c_int32()
+        _lib.check(self.lib.mg_profile_read(self.h, 0, None, None, None, ctypes.byref(nf)))
+        m = nf.value
+        names = ctypes.create_string_buffer(32 * m)
+        ms = (ctypes.c_double * m)()
+        cnt = (ctypes.c_int64 * m)()
+        _lib.check(self.lib.mg_profile_read(self.h, m, names, ms, cnt, ctypes.byref(nf)))
+        out = {}
+        for i in range(m):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+            out[nm] = (ms[i], int(cnt[i]))
+        return out

@@ -72,6 +72,12 @@ struct mg_forest {
     int *flag = nullptr;                      // input-check flag
     bool rhs_set = false;
     double fnorm = 0.0;
+    // per-kernel-family launch counters (always on) and CUDA-event timing (mg_profile)
+    bool prof = false;
+    int64_t nlaunch[16] = {};
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> recs;  // (family, index of the start event; stop = +1)
 };
 
 namespace octmg {
@@ -99,6 +105,52 @@ mg_status upload(mg_forest *F, T **p, const std::vector<T> &v) {
     return MG_OK;
 }
 
+// Kernel families for launch counting and timing.
+enum ProfCat {
+    P_EXCH64 = 0, P_EXCH32, P_SMOOTH64, P_SMOOTH32, P_RESTR64, P_RESTR32, P_PROL64, P_PROL32, P_COARSE64,
+    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_NCAT
+};
+const char *const kProfNames[P_NCAT] = {"exchange_f64", "exchange_f32", "smooth_f64", "smooth_f32",
+                                         "residual_restrict_f64", "residual_restrict_f32", "prolong_f64",
+                                         "prolong_f32", "coarse_f64", "coarse_f32", "residual_f64",
+                                         "update_mixed", "layout", "adjoint"};
+
+template <typename T> constexpr int cat_of(int cat64) { return sizeof(T) == 8 ? cat64 : cat64 + 1; }
+
+cudaEvent_t next_event(mg_forest *F) {
+    if (F->ev_used == F->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        F->ev_pool.push_back(e);
+    }
+    return F->ev_pool[F->ev_used++];
+}
+
+// RAII scope around the launches of one kernel family.
+struct Prof {
+    mg_forest *F;
+    int cat;
+    size_t start = 0;
+    bool on = false;
+    Prof(mg_forest *f, int c, int launches) : F(f), cat(c) {
+        F->nlaunch[c] += launches;
+        if (F->prof) {
+            cudaEvent_t a = next_event(F), b = next_event(F);
+            if (a && b) {
+                start = F->ev_used - 2;
+                cudaEventRecord(a, F->st);
+                on = true;
+            }
+        }
+    }
+    ~Prof() {
+        if (on) {
+            cudaEventRecord(F->ev_pool[start + 1], F->st);
+            F->recs.emplace_back(cat, start);
+        }
+    }
+};
+
 int ilog2(int n) {
     int l = 0;
     while ((1 << l) < n) ++l;
@@ -120,6 +172,7 @@ template <> Coef coef_of<float>(const DevLevel &d) { return d.c32(); }
 
 template <typename T, int MODE>
 void exchange(mg_forest *F, DevLevel &d, T *u) {
+    Prof p(F, cat_of<T>(P_EXCH64), (d.nfaces ? 1 : 0) + (d.nsegs ? 1 : 0));
     if (d.nfaces)
         k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(d.nfaces) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
             u, d.faces, d.nfaces, d.g);
@@ -149,6 +202,7 @@ void exchange_k(mg_forest *F, DevLevel &d) {
 
 template <typename T, int MODE>
 void smooth(mg_forest *F, DevLevel &d, int colour) {
+    Prof p(F, cat_of<T>(P_SMOOTH64), 1);
     k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2,
                                                                        d.g, colour);
 }
@@ -158,6 +212,7 @@ void vcycle(mg_forest *F, int l) {
     DevLevel &d = F->L[l];
     const int last = static_cast<int>(F->L.size()) - 1;
     if (l == last) {
+        Prof p(F, cat_of<T>(P_COARSE64), 1);
         k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d),
                                                                                           F->Ainv, F->cmap, F->Nc);
         return;
@@ -170,11 +225,17 @@ void vcycle(mg_forest *F, int l) {
     }
     exchange<T, MODE>(F, d, ufield<T>(d));
     DevLevel &c = F->L[l + 1];
-    k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
-        ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2, d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
+    {
+        Prof p(F, cat_of<T>(P_RESTR64), 1);
+        k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
+            ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2, d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
+    }
     vcycle<T, MODE>(F, l + 1);
     exchange<T, MODE>(F, c, ufield<T>(c));
-    k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
+    {
+        Prof p(F, cat_of<T>(P_PROL64), 1);
+        k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
+    }
     for (int i = 0; i < F->cfg.nu2; ++i) {
         exchange<T, MODE>(F, d, ufield<T>(d));
         smooth<T, MODE>(F, d, 0);
@@ -191,6 +252,7 @@ mg_status residual64(mg_forest *F, double *u, const double *f, TO *out, double s
     DevLevel &d = F->L[0];
     exchange<double, MODE>(F, d, u);
     const int grid = grid_for(d.cells());
+    Prof p(F, P_RESID64, 2);
     k_residual_full<double, MODE, TO><<<grid, kThreads, 0, F->st>>>(u, f, d.c64(), d.h2, d.g, out, scale, F->partial,
                                                                      zero_out);
     k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
@@ -273,6 +335,7 @@ mg_status build_coefficients(mg_forest *F) {
 
 template <typename T>
 mg_status pack_user(mg_forest *F, DevLevel &d, T *pool, const double *user) {
+    Prof p(F, P_LAYOUT, 1);
     k_pack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(pool, user, d.g);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -280,6 +343,7 @@ mg_status pack_user(mg_forest *F, DevLevel &d, T *pool, const double *user) {
 
 template <typename T>
 mg_status unpack_user(mg_forest *F, DevLevel &d, double *user, const T *pool) {
+    Prof p(F, P_LAYOUT, 1);
     k_unpack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(user, pool, d.g);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -314,6 +378,7 @@ mg_status mixed_step(mg_forest *F, double scale, double *rr) {
 mg_status finish_mixed_cycle(mg_forest *F, double scale) {
     DevLevel &d = F->L[0];
     vcycle32(F);
+    Prof p(F, P_UPDATE, 1);
     k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, scale, d.g);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -550,6 +615,7 @@ void mg_forest_destroy(mg_forest *F) {
     if (!F) return;
     cudaStreamSynchronize(F->st);
     for (void *p : F->allocs) cudaFree(p);
+    for (cudaEvent_t e : F->ev_pool) cudaEventDestroy(e);
     if (F->pinned) cudaFreeHost(F->pinned);
     delete F;
 }
@@ -627,6 +693,46 @@ mg_status mg_exchange_level(mg_forest *F, int32_t level, const double *u_dev, do
     if (e != cudaSuccess) {
         set_error(std::string("exchange_level: ") + cudaGetErrorString(e));
         return MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+mg_status mg_profile(mg_forest *F, int32_t enable) {
+    if (!F) {
+        set_error("null forest");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (enable) {
+        F->recs.clear();
+        F->ev_used = 0;
+        for (int c = 0; c < P_NCAT; ++c) F->nlaunch[c] = 0;
+    }
+    F->prof = enable != 0;
+    return MG_OK;
+}
+
+mg_status mg_profile_read(mg_forest *F, int32_t max_families, char *names, double *ms, int64_t *launches,
+                          int32_t *n_families) {
+    if (!F || !n_families || max_families < 0) {
+        set_error("bad argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    double acc[P_NCAT] = {};
+    for (auto &r : F->recs) {
+        float t = 0.0f;
+        MG_CUDA(cudaEventElapsedTime(&t, F->ev_pool[r.second], F->ev_pool[r.second + 1]));
+        acc[r.first] += t;
+    }
+    *n_families = P_NCAT;
+    for (int c = 0; c < P_NCAT && c < max_families; ++c) {
+        if (names) {
+            std::strncpy(names + 32 * c, kProfNames[c], 31);
+            names[32 * c + 31] = 0;
+        }
+        if (ms) ms[c] = acc[c];
+        if (launches) launches[c] = F->nlaunch[c];
     }
     return MG_OK;
 }
