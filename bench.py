@@ -55,7 +55,7 @@ def _inputs(workload, device, seed=0):
 # ------------------------------------------------------------------------------------------------------------
 # byte and flop models of the kernel families (per cell of the level a launch covers)
 # ------------------------------------------------------------------------------------------------------------
-def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total):
+def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launches=0):
     """Algorithmic bytes and FP64 flops of one family over the timed region.
 
     Per cell of the level a launch sweeps:
@@ -77,7 +77,7 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total):
     if fam == "residual_f64":
         return cells[0] * 32 * outer_total, cells[0] * 27.0 * outer_total
     if fam == "update_mixed":
-        return cells[0] * 20 * cycles_total, 0.0
+        return cells[0] * 20 * launches, 0.0
     return None, None
 
 
@@ -240,7 +240,7 @@ def run_ours(args):
     R, n, keys, k, f = _inputs(args.workload, dev)
     coeff = k is not None
     cells = len(keys) * n ** 3
-    F = Forest(R, n, keys, coeff=coeff, precision=1)
+    F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=args.inner_cycles)
     F.set_rhs(f, k)
     levels = F.levels()
     u = torch.zeros_like(f)
@@ -259,6 +259,7 @@ def run_ours(args):
     _barrier(dist)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("mg_timed")
     e0.record(stream)
     cycles = []
     rels = []
@@ -267,6 +268,7 @@ def run_ours(args):
         cycles.append(c)
         rels.append(r)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     _barrier(dist)
     clocks = sampler.stop()
@@ -279,8 +281,8 @@ def run_ours(args):
 
     # roofline of the dominant family
     fam = max((k_ for k_ in prof if prof[k_][1] > 0), key=lambda k_: prof[k_][0])
-    outer = tot_cycles + args.steps  # one FP64 residual per cycle plus the initial one
-    bytes_, flops = _family_work(fam, levels, 2, 2, coeff, tot_cycles, outer)
+    outer = prof.get("residual_f64", (0, 0))[1] // 2  # k_residual_norm + partial-sum launches per residual
+    bytes_, flops = _family_work(fam, levels, 2, 2, coeff, tot_cycles, outer, prof[fam][1])
     hbm, src = _peaks()
     fam_s = prof[fam][0] / 1e3
     roof = None
@@ -347,6 +349,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "cells": cells, "blocks": len(keys), "block": f"{n}^3",
                        "levels": levels, "coefficient": "log-normal k (sigma 1, ell 0.1)" if coeff else "1",
                        "rhs": WORKLOADS[args.workload][2], "rtol": args.rtol, "cycle": "V(2,2) red-black GS",
+                       "inner_cycles": args.inner_cycles,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"{ws} independent replicas"},
             "cycles_per_solve": cycles, "final_rel_residual": rels[-1],
             "time_to_rtol_s": {"fp32_in_fp64": tmix, "fp64": t64, "speedup": t64 / tmix},
@@ -378,6 +381,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform_8x64_k")
     ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--inner-cycles", type=int, default=3,
+                    help="FP32 V-cycles per FP64 defect-correction step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

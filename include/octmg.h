@@ -56,6 +56,8 @@ typedef struct {
     int32_t nu1, nu2;         /* pre/post red-black Gauss-Seidel iterations (2, 2) */
     int32_t max_coarse;       /* octets are merged below 4^3 blocks until the coarsest level has at most this many
                                  unknowns (default 512 when <= 0); that level is solved by a dense FP64 inverse */
+    int32_t inner_cycles;     /* precision == 1: FP32 V-cycles per FP64 defect-correction step (default 1 when <= 0;
+                                 FP32 resolves about 6 digits per step, so up to ~5 cycles still pay) */
     void *stream;             /* cudaStream_t, or NULL for the legacy default stream */
 } mg_config;
 

@@ -36,6 +36,7 @@ class MGConfig(ctypes.Structure):
         ("nu1", ctypes.c_int32),
         ("nu2", ctypes.c_int32),
         ("max_coarse", ctypes.c_int32),
+        ("inner_cycles", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

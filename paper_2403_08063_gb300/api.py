@@ -31,7 +31,7 @@ class Forest:
     """
 
     def __init__(self, R, n, leaves, coeff=False, interface_flux=True, precision=0, nu1=2, nu2=2, max_coarse=512,
-                 stream=None):
+                 inner_cycles=1, stream=None):
         self.lib = _lib.load()
         arr = np.asarray(leaves, dtype=np.int32)
         if arr.ndim == 2 and arr.shape[1] == 4:
@@ -46,6 +46,7 @@ class Forest:
         cfg.leaves = self._leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         cfg.coeff, cfg.interface_flux, cfg.precision = int(coeff), int(interface_flux), int(precision)
         cfg.nu1, cfg.nu2, cfg.max_coarse = int(nu1), int(nu2), int(max_coarse)
+        cfg.inner_cycles = int(inner_cycles)
         cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
         h = ctypes.c_void_p()
         _lib.check(self.lib.mg_forest_create(ctypes.byref(cfg), ctypes.byref(h)))

@@ -6,8 +6,10 @@
 //
 // Coefficient modes (template parameter MODE):
 //   0  constant coefficient, -Laplace: every face coefficient T_f = 1;
-//   1  variable k, face coefficients precomputed in FP64: tx/ty/tz[idx] hold T of the face between padded
-//      cells idx - stride and idx along that axis (harmonic mean 2 k_a k_b / (k_a + k_b)), dinv[idx] = 1 / sum_f T_f;
+//   1  variable k in FP64, face coefficients precomputed and scaled by the block's 1/h^2:
+//      tx/ty/tz[idx] = T_f / h^2 of the face between padded cells idx - stride and idx along that axis
+//      (T_f the harmonic mean 2 k_a k_b / (k_a + k_b)), dg[idx] = their sum over the six faces, dinv = 1 / dg;
+//      the residual is then f + sum_f T~_f u_f - dg u, seven FMAs per cell;
 //   2  variable k in FP32: kap[idx] = 1/k with ghosts; T_f = 2 / (kap_i + kap_nb) evaluated with rcp.approx.
 #pragma once
 #include <cstdint>
@@ -21,15 +23,15 @@ constexpr int kThreads = 256;
 
 struct LevelGeom {
     int32_t nb;     // blocks
-    int32_t n;      // interior cells per edge
+    int32_t n;      // interior cells per edge (power of two)
     int32_t lg;     // log2(n)
     int32_t P;      // n + 2
     int64_t bs;     // block stride in elements
 };
 
 struct Coef {       // coefficient arrays of one level (unused members are null)
-    const double *tx, *ty, *tz, *dinv;  // MODE 1
-    const float *kap;                   // MODE 2
+    const double *tx, *ty, *tz, *dg, *dinv;  // MODE 1
+    const float *kap;                        // MODE 2
 };
 
 __host__ __device__ inline int64_t off3(int X, int Y, int Z, int P) {
@@ -65,6 +67,18 @@ __constant__ double c_wt[3][2][3] = {
     {{45.0 / 32, -18.0 / 32, 5.0 / 32}, {21.0 / 32, 14.0 / 32, -3.0 / 32}},
     {{-3.0 / 32, 14.0 / 32, 21.0 / 32}, {5.0 / 32, -18.0 / 32, 45.0 / 32}}};
 __constant__ int c_base[3][3] = {{-1, 0, 1}, {0, 1, 2}, {-2, -1, 0}};
+__constant__ float c_wn_f[3] = {45.0f / 32, -18.0f / 32, 5.0f / 32};
+__constant__ float c_wt_f[3][2][3] = {
+    {{5.0f / 32, 30.0f / 32, -3.0f / 32}, {-3.0f / 32, 30.0f / 32, 5.0f / 32}},
+    {{45.0f / 32, -18.0f / 32, 5.0f / 32}, {21.0f / 32, 14.0f / 32, -3.0f / 32}},
+    {{-3.0f / 32, 14.0f / 32, 21.0f / 32}, {5.0f / 32, -18.0f / 32, 45.0f / 32}}};
+
+template <typename T> __device__ inline T w_normal(int a);
+template <> __device__ inline double w_normal<double>(int a) { return c_wn[a]; }
+template <> __device__ inline float w_normal<float>(int a) { return c_wn_f[a]; }
+template <typename T> __device__ inline T w_tang(int c, int al, int b);
+template <> __device__ inline double w_tang<double>(int c, int al, int b) { return c_wt[c][al][b]; }
+template <> __device__ inline float w_tang<float>(int c, int al, int b) { return c_wt_f[c][al][b]; }
 
 __device__ inline float frcp(float x) {
     float r;
@@ -72,66 +86,93 @@ __device__ inline float frcp(float x) {
     return r;
 }
 
-// Face coefficient between padded cells idx and idx + s*stride(axis) (s = -1 or +1) of one block.
+// Face coefficient of the face between depth 0 and depth 1 of a block face, stored (MODE 1) or evaluated (MODE 2)
+// at the cell with the larger padded coordinate along the axis: `loc`; `other` is the cell across the face.
 template <typename T, int MODE>
-__device__ inline T face_T(const Coef &c, int64_t gidx, int axis, int s, int P) {
+__device__ inline T face_coef(const Coef &c, int64_t loc, int64_t other, int axis) {
     if (MODE == 0) return T(1);
-    const int st = axis_stride(axis, P);
     if (MODE == 1) {
         const double *t = axis == 0 ? c.tx : (axis == 1 ? c.ty : c.tz);
-        return T(t[s > 0 ? gidx + st : gidx]);
+        return T(t[loc]);
     }
-    const float a = c.kap[gidx], b = c.kap[gidx + (s > 0 ? st : -st)];
-    return T(2.0f * frcp(a + b));
+    return T(2.0f * frcp(c.kap[loc] + c.kap[other]));
 }
 
-// sum_f T_f u_f and sum_f T_f at padded cell gidx.
-template <typename T, int MODE>
-__device__ inline void stencil(const T *__restrict__ u, const Coef &c, int64_t g, int P, T &S, T &D) {
+// MODE 1: init + sum_f T~_f u_f over the six faces of padded cell g.
+__device__ inline double sten1(const double *__restrict__ u, const Coef &c, int64_t g, int P, double init) {
     const int64_t PP = static_cast<int64_t>(P) * P;
-    if (MODE == 0) {
-        S = ((u[g - 1] + u[g + 1]) + (u[g - P] + u[g + P])) + (u[g - PP] + u[g + PP]);
-        D = T(6);
-    } else if (MODE == 1) {
-        const T a0 = T(c.tx[g]), a1 = T(c.tx[g + 1]), b0 = T(c.ty[g]), b1 = T(c.ty[g + P]);
-        const T c0 = T(c.tz[g]), c1 = T(c.tz[g + PP]);
-        S = a0 * u[g - 1];
-        S = fma(a1, u[g + 1], S);
-        S = fma(b0, u[g - P], S);
-        S = fma(b1, u[g + P], S);
-        S = fma(c0, u[g - PP], S);
-        S = fma(c1, u[g + PP], S);
-        D = ((a0 + a1) + (b0 + b1)) + (c0 + c1);
+    double a = fma(c.tx[g], u[g - 1], init);
+    a = fma(c.tx[g + 1], u[g + 1], a);
+    a = fma(c.ty[g], u[g - P], a);
+    a = fma(c.ty[g + P], u[g + P], a);
+    a = fma(c.tz[g], u[g - PP], a);
+    a = fma(c.tz[g + PP], u[g + PP], a);
+    return a;
+}
+
+// MODE 0: plain sum of the six neighbours.
+template <typename T>
+__device__ inline T sten0(const T *__restrict__ u, int64_t g, int P) {
+    const int64_t PP = static_cast<int64_t>(P) * P;
+    return ((u[g - 1] + u[g + 1]) + (u[g - P] + u[g + P])) + (u[g - PP] + u[g + PP]);
+}
+
+// MODE 2: S = sum_f T_f u_f and D = sum_f T_f with T_f = 2 / (kap_i + kap_f), in FP32.
+__device__ inline void sten2(const float *__restrict__ u, const float *__restrict__ kap, int64_t g, int P, float &S,
+                             float &D) {
+    const int64_t PP = static_cast<int64_t>(P) * P;
+    const float k0 = kap[g];
+    const float a0 = frcp(k0 + kap[g - 1]), a1 = frcp(k0 + kap[g + 1]);
+    const float b0 = frcp(k0 + kap[g - P]), b1 = frcp(k0 + kap[g + P]);
+    const float c0 = frcp(k0 + kap[g - PP]), c1 = frcp(k0 + kap[g + PP]);
+    float s = a0 * u[g - 1];
+    s = fmaf(a1, u[g + 1], s);
+    s = fmaf(b0, u[g - P], s);
+    s = fmaf(b1, u[g + P], s);
+    s = fmaf(c0, u[g - PP], s);
+    s = fmaf(c1, u[g + PP], s);
+    S = 2.0f * s;
+    D = 2.0f * (((a0 + a1) + (b0 + b1)) + (c0 + c1));
+}
+
+// Point-form residual r = f - A u at padded cell g (ih2 = 1/h^2 of the block; unused in MODE 1).
+template <typename T, int MODE>
+__device__ inline T residual_at(const T *__restrict__ u, const T *__restrict__ f, const Coef &cf, int64_t g, int P,
+                                T ih2) {
+    const T fv = f ? f[g] : T(0);
+    if constexpr (MODE == 1) {
+        return fma(-cf.dg[g], u[g], sten1(u, cf, g, P, fv));
+    } else if constexpr (MODE == 0) {
+        const T S = sten0<T>(u, g, P);
+        return fma(fma(T(-6), u[g], S), ih2, fv);
     } else {
-        const float k0 = c.kap[g];
-        const float a0 = frcp(k0 + c.kap[g - 1]), a1 = frcp(k0 + c.kap[g + 1]);
-        const float b0 = frcp(k0 + c.kap[g - P]), b1 = frcp(k0 + c.kap[g + P]);
-        const float c0 = frcp(k0 + c.kap[g - PP]), c1 = frcp(k0 + c.kap[g + PP]);
-        float s = a0 * float(u[g - 1]);
-        s = fmaf(a1, float(u[g + 1]), s);
-        s = fmaf(b0, float(u[g - P]), s);
-        s = fmaf(b1, float(u[g + P]), s);
-        s = fmaf(c0, float(u[g - PP]), s);
-        s = fmaf(c1, float(u[g + PP]), s);
-        S = T(2.0f * s);
-        D = T(2.0f * (((a0 + a1) + (b0 + b1)) + (c0 + c1)));
+        float S, D;
+        sten2(reinterpret_cast<const float *>(u), cf.kap, g, P, S, D);
+        return T(fmaf(fmaf(-D, float(u[g]), S), float(ih2), float(fv)));
     }
+}
+
+// A u at padded cell g (FP64 operator application; f = 0).
+template <int MODE>
+__device__ inline double apply_at(const double *__restrict__ u, const Coef &cf, int64_t g, int P, double ih2) {
+    return -residual_at<double, MODE>(u, nullptr, cf, g, P, ih2);
 }
 
 // ------------------------------------------------------------------------------------------------------------
 // Ghost exchange, part 1: whole faces filled from one source block (boundary, same level, C2F).
 // KIND_K = false: solution-type field (Dirichlet reflection ghost = -u_i; quadratic C2F extrapolation).
 // KIND_K = true:  coefficient field k (ghost = k_i at the boundary; fine ghosts inject the covering coarse k).
+// One thread per ghost cell; n is a power of two, so items and cells decode with shifts.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, bool KIND_K>
 __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g) {
-    const int n = g.n, P = g.P, nn = n * n, h = n >> 1;
-    const int64_t total = static_cast<int64_t>(nitems) * nn;
+    const int n = g.n, P = g.P, lg = g.lg, h = n >> 1;
+    const int64_t total = static_cast<int64_t>(nitems) << (2 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int it = static_cast<int>(t / nn);
-        const int r = static_cast<int>(t - static_cast<int64_t>(it) * nn);
-        const int i1 = r % n, i2 = r / n;
+        const int it = static_cast<int>(t >> (2 * lg));
+        const int r = static_cast<int>(t) & ((1 << (2 * lg)) - 1);
+        const int i1 = r & (n - 1), i2 = r >> lg;
         const FaceItem F = items[it];
         T *ub = u + F.blk * g.bs;
         T val;
@@ -156,12 +197,12 @@ __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
                         const int y = yc + c_base[cy][b], z = zc + c_base[cz][c];
-                        T e = T(c_wn[0]) * uc[face_off(F.axis, 1 - F.side, 1, y, z, n, P)];
-                        e = fma(T(c_wn[1]), uc[face_off(F.axis, 1 - F.side, 2, y, z, n, P)], e);
-                        e = fma(T(c_wn[2]), uc[face_off(F.axis, 1 - F.side, 3, y, z, n, P)], e);
-                        accb = fma(T(c_wt[cy][a1][b]), e, accb);
+                        T e = w_normal<T>(0) * uc[face_off(F.axis, 1 - F.side, 1, y, z, n, P)];
+                        e = fma(w_normal<T>(1), uc[face_off(F.axis, 1 - F.side, 2, y, z, n, P)], e);
+                        e = fma(w_normal<T>(2), uc[face_off(F.axis, 1 - F.side, 3, y, z, n, P)], e);
+                        accb = fma(w_tang<T>(cy, a1, b), e, accb);
                     }
-                    acc = fma(T(c_wt[cz][a2][c]), accb, acc);
+                    acc = fma(w_tang<T>(cz, a2, c), accb, acc);
                 }
                 val = acc;
             }
@@ -174,18 +215,19 @@ __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__
 // Ghost exchange, part 2: coarse ghost segments next to finer neighbours.
 // FLUX = false: F2C mean of the 2x2x2 fine inner cells overlapping each coarse ghost cell (Sec. 3.3.1).
 // FLUX = true:  conservative coarse ghost G with T_C (u_C - G) = 1/2 sum_j T_j (g_j - u_j) over the four fine
-//               sub-faces j, g_j the fine ghosts (C2F, part 1 must have run), u_j the first fine layer.
+//               sub-faces j, g_j the fine ghosts (C2F, part 1 must have run), u_j the first fine layer.  With the
+//               1/h^2-scaled coefficients of MODE 1, T_j / (2 T_C) = T~_j / (8 T~_C) since h_C = 2 h_j.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, int MODE, bool FLUX>
 __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
                                 LevelGeom g) {
-    const int n = g.n, P = g.P, h = n >> 1, hh = h * h;
-    const int64_t total = static_cast<int64_t>(nitems) * hh;
+    const int n = g.n, P = g.P, lgh = g.lg - 1, h = n >> 1;
+    const int64_t total = static_cast<int64_t>(nitems) << (2 * lgh);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int it = static_cast<int>(t / hh);
-        const int r = static_cast<int>(t - static_cast<int64_t>(it) * hh);
-        const int p = r % h, q = r / h;
+        const int it = static_cast<int>(t >> (2 * lgh));
+        const int r = static_cast<int>(t) & ((1 << (2 * lgh)) - 1);
+        const int p = r & (h - 1), q = r >> lgh;
         const SegItem S = items[it];
         const int64_t cb = S.coarse * g.bs, fb = S.fine * g.bs;
         const int fs = 1 - S.side;
@@ -201,9 +243,8 @@ __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__res
                     for (int a = 0; a < 2; ++a) s += u[fb + face_off(S.axis, fs, d, 2 * p + a, 2 * q + b, n, P)];
             val = T(0.125) * s;
         } else {
-            // The face coefficient between depth 0 and depth 1 of a face sits at depth 1 (minus face) or at the
-            // ghost (plus face), i.e. at the cell with the larger padded coordinate.
             const int64_t gC = cb + face_off(S.axis, S.side, 1, yc, zc, n, P);
+            const int64_t g0c = cb + face_off(S.axis, S.side, 0, yc, zc, n, P);
             const T uC = u[gC];
             T flux = T(0);
 #pragma unroll
@@ -212,12 +253,11 @@ __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__res
                 for (int a = 0; a < 2; ++a) {
                     const int64_t g0 = fb + face_off(S.axis, fs, 0, 2 * p + a, 2 * q + b, n, P);
                     const int64_t g1 = fb + face_off(S.axis, fs, 1, 2 * p + a, 2 * q + b, n, P);
-                    const T Tj = face_T<T, MODE>(cf, fs ? g0 : g1, S.axis, -1, P);
+                    const T Tj = face_coef<T, MODE>(cf, fs ? g0 : g1, fs ? g1 : g0, S.axis);
                     flux = fma(Tj, u[g0] - u[g1], flux);
                 }
-            const int64_t g0c = cb + face_off(S.axis, S.side, 0, yc, zc, n, P);
-            const T Tc = face_T<T, MODE>(cf, S.side ? g0c : gC, S.axis, -1, P);
-            val = uC - flux / (T(2) * Tc);
+            const T Tc = face_coef<T, MODE>(cf, S.side ? g0c : gC, S.side ? gC : g0c, S.axis);
+            val = uC - flux / (T(MODE == 1 ? 8 : 2) * Tc);
         }
         u[cb + face_off(S.axis, S.side, 0, yc, zc, n, P)] = val;
     }
@@ -227,10 +267,11 @@ __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__res
 // Red-black Gauss-Seidel half-sweep of one colour ((x+y+z) mod 2 of the block-local interior index; red = 0):
 //     u_i = (h^2 f_i + sum_f T_f u_f) / sum_f T_f
 // over every block of the level, ghosts as left by the last exchange.  One thread per updated cell.
+// h2 is h^2 per block in the field's precision (unused in MODE 1, whose coefficients carry 1/h^2).
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const double *__restrict__ h2,
-                         LevelGeom g, int colour) {
+__global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2, LevelGeom g,
+                         int colour) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg - 1);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -241,35 +282,26 @@ __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, co
         const int64_t b = t >> (3 * lg - 1);
         const int x = 2 * m + ((y + z + colour) & 1);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
-        T S, D;
-        stencil<T, MODE>(u, cf, gi, P, S, D);
-        const T rhs = fma(T(h2[b]), f[gi], S);
-        if (MODE == 1)
-            u[gi] = rhs * T(cf.dinv[gi]);
-        else if (MODE == 0)
-            u[gi] = rhs * T(1.0 / 6.0);
-        else
-            u[gi] = T(float(rhs) * frcp(float(D)));
+        if constexpr (MODE == 1) {
+            u[gi] = sten1(u, cf, gi, P, f[gi]) * cf.dinv[gi];
+        } else if constexpr (MODE == 0) {
+            u[gi] = fma(h2[b], f[gi], sten0<T>(u, gi, P)) * T(1.0 / 6.0);
+        } else {
+            float S, D;
+            sten2(reinterpret_cast<const float *>(u), cf.kap, gi, P, S, D);
+            u[gi] = T(fmaf(float(h2[b]), float(f[gi]), S) * frcp(D));
+        }
     }
-}
-
-// Point-form residual r = f - (D u - S) / h^2 at padded cell gi of block b.
-template <typename T, int MODE>
-__device__ inline T residual_at(const T *__restrict__ u, const T *__restrict__ f, const Coef &cf, int64_t gi,
-                                int P, T inv_h2) {
-    T S, D;
-    stencil<T, MODE>(u, cf, gi, P, S, D);
-    return (f ? f[gi] : T(0)) - (D * u[gi] - S) * inv_h2;
 }
 
 // ------------------------------------------------------------------------------------------------------------
 // Residual of the fine level restricted to the next level (mean of the 8 children), written as the coarse
 // right-hand side; the coarse solution's interior is zeroed (coarse-grid correction starts from 0).
-// One thread per coarse cell.
+// One thread per coarse cell.  ih2f: 1/h^2 per fine block.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, int MODE>
 __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
-                                    const double *__restrict__ h2f, LevelGeom gf, T *__restrict__ fc,
+                                    const T *__restrict__ ih2f, LevelGeom gf, T *__restrict__ fc,
                                     T *__restrict__ uc, const XferItem *__restrict__ xf, LevelGeom gc) {
     const int lgc = gc.lg, nc = gc.n;
     const int64_t total = static_cast<int64_t>(gc.nb) << (3 * lgc);
@@ -284,8 +316,7 @@ __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict
         uc[gcell] = T(0);
         if (xi.kind == XF_COPY) {
             const int64_t b = xi.src[0];
-            fc[gcell] = residual_at<T, MODE>(u, f, cf, b * gf.bs + off3(X + 1, Y + 1, Z + 1, gf.P), gf.P,
-                                             T(1.0 / h2f[b]));
+            fc[gcell] = residual_at<T, MODE>(u, f, cf, b * gf.bs + off3(X + 1, Y + 1, Z + 1, gf.P), gf.P, ih2f[b]);
             continue;
         }
         int64_t b;
@@ -303,7 +334,7 @@ __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict
             y0 = 2 * Y - oy * nc;
             z0 = 2 * Z - oz * nc;
         }
-        const T ih2 = T(1.0 / h2f[b]);
+        const T ih2 = ih2f[b];
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < 2; ++c)
@@ -431,16 +462,19 @@ __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Residual over a whole level into an interior-shaped output, optionally scaled and cast, plus per-CTA partial
-// sums of h^3 r^2 (volume-weighted squared norm) and of h^3 f^2.
+// FP64 residual over the finest level, r = f - A u, written as FP32 r * scale (scale a power of two, so the
+// scaling is exact), with the FP32 correction field zeroed, and per-CTA partial sums of h^3 (r * scale)^2.
+// The squared norm is accumulated in FP32 per thread (it only decides convergence and is reported to ~1e-6
+// relative) and in FP64 across threads.  out / zero_out may be null (convergence check of FP64 cycles).
 // ------------------------------------------------------------------------------------------------------------
-template <typename T, int MODE, typename TO>
-__global__ void k_residual_full(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
-                                const double *__restrict__ h2, LevelGeom g, TO *__restrict__ out, double scale,
-                                double *__restrict__ partial, TO *__restrict__ zero_out) {
+template <int MODE>
+__global__ void k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
+                                const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
+                                float *__restrict__ out, float scale, double *__restrict__ partial,
+                                float *__restrict__ zero_out) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
-    double acc_r = 0.0, acc_f = 0.0;
+    float acc = 0.0f;
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int x = static_cast<int>(t & (n - 1));
@@ -448,59 +482,81 @@ __global__ void k_residual_full(const T *__restrict__ u, const T *__restrict__ f
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
-        const double hb2 = h2[b];
-        const T r = residual_at<T, MODE>(u, f, cf, gi, P, T(1.0 / hb2));
-        if (out) out[gi] = TO(static_cast<double>(r) * scale);
-        if (zero_out) zero_out[gi] = TO(0);
-        const double vol = hb2 * sqrt(hb2);
-        const double fv = f ? double(f[gi]) : 0.0;
-        acc_r = fma(vol * double(r), double(r), acc_r);
-        acc_f = fma(vol * fv, fv, acc_f);
+        const double r = residual_at<double, MODE>(u, f, cf, gi, P, MODE == 1 ? 0.0 : ih2[b]);
+        const float rs = static_cast<float>(r) * scale;
+        if (out) out[gi] = rs;
+        if (zero_out) zero_out[gi] = 0.0f;
+        acc = fmaf(vol[b] * rs, rs, acc);
     }
-    if (!partial) return;
-    __shared__ double sr[kThreads / 32], sf[kThreads / 32];
+    __shared__ double sm[kThreads / 32];
+    double a = acc;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc_r += __shfl_xor_sync(0xffffffffu, acc_r, o);
-        acc_f += __shfl_xor_sync(0xffffffffu, acc_f, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sr[threadIdx.x >> 5] = acc_r;
-        sf[threadIdx.x >> 5] = acc_f;
-    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            a += sr[w];
-            b += sf[w];
-        }
-        partial[2 * blockIdx.x] = a;
-        partial[2 * blockIdx.x + 1] = b;
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sm[w];
+        partial[blockIdx.x] = s;
     }
 }
 
-__global__ void k_sum_partials(const double *__restrict__ partial, int nparts, double *__restrict__ out) {
-    __shared__ double sa[kThreads], sb[kThreads];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        a += partial[2 * i];
-        b += partial[2 * i + 1];
+// A u over a whole level in FP64 (operator application; ghosts already exchanged).
+template <int MODE>
+__global__ void k_apply64(const double *__restrict__ u, Coef cf, const double *__restrict__ ih2, LevelGeom g,
+                          double *__restrict__ out) {
+    const int lg = g.lg, n = g.n, P = g.P;
+    const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t & (n - 1));
+        const int y = static_cast<int>((t >> lg) & (n - 1));
+        const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
+        const int64_t b = t >> (3 * lg);
+        const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
+        out[gi] = apply_at<MODE>(u, cf, gi, P, MODE == 1 ? 0.0 : ih2[b]);
     }
+}
+
+// Per-CTA partial sums of h^3 x^2 over the interior of a padded FP64 field (vol = h^3 per block, FP64).
+__global__ void k_norm64(const double *__restrict__ x, const double *__restrict__ vol, LevelGeom g,
+                         double *__restrict__ partial) {
+    const int lg = g.lg, n = g.n, P = g.P;
+    const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int xx = static_cast<int>(t & (n - 1));
+        const int y = static_cast<int>((t >> lg) & (n - 1));
+        const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
+        const int64_t b = t >> (3 * lg);
+        const double v = x[b * g.bs + off3(xx + 1, y + 1, z + 1, P)];
+        acc = fma(vol[b] * v, v, acc);
+    }
+    __shared__ double sm[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sm[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// Deterministic sum of the per-CTA partials (fixed order for a fixed grid).
+__global__ void k_sum_partials(const double *__restrict__ partial, int nparts, double *__restrict__ out) {
+    __shared__ double sa[kThreads];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += partial[i];
     sa[threadIdx.x] = a;
-    sb[threadIdx.x] = b;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sa[threadIdx.x] += sa[threadIdx.x + s];
-            sb[threadIdx.x] += sb[threadIdx.x + s];
-        }
+        if (threadIdx.x < s) sa[threadIdx.x] += sa[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        out[0] = sa[0];
-        out[1] = sb[0];
-    }
+    if (threadIdx.x == 0) out[0] = sa[0];
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -550,10 +606,12 @@ __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__
     }
 }
 
-// Face coefficients of a level from k with ghosts (MODE 1 arrays) and 1/k for FP32 (MODE 2).
-// tx at padded (X, Y, Z) = harmonic mean of k at X-1 and X, for X in 1..n+1 and interior Y, Z (same for ty, tz).
-__global__ void k_face_coefs(const double *__restrict__ k, LevelGeom g, double *__restrict__ tx,
-                             double *__restrict__ ty, double *__restrict__ tz, float *__restrict__ kap) {
+// Face coefficients of a level from k with ghosts: MODE 1 arrays (harmonic mean times the block's 1/h^2) and
+// 1/k for FP32 (MODE 2).  tx at padded (X, Y, Z) is the face between X-1 and X, for X in 1..n+1 and interior
+// Y, Z (same for ty, tz).
+__global__ void k_face_coefs(const double *__restrict__ k, const double *__restrict__ ih2, LevelGeom g,
+                             double *__restrict__ tx, double *__restrict__ ty, double *__restrict__ tz,
+                             float *__restrict__ kap) {
     const int P = g.P, n = g.n;
     const int64_t per = static_cast<int64_t>(P) * P * P;
     const int64_t total = static_cast<int64_t>(g.nb) * per;
@@ -563,19 +621,20 @@ __global__ void k_face_coefs(const double *__restrict__ k, LevelGeom g, double *
         const int r = static_cast<int>(t - b * per);
         const int X = r % P, Y = (r / P) % P, Z = r / (P * P);
         const int64_t gi = b * g.bs + r;
-        const double kc = k[gi];
+        const double kc = k[gi], s = ih2[b];
         const bool inY = Y >= 1 && Y <= n, inZ = Z >= 1 && Z <= n, inX = X >= 1 && X <= n;
         const auto harm = [](double a, double c) { return 2.0 * a * c / (a + c); };
-        if (X >= 1 && inY && inZ) tx[gi] = harm(k[gi - 1], kc);
-        if (Y >= 1 && inX && inZ) ty[gi] = harm(k[gi - P], kc);
-        if (Z >= 1 && inX && inY) tz[gi] = harm(k[gi - static_cast<int64_t>(P) * P], kc);
+        if (X >= 1 && inY && inZ) tx[gi] = harm(k[gi - 1], kc) * s;
+        if (Y >= 1 && inX && inZ) ty[gi] = harm(k[gi - P], kc) * s;
+        if (Z >= 1 && inX && inY) tz[gi] = harm(k[gi - static_cast<int64_t>(P) * P], kc) * s;
         const bool face_or_interior = (inX && inY) || (inX && inZ) || (inY && inZ);
         if (kap && face_or_interior && kc > 0.0) kap[gi] = static_cast<float>(1.0 / kc);
     }
 }
 
-__global__ void k_diag_inv(const double *__restrict__ tx, const double *__restrict__ ty,
-                           const double *__restrict__ tz, LevelGeom g, double *__restrict__ dinv) {
+// Diagonal (sum of the six scaled face coefficients) and its inverse, interior cells.
+__global__ void k_diag(const double *__restrict__ tx, const double *__restrict__ ty, const double *__restrict__ tz,
+                       LevelGeom g, double *__restrict__ dg, double *__restrict__ dinv) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t PP = static_cast<int64_t>(P) * P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
@@ -587,6 +646,7 @@ __global__ void k_diag_inv(const double *__restrict__ tx, const double *__restri
         const int64_t b = t >> (3 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
         const double D = ((tx[gi] + tx[gi + 1]) + (ty[gi] + ty[gi + P])) + (tz[gi] + tz[gi + PP]);
+        dg[gi] = D;
         dinv[gi] = 1.0 / D;
     }
 }
@@ -597,10 +657,10 @@ namespace octmg {
 __global__ void k_set_unit(double *__restrict__ u, const int64_t *__restrict__ cmap, int m) {
     if (threadIdx.x == 0 && blockIdx.x == 0) u[cmap[m]] = 1.0;
 }
-// A[i, m] = -r[cmap[i]]: column m of the operator from the residual of a unit vector with f = 0
+// A[i, m] = (A e_m)[cmap[i]]: column m of the operator from its application to a unit vector
 __global__ void k_gather_column(const double *__restrict__ r, const int64_t *__restrict__ cmap, int N,
                                 double *__restrict__ A, int m) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) A[static_cast<int64_t>(i) * N + m] = -r[cmap[i]];
+    if (i < N) A[static_cast<int64_t>(i) * N + m] = r[cmap[i]];
 }
 }  // namespace octmg

@@ -42,13 +42,14 @@ struct DevLevel {
     SegItem *segs = nullptr;
     int nsegs = 0;
     XferItem *xfer = nullptr;  // from this level to the next (per block of the next level)
-    double *h2 = nullptr;      // per block h^2
+    double *h2_64 = nullptr, *ih2_64 = nullptr, *vol_64 = nullptr;  // per block h^2, 1/h^2, h^3
+    float *h2_32 = nullptr, *ih2_32 = nullptr, *vol_32 = nullptr;
     double *u64 = nullptr, *f64 = nullptr;
     float *u32 = nullptr, *f32 = nullptr;
-    double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dinv = nullptr;
+    double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dg = nullptr, *dinv = nullptr;
     float *kap = nullptr;
-    Coef c64() const { return Coef{tx, ty, tz, dinv, nullptr}; }
-    Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, kap}; }
+    Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr}; }
+    Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap}; }
     int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }
     int64_t cells() const { return static_cast<int64_t>(g.nb) << (3 * g.lg); }
 };
@@ -166,6 +167,12 @@ template <> float *ufield<float>(DevLevel &d) { return d.u32; }
 template <typename T> T *ffield(DevLevel &d);
 template <> double *ffield<double>(DevLevel &d) { return d.f64; }
 template <> float *ffield<float>(DevLevel &d) { return d.f32; }
+template <typename T> const T *h2_of(const DevLevel &d);
+template <> const double *h2_of<double>(const DevLevel &d) { return d.h2_64; }
+template <> const float *h2_of<float>(const DevLevel &d) { return d.h2_32; }
+template <typename T> const T *ih2_of(const DevLevel &d);
+template <> const double *ih2_of<double>(const DevLevel &d) { return d.ih2_64; }
+template <> const float *ih2_of<float>(const DevLevel &d) { return d.ih2_32; }
 template <typename T> Coef coef_of(const DevLevel &d);
 template <> Coef coef_of<double>(const DevLevel &d) { return d.c64(); }
 template <> Coef coef_of<float>(const DevLevel &d) { return d.c32(); }
@@ -203,8 +210,8 @@ void exchange_k(mg_forest *F, DevLevel &d) {
 template <typename T, int MODE>
 void smooth(mg_forest *F, DevLevel &d, int colour) {
     Prof p(F, cat_of<T>(P_SMOOTH64), 1);
-    k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2,
-                                                                       d.g, colour);
+    k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d),
+                                                                       h2_of<T>(d), d.g, colour);
 }
 
 template <typename T, int MODE>
@@ -228,7 +235,7 @@ void vcycle(mg_forest *F, int l) {
     {
         Prof p(F, cat_of<T>(P_RESTR64), 1);
         k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
-            ufield<T>(d), ffield<T>(d), coef_of<T>(d), d.h2, d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
+            ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
     }
     vcycle<T, MODE>(F, l + 1);
     exchange<T, MODE>(F, c, ufield<T>(c));
@@ -244,31 +251,40 @@ void vcycle(mg_forest *F, int l) {
     }
 }
 
-// Level-0 FP64 residual r = f - A u (exchange first), optional output (scaled, cast) and zeroing; returns
-// ||r||^2 and ||f||^2 (volume-weighted) to the host.
-template <int MODE, typename TO>
-mg_status residual64(mg_forest *F, double *u, const double *f, TO *out, double scale, TO *zero_out, double *rr,
-                     double *ff) {
+// Level-0 FP64 residual r = f - A u (exchange first); optionally written as FP32 r * scale with the FP32
+// correction zeroed; returns ||r||^2 (volume-weighted) to the host when rr is not null.  scale is a power of two
+// close to 1 / ||r|| so the FP32 values stay near unit size.
+template <int MODE>
+mg_status residual64(mg_forest *F, double *u, const double *f, float *out, double scale, float *zero_out,
+                     double *rr) {
     DevLevel &d = F->L[0];
     exchange<double, MODE>(F, d, u);
     const int grid = grid_for(d.cells());
-    Prof p(F, P_RESID64, 2);
-    k_residual_full<double, MODE, TO><<<grid, kThreads, 0, F->st>>>(u, f, d.c64(), d.h2, d.g, out, scale, F->partial,
-                                                                     zero_out);
-    k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
-    if (rr || ff) {
-        MG_CUDA(cudaMemcpyAsync(F->pinned, F->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, F->st));
+    {
+        Prof p(F, P_RESID64, 2);
+        k_residual_norm<MODE><<<grid, kThreads, 0, F->st>>>(u, f, d.c64(), d.ih2_64, d.vol_32, d.g, out,
+                                                            static_cast<float>(scale), F->partial, zero_out);
+        k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
+    }
+    if (rr) {
+        MG_CUDA(cudaMemcpyAsync(F->pinned, F->sums, sizeof(double), cudaMemcpyDeviceToHost, F->st));
         MG_CUDA(cudaStreamSynchronize(F->st));
-        if (rr) *rr = F->pinned[0];
-        if (ff) *ff = F->pinned[1];
+        *rr = F->pinned[0] / (scale * scale);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
 
-mg_status residual64_any(mg_forest *F, double *u, const double *f, double *rr, double *ff) {
-    if (F->cfg.coeff) return residual64<1, double>(F, u, f, nullptr, 1.0, nullptr, rr, ff);
-    return residual64<0, double>(F, u, f, nullptr, 1.0, nullptr, rr, ff);
+mg_status residual64_any(mg_forest *F, double *u, const double *f, double scale, double *rr) {
+    if (F->cfg.coeff) return residual64<1>(F, u, f, nullptr, scale, nullptr, rr);
+    return residual64<0>(F, u, f, nullptr, scale, nullptr, rr);
+}
+
+void apply64(mg_forest *F, DevLevel &d, const double *u, double *out) {
+    if (F->cfg.coeff)
+        k_apply64<1><<<grid_for(d.cells()), kThreads, 0, F->st>>>(u, d.c64(), d.ih2_64, d.g, out);
+    else
+        k_apply64<0><<<grid_for(d.cells()), kThreads, 0, F->st>>>(u, d.c64(), d.ih2_64, d.g, out);
 }
 
 // Coarsest-level dense operator (FP64 kernels on unit vectors), inverted on the host, uploaded.
@@ -292,15 +308,8 @@ mg_status assemble_coarse(mg_forest *F) {
     for (int m = 0; m < N; ++m) {
         MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
         k_set_unit<<<1, 32, 0, F->st>>>(d.u64, F->cmap, m);
-        if (F->cfg.coeff) {
-            exchange<double, 1>(F, d, d.u64);
-            k_residual_full<double, 1, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
-                d.u64, nullptr, d.c64(), d.h2, d.g, r, 1.0, nullptr, nullptr);
-        } else {
-            exchange<double, 0>(F, d, d.u64);
-            k_residual_full<double, 0, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
-                d.u64, nullptr, d.c64(), d.h2, d.g, r, 1.0, nullptr, nullptr);
-        }
+        exchange_any64(F, d, d.u64);
+        apply64(F, d, d.u64, r);
         k_gather_column<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, N, Adev, m);
     }
     MG_CUDA(cudaGetLastError());
@@ -326,8 +335,9 @@ mg_status build_coefficients(mg_forest *F) {
             k_restrict_field<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(p.k64, p.g, d.k64, p.xfer, d.g);
         }
         exchange_k(F, d);
-        k_face_coefs<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.k64, d.g, d.tx, d.ty, d.tz, d.kap);
-        k_diag_inv<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.g, d.dinv);
+        k_face_coefs<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.k64, d.ih2_64, d.g, d.tx, d.ty, d.tz,
+                                                                        d.kap);
+        k_diag<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.g, d.dg, d.dinv);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -369,17 +379,18 @@ double pow2_near(double x) {
 mg_status mixed_step(mg_forest *F, double scale, double *rr) {
     DevLevel &d = F->L[0];
     if (F->cfg.coeff)
-        MG_TRY((residual64<1, float>(F, d.u64, d.f64, d.f32, 1.0 / scale, d.u32, rr, nullptr)));
+        MG_TRY((residual64<1>(F, d.u64, d.f64, d.f32, scale, d.u32, rr)));
     else
-        MG_TRY((residual64<0, float>(F, d.u64, d.f64, d.f32, 1.0 / scale, d.u32, rr, nullptr)));
+        MG_TRY((residual64<0>(F, d.u64, d.f64, d.f32, scale, d.u32, rr)));
     return MG_OK;
 }
 
-mg_status finish_mixed_cycle(mg_forest *F, double scale) {
+// `cycles` FP32 V-cycles on the scaled residual, then u64 += e32 / mult (mult a power of two: exact).
+mg_status finish_mixed_cycle(mg_forest *F, double inv_mult, int cycles) {
     DevLevel &d = F->L[0];
-    vcycle32(F);
+    for (int i = 0; i < cycles; ++i) vcycle32(F);
     Prof p(F, P_UPDATE, 1);
-    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, scale, d.g);
+    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, inv_mult, d.g);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -404,14 +415,16 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
     const double fn = F->fnorm > 0.0 ? F->fnorm : 1.0;
     int done = 0;
     double rel = -1.0;
+    double mult = pow2_near(1.0 / fn);  // FP32 values of residuals are scaled by a power of two near 1/||r||
     if (F->cfg.precision == 0) {
         for (; done < max_cycles; ++done) {
             if (rtol >= 0.0 && done > 0 && rel <= rtol) break;
             vcycle64(F);
             double rr = 0.0;
             if (rtol >= 0.0 || rel_out || done + 1 == max_cycles) {
-                MG_TRY(residual64_any(F, d.u64, d.f64, &rr, nullptr));
+                MG_TRY(residual64_any(F, d.u64, d.f64, mult, &rr));
                 rel = std::sqrt(rr) / fn;
+                mult = pow2_near(1.0 / std::sqrt(rr));
                 if (!std::isfinite(rel)) {
                     set_error("residual is not finite");
                     ++done;
@@ -421,18 +434,19 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
         }
     } else {
         double rr = 0.0;
-        double scale = pow2_near(F->fnorm);
-        MG_TRY(mixed_step(F, scale, &rr));
+        MG_TRY(mixed_step(F, mult, &rr));
         rel = std::sqrt(rr) / fn;
-        for (; done < max_cycles; ++done) {
+        const int inner = std::max(1, F->cfg.inner_cycles);
+        while (done < max_cycles) {
             if (rtol >= 0.0 && rel <= rtol) break;
-            MG_TRY(finish_mixed_cycle(F, scale));
-            scale = pow2_near(std::sqrt(rr));
-            MG_TRY(mixed_step(F, scale, &rr));
+            const int m = std::min(inner, max_cycles - done);
+            MG_TRY(finish_mixed_cycle(F, 1.0 / mult, m));
+            done += m;
+            mult = pow2_near(1.0 / std::sqrt(rr));
+            MG_TRY(mixed_step(F, mult, &rr));
             rel = std::sqrt(rr) / fn;
             if (!std::isfinite(rel)) {
                 set_error("residual is not finite");
-                ++done;
                 break;
             }
         }
@@ -501,9 +515,22 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         if ((st = upload(F, &d.faces, h.faces)) != MG_OK) return fail(st);
         if ((st = upload(F, &d.segs, h.segs)) != MG_OK) return fail(st);
         if (!h.to_next.empty() && (st = upload(F, &d.xfer, h.to_next)) != MG_OK) return fail(st);
-        std::vector<double> h2(h.h.size());
-        for (size_t b = 0; b < h2.size(); ++b) h2[b] = h.h[b] * h.h[b];
-        if ((st = upload(F, &d.h2, h2)) != MG_OK) return fail(st);
+        std::vector<double> h2(h.h.size()), ih2(h.h.size()), vol(h.h.size());
+        std::vector<float> h2f(h.h.size()), ih2f(h.h.size()), volf(h.h.size());
+        for (size_t b = 0; b < h2.size(); ++b) {
+            h2[b] = h.h[b] * h.h[b];
+            ih2[b] = 1.0 / h2[b];
+            vol[b] = h2[b] * h.h[b];
+            h2f[b] = static_cast<float>(h2[b]);
+            ih2f[b] = static_cast<float>(ih2[b]);
+            volf[b] = static_cast<float>(vol[b]);
+        }
+        if ((st = upload(F, &d.h2_64, h2)) != MG_OK) return fail(st);
+        if ((st = upload(F, &d.ih2_64, ih2)) != MG_OK) return fail(st);
+        if ((st = upload(F, &d.vol_64, vol)) != MG_OK) return fail(st);
+        if ((st = upload(F, &d.h2_32, h2f)) != MG_OK) return fail(st);
+        if ((st = upload(F, &d.ih2_32, ih2f)) != MG_OK) return fail(st);
+        if ((st = upload(F, &d.vol_32, volf)) != MG_OK) return fail(st);
         const int64_t pe = d.pool_elems();
         if ((st = dalloc(F, &d.u64, pe)) != MG_OK) return fail(st);
         if ((st = dalloc(F, &d.f64, pe)) != MG_OK) return fail(st);
@@ -516,6 +543,7 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
             if ((st = dalloc(F, &d.tx, pe)) != MG_OK) return fail(st);
             if ((st = dalloc(F, &d.ty, pe)) != MG_OK) return fail(st);
             if ((st = dalloc(F, &d.tz, pe)) != MG_OK) return fail(st);
+            if ((st = dalloc(F, &d.dg, pe)) != MG_OK) return fail(st);
             if ((st = dalloc(F, &d.dinv, pe)) != MG_OK) return fail(st);
             if (cfg->precision == 1 && (st = dalloc(F, &d.kap, pe)) != MG_OK) return fail(st);
         }
@@ -570,10 +598,12 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
         MG_TRY(build_coefficients(F));
         MG_TRY(assemble_coarse(F));
     }
-    double ff = 0.0;
-    MG_CUDA(cudaMemsetAsync(F->s64a, 0, d.pool_elems() * sizeof(double), F->st));
-    MG_TRY(residual64_any(F, F->s64a, d.f64, nullptr, &ff));
-    F->fnorm = std::sqrt(ff);
+    const int grid = grid_for(d.cells());
+    k_norm64<<<grid, kThreads, 0, F->st>>>(d.f64, d.vol_64, d.g, F->partial);
+    k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
+    MG_CUDA(cudaMemcpyAsync(F->pinned, F->sums, sizeof(double), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    F->fnorm = std::sqrt(F->pinned[0]);
     F->rhs_set = true;
     return MG_OK;
 }
@@ -590,12 +620,7 @@ mg_status apply_op(mg_forest *F, const double *u_dev, double *Au_dev) {
     DevLevel &d = F->L[0];
     MG_TRY(pack_user<double>(F, d, F->s64a, u_dev));
     exchange_any64(F, d, F->s64a);
-    if (F->cfg.coeff)
-        k_residual_full<double, 1, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
-            F->s64a, nullptr, d.c64(), d.h2, d.g, F->s64b, -1.0, nullptr, nullptr);
-    else
-        k_residual_full<double, 0, double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(
-            F->s64a, nullptr, d.c64(), d.h2, d.g, F->s64b, -1.0, nullptr, nullptr);
+    apply64(F, d, F->s64a, F->s64b);
     MG_TRY(unpack_user<double>(F, d, Au_dev, F->s64b));
     return MG_OK;
 }

@@ -131,10 +131,10 @@ def test_refined_solve_to_1e10_property(coeff):
     assert ref.rel_residual(u.cpu().numpy(), f.numpy()) <= 1.05e-10
 
 
-@pytest.mark.parametrize("coeff", [False, True])
-def test_mixed_precision_solve_error_vs_fp64_oracle(coeff):
+@pytest.mark.parametrize("coeff,inner", [(False, 1), (True, 1), (True, 3)])
+def test_mixed_precision_solve_error_vs_fp64_oracle(coeff, inner):
     R, n, keys, k, f = _inputs("sphere_2x8", coeff, seed=41)
-    F = _forest(R, n, keys, coeff=coeff, precision=1)
+    F = _forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=inner)
     F.set_rhs(f.to(DEV), k.to(DEV) if coeff else None)
     u = torch.zeros_like(f, device=DEV)
     cyc, rel = F.solve(u, rtol=1e-10, max_cycles=40)
