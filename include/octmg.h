@@ -110,6 +110,18 @@ mg_status mg_apply_transpose(mg_forest *forest, const double *y_dev, double *ATy
  * doubles, block-major, x fastest) to padded_dev. */
 mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
 
+/* mg_exchange_level without device allocation.  The paper has no counterpart: this serves callers that cannot
+ * call cudaMalloc at the time they need the exchange (during a CUDA stream capture, when all device memory is owned
+ * by a caching allocator, or in loops that must not enter the driver's allocator).  Same arguments, result and
+ * errors as mg_exchange_level, but the level's padded scratch pool is a static device array of 524,288 doubles
+ * (4 MiB) inside the library, which every GPU that loads the library holds until the process exits; a level whose
+ * pool (nb * (n+2)^3 rounded up to 32 doubles per block) is larger is rejected with MG_ERR_INVALID_ARG and a
+ * message.  The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other threads, other forests) race on it.  The call clears the part of the array it uses, enqueues
+ * its work on the forest's stream and synchronises that stream before returning. */
+mg_status mg_exchange_level_noalloc(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
+
 /* Kernel accounting.  Launch counters per kernel family always run; mg_profile(forest, 1) clears them and starts
  * recording a CUDA-event pair on the forest's stream around every family's launches, mg_profile(forest, 0) stops.
  * mg_profile_read synchronises the stream and, for up to max_families families, writes the family name (32 bytes

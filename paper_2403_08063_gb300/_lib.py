@@ -60,6 +60,7 @@ SIGNATURES = {
     "mg_apply": (I32, [P, P, P]),
     "mg_apply_transpose": (I32, [P, P, P]),
     "mg_exchange_level": (I32, [P, I32, P, P]),
+    "mg_exchange_level_noalloc": (I32, [P, I32, P, P]),
     "mg_profile": (I32, [P, I32]),
     "mg_profile_read": (I32, [P, I32, _c.c_char_p, DP, _c.POINTER(_c.c_int64), IP]),
     "mg_last_error": (_c.c_char_p, []),

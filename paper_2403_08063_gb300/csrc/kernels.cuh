@@ -61,14 +61,14 @@ __device__ inline int face_off(int axis, int side, int depth, int i1, int i2, in
 //   Upwind neighbour remapped to -2 (case 2, bases {-2, -1, 0}):
 //     (-3, 14, 21) / 32 and (5, -18, 45) / 32.
 // ------------------------------------------------------------------------------------------------------------
-__constant__ double c_wn[3] = {45.0 / 32, -18.0 / 32, 5.0 / 32};
-__constant__ double c_wt[3][2][3] = {
+static __constant__ double c_wn[3] = {45.0 / 32, -18.0 / 32, 5.0 / 32};
+static __constant__ double c_wt[3][2][3] = {
     {{5.0 / 32, 30.0 / 32, -3.0 / 32}, {-3.0 / 32, 30.0 / 32, 5.0 / 32}},
     {{45.0 / 32, -18.0 / 32, 5.0 / 32}, {21.0 / 32, 14.0 / 32, -3.0 / 32}},
     {{-3.0 / 32, 14.0 / 32, 21.0 / 32}, {5.0 / 32, -18.0 / 32, 45.0 / 32}}};
-__constant__ int c_base[3][3] = {{-1, 0, 1}, {0, 1, 2}, {-2, -1, 0}};
-__constant__ float c_wn_f[3] = {45.0f / 32, -18.0f / 32, 5.0f / 32};
-__constant__ float c_wt_f[3][2][3] = {
+static __constant__ int c_base[3][3] = {{-1, 0, 1}, {0, 1, 2}, {-2, -1, 0}};
+static __constant__ float c_wn_f[3] = {45.0f / 32, -18.0f / 32, 5.0f / 32};
+static __constant__ float c_wt_f[3][2][3] = {
     {{5.0f / 32, 30.0f / 32, -3.0f / 32}, {-3.0f / 32, 30.0f / 32, 5.0f / 32}},
     {{45.0f / 32, -18.0f / 32, 5.0f / 32}, {21.0f / 32, 14.0f / 32, -3.0f / 32}},
     {{-3.0f / 32, 14.0f / 32, 21.0f / 32}, {5.0f / 32, -18.0f / 32, 45.0f / 32}}};
@@ -165,7 +165,7 @@ __device__ inline double apply_at(const double *__restrict__ u, const Coef &cf, 
 // One thread per ghost cell; n is a power of two, so items and cells decode with shifts.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, bool KIND_K>
-__global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g) {
+static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g) {
     const int n = g.n, P = g.P, lg = g.lg, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -219,7 +219,7 @@ __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__
 //               1/h^2-scaled coefficients of MODE 1, T_j / (2 T_C) = T~_j / (8 T~_C) since h_C = 2 h_j.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, int MODE, bool FLUX>
-__global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
+static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
                                 LevelGeom g) {
     const int n = g.n, P = g.P, lgh = g.lg - 1, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lgh);
@@ -270,7 +270,7 @@ __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__res
 // h2 is h^2 per block in the field's precision (unused in MODE 1, whose coefficients carry 1/h^2).
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2, LevelGeom g,
+static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2, LevelGeom g,
                          int colour) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg - 1);
@@ -300,7 +300,7 @@ __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, co
 // One thread per coarse cell.  ih2f: 1/h^2 per fine block.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
+static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
                                     const T *__restrict__ ih2f, LevelGeom gf, T *__restrict__ fc,
                                     T *__restrict__ uc, const XferItem *__restrict__ xf, LevelGeom gc) {
     const int lgc = gc.lg, nc = gc.n;
@@ -350,7 +350,7 @@ __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict
 
 // Restriction of a plain field (mean of the 8 children; copy for carried-over blocks), e.g. the coefficient k.
 template <typename T>
-__global__ void k_restrict_field(const T *__restrict__ xf_in, LevelGeom gf, T *__restrict__ xc,
+static __global__ void k_restrict_field(const T *__restrict__ xf_in, LevelGeom gf, T *__restrict__ xc,
                                  const XferItem *__restrict__ xf, LevelGeom gc) {
     const int lgc = gc.lg, nc = gc.n;
     const int64_t total = static_cast<int64_t>(gc.nb) << (3 * lgc);
@@ -395,7 +395,7 @@ __global__ void k_restrict_field(const T *__restrict__ xf_in, LevelGeom gf, T *_
 // One thread per coarse cell, writing its 8 children.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
+static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
                           const XferItem *__restrict__ xf, LevelGeom gc) {
     const int lgc = gc.lg, nc = gc.n, Pc = gc.P;
     const int64_t PPc = static_cast<int64_t>(Pc) * Pc;
@@ -448,7 +448,7 @@ __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict_
 // pool through cmap, the padded offset of every unknown).
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const double *__restrict__ Ainv,
+static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const double *__restrict__ Ainv,
                                const int64_t *__restrict__ cmap, int N) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -468,7 +468,7 @@ __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const
 // relative) and in FP64 across threads.  out / zero_out may be null (convergence check of FP64 cycles).
 // ------------------------------------------------------------------------------------------------------------
 template <int MODE>
-__global__ void k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
+static __global__ void k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
                                 const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
                                 float *__restrict__ out, float scale, double *__restrict__ partial,
                                 float *__restrict__ zero_out) {
@@ -503,7 +503,7 @@ __global__ void k_residual_norm(const double *__restrict__ u, const double *__re
 
 // A u over a whole level in FP64 (operator application; ghosts already exchanged).
 template <int MODE>
-__global__ void k_apply64(const double *__restrict__ u, Coef cf, const double *__restrict__ ih2, LevelGeom g,
+static __global__ void k_apply64(const double *__restrict__ u, Coef cf, const double *__restrict__ ih2, LevelGeom g,
                           double *__restrict__ out) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
@@ -519,7 +519,7 @@ __global__ void k_apply64(const double *__restrict__ u, Coef cf, const double *_
 }
 
 // Per-CTA partial sums of h^3 x^2 over the interior of a padded FP64 field (vol = h^3 per block, FP64).
-__global__ void k_norm64(const double *__restrict__ x, const double *__restrict__ vol, LevelGeom g,
+static __global__ void k_norm64(const double *__restrict__ x, const double *__restrict__ vol, LevelGeom g,
                          double *__restrict__ partial) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
@@ -546,7 +546,7 @@ __global__ void k_norm64(const double *__restrict__ x, const double *__restrict_
 }
 
 // Deterministic sum of the per-CTA partials (fixed order for a fixed grid).
-__global__ void k_sum_partials(const double *__restrict__ partial, int nparts, double *__restrict__ out) {
+static __global__ void k_sum_partials(const double *__restrict__ partial, int nparts, double *__restrict__ out) {
     __shared__ double sa[kThreads];
     double a = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += partial[i];
@@ -564,7 +564,7 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nparts, d
 // ------------------------------------------------------------------------------------------------------------
 // user layout (n_leaves, n^3) FP64 <-> padded pool of type T (interior only)
 template <typename T>
-__global__ void k_pack(T *__restrict__ pool, const double *__restrict__ user, LevelGeom g) {
+static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ user, LevelGeom g) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -578,7 +578,7 @@ __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ user, Le
 }
 
 template <typename T>
-__global__ void k_unpack(double *__restrict__ user, const T *__restrict__ pool, LevelGeom g) {
+static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__ pool, LevelGeom g) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -592,7 +592,7 @@ __global__ void k_unpack(double *__restrict__ user, const T *__restrict__ pool, 
 }
 
 // u64 += s * e32 over the interior (mixed-precision defect correction update)
-__global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__ e, double s, LevelGeom g) {
+static __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__ e, double s, LevelGeom g) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -609,7 +609,7 @@ __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__
 // Face coefficients of a level from k with ghosts: MODE 1 arrays (harmonic mean times the block's 1/h^2) and
 // 1/k for FP32 (MODE 2).  tx at padded (X, Y, Z) is the face between X-1 and X, for X in 1..n+1 and interior
 // Y, Z (same for ty, tz).
-__global__ void k_face_coefs(const double *__restrict__ k, const double *__restrict__ ih2, LevelGeom g,
+static __global__ void k_face_coefs(const double *__restrict__ k, const double *__restrict__ ih2, LevelGeom g,
                              double *__restrict__ tx, double *__restrict__ ty, double *__restrict__ tz,
                              float *__restrict__ kap) {
     const int P = g.P, n = g.n;
@@ -633,7 +633,7 @@ __global__ void k_face_coefs(const double *__restrict__ k, const double *__restr
 }
 
 // Diagonal (sum of the six scaled face coefficients) and its inverse, interior cells.
-__global__ void k_diag(const double *__restrict__ tx, const double *__restrict__ ty, const double *__restrict__ tz,
+static __global__ void k_diag(const double *__restrict__ tx, const double *__restrict__ ty, const double *__restrict__ tz,
                        LevelGeom g, double *__restrict__ dg, double *__restrict__ dinv) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t PP = static_cast<int64_t>(P) * P;
@@ -654,11 +654,11 @@ __global__ void k_diag(const double *__restrict__ tx, const double *__restrict__
 }  // namespace octmg
 
 namespace octmg {
-__global__ void k_set_unit(double *__restrict__ u, const int64_t *__restrict__ cmap, int m) {
+static __global__ void k_set_unit(double *__restrict__ u, const int64_t *__restrict__ cmap, int m) {
     if (threadIdx.x == 0 && blockIdx.x == 0) u[cmap[m]] = 1.0;
 }
 // A[i, m] = (A e_m)[cmap[i]]: column m of the operator from its application to a unit vector
-__global__ void k_gather_column(const double *__restrict__ r, const int64_t *__restrict__ cmap, int N,
+static __global__ void k_gather_column(const double *__restrict__ r, const int64_t *__restrict__ cmap, int N,
                                 double *__restrict__ A, int m) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) A[static_cast<int64_t>(i) * N + m] = r[cmap[i]];

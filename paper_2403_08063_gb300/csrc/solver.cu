@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "forest_state.h"
 #include "kernels.cuh"
 #include "octmg_internal.h"
 
@@ -12,76 +13,6 @@ namespace octmg {
 
 thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
-
-#define MG_CUDA(call)                                                                          \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess) {                                                               \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                     \
-            return MG_ERR_CUDA;                                                                \
-        }                                                                                      \
-    } while (0)
-
-#define MG_TRY(expr)                      \
-    do {                                  \
-        mg_status s_ = (expr);            \
-        if (s_ != MG_OK) return s_;       \
-    } while (0)
-
-constexpr int kMaxGrid = 152 * 32;  // grid-stride loops: at most 32 CTAs of 256 threads per SM
-
-inline int grid_for(int64_t total) {
-    int64_t g = (total + kThreads - 1) / kThreads;
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, kMaxGrid)));
-}
-
-struct DevLevel {
-    LevelGeom g{};
-    FaceItem *faces = nullptr;
-    int nfaces = 0;
-    SegItem *segs = nullptr;
-    int nsegs = 0;
-    XferItem *xfer = nullptr;  // from this level to the next (per block of the next level)
-    double *h2_64 = nullptr, *ih2_64 = nullptr, *vol_64 = nullptr;  // per block h^2, 1/h^2, h^3
-    float *h2_32 = nullptr, *ih2_32 = nullptr, *vol_32 = nullptr;
-    double *u64 = nullptr, *f64 = nullptr;
-    float *u32 = nullptr, *f32 = nullptr;
-    double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dg = nullptr, *dinv = nullptr;
-    float *kap = nullptr;
-    Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr}; }
-    Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap}; }
-    int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }
-    int64_t cells() const { return static_cast<int64_t>(g.nb) << (3 * g.lg); }
-};
-
-}  // namespace octmg
-
-struct mg_forest {
-    mg_config cfg{};
-    cudaStream_t st = nullptr;
-    octmg::HostHierarchy H;
-    std::vector<octmg::DevLevel> L;
-    std::vector<void *> allocs;
-    double *Ainv = nullptr;
-    int64_t *cmap = nullptr;
-    int Nc = 0;
-    double *partial = nullptr;  // 2 * kMaxGrid
-    double *sums = nullptr;     // 2 doubles on the device
-    double *pinned = nullptr;   // 2 doubles, host pinned
-    double *s64a = nullptr, *s64b = nullptr;  // level-0 FP64 scratch pools
-    double *coarse_r = nullptr;               // coarsest-level scratch pool (operator assembly)
-    int *flag = nullptr;                      // input-check flag
-    bool rhs_set = false;
-    double fnorm = 0.0;
-    // per-kernel-family launch counters (always on) and CUDA-event timing (mg_profile)
-    bool prof = false;
-    int64_t nlaunch[16] = {};
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    std::vector<std::pair<int, size_t>> recs;  // (family, index of the start event; stop = +1)
-};
-
-namespace octmg {
 
 template <typename T>
 mg_status dalloc(mg_forest *F, T **p, int64_t count, bool zero = true) {
