@@ -52,6 +52,7 @@ class Forest:
         _lib.check(self.lib.mg_forest_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
         self.numel = self.n_leaves * self.n ** 3
+        self.version = 0  # bumped by set_rhs; the autograd function re-sets (f, k) if it changed
 
     # -- lifetime ----------------------------------------------------------------------------------------
     def close(self):
@@ -86,6 +87,7 @@ class Forest:
         if self.coeff:
             _dev_f64(k, self.numel, "k")
         _lib.check(self.lib.mg_set_rhs(self.h, _ptr(f), _ptr(k) if self.coeff else None))
+        self.version += 1
 
     def vcycle(self, u, ncycles=1):
         _dev_f64(u, self.numel, "u")
@@ -150,3 +152,36 @@ class Forest:
             nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
             out[nm] = (ms[i], int(cnt[i]))
         return out
+
+
+class MGSolveFn(torch.autograd.Function):
+    """u = A(k)^-1 f through the forest's multigrid solve, differentiable in f and k.
+
+    backward re-runs multigrid on the transposed operator (mg_adjoint_solve): lambda = A^-T grad_u is dL/df and
+    dL/dk = -lambda^T (dA/dk) u.  The checkpointed forward state is u itself plus the forest's set-up hierarchy
+    (coefficient pyramid, coarsest inverse); if the forest was re-used with other inputs in between, backward
+    restores (f, k) first.  Usage: u = MGSolveFn.apply(f, k, forest, rtol, max_cycles) (k may be None).
+    """
+
+    @staticmethod
+    def forward(ctx, f, k, forest, rtol=1e-10, max_cycles=100):
+        fd = f.detach().contiguous()
+        kd = k.detach().contiguous() if k is not None else None
+        forest.set_rhs(fd, kd)
+        u = torch.zeros_like(fd)
+        forest.solve(u, rtol=rtol, max_cycles=max_cycles)
+        ctx.forest, ctx.version, ctx.rtol, ctx.max_cycles = forest, forest.version, rtol, max_cycles
+        ctx.save_for_backward(u, fd, kd if kd is not None else torch.empty(0, device=fd.device))
+        ctx.has_k = kd is not None
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        u, fd, kd = ctx.saved_tensors
+        forest = ctx.forest
+        if forest.version != ctx.version:
+            forest.set_rhs(fd, kd if ctx.has_k else None)
+        want_k = ctx.has_k and ctx.needs_input_grad[1]
+        lam, gk = forest.adjoint(u, grad_u.contiguous().to(torch.float64), want_k=want_k,
+                                 rtol=min(ctx.rtol, 1e-10), max_cycles=max(ctx.max_cycles, 100))
+        return lam, gk, None, None, None

@@ -11,7 +11,7 @@ namespace {
 
 struct KeyHash {
     size_t operator()(const Key &k) const {
-        uint64_t h = static_cast<uint64_t>(k.lev + 64);
+        uint64_t h = static_cast<uint64_t>(k.p) * 0x100000001B3ull + static_cast<uint64_t>(k.lev + 64);
         h = h * 0x9E3779B97F4A7C15ull ^ static_cast<uint32_t>(k.i);
         h = h * 0x9E3779B97F4A7C15ull ^ static_cast<uint32_t>(k.j);
         h = h * 0x9E3779B97F4A7C15ull ^ static_cast<uint32_t>(k.k);
@@ -78,7 +78,7 @@ mg_status build_faces(int32_t R, HostLevel &L, std::string &err) {
                     L.faces.push_back(fi);
                     continue;
                 }
-                Key parent{p.lev - 1, p.i >> 1, p.j >> 1, p.k >> 1};
+                Key parent{p.p, p.lev - 1, p.i >> 1, p.j >> 1, p.k >> 1};
                 it = idx.find(parent);
                 if (it != idx.end()) {
                     fi.kind = FK_C2F;
@@ -90,13 +90,14 @@ mg_status build_faces(int32_t R, HostLevel &L, std::string &err) {
                 }
                 for (int s2 = 0; s2 < 2; ++s2) {
                     for (int s1 = 0; s1 < 2; ++s1) {
-                        Key c{p.lev + 1, 0, 0, 0};
+                        Key c{p.p, p.lev + 1, 0, 0, 0};
                         set_coord(c, axis, 2 * coord(p, axis) + (side == 0 ? 1 : 0));
                         set_coord(c, t1, 2 * coord(p, t1) + s1);
                         set_coord(c, t2, 2 * coord(p, t2) + s2);
                         auto ic = idx.find(c);
                         if (ic == idx.end()) {
-                            err = "leaf (" + std::to_string(key.lev) + "," + std::to_string(key.i) + "," +
+                            err = "problem " + std::to_string(key.p) + " leaf (" + std::to_string(key.lev) + "," +
+                                  std::to_string(key.i) + "," +
                                   std::to_string(key.j) + "," + std::to_string(key.k) +
                                   ") has a face neighbourhood that is not 2:1 balanced";
                             return MG_ERR_UNBALANCED;
@@ -117,15 +118,20 @@ mg_status build_faces(int32_t R, HostLevel &L, std::string &err) {
     return MG_OK;
 }
 
-mg_status validate_leaves(int32_t R, const std::vector<Key> &leaves, std::string &err) {
+mg_status validate_leaves(int32_t R, int32_t n_problems, const std::vector<Key> &leaves, std::string &err) {
     if (leaves.empty()) {
         err = "no leaves";
         return MG_ERR_INVALID_ARG;
     }
     KeyMap idx;
-    int32_t maxlev = 0;
+    std::vector<int32_t> maxlev(n_problems, 0);
+    std::vector<int64_t> count(n_problems, 0);
     for (size_t b = 0; b < leaves.size(); ++b) {
         const Key &k = leaves[b];
+        if (k.p < 0 || k.p >= n_problems) {
+            err = "leaf problem index outside 0..n_problems-1";
+            return MG_ERR_INVALID_ARG;
+        }
         int64_t m;
         if (k.lev < 0 || k.lev > 20 || !blocks_per_axis(R, k.lev, m) || k.i < 0 || k.j < 0 || k.k < 0 || k.i >= m ||
             k.j >= m || k.k >= m) {
@@ -136,50 +142,64 @@ mg_status validate_leaves(int32_t R, const std::vector<Key> &leaves, std::string
             err = "duplicate leaf";
             return MG_ERR_UNBALANCED;
         }
-        maxlev = std::max(maxlev, k.lev);
+        maxlev[k.p] = std::max(maxlev[k.p], k.lev);
+        count[k.p] += 1;
     }
-    // no leaf has an ancestor among the leaves, and the volumes (in finest-level units) sum to the domain's
-    int64_t mfin = static_cast<int64_t>(R) << maxlev;
-    if (mfin > (1 << 20)) {
-        err = "forest too deep";
-        return MG_ERR_INVALID_ARG;
-    }
-    long double vol = 0.0L;
+    // per problem: no leaf has an ancestor among the leaves, and the volumes (in finest-level units) sum to the
+    // domain's
+    std::vector<long double> vol(n_problems, 0.0L);
     for (const Key &k : leaves) {
+        if ((static_cast<int64_t>(R) << maxlev[k.p]) > (1 << 20)) {
+            err = "forest too deep";
+            return MG_ERR_INVALID_ARG;
+        }
         Key a = k;
         while (a.lev > 0) {
-            a = Key{a.lev - 1, a.i >> 1, a.j >> 1, a.k >> 1};
+            a = Key{a.p, a.lev - 1, a.i >> 1, a.j >> 1, a.k >> 1};
             if (idx.count(a)) {
                 err = "overlapping leaves";
                 return MG_ERR_UNBALANCED;
             }
         }
-        vol += std::ldexp(1.0L, 3 * (maxlev - k.lev));
+        vol[k.p] += std::ldexp(1.0L, 3 * (maxlev[k.p] - k.lev));
     }
-    long double want = static_cast<long double>(mfin) * mfin * mfin;
-    if (vol != want) {
-        err = "leaves do not cover the domain";
-        return MG_ERR_UNBALANCED;
+    for (int32_t p = 0; p < n_problems; ++p) {
+        const int64_t mfin = static_cast<int64_t>(R) << maxlev[p];
+        const long double want = static_cast<long double>(mfin) * mfin * mfin;
+        if (count[p] == 0 || vol[p] != want) {
+            err = "leaves do not cover the domain (problem " + std::to_string(p) + ")";
+            return MG_ERR_UNBALANCED;
+        }
     }
     return MG_OK;
 }
 
-// Merge every complete octet of siblings at the deepest level into its parent.  false if nothing merges.
-bool merge_deepest(int32_t R, const HostLevel &L, HostLevel &C) {
-    int32_t deepest = -1000;
-    for (const Key &k : L.keys) deepest = std::max(deepest, k.lev);
-    int64_t m;
-    if (!blocks_per_axis(R, deepest - 1, m)) return false;
+// For every problem whose level has more than max_coarse unknowns, merge each complete octet of siblings at its
+// deepest level into the parent; every other block is carried over.  false if nothing merges.
+bool merge_deepest(int32_t R, int32_t n_problems, int64_t max_coarse, const HostLevel &L, HostLevel &C) {
+    const int64_t cells = static_cast<int64_t>(L.n) * L.n * L.n;
+    std::vector<int32_t> deepest(n_problems, -1000);
+    std::vector<int64_t> nblk(n_problems, 0);
+    for (const Key &k : L.keys) {
+        deepest[k.p] = std::max(deepest[k.p], k.lev);
+        nblk[k.p] += 1;
+    }
+    std::vector<char> wants(n_problems, 0);
+    for (int32_t p = 0; p < n_problems; ++p) {
+        int64_t m;
+        wants[p] = nblk[p] * cells > max_coarse && blocks_per_axis(R, deepest[p] - 1, m);
+    }
     KeyMap idx;
     for (size_t b = 0; b < L.keys.size(); ++b) idx[L.keys[b]] = static_cast<int32_t>(b);
     KeyMap counts;
     for (const Key &k : L.keys)
-        if (k.lev == deepest) counts[Key{deepest - 1, k.i >> 1, k.j >> 1, k.k >> 1}] += 1;
+        if (wants[k.p] && k.lev == deepest[k.p]) counts[Key{k.p, k.lev - 1, k.i >> 1, k.j >> 1, k.k >> 1}] += 1;
     std::vector<Key> parents;
     for (auto &kv : counts)
         if (kv.second == 8) parents.push_back(kv.first);
     if (parents.empty()) return false;
     std::sort(parents.begin(), parents.end(), [](const Key &a, const Key &b) {
+        if (a.p != b.p) return a.p < b.p;
         if (a.k != b.k) return a.k < b.k;
         if (a.j != b.j) return a.j < b.j;
         return a.i < b.i;
@@ -192,7 +212,7 @@ bool merge_deepest(int32_t R, const HostLevel &L, HostLevel &C) {
     std::vector<XferItem> xf;
     for (size_t b = 0; b < L.keys.size(); ++b) {
         const Key &k = L.keys[b];
-        if (k.lev == deepest && is_parent.count(Key{deepest - 1, k.i >> 1, k.j >> 1, k.k >> 1})) continue;
+        if (is_parent.count(Key{k.p, k.lev - 1, k.i >> 1, k.j >> 1, k.k >> 1})) continue;
         C.keys.push_back(k);
         XferItem x{};
         x.kind = XF_COPY;
@@ -204,7 +224,7 @@ bool merge_deepest(int32_t R, const HostLevel &L, HostLevel &C) {
         XferItem x{};
         x.kind = XF_MERGE;
         for (int o = 0; o < 8; ++o) {
-            Key c{p.lev + 1, 2 * p.i + (o & 1), 2 * p.j + ((o >> 1) & 1), 2 * p.k + ((o >> 2) & 1)};
+            Key c{p.p, p.lev + 1, 2 * p.i + (o & 1), 2 * p.j + ((o >> 1) & 1), 2 * p.k + ((o >> 2) & 1)};
             x.src[o] = idx.at(c);
         }
         xf.push_back(x);
@@ -215,8 +235,8 @@ bool merge_deepest(int32_t R, const HostLevel &L, HostLevel &C) {
 
 }  // namespace
 
-mg_status build_hierarchy(int32_t R, int32_t n, const std::vector<Key> &leaves, int32_t max_coarse,
-                          HostHierarchy &out, std::string &err) {
+mg_status build_hierarchy(int32_t R, int32_t n, int32_t n_problems, const std::vector<Key> &leaves,
+                          int32_t max_coarse, HostHierarchy &out, std::string &err) {
     if (R < 1 || R > 4096) {
         err = "roots must be in 1..4096";
         return MG_ERR_INVALID_ARG;
@@ -225,7 +245,11 @@ mg_status build_hierarchy(int32_t R, int32_t n, const std::vector<Key> &leaves, 
         err = "n must be a power of two in 4..1024";
         return MG_ERR_BLOCK_SIZE;
     }
-    mg_status st = validate_leaves(R, leaves, err);
+    if (n_problems < 1) {
+        err = "n_problems must be >= 1";
+        return MG_ERR_INVALID_ARG;
+    }
+    mg_status st = validate_leaves(R, n_problems, leaves, err);
     if (st != MG_OK) return st;
     out.R = R;
     out.levels.clear();
@@ -246,10 +270,9 @@ mg_status build_hierarchy(int32_t R, int32_t n, const std::vector<Key> &leaves, 
         out.levels.back().to_next = xf;
         out.levels.push_back(nx);
     }
-    while (static_cast<int64_t>(out.levels.back().keys.size()) * out.levels.back().n * out.levels.back().n *
-               out.levels.back().n > max_coarse) {
+    for (;;) {
         HostLevel nx;
-        if (!merge_deepest(R, out.levels.back(), nx)) break;
+        if (!merge_deepest(R, n_problems, max_coarse, out.levels.back(), nx)) break;
         out.levels.back().to_next = nx.to_next;
         nx.to_next.clear();
         out.levels.push_back(nx);

@@ -1,6 +1,7 @@
 // Forest state shared by the solver translation units: device level structures and the opaque mg_forest.
 #pragma once
 #include <algorithm>
+#include <cstdio>
 #include <string>
 #include <utility>
 #include <vector>
@@ -47,6 +48,9 @@ struct DevLevel {
     float *u32 = nullptr, *f32 = nullptr;
     double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dg = nullptr, *dinv = nullptr;
     float *kap = nullptr;
+    int8_t *fkind = nullptr;   // per block face (b * 6 + 2 * axis + side): 0 boundary, 1 same, 2 C2F, 3 F2C
+    // adjoint work pools (allocated by the first adjoint call)
+    double *a_ub = nullptr, *a_fb = nullptr, *a_z = nullptr, *a_tmp = nullptr;
     Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr}; }
     Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap}; }
     int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }
@@ -70,6 +74,8 @@ struct mg_forest {
     double *s64a = nullptr, *s64b = nullptr;  // level-0 FP64 scratch pools
     double *coarse_r = nullptr;               // coarsest-level scratch pool (operator assembly)
     int *flag = nullptr;                      // input-check flag
+    double *AinvT = nullptr;                  // transpose of the coarsest inverse (adjoint cycles)
+    double *a_g = nullptr, *a_lam = nullptr;  // adjoint right-hand side and solution (level 0)
     bool rhs_set = false;
     double fnorm = 0.0;
     // per-kernel-family launch counters (always on) and CUDA-event timing (mg_profile)
@@ -82,6 +88,52 @@ struct mg_forest {
 
 
 namespace octmg {
+// Kernel families for launch counting and timing.
+enum ProfCat {
+    P_EXCH64 = 0, P_EXCH32, P_SMOOTH64, P_SMOOTH32, P_RESTR64, P_RESTR32, P_PROL64, P_PROL32, P_COARSE64,
+    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_NCAT
+};
+template <typename T> constexpr int cat_of(int cat64) { return sizeof(T) == 8 ? cat64 : cat64 + 1; }
+
+cudaEvent_t next_event(mg_forest *F);
+
+// RAII scope around the launches of one kernel family.
+struct Prof {
+    mg_forest *F;
+    int cat;
+    size_t start = 0;
+    bool on = false;
+    Prof(mg_forest *f, int c, int launches) : F(f), cat(c) {
+        F->nlaunch[c] += launches;
+        if (F->prof) {
+            cudaEvent_t a = next_event(F), b = next_event(F);
+            if (a && b) {
+                start = F->ev_used - 2;
+                cudaEventRecord(a, F->st);
+                on = true;
+            }
+        }
+    }
+    ~Prof() {
+        if (on) {
+            cudaEventRecord(F->ev_pool[start + 1], F->st);
+            F->recs.emplace_back(cat, start);
+        }
+    }
+};
+
+inline std::string fmt_e(double v) {
+    char b[32];
+    std::snprintf(b, sizeof(b), "%.3e", v);
+    return b;
+}
+
+// FP64 operator application A u on a level (ghosts of u already exchanged), defined in solver.cu.
+void apply64(mg_forest *F, DevLevel &d, const double *u, double *out);
+
 // FP64 ghost exchange of one level on a pool laid out like the level's pools (defined in solver.cu).
 void exchange_any64(mg_forest *F, DevLevel &d, double *u);
+// Device allocation owned by the forest (freed by mg_forest_destroy), zero-filled (defined in solver.cu).
+mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
+mg_status check_ready(mg_forest *F);
 }  // namespace octmg

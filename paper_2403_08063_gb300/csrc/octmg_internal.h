@@ -41,9 +41,11 @@ struct XferItem {
     int32_t src[8];  // level-l blocks: HALVE/COPY use src[0]; MERGE: child of octant (a + 2b + 4c)
 };
 
+// A block of problem p: (level, i, j, k) covers [i, i+1] x [j, j+1] x [k, k+1] / (R 2^level) of that problem's
+// unit cube.  Problems are independent forests solved together.
 struct Key {
-    int32_t lev, i, j, k;
-    bool operator==(const Key &o) const { return lev == o.lev && i == o.i && j == o.j && k == o.k; }
+    int32_t p, lev, i, j, k;
+    bool operator==(const Key &o) const { return p == o.p && lev == o.lev && i == o.i && j == o.j && k == o.k; }
 };
 
 struct HostLevel {
@@ -60,9 +62,11 @@ struct HostHierarchy {
     std::vector<HostLevel> levels;
 };
 
-// Builds the hierarchy; returns MG_OK or an error with a message.
-mg_status build_hierarchy(int32_t R, int32_t n, const std::vector<Key> &leaves, int32_t max_coarse,
-                          HostHierarchy &out, std::string &err);
+// Builds the hierarchy of n_problems independent forests sharing R and n; returns MG_OK or an error with a message.
+// Below 4^3, problems whose level still has more than max_coarse unknowns merge their deepest complete octets;
+// the others carry their blocks over unchanged.
+mg_status build_hierarchy(int32_t R, int32_t n, int32_t n_problems, const std::vector<Key> &leaves,
+                          int32_t max_coarse, HostHierarchy &out, std::string &err);
 
 // Dense inverse by Gauss-Jordan elimination with partial pivoting (row-major, in place); false if singular.
 bool invert_dense(std::vector<double> &A, int N);

@@ -37,17 +37,10 @@ mg_status upload(mg_forest *F, T **p, const std::vector<T> &v) {
     return MG_OK;
 }
 
-// Kernel families for launch counting and timing.
-enum ProfCat {
-    P_EXCH64 = 0, P_EXCH32, P_SMOOTH64, P_SMOOTH32, P_RESTR64, P_RESTR32, P_PROL64, P_PROL32, P_COARSE64,
-    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_NCAT
-};
 const char *const kProfNames[P_NCAT] = {"exchange_f64", "exchange_f32", "smooth_f64", "smooth_f32",
                                          "residual_restrict_f64", "residual_restrict_f32", "prolong_f64",
                                          "prolong_f32", "coarse_f64", "coarse_f32", "residual_f64",
                                          "update_mixed", "layout", "adjoint"};
-
-template <typename T> constexpr int cat_of(int cat64) { return sizeof(T) == 8 ? cat64 : cat64 + 1; }
 
 cudaEvent_t next_event(mg_forest *F) {
     if (F->ev_used == F->ev_pool.size()) {
@@ -58,30 +51,12 @@ cudaEvent_t next_event(mg_forest *F) {
     return F->ev_pool[F->ev_used++];
 }
 
-// RAII scope around the launches of one kernel family.
-struct Prof {
-    mg_forest *F;
-    int cat;
-    size_t start = 0;
-    bool on = false;
-    Prof(mg_forest *f, int c, int launches) : F(f), cat(c) {
-        F->nlaunch[c] += launches;
-        if (F->prof) {
-            cudaEvent_t a = next_event(F), b = next_event(F);
-            if (a && b) {
-                start = F->ev_used - 2;
-                cudaEventRecord(a, F->st);
-                on = true;
-            }
-        }
-    }
-    ~Prof() {
-        if (on) {
-            cudaEventRecord(F->ev_pool[start + 1], F->st);
-            F->recs.emplace_back(cat, start);
-        }
-    }
-};
+mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes) {
+    char *q = nullptr;
+    MG_TRY(dalloc(F, &q, bytes));
+    *p = q;
+    return MG_OK;
+}
 
 int ilog2(int n) {
     int l = 0;
@@ -252,6 +227,14 @@ mg_status assemble_coarse(mg_forest *F) {
         return MG_ERR_INVALID_ARG;
     }
     MG_CUDA(cudaMemcpyAsync(Adev, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
+    {
+        std::vector<double> At(A.size());
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) At[static_cast<size_t>(j) * N + i] = A[static_cast<size_t>(i) * N + j];
+        if (!F->AinvT) MG_TRY(dalloc(F, &F->AinvT, static_cast<int64_t>(N) * N));
+        MG_CUDA(cudaMemcpyAsync(F->AinvT, At.data(), At.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
+        MG_CUDA(cudaStreamSynchronize(F->st));
+    }
     MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
     MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
@@ -388,7 +371,7 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
     if (rel_out) *rel_out = rel;
     if (!std::isfinite(rel)) return MG_ERR_NOT_CONVERGED;
     if (rtol >= 0.0 && !(rel <= rtol)) {
-        set_error("relative residual " + std::to_string(rel) + " above rtol after " + std::to_string(done) + " cycles");
+        set_error("relative residual " + fmt_e(rel) + " above rtol after " + std::to_string(done) + " cycles");
         return MG_ERR_NOT_CONVERGED;
     }
     return MG_OK;
@@ -444,6 +427,12 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         d.nfaces = static_cast<int>(h.faces.size());
         d.nsegs = static_cast<int>(h.segs.size());
         if ((st = upload(F, &d.faces, h.faces)) != MG_OK) return fail(st);
+        {
+            std::vector<int8_t> fk(static_cast<size_t>(h.keys.size()) * 6, 0);
+            for (const FaceItem &fi : h.faces) fk[static_cast<size_t>(fi.blk) * 6 + 2 * fi.axis + fi.side] = fi.kind;
+            for (const SegItem &si : h.segs) fk[static_cast<size_t>(si.coarse) * 6 + 2 * si.axis + si.side] = 3;
+            if ((st = upload(F, &d.fkind, fk)) != MG_OK) return fail(st);
+        }
         if ((st = upload(F, &d.segs, h.segs)) != MG_OK) return fail(st);
         if (!h.to_next.empty() && (st = upload(F, &d.xfer, h.to_next)) != MG_OK) return fail(st);
         std::vector<double> h2(h.h.size()), ih2(h.h.size()), vol(h.h.size());
@@ -697,16 +686,3 @@ const char *mg_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
 
-extern "C" {
-// Placeholders until the adjoint translation unit lands; they report MG_ERR_STATE.
-mg_status mg_apply_transpose(mg_forest *F, const double *, double *) {
-    (void)F;
-    octmg::set_error("mg_apply_transpose: not available in this build");
-    return MG_ERR_STATE;
-}
-mg_status mg_adjoint_solve(mg_forest *F, const double *, const double *, double *, double *, double, int32_t) {
-    (void)F;
-    octmg::set_error("mg_adjoint_solve: not available in this build");
-    return MG_ERR_STATE;
-}
-}

@@ -149,3 +149,30 @@ def workload_forest(name: str):
     else:
         keys = balance_2to1(refine_ball(R, (0.5, 0.5, 0.5), 0.25, 2, open_ball=True), R, "26")
     return R, n, keys
+
+
+def batch_problems(count=256, seed=0, sizes=(16, 32, 64, 128), max_depth=2, box=(0.1, 0.4)):
+    """Independent single-root problems: per problem (drawn in this order) the block size n from ``sizes``, the
+    refinement depth from {0..max_depth}, box sides U(box) per axis, and the box corner uniform so the box fits;
+    blocks meeting the box are refined `depth` times, then 26-neighbour 2:1 balance.
+
+    Returns a list of (n, keys) with keys (level, i, j, k) of a forest with R = 1.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice(list(sizes)))
+        depth = int(rng.integers(0, max_depth + 1))
+        side = rng.uniform(box[0], box[1], size=3)
+        lo = rng.uniform(0.0, 1.0 - side)
+        keys = balance_2to1(refine_box(1, lo, lo + side, depth), 1, "26")
+        out.append((n, keys))
+    return out
+
+
+def batch_leaves(problems):
+    """Leaf rows (problem, level, i, j, k) of a batch, problems in order, and the per-problem block sizes."""
+    rows = []
+    for p, (_, keys) in enumerate(problems):
+        rows.extend((p, *key) for key in keys)
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 5), np.asarray([n for n, _ in problems], dtype=np.int32)
