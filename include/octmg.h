@@ -47,8 +47,9 @@ typedef struct {
     int32_t roots;            /* R: root blocks per axis; the roots are R^3 cubes of edge 1/R over [0,1]^3 (Sec. 2) */
     int32_t n;                /* cells per block edge on the finest level; power of two, >= 4 */
     int32_t n_leaves;
-    const int32_t *leaves;    /* host, 5 * n_leaves int32: (problem, level, i, j, k); problem must be 0 here.
-                                 Leaf (level, i, j, k) covers [i, i+1] x [j, j+1] x [k, k+1] / (R 2^level). */
+    const int32_t *leaves;    /* host, 5 * n_leaves int32: (problem, level, i, j, k), problem in 0..n_problems-1.
+                                 Leaf (level, i, j, k) covers [i, i+1] x [j, j+1] x [k, k+1] / (R 2^level) of its
+                                 problem's unit cube; every problem's leaves must tile its cube, 2:1 face balanced. */
     int32_t coeff;            /* 0: -Laplace(u) = f;  1: -div(k grad u) = f with per-cell k > 0 */
     int32_t interface_flux;   /* 1 (default): conservative coarse-fine faces (the coarse flux is the sum of the four
                                  fine sub-face fluxes); 0: the paper's ghost-only scheme (coarse ghost = F2C mean) */
@@ -58,6 +59,7 @@ typedef struct {
                                  unknowns (default 512 when <= 0); that level is solved by a dense FP64 inverse */
     int32_t inner_cycles;     /* precision == 1: FP32 V-cycles per FP64 defect-correction step (default 1 when <= 0;
                                  FP32 resolves about 6 digits per step, so up to ~5 cycles still pay) */
+    int32_t n_problems;       /* independent problems sharing R and n, solved together (default 1 when <= 0) */
     void *stream;             /* cudaStream_t, or NULL for the legacy default stream */
 } mg_config;
 
@@ -83,20 +85,24 @@ mg_status mg_level_keys(const mg_forest *forest, int32_t level, int32_t *keys_ho
 mg_status mg_set_rhs(mg_forest *forest, const double *f_dev, const double *k_dev);
 
 /* Run exactly ncycles V(nu1, nu2) cycles on u_dev (initial guess on entry, iterate on exit; FP64 cycles, or FP32
- * cycles inside FP64 defect correction when precision == 1).  If rel_res_out is not NULL it receives
- * ||f - A u|| / ||f|| after the last cycle (volume-weighted L2 norm sqrt(sum h^3 r^2)).  Requires mg_set_rhs. */
+ * cycles inside FP64 defect correction when precision == 1).  If rel_res_out is not NULL it receives, per problem
+ * (n_problems doubles), ||f - A u|| / ||f|| after the last cycle (volume-weighted L2 norm sqrt(sum h^3 r^2) over that
+ * problem's cells).  Requires mg_set_rhs. */
 mg_status mg_vcycle(mg_forest *forest, double *u_dev, int32_t ncycles, double *rel_res_out);
 
-/* Cycle from the initial guess in u_dev until ||f - A u|| / ||f|| <= rtol or max_cycles cycles ran.
- * cycles_out / rel_res_out (host, may be NULL) receive the cycle count and final relative residual.
- * Returns MG_ERR_NOT_CONVERGED (u_dev still holds the last iterate) when rtol is not reached. */
+/* Cycle from the initial guess in u_dev until every problem has ||f - A u|| / ||f|| <= rtol, or max_cycles cycles
+ * ran.  cycles_out / rel_res_out (host arrays of n_problems entries, may be NULL) receive per problem the number of
+ * cycles after which it first met rtol (or the total) and its final relative residual.  All problems keep cycling
+ * until the last one converges.  Returns MG_ERR_NOT_CONVERGED (u_dev still holds the last iterate) when a problem
+ * does not reach rtol. */
 mg_status mg_solve(mg_forest *forest, double *u_dev, double rtol, int32_t max_cycles, int32_t *cycles_out,
                    double *rel_res_out);
 
 /* Adjoint of the converged solve for L = 1/2 sum_i (u_i - u_t,i)^2: given u_dev (the forward solution) and
  * dLdu_dev = u - u_t, solve A^T lambda = dL/du by defect correction with the transposed V-cycle, write lambda
  * (= dL/df) to lambda_dev and, when dLdk_dev is not NULL and coeff == 1, dL/dk = -lambda^T (dA/dk) u.
- * All arrays n_leaves * n^3 doubles on the device.  Returns MG_ERR_NOT_CONVERGED if rtol is not reached. */
+ * All arrays n_leaves * n^3 doubles on the device.  With several problems, rtol applies to the norm over all of
+ * them.  Returns MG_ERR_NOT_CONVERGED if rtol is not reached. */
 mg_status mg_adjoint_solve(mg_forest *forest, const double *u_dev, const double *dLdu_dev, double *lambda_dev,
                            double *dLdk_dev, double rtol, int32_t max_cycles);
 
@@ -130,6 +136,34 @@ mg_status mg_exchange_level_noalloc(mg_forest *forest, int32_t level, const doub
 mg_status mg_profile(mg_forest *forest, int32_t enable);
 mg_status mg_profile_read(mg_forest *forest, int32_t max_families, char *names, double *ms, int64_t *launches,
                           int32_t *n_families);
+
+/* ---------------------------------------------------------------------------------------------------------------
+ * Batches: many independent problems with different block sizes (uneven octree forests), solved together.
+ * Every problem is its own forest over [0,1]^3 with cfg->roots root blocks per axis; its leaves are the rows of
+ * cfg->leaves whose problem index is p.  problem_n (host, n_problems entries, may be NULL) gives each problem's
+ * block size (NULL: cfg->n for all).  Field layout: the leaves in the order of cfg->leaves, each holding its
+ * problem's n_p^3 cells, x fastest.  Problems with the same n share one multi-problem forest; all run on an
+ * internal stream ordered after cfg->stream on entry and before it on exit.  Solves use FP32 cycles inside FP64
+ * defect correction (cfg->precision must be 1); each defect-correction step of every group is captured once in a
+ * CUDA graph and replayed.  The paper solves one forest at a time (Sec. 5); batching is this library's extension.
+ * --------------------------------------------------------------------------------------------------------------- */
+typedef struct mg_batch mg_batch;
+
+mg_status mg_batch_create(const mg_config *cfg, const int32_t *problem_n, mg_batch **out);
+void mg_batch_destroy(mg_batch *batch);
+/* f_dev, k_dev: device arrays of the batch layout (total cells doubles); k_dev NULL when cfg->coeff == 0. */
+mg_status mg_batch_set_rhs(mg_batch *batch, const double *f_dev, const double *k_dev);
+/* Cycle from the initial guess in u_dev (batch layout) until every problem has ||f - A u|| / ||f|| <= rtol.
+ * cycles_out / rel_res_out: host arrays of n_problems entries (may be NULL), as in mg_solve. */
+mg_status mg_batch_solve(mg_batch *batch, double *u_dev, double rtol, int32_t max_cycles, int32_t *cycles_out,
+                         double *rel_res_out);
+/* Number of block-size groups, total cells, and per group its block size and problem count (arrays may be NULL). */
+mg_status mg_batch_info(const mg_batch *batch, int32_t *n_groups, int64_t *total_cells, int32_t *group_n,
+                        int32_t *group_problems);
+/* Kernel accounting of every group (mg_profile); while enabled, solves launch kernels without graphs. */
+mg_status mg_batch_profile(mg_batch *batch, int32_t enable);
+/* The multi-problem forest of group g (owned by the batch), e.g. for mg_profile_read; NULL if out of range. */
+mg_forest *mg_batch_group(mg_batch *batch, int32_t g);
 
 /* Thread-local description of the last error (empty string if none). */
 const char *mg_last_error(void);

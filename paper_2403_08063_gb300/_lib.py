@@ -37,6 +37,7 @@ class MGConfig(ctypes.Structure):
         ("nu2", ctypes.c_int32),
         ("max_coarse", ctypes.c_int32),
         ("inner_cycles", ctypes.c_int32),
+        ("n_problems", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -63,6 +64,13 @@ SIGNATURES = {
     "mg_exchange_level_noalloc": (I32, [P, I32, P, P]),
     "mg_profile": (I32, [P, I32]),
     "mg_profile_read": (I32, [P, I32, _c.c_char_p, DP, _c.POINTER(_c.c_int64), IP]),
+    "mg_batch_create": (I32, [_c.POINTER(MGConfig), IP, _c.POINTER(P)]),
+    "mg_batch_destroy": (None, [P]),
+    "mg_batch_set_rhs": (I32, [P, P, P]),
+    "mg_batch_solve": (I32, [P, P, _c.c_double, I32, IP, DP]),
+    "mg_batch_info": (I32, [P, IP, _c.POINTER(_c.c_int64), IP, IP]),
+    "mg_batch_profile": (I32, [P, I32]),
+    "mg_batch_group": (P, [P, I32]),
     "mg_last_error": (_c.c_char_p, []),
 }
 

@@ -31,7 +31,7 @@ class Forest:
     """
 
     def __init__(self, R, n, leaves, coeff=False, interface_flux=True, precision=0, nu1=2, nu2=2, max_coarse=512,
-                 inner_cycles=1, stream=None):
+                 inner_cycles=1, n_problems=None, stream=None):
         self.lib = _lib.load()
         arr = np.asarray(leaves, dtype=np.int32)
         if arr.ndim == 2 and arr.shape[1] == 4:
@@ -47,6 +47,8 @@ class Forest:
         cfg.coeff, cfg.interface_flux, cfg.precision = int(coeff), int(interface_flux), int(precision)
         cfg.nu1, cfg.nu2, cfg.max_coarse = int(nu1), int(nu2), int(max_coarse)
         cfg.inner_cycles = int(inner_cycles)
+        self.n_problems = int(n_problems) if n_problems else int(self._leaves[:, 0].max()) + 1
+        cfg.n_problems = self.n_problems
         cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
         h = ctypes.c_void_p()
         _lib.check(self.lib.mg_forest_create(ctypes.byref(cfg), ctypes.byref(h)))
@@ -90,20 +92,25 @@ class Forest:
         self.version += 1
 
     def vcycle(self, u, ncycles=1):
+        """ncycles V-cycles on u in place; returns the relative residual (a list with several problems)."""
         _dev_f64(u, self.numel, "u")
-        rel = ctypes.c_double()
-        _lib.check(self.lib.mg_vcycle(self.h, _ptr(u), int(ncycles), ctypes.byref(rel)))
-        return rel.value
+        rel = (ctypes.c_double * self.n_problems)()
+        _lib.check(self.lib.mg_vcycle(self.h, _ptr(u), int(ncycles), rel))
+        return rel[0] if self.n_problems == 1 else list(rel)
 
     def solve(self, u, rtol=1e-10, max_cycles=100, raise_on_failure=True):
-        """Cycle on u (initial guess in place) until ||f - A u|| / ||f|| <= rtol.  Returns (cycles, rel)."""
+        """Cycle on u (initial guess in place) until ||f - A u|| / ||f|| <= rtol for every problem.
+
+        Returns (cycles, rel), or (list of cycles, list of rel) with several problems."""
         _dev_f64(u, self.numel, "u")
-        cyc = ctypes.c_int32()
-        rel = ctypes.c_double()
-        st = self.lib.mg_solve(self.h, _ptr(u), float(rtol), int(max_cycles), ctypes.byref(cyc), ctypes.byref(rel))
+        cyc = (ctypes.c_int32 * self.n_problems)()
+        rel = (ctypes.c_double * self.n_problems)()
+        st = self.lib.mg_solve(self.h, _ptr(u), float(rtol), int(max_cycles), cyc, rel)
         if st != 0 and (raise_on_failure or st != 6):
             _lib.check(st)
-        return cyc.value, rel.value
+        if self.n_problems == 1:
+            return cyc[0], rel[0]
+        return list(cyc), list(rel)
 
     def apply(self, u):
         _dev_f64(u, self.numel, "u")
@@ -140,18 +147,101 @@ class Forest:
 
     def profile_read(self):
         """{family: (milliseconds, launches)} of the kernel families since the last profile(True)."""
-        nf = ctypes.c_int32()
-        _lib.check(self.lib.mg_profile_read(self.h, 0, None, None, None, ctypes.byref(nf)))
-        m = nf.value
-        names = ctypes.create_string_buffer(32 * m)
-        ms = (ctypes.c_double * m)()
-        cnt = (ctypes.c_int64 * m)()
-        _lib.check(self.lib.mg_profile_read(self.h, m, names, ms, cnt, ctypes.byref(nf)))
+        return _profile_read_handle(self.lib, self.h)
+
+
+class Batch:
+    """Independent problems with per-problem block sizes solved together (wraps mg_batch_*).
+
+    leaves: (n_leaves, 5) int32 rows (problem, level, i, j, k); problem_n: block size per problem.  Fields are flat
+    float64 CUDA tensors: the leaves in order, each with its problem's n^3 cells, x fastest.
+    """
+
+    def __init__(self, leaves, problem_n, R=1, coeff=True, interface_flux=True, inner_cycles=3, nu1=2, nu2=2,
+                 max_coarse=64, stream=None):
+        self.lib = _lib.load()
+        self._leaves = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32))
+        self._pn = np.ascontiguousarray(np.asarray(problem_n, dtype=np.int32))
+        self.n_problems = int(self._pn.shape[0])
+        self.coeff = bool(coeff)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = _lib.MGConfig()
+        cfg.roots, cfg.n, cfg.n_leaves = int(R), int(self._pn[0]), int(self._leaves.shape[0])
+        cfg.leaves = self._leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        cfg.coeff, cfg.interface_flux, cfg.precision = int(coeff), int(interface_flux), 1
+        cfg.nu1, cfg.nu2, cfg.max_coarse, cfg.inner_cycles = int(nu1), int(nu2), int(max_coarse), int(inner_cycles)
+        cfg.n_problems = self.n_problems
+        cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.mg_batch_create(ctypes.byref(cfg), self._pn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            ctypes.byref(h)))
+        self.h = h
+        self.numel = int(sum(int(self._pn[p]) ** 3 for p in self._leaves[:, 0]))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.mg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        ng = ctypes.c_int32()
+        tot = ctypes.c_int64()
+        _lib.check(self.lib.mg_batch_info(self.h, ctypes.byref(ng), ctypes.byref(tot), None, None))
+        gn = (ctypes.c_int32 * ng.value)()
+        gp = (ctypes.c_int32 * ng.value)()
+        _lib.check(self.lib.mg_batch_info(self.h, ctypes.byref(ng), ctypes.byref(tot), gn, gp))
+        return {"groups": [(gn[i], gp[i]) for i in range(ng.value)], "cells": tot.value}
+
+    def set_rhs(self, f, k=None):
+        _dev_f64(f, self.numel, "f")
+        if self.coeff:
+            _dev_f64(k, self.numel, "k")
+        _lib.check(self.lib.mg_batch_set_rhs(self.h, _ptr(f), _ptr(k) if self.coeff else None))
+
+    def solve(self, u, rtol=1e-8, max_cycles=100, raise_on_failure=True):
+        """Cycle on u in place until every problem meets rtol; returns (cycles per problem, rel per problem)."""
+        _dev_f64(u, self.numel, "u")
+        cyc = (ctypes.c_int32 * self.n_problems)()
+        rel = (ctypes.c_double * self.n_problems)()
+        st = self.lib.mg_batch_solve(self.h, _ptr(u), float(rtol), int(max_cycles), cyc, rel)
+        if st != 0 and (raise_on_failure or st != 6):
+            _lib.check(st)
+        return list(cyc), list(rel)
+
+    def profile(self, enable=True):
+        _lib.check(self.lib.mg_batch_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """Per kernel family (milliseconds, launches), summed over the groups (the group forests stay owned by
+        the batch: they are read through their handles, never wrapped in a Forest that would destroy them)."""
         out = {}
-        for i in range(m):
-            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
-            out[nm] = (ms[i], int(cnt[i]))
+        for g in range(len(self.info()["groups"])):
+            fh = ctypes.c_void_p(self.lib.mg_batch_group(self.h, g))
+            for k, (ms, n) in _profile_read_handle(self.lib, fh).items():
+                a = out.get(k, (0.0, 0))
+                out[k] = (a[0] + ms, a[1] + n)
         return out
+
+
+def _profile_read_handle(lib, h):
+    nf = ctypes.c_int32()
+    _lib.check(lib.mg_profile_read(h, 0, None, None, None, ctypes.byref(nf)))
+    m = nf.value
+    names = ctypes.create_string_buffer(32 * m)
+    ms = (ctypes.c_double * m)()
+    cnt = (ctypes.c_int64 * m)()
+    _lib.check(lib.mg_profile_read(h, m, names, ms, cnt, ctypes.byref(nf)))
+    out = {}
+    for i in range(m):
+        nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+        out[nm] = (ms[i], int(cnt[i]))
+    return out
 
 
 class MGSolveFn(torch.autograd.Function):

@@ -453,8 +453,8 @@ void vcycle_T(mg_forest *F, int l) {
     const int last = static_cast<int>(F->L.size()) - 1;
     if (l == last) {
         Prof p(F, P_ADJ, 1);
-        k_coarse_solve<double><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(d.a_fb, d.a_ub, F->AinvT,
-                                                                                               F->cmap, F->Nc);
+        k_coarse_solve<double><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(
+            d.a_fb, d.a_ub, F->AinvT, F->cmap, F->uprob, F->ustart, F->moff, F->Nc);
         return;
     }
     cudaMemsetAsync(d.a_fb, 0, d.pool_elems() * sizeof(double), F->st);
@@ -481,6 +481,8 @@ void vcycle_T(mg_forest *F, int l) {
 }
 
 mg_status ensure_adjoint_pools(mg_forest *F) {
+    MG_TRY(ensure_scratch64(F));
+    MG_TRY(ensure_fp64_coefficients(F));
     if (F->a_g) return MG_OK;
     for (DevLevel &d : F->L) {
         const int64_t bytes = d.pool_elems() * static_cast<int64_t>(sizeof(double));
@@ -518,7 +520,7 @@ mg_status adjoint_solve(mg_forest *F, const double *u_dev, const double *dLdu_de
     DevLevel &d = F->L[0];
     const int grid = grid_for(d.cells());
     MG_CUDA(cudaMemsetAsync(F->a_lam, 0, d.pool_elems() * sizeof(double), F->st));
-    k_pack<double><<<grid, kThreads, 0, F->st>>>(F->a_g, dLdu_dev, d.g);
+    k_pack<double><<<grid, kThreads, 0, F->st>>>(F->a_g, dLdu_dev, d.g, F->leaf_off);
     k_norm64<<<grid, kThreads, 0, F->st>>>(F->a_g, d.vol_64, d.g, F->partial);
     double gg = 0.0;
     MG_TRY(read_sum(F, grid, &gg));
@@ -535,12 +537,12 @@ mg_status adjoint_solve(mg_forest *F, const double *u_dev, const double *dLdu_de
         vcycle_T<MODE>(F, 0);
         k_axpy<<<grid, kThreads, 0, F->st>>>(F->a_lam, d.a_fb, 1.0, d.g);
     }
-    k_unpack<double><<<grid, kThreads, 0, F->st>>>(lambda_dev, F->a_lam, d.g);
+    k_unpack<double><<<grid, kThreads, 0, F->st>>>(lambda_dev, F->a_lam, d.g, F->leaf_off);
     MG_CUDA(cudaGetLastError());
     if (dLdk_dev && F->cfg.coeff) {
         // forward ghosts of u, then the face terms, the ghost-k maps and (conservative variant) the coarse rows
         MG_CUDA(cudaMemsetAsync(F->s64a, 0, d.pool_elems() * sizeof(double), F->st));
-        k_pack<double><<<grid, kThreads, 0, F->st>>>(F->s64a, u_dev, d.g);
+        k_pack<double><<<grid, kThreads, 0, F->st>>>(F->s64a, u_dev, d.g, F->leaf_off);
         exchange_any64(F, d, F->s64a);
         MG_CUDA(cudaMemsetAsync(F->s64b, 0, d.pool_elems() * sizeof(double), F->st));
         MG_CUDA(cudaMemsetAsync(d.a_tmp, 0, d.pool_elems() * sizeof(double), F->st));
@@ -558,7 +560,7 @@ mg_status adjoint_solve(mg_forest *F, const double *u_dev, const double *dLdu_de
             else
                 k_gradk_ghost_segs<<<gs, kThreads, 0, F->st>>>(F->s64b, d.a_tmp, d.segs, d.nsegs, d.g);
         }
-        k_unpack<double><<<grid, kThreads, 0, F->st>>>(dLdk_dev, F->s64b, d.g);
+        k_unpack<double><<<grid, kThreads, 0, F->st>>>(dLdk_dev, F->s64b, d.g, F->leaf_off);
     }
     MG_CUDA(cudaStreamSynchronize(F->st));
     if (!std::isfinite(rel) || rel > rtol) {
@@ -586,12 +588,12 @@ extern "C" mg_status mg_apply_transpose(mg_forest *F, const double *y_dev, doubl
     MG_TRY(ensure_adjoint_pools(F));
     DevLevel &d = F->L[0];
     MG_CUDA(cudaMemsetAsync(d.a_z, 0, d.pool_elems() * sizeof(double), F->st));
-    k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.a_z, y_dev, d.g);
+    k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.a_z, y_dev, d.g, F->leaf_off);
     if (F->cfg.coeff)
         apply_T<1>(F, d, d.a_z, d.a_tmp);
     else
         apply_T<0>(F, d, d.a_z, d.a_tmp);
-    k_unpack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(ATy_dev, d.a_tmp, d.g);
+    k_unpack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(ATy_dev, d.a_tmp, d.g, F->leaf_off);
     MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
 }

@@ -1,0 +1,347 @@
+// Batches of independent problems with different block sizes (many uneven octree forests solved together).
+//
+// Problems sharing a block size n live in one multi-problem forest (its blocks carry a problem id; neighbours,
+// octet merging, norms and the block-diagonal coarsest inverse are per problem).  The batch owns one such forest
+// per distinct n, all on one stream, reading and writing the caller's arrays in place through per-leaf offsets.
+// With FP32 cycles, one defect-correction step of every group (m FP32 V-cycles, the FP64 update, the next FP64
+// residual and its per-problem norms) is captured once in a CUDA graph and replayed until every problem meets rtol.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "forest_state.h"
+
+struct mg_batch {
+    mg_config cfg{};
+    cudaStream_t user = nullptr;  // caller's stream (may be the legacy default stream)
+    cudaStream_t st = nullptr;    // batch stream (non-blocking; graphs are captured on it)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int np = 0;
+    int64_t total_cells = 0;
+    std::vector<mg_forest *> groups;
+    std::vector<int32_t> gn;                  // block size per group
+    std::vector<std::vector<int32_t>> gprob;  // batch problem ids per group (local id = position)
+    int *flag = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_m = 0;
+    bool rhs_set = false;
+};
+
+namespace octmg {
+namespace {
+
+__global__ void k_check_batch(const double *__restrict__ f, const double *__restrict__ k, int64_t n,
+                              int *__restrict__ bad) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (!isfinite(f[i])) atomicOr(bad, 1);
+        if (k && !(isfinite(k[i]) && k[i] > 0.0)) atomicOr(bad, 2);
+    }
+}
+
+void destroy_batch(mg_batch *B) {
+    if (!B) return;
+    if (B->st) cudaStreamSynchronize(B->st);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    for (mg_forest *F : B->groups) mg_forest_destroy(F);
+    if (B->flag) cudaFree(B->flag);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
+    if (B->st) cudaStreamDestroy(B->st);
+    delete B;
+}
+
+// Order the batch stream after the caller's stream on entry, and the caller's after the batch's on exit.
+mg_status enter(mg_batch *B) {
+    MG_CUDA(cudaEventRecord(B->ev_in, B->user));
+    MG_CUDA(cudaStreamWaitEvent(B->st, B->ev_in, 0));
+    return MG_OK;
+}
+mg_status leave(mg_batch *B) {
+    MG_CUDA(cudaEventRecord(B->ev_out, B->st));
+    MG_CUDA(cudaStreamWaitEvent(B->user, B->ev_out, 0));
+    return MG_OK;
+}
+
+// One FP32 defect-correction step of every group with unconverged problems is enqueued (no synchronisation).
+mg_status enqueue_step(mg_batch *B, int m) {
+    for (mg_forest *F : B->groups) {
+        MG_TRY(enqueue_fp32_step(F, m));
+        MG_TRY(enqueue_scales(F));
+        MG_TRY(enqueue_residual(F));
+        MG_TRY(enqueue_problem_sums(F));
+    }
+    return MG_OK;
+}
+
+bool profiling(const mg_batch *B) {
+    for (const mg_forest *F : B->groups)
+        if (F->prof) return true;
+    return false;
+}
+
+mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, int32_t *cycles_out,
+                      double *rel_out) {
+    if (!B->rhs_set) {
+        set_error("mg_batch_set_rhs has not been called");
+        return MG_ERR_STATE;
+    }
+    if (B->cfg.precision != 1) {
+        set_error("batched solves run FP32 cycles inside FP64 defect correction (precision = 1)");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_TRY(enter(B));
+    const size_t G = B->groups.size();
+    std::vector<std::vector<double>> fn(G), mult(G), rel(G), rr(G);
+    std::vector<std::vector<int32_t>> met(G);
+    for (size_t g = 0; g < G; ++g) {
+        mg_forest *F = B->groups[g];
+        DevLevel &d = F->L[0];
+        k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, u_dev, d.g, F->leaf_off);
+        fn[g].resize(F->np);
+        mult[g].resize(F->np);
+        rel[g].assign(F->np, -1.0);
+        rr[g].assign(F->np, 0.0);
+        met[g].assign(F->np, -1);
+        for (int p = 0; p < F->np; ++p) {
+            fn[g][p] = F->fnorm_p[p] > 0.0 ? F->fnorm_p[p] : 1.0;
+            mult[g][p] = pow2_near(1.0 / fn[g][p]);
+        }
+        set_scales_host(F, mult[g]);
+        MG_TRY(enqueue_scales(F));
+        MG_TRY(enqueue_residual(F));
+        MG_TRY(enqueue_problem_sums(F));
+    }
+    int done = 0;
+    bool all = false, finite = true;
+    const int inner = std::max(1, B->cfg.inner_cycles);
+    for (;;) {
+        MG_CUDA(cudaStreamSynchronize(B->st));
+        all = true;
+        for (size_t g = 0; g < G; ++g) {
+            mg_forest *F = B->groups[g];
+            for (int p = 0; p < F->np; ++p) {
+                rr[g][p] = F->psum_h[p] / (mult[g][p] * mult[g][p]);
+                rel[g][p] = std::sqrt(rr[g][p]) / fn[g][p];
+                if (!std::isfinite(rel[g][p])) finite = false;
+                if (rel[g][p] <= rtol && met[g][p] < 0) met[g][p] = done;
+                if (!(rel[g][p] <= rtol)) all = false;
+            }
+        }
+        if (all || !finite || done >= max_cycles) break;
+        const int m = std::min(inner, max_cycles - done);
+        // scales of the next residual; the update of this step still uses the previous ones (device pinv)
+        for (size_t g = 0; g < G; ++g) {
+            for (int p = 0; p < B->groups[g]->np; ++p) mult[g][p] = pow2_near(1.0 / std::sqrt(rr[g][p]));
+        }
+        // the update reads pinv on the device before the captured copies overwrite it: keep host copies of the
+        // new scales until the step is enqueued
+        if (m == inner && !profiling(B)) {
+            if (!B->graph || B->graph_m != m) {
+                if (B->graph) cudaGraphExecDestroy(B->graph);
+                B->graph = nullptr;
+                cudaGraph_t graph = nullptr;
+                MG_CUDA(cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal));
+                mg_status es = enqueue_step(B, m);
+                cudaError_t ce = cudaStreamEndCapture(B->st, &graph);
+                if (es != MG_OK) return es;
+                if (ce != cudaSuccess) {
+                    set_error(std::string("graph capture: ") + cudaGetErrorString(ce));
+                    return MG_ERR_CUDA;
+                }
+                ce = cudaGraphInstantiate(&B->graph, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ce != cudaSuccess) {
+                    set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce));
+                    return MG_ERR_CUDA;
+                }
+                B->graph_m = m;
+            }
+            for (size_t g = 0; g < G; ++g) set_scales_host(B->groups[g], mult[g]);
+            MG_CUDA(cudaGraphLaunch(B->graph, B->st));
+        } else {
+            for (size_t g = 0; g < G; ++g) set_scales_host(B->groups[g], mult[g]);
+            MG_TRY(enqueue_step(B, m));
+        }
+        done += m;
+    }
+    for (size_t g = 0; g < G; ++g) {
+        mg_forest *F = B->groups[g];
+        DevLevel &d = F->L[0];
+        k_unpack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(u_dev, d.u64, d.g, F->leaf_off);
+        for (int p = 0; p < F->np; ++p) {
+            const int32_t bp = B->gprob[g][p];
+            if (cycles_out) cycles_out[bp] = met[g][p] >= 0 ? met[g][p] : done;
+            if (rel_out) rel_out[bp] = rel[g][p];
+        }
+    }
+    MG_CUDA(cudaGetLastError());
+    MG_TRY(leave(B));
+    MG_CUDA(cudaStreamSynchronize(B->st));
+    if (!finite) {
+        set_error("residual is not finite");
+        return MG_ERR_NOT_CONVERGED;
+    }
+    if (!all) {
+        set_error("some problems did not reach rtol within " + std::to_string(done) + " cycles");
+        return MG_ERR_NOT_CONVERGED;
+    }
+    return MG_OK;
+}
+
+}  // namespace
+}  // namespace octmg
+
+using namespace octmg;
+
+extern "C" {
+
+mg_status mg_batch_create(const mg_config *cfg, const int32_t *problem_n, mg_batch **out) {
+    if (out) *out = nullptr;
+    if (!cfg || !out || !cfg->leaves || cfg->n_leaves <= 0) {
+        set_error("null config, output or leaves");
+        return MG_ERR_INVALID_ARG;
+    }
+    const int np = std::max(1, cfg->n_problems);
+    std::vector<int32_t> pn(np, cfg->n);
+    if (problem_n)
+        for (int p = 0; p < np; ++p) pn[p] = problem_n[p];
+    for (int p = 0; p < np; ++p)
+        if (pn[p] < 4 || (pn[p] & (pn[p] - 1)) != 0 || pn[p] > 1024) {
+            set_error("problem " + std::to_string(p) + ": block size must be a power of two in 4..1024");
+            return MG_ERR_BLOCK_SIZE;
+        }
+    mg_batch *B = new (std::nothrow) mg_batch();
+    if (!B) return MG_ERR_OOM;
+    B->cfg = *cfg;
+    B->cfg.leaves = nullptr;
+    B->np = np;
+    B->user = static_cast<cudaStream_t>(cfg->stream);
+    auto fail = [&](mg_status s) {
+        destroy_batch(B);
+        return s;
+    };
+    if (cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&B->flag, sizeof(int)) != cudaSuccess) {
+        set_error("batch stream / event / flag allocation failed");
+        return fail(MG_ERR_CUDA);
+    }
+    // leaf offsets in the caller's layout (leaves in order, each n_p^3 cells), groups by block size
+    std::vector<int64_t> off(cfg->n_leaves);
+    int64_t run = 0;
+    for (int i = 0; i < cfg->n_leaves; ++i) {
+        const int32_t p = cfg->leaves[5 * static_cast<int64_t>(i)];
+        if (p < 0 || p >= np) {
+            set_error("leaf problem index outside 0..n_problems-1");
+            return fail(MG_ERR_INVALID_ARG);
+        }
+        off[i] = run;
+        run += static_cast<int64_t>(pn[p]) * pn[p] * pn[p];
+    }
+    B->total_cells = run;
+    std::map<int32_t, std::vector<int32_t>> byn;
+    for (int p = 0; p < np; ++p) byn[pn[p]].push_back(p);
+    for (auto &kv : byn) {
+        std::vector<int32_t> local(np, -1);
+        for (size_t q = 0; q < kv.second.size(); ++q) local[kv.second[q]] = static_cast<int32_t>(q);
+        std::vector<int32_t> rows;
+        std::vector<int64_t> goff;
+        for (int i = 0; i < cfg->n_leaves; ++i) {
+            const int32_t *r = cfg->leaves + 5 * static_cast<int64_t>(i);
+            if (local[r[0]] < 0) continue;
+            rows.insert(rows.end(), {local[r[0]], r[1], r[2], r[3], r[4]});
+            goff.push_back(off[i]);
+        }
+        mg_config gc = *cfg;
+        gc.n = kv.first;
+        gc.n_leaves = static_cast<int32_t>(goff.size());
+        gc.leaves = rows.data();
+        gc.n_problems = static_cast<int32_t>(kv.second.size());
+        gc.stream = B->st;
+        mg_forest *F = nullptr;
+        mg_status st = create(&gc, &F);
+        if (st != MG_OK) return fail(st);
+        B->groups.push_back(F);
+        B->gn.push_back(kv.first);
+        B->gprob.push_back(kv.second);
+        F->batch_member = true;
+        void *p = nullptr;
+        if ((st = forest_alloc(F, &p, static_cast<int64_t>(goff.size() * sizeof(int64_t)))) != MG_OK) return fail(st);
+        F->leaf_off = static_cast<int64_t *>(p);
+        // same stream as the zero-fill of the allocation, then wait: the host vector dies at the end of the loop
+        if (cudaMemcpyAsync(F->leaf_off, goff.data(), goff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, B->st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(B->st) != cudaSuccess) {
+            set_error("leaf offset upload failed");
+            return fail(MG_ERR_CUDA);
+        }
+    }
+    *out = B;
+    return MG_OK;
+}
+
+void mg_batch_destroy(mg_batch *B) { destroy_batch(B); }
+
+mg_status mg_batch_set_rhs(mg_batch *B, const double *f_dev, const double *k_dev) {
+    if (!B || !f_dev || (B->cfg.coeff && !k_dev)) {
+        set_error("null batch, f, or k for a coefficient problem");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_TRY(enter(B));
+    MG_CUDA(cudaMemsetAsync(B->flag, 0, sizeof(int), B->st));
+    k_check_batch<<<grid_for(B->total_cells), kThreads, 0, B->st>>>(f_dev, B->cfg.coeff ? k_dev : nullptr,
+                                                                   B->total_cells, B->flag);
+    int hbad = 0;
+    MG_CUDA(cudaMemcpyAsync(&hbad, B->flag, sizeof(int), cudaMemcpyDeviceToHost, B->st));
+    MG_CUDA(cudaStreamSynchronize(B->st));
+    if (hbad) {
+        set_error(hbad & 2 ? "k must be finite and > 0" : "f has a non-finite entry");
+        return MG_ERR_NONFINITE;
+    }
+    for (mg_forest *F : B->groups) MG_TRY(set_rhs(F, f_dev, k_dev));
+    B->rhs_set = true;
+    MG_TRY(leave(B));
+    return MG_OK;
+}
+
+mg_status mg_batch_solve(mg_batch *B, double *u_dev, double rtol, int32_t max_cycles, int32_t *cycles_out,
+                         double *rel_res_out) {
+    if (!B || !u_dev || max_cycles < 0 || !(rtol >= 0.0)) {
+        set_error("bad argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    return batch_solve(B, u_dev, rtol, max_cycles, cycles_out, rel_res_out);
+}
+
+mg_status mg_batch_info(const mg_batch *B, int32_t *n_groups, int64_t *total_cells, int32_t *group_n,
+                        int32_t *group_problems) {
+    if (!B || !n_groups) {
+        set_error("null argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    *n_groups = static_cast<int32_t>(B->groups.size());
+    if (total_cells) *total_cells = B->total_cells;
+    for (size_t g = 0; g < B->groups.size(); ++g) {
+        if (group_n) group_n[g] = B->gn[g];
+        if (group_problems) group_problems[g] = static_cast<int32_t>(B->gprob[g].size());
+    }
+    return MG_OK;
+}
+
+mg_status mg_batch_profile(mg_batch *B, int32_t enable) {
+    if (!B) {
+        set_error("null batch");
+        return MG_ERR_INVALID_ARG;
+    }
+    for (mg_forest *F : B->groups) MG_TRY(mg_profile(F, enable));
+    return MG_OK;
+}
+
+mg_forest *mg_batch_group(mg_batch *B, int32_t g) {
+    if (!B || g < 0 || g >= static_cast<int32_t>(B->groups.size())) return nullptr;
+    return B->groups[g];
+}
+
+}  // extern "C"

@@ -48,6 +48,10 @@ struct DevLevel {
     float *u32 = nullptr, *f32 = nullptr;
     double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dg = nullptr, *dinv = nullptr;
     float *kap = nullptr;
+    int32_t *bprob = nullptr;  // problem of each block
+    int32_t *nbr6 = nullptr;   // per block face: same-level neighbour, -1 boundary, -2 refinement interface
+    FaceItem *ifaces = nullptr;  // the C2F faces alone (interface-only exchange)
+    int nifaces = 0;
     int8_t *fkind = nullptr;   // per block face (b * 6 + 2 * axis + side): 0 boundary, 1 same, 2 C2F, 3 F2C
     // adjoint work pools (allocated by the first adjoint call)
     double *a_ub = nullptr, *a_fb = nullptr, *a_z = nullptr, *a_tmp = nullptr;
@@ -74,7 +78,20 @@ struct mg_forest {
     double *s64a = nullptr, *s64b = nullptr;  // level-0 FP64 scratch pools
     double *coarse_r = nullptr;               // coarsest-level scratch pool (operator assembly)
     int *flag = nullptr;                      // input-check flag
-    double *AinvT = nullptr;                  // transpose of the coarsest inverse (adjoint cycles)
+    double *AinvT = nullptr;                  // transpose of the coarsest inverses (adjoint cycles)
+    // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse
+    int np = 1;
+    int32_t *pstart = nullptr, *pblk = nullptr;  // level-0 blocks of problem p: pblk[pstart[p] .. pstart[p+1])
+    double *bsum = nullptr;                      // per level-0 block sums of h^3 x^2
+    double *psum = nullptr, *psum_h = nullptr;   // per-problem sums (device, pinned host)
+    float *pscale = nullptr, *pscale_h = nullptr;  // per-problem power-of-two residual scale (device, pinned host)
+    double *pinv = nullptr, *pinv_h = nullptr;     // its inverse in FP64
+    int32_t *uprob = nullptr;                    // coarsest unknown -> problem
+    int64_t *ustart = nullptr, *moff = nullptr;  // coarsest unknowns / inverse offsets per problem
+    std::vector<int64_t> ustart_h, moff_h;
+    std::vector<double> fnorm_p;                 // ||f|| per problem
+    int64_t *leaf_off = nullptr;                 // optional: start of every leaf in the user arrays (elements)
+    bool batch_member = false;                   // inputs are checked by the owning batch
     double *a_g = nullptr, *a_lam = nullptr;  // adjoint right-hand side and solution (level 0)
     bool rhs_set = false;
     double fnorm = 0.0;
@@ -136,4 +153,15 @@ void exchange_any64(mg_forest *F, DevLevel &d, double *u);
 // Device allocation owned by the forest (freed by mg_forest_destroy), zero-filled (defined in solver.cu).
 mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
 mg_status check_ready(mg_forest *F);
+mg_status ensure_scratch64(mg_forest *F);
+mg_status create(const mg_config *cfg, mg_forest **out);
+mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev);
+double pow2_near(double x);
+void set_scales_host(mg_forest *F, const std::vector<double> &mult);
+mg_status enqueue_scales(mg_forest *F);
+mg_status enqueue_residual(mg_forest *F);   // FP64 residual -> FP32 scaled rhs, zeroed correction, per-block sums
+mg_status enqueue_problem_sums(mg_forest *F);  // per-problem sums -> pinned psum_h (no synchronisation)
+mg_status enqueue_fp32_step(mg_forest *F, int cycles);  // `cycles` FP32 V-cycles and the FP64 update
+
+mg_status ensure_fp64_coefficients(mg_forest *F);
 }  // namespace octmg

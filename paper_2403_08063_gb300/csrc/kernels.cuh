@@ -269,9 +269,15 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
 // over every block of the level, ghosts as left by the last exchange.  One thread per updated cell.
 // h2 is h^2 per block in the field's precision (unused in MODE 1, whose coefficients carry 1/h^2).
 // ------------------------------------------------------------------------------------------------------------
+// nbr6 (optional): per block face (b * 6 + 2 * axis + side) the same-level neighbour block, -1 on the domain
+// boundary, -2 on a refinement interface.  When given, every updated cell on a block face also writes its new value
+// into the neighbour's ghost cell that mirrors it (or the reflected -u into its own boundary ghost), so same-level and
+// boundary ghosts stay current without an exchange launch; interface ghosts are left to the exchange kernels.  The
+// ghost cells written have the colour being updated, which no cell of this half-sweep reads (its neighbours all
+// have the other colour), so the writes cannot race with the reads.
 template <typename T, int MODE>
-static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2, LevelGeom g,
-                         int colour) {
+static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2,
+                                LevelGeom g, int colour, const int32_t *__restrict__ nbr6) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg - 1);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -282,14 +288,32 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
         const int64_t b = t >> (3 * lg - 1);
         const int x = 2 * m + ((y + z + colour) & 1);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
+        T val;
         if constexpr (MODE == 1) {
-            u[gi] = sten1(u, cf, gi, P, f[gi]) * cf.dinv[gi];
+            val = sten1(u, cf, gi, P, f[gi]) * cf.dinv[gi];
         } else if constexpr (MODE == 0) {
-            u[gi] = fma(h2[b], f[gi], sten0<T>(u, gi, P)) * T(1.0 / 6.0);
+            val = fma(h2[b], f[gi], sten0<T>(u, gi, P)) * T(1.0 / 6.0);
         } else {
             float S, D;
             sten2(reinterpret_cast<const float *>(u), cf.kap, gi, P, S, D);
-            u[gi] = T(fmaf(float(h2[b]), float(f[gi]), S) * frcp(D));
+            val = T(fmaf(float(h2[b]), float(f[gi]), S) * frcp(D));
+        }
+        u[gi] = val;
+        if (nbr6 && (x == 0 || x == n - 1 || y == 0 || y == n - 1 || z == 0 || z == n - 1)) {
+            const int c[3] = {x, y, z};
+#pragma unroll
+            for (int axis = 0; axis < 3; ++axis) {
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    if (c[axis] != (side ? n - 1 : 0)) continue;
+                    const int nb = nbr6[b * 6 + 2 * axis + side];
+                    const int i1 = axis == 0 ? y : x, i2 = axis == 2 ? y : z;
+                    if (nb >= 0)
+                        u[static_cast<int64_t>(nb) * g.bs + face_off(axis, 1 - side, 0, i1, i2, n, P)] = val;
+                    else if (nb == -1)
+                        u[b * g.bs + face_off(axis, side, 0, i1, i2, n, P)] = -val;
+                }
+            }
         }
     }
 }
@@ -444,52 +468,59 @@ static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__re
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Coarsest level: u = A_c^{-1} f with the dense FP64 inverse (one warp per unknown; f gathered from the padded
-// pool through cmap, the padded offset of every unknown).
+// Coarsest level: u = A_c^{-1} f with the dense FP64 inverse of every problem (block-diagonal: the unknowns of
+// problem p are cmap[ustart[p] .. ustart[p+1]), its inverse is the row-major N_p x N_p matrix at Ainv + moff[p]).
+// One warp per unknown; f gathered from the padded pool through cmap.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
 static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const double *__restrict__ Ainv,
-                               const int64_t *__restrict__ cmap, int N) {
+                                      const int64_t *__restrict__ cmap, const int32_t *__restrict__ uprob,
+                                      const int64_t *__restrict__ ustart, const int64_t *__restrict__ moff, int N) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
-    const double *row = Ainv + static_cast<int64_t>(warp) * N;
+    const int p = uprob[warp];
+    const int64_t base = ustart[p];
+    const int Np = static_cast<int>(ustart[p + 1] - base);
+    const double *row = Ainv + moff[p] + static_cast<int64_t>(warp - base) * Np;
     double s = 0.0;
-    for (int j = lane; j < N; j += 32) s = fma(row[j], static_cast<double>(f[cmap[j]]), s);
+    for (int j = lane; j < Np; j += 32) s = fma(row[j], static_cast<double>(f[cmap[base + j]]), s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) u[cmap[warp]] = T(s);
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// FP64 residual over the finest level, r = f - A u, written as FP32 r * scale (scale a power of two, so the
-// scaling is exact), with the FP32 correction field zeroed, and per-CTA partial sums of h^3 (r * scale)^2.
-// The squared norm is accumulated in FP32 per thread (it only decides convergence and is reported to ~1e-6
-// relative) and in FP64 across threads.  out / zero_out may be null (convergence check of FP64 cycles).
+// FP64 residual over the finest level, r = f - A u, written as FP32 r * scale_p (scale_p a power of two per
+// problem, so the scaling is exact), with the FP32 correction field zeroed, and per-block sums of h^3 (r scale_p)^2.
+// Grid: nb * cpb CTAs, CTA (b, c) covers the c-th of cpb contiguous chunks of block b, so each CTA adds one value
+// to its block's sum.  The squared norm is accumulated in FP32 per thread (it decides convergence and is reported
+// to ~1e-6 relative) and in FP64 across threads.  out / zero_out may be null.
 // ------------------------------------------------------------------------------------------------------------
 template <int MODE>
 static __global__ void k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
-                                const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
-                                float *__restrict__ out, float scale, double *__restrict__ partial,
-                                float *__restrict__ zero_out) {
+                                       const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
+                                       int cpb, float *__restrict__ out, const float *__restrict__ pscale,
+                                       const int32_t *__restrict__ bprob, double *__restrict__ bsum,
+                                       float *__restrict__ zero_out) {
     const int lg = g.lg, n = g.n, P = g.P;
-    const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+    const int64_t b = blockIdx.x / cpb;
+    const int chunk = blockIdx.x - static_cast<int>(b * cpb);
+    const int per = (1 << (3 * lg)) / cpb;
+    const float scale = pscale[bprob[b]];
+    const double ihb = MODE == 1 ? 0.0 : ih2[b];
     float acc = 0.0f;
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t & (n - 1));
-        const int y = static_cast<int>((t >> lg) & (n - 1));
-        const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
-        const int64_t b = t >> (3 * lg);
+    for (int c = chunk * per + threadIdx.x; c < (chunk + 1) * per; c += blockDim.x) {
+        const int x = c & (n - 1), y = (c >> lg) & (n - 1), z = c >> (2 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
-        const double r = residual_at<double, MODE>(u, f, cf, gi, P, MODE == 1 ? 0.0 : ih2[b]);
+        const double r = residual_at<double, MODE>(u, f, cf, gi, P, ihb);
         const float rs = static_cast<float>(r) * scale;
         if (out) out[gi] = rs;
         if (zero_out) zero_out[gi] = 0.0f;
-        acc = fmaf(vol[b] * rs, rs, acc);
+        acc = fmaf(rs, rs, acc);
     }
     __shared__ double sm[kThreads / 32];
-    double a = acc;
+    double a = static_cast<double>(acc) * vol[b];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
@@ -497,8 +528,44 @@ static __global__ void k_residual_norm(const double *__restrict__ u, const doubl
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) s += sm[w];
-        partial[blockIdx.x] = s;
+        atomicAdd(&bsum[b], s);
     }
+}
+
+// Per-block sums of h^3 x^2 over the interior of an FP64 field (same grid shape as k_residual_norm).
+static __global__ void k_block_norm64(const double *__restrict__ x, const double *__restrict__ vol, LevelGeom g,
+                                      int cpb, double *__restrict__ bsum) {
+    const int lg = g.lg, n = g.n, P = g.P;
+    const int64_t b = blockIdx.x / cpb;
+    const int chunk = blockIdx.x - static_cast<int>(b * cpb);
+    const int per = (1 << (3 * lg)) / cpb;
+    double acc = 0.0;
+    for (int c = chunk * per + threadIdx.x; c < (chunk + 1) * per; c += blockDim.x) {
+        const int xx = c & (n - 1), y = (c >> lg) & (n - 1), z = c >> (2 * lg);
+        const double v = x[b * g.bs + off3(xx + 1, y + 1, z + 1, P)];
+        acc = fma(v, v, acc);
+    }
+    __shared__ double sm[kThreads / 32];
+    acc *= vol[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sm[w];
+        atomicAdd(&bsum[b], s);
+    }
+}
+
+// Per-problem sums of the per-block sums, blocks of problem p listed in pblk[pstart[p] .. pstart[p+1]).
+static __global__ void k_problem_sums(const double *__restrict__ bsum, const int32_t *__restrict__ pstart,
+                                      const int32_t *__restrict__ pblk, int np, double *__restrict__ psum) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    double s = 0.0;
+    for (int i = pstart[p]; i < pstart[p + 1]; ++i) s += bsum[pblk[i]];
+    psum[p] = s;
 }
 
 // A u over a whole level in FP64 (operator application; ghosts already exchanged).
@@ -563,8 +630,10 @@ static __global__ void k_sum_partials(const double *__restrict__ partial, int np
 // Layout moves and small updates.
 // ------------------------------------------------------------------------------------------------------------
 // user layout (n_leaves, n^3) FP64 <-> padded pool of type T (interior only)
+// Leaf b of the user array starts at element off[b] (or b * n^3 when off is null).
 template <typename T>
-static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ user, LevelGeom g) {
+static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ user, LevelGeom g,
+                              const int64_t *__restrict__ off = nullptr) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -573,12 +642,14 @@ static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ u
         const int y = static_cast<int>((t >> lg) & (n - 1));
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
-        pool[b * g.bs + off3(x + 1, y + 1, z + 1, g.P)] = T(user[t]);
+        const int64_t src = off ? off[b] + (t & ((int64_t(1) << (3 * lg)) - 1)) : t;
+        pool[b * g.bs + off3(x + 1, y + 1, z + 1, g.P)] = T(user[src]);
     }
 }
 
 template <typename T>
-static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__ pool, LevelGeom g) {
+static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__ pool, LevelGeom g,
+                                const int64_t *__restrict__ off = nullptr) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -587,12 +658,15 @@ static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__
         const int y = static_cast<int>((t >> lg) & (n - 1));
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
-        user[t] = static_cast<double>(pool[b * g.bs + off3(x + 1, y + 1, z + 1, g.P)]);
+        const int64_t dst = off ? off[b] + (t & ((int64_t(1) << (3 * lg)) - 1)) : t;
+        user[dst] = static_cast<double>(pool[b * g.bs + off3(x + 1, y + 1, z + 1, g.P)]);
     }
 }
 
-// u64 += s * e32 over the interior (mixed-precision defect correction update)
-static __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__ e, double s, LevelGeom g) {
+// u64 += e32 / scale_p over the interior (mixed-precision defect correction update; pinv = 1 / scale_p per problem)
+static __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__ e,
+                                      const double *__restrict__ pinv, const int32_t *__restrict__ bprob,
+                                      LevelGeom g) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -602,7 +676,7 @@ static __global__ void k_update_mixed(double *__restrict__ u, const float *__res
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, g.P);
-        u[gi] = fma(s, static_cast<double>(e[gi]), u[gi]);
+        u[gi] = fma(pinv[bprob[b]], static_cast<double>(e[gi]), u[gi]);
     }
 }
 
@@ -624,9 +698,9 @@ static __global__ void k_face_coefs(const double *__restrict__ k, const double *
         const double kc = k[gi], s = ih2[b];
         const bool inY = Y >= 1 && Y <= n, inZ = Z >= 1 && Z <= n, inX = X >= 1 && X <= n;
         const auto harm = [](double a, double c) { return 2.0 * a * c / (a + c); };
-        if (X >= 1 && inY && inZ) tx[gi] = harm(k[gi - 1], kc) * s;
-        if (Y >= 1 && inX && inZ) ty[gi] = harm(k[gi - P], kc) * s;
-        if (Z >= 1 && inX && inY) tz[gi] = harm(k[gi - static_cast<int64_t>(P) * P], kc) * s;
+        if (tx && X >= 1 && inY && inZ) tx[gi] = harm(k[gi - 1], kc) * s;
+        if (ty && Y >= 1 && inX && inZ) ty[gi] = harm(k[gi - P], kc) * s;
+        if (tz && Z >= 1 && inX && inY) tz[gi] = harm(k[gi - static_cast<int64_t>(P) * P], kc) * s;
         const bool face_or_interior = (inX && inY) || (inX && inZ) || (inY && inZ);
         if (kap && face_or_interior && kc > 0.0) kap[gi] = static_cast<float>(1.0 / kc);
     }
@@ -647,20 +721,28 @@ static __global__ void k_diag(const double *__restrict__ tx, const double *__res
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
         const double D = ((tx[gi] + tx[gi + 1]) + (ty[gi] + ty[gi + P])) + (tz[gi] + tz[gi + PP]);
         dg[gi] = D;
-        dinv[gi] = 1.0 / D;
+        if (dinv) dinv[gi] = 1.0 / D;
     }
 }
 
 }  // namespace octmg
 
 namespace octmg {
-static __global__ void k_set_unit(double *__restrict__ u, const int64_t *__restrict__ cmap, int m) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) u[cmap[m]] = 1.0;
+// Unit entry m of every problem with more than m coarsest unknowns.
+static __global__ void k_set_units(double *__restrict__ u, const int64_t *__restrict__ cmap,
+                                   const int64_t *__restrict__ ustart, int np, int m) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np && ustart[p] + m < ustart[p + 1]) u[cmap[ustart[p] + m]] = 1.0;
 }
-// A[i, m] = (A e_m)[cmap[i]]: column m of the operator from its application to a unit vector
-static __global__ void k_gather_column(const double *__restrict__ r, const int64_t *__restrict__ cmap, int N,
-                                double *__restrict__ A, int m) {
+// Column m of every problem's block: A_p[i, m] = (A e_m)[cmap[ustart[p] + i]].
+static __global__ void k_gather_columns(const double *__restrict__ r, const int64_t *__restrict__ cmap,
+                                        const int32_t *__restrict__ uprob, const int64_t *__restrict__ ustart,
+                                        const int64_t *__restrict__ moff, int N, double *__restrict__ A, int m) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) A[static_cast<int64_t>(i) * N + m] = r[cmap[i]];
+    if (i >= N) return;
+    const int p = uprob[i];
+    const int64_t base = ustart[p];
+    const int64_t Np = ustart[p + 1] - base;
+    if (m < Np) A[moff[p] + (i - base) * Np + m] = r[cmap[i]];
 }
 }  // namespace octmg

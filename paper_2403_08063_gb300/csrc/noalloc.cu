@@ -55,6 +55,7 @@ extern "C" mg_status mg_exchange_level_noalloc(mg_forest *F, int32_t level, cons
         set_error("mg_set_rhs (k) has not been called");
         return MG_ERR_STATE;
     }
+    MG_TRY(ensure_fp64_coefficients(F));
     DevLevel &d = F->L[level];
     const int64_t need = d.pool_elems();
     if (need > kScratchElems) {

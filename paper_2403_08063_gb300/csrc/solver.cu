@@ -1,5 +1,7 @@
 // The forest object, the V-cycle driver and the C-ABI entry points (include/octmg.h).
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -83,12 +85,17 @@ template <typename T> Coef coef_of(const DevLevel &d);
 template <> Coef coef_of<double>(const DevLevel &d) { return d.c64(); }
 template <> Coef coef_of<float>(const DevLevel &d) { return d.c32(); }
 
+// Ghost exchange of a level: every face (full), or only the refinement-interface faces (C2F and F2C), whose
+// ghosts the smoother's write-through does not maintain.
 template <typename T, int MODE>
-void exchange(mg_forest *F, DevLevel &d, T *u) {
-    Prof p(F, cat_of<T>(P_EXCH64), (d.nfaces ? 1 : 0) + (d.nsegs ? 1 : 0));
-    if (d.nfaces)
-        k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(d.nfaces) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
-            u, d.faces, d.nfaces, d.g);
+void exchange(mg_forest *F, DevLevel &d, T *u, bool interface_only = false) {
+    const FaceItem *items = interface_only ? d.ifaces : d.faces;
+    const int nitems = interface_only ? d.nifaces : d.nfaces;
+    if (!nitems && !d.nsegs) return;
+    Prof p(F, cat_of<T>(P_EXCH64), (nitems ? 1 : 0) + (d.nsegs ? 1 : 0));
+    if (nitems)
+        k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(nitems) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
+            u, items, nitems, d.g);
     if (d.nsegs) {
         const int64_t tot = static_cast<int64_t>(d.nsegs) * (d.g.n / 2) * (d.g.n / 2);
         if (F->cfg.interface_flux)
@@ -117,26 +124,31 @@ template <typename T, int MODE>
 void smooth(mg_forest *F, DevLevel &d, int colour) {
     Prof p(F, cat_of<T>(P_SMOOTH64), 1);
     k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d),
-                                                                       h2_of<T>(d), d.g, colour);
+                                                                       h2_of<T>(d), d.g, colour, d.nbr6);
 }
 
+// V(nu1, nu2) on level l.  Exchange schedule: a full exchange when the level is entered (its u changed outside
+// the smoother), before each half-sweep and before the restriction only the refinement-interface ghosts (the
+// smoother writes same-level and boundary ghosts through), and a full exchange after the prolongation.
 template <typename T, int MODE>
 void vcycle(mg_forest *F, int l) {
     DevLevel &d = F->L[l];
     const int last = static_cast<int>(F->L.size()) - 1;
     if (l == last) {
         Prof p(F, cat_of<T>(P_COARSE64), 1);
-        k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d),
-                                                                                          F->Ainv, F->cmap, F->Nc);
+        k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(
+            ufield<T>(d), ffield<T>(d), F->Ainv, F->cmap, F->uprob, F->ustart, F->moff, F->Nc);
+        exchange<T, MODE>(F, d, ufield<T>(d));
         return;
     }
+    exchange<T, MODE>(F, d, ufield<T>(d));
     for (int i = 0; i < F->cfg.nu1; ++i) {
-        exchange<T, MODE>(F, d, ufield<T>(d));
+        if (i) exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 0);
-        exchange<T, MODE>(F, d, ufield<T>(d));
+        exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 1);
     }
-    exchange<T, MODE>(F, d, ufield<T>(d));
+    exchange<T, MODE>(F, d, ufield<T>(d), true);
     DevLevel &c = F->L[l + 1];
     {
         Prof p(F, cat_of<T>(P_RESTR64), 1);
@@ -144,46 +156,84 @@ void vcycle(mg_forest *F, int l) {
             ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
     }
     vcycle<T, MODE>(F, l + 1);
-    exchange<T, MODE>(F, c, ufield<T>(c));
+    if (l + 1 != last) exchange<T, MODE>(F, c, ufield<T>(c), true);
     {
         Prof p(F, cat_of<T>(P_PROL64), 1);
         k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
     }
+    exchange<T, MODE>(F, d, ufield<T>(d));
     for (int i = 0; i < F->cfg.nu2; ++i) {
-        exchange<T, MODE>(F, d, ufield<T>(d));
+        if (i) exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 0);
-        exchange<T, MODE>(F, d, ufield<T>(d));
+        exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 1);
     }
 }
 
-// Level-0 FP64 residual r = f - A u (exchange first); optionally written as FP32 r * scale with the FP32
-// correction zeroed; returns ||r||^2 (volume-weighted) to the host when rr is not null.  scale is a power of two
-// close to 1 / ||r|| so the FP32 values stay near unit size.
+// CTA chunks per block for the per-block reductions: about 2048 cells per CTA.
+int chunks_per_block(const DevLevel &d) { return std::max(1, static_cast<int>(d.cells() / d.g.nb) / 2048); }
+
+// Per-problem sums of the per-block sums to the host (pinned psum_h), synchronising the stream.
+mg_status read_problem_sums(mg_forest *F) {
+    k_problem_sums<<<(F->np + 127) / 128, 128, 0, F->st>>>(F->bsum, F->pstart, F->pblk, F->np, F->psum);
+    MG_CUDA(cudaMemcpyAsync(F->psum_h, F->psum, F->np * sizeof(double), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    return MG_OK;
+}
+
+// Per-problem residual scales (powers of two, exact in FP32 and FP64): host pinned copies, then the device copies.
+void set_scales_host(mg_forest *F, const std::vector<double> &mult) {
+    for (int p = 0; p < F->np; ++p) {
+        F->pscale_h[p] = static_cast<float>(mult[p]);
+        F->pinv_h[p] = 1.0 / mult[p];
+    }
+}
+
+mg_status enqueue_scales(mg_forest *F) {
+    MG_CUDA(cudaMemcpyAsync(F->pscale, F->pscale_h, F->np * sizeof(float), cudaMemcpyHostToDevice, F->st));
+    MG_CUDA(cudaMemcpyAsync(F->pinv, F->pinv_h, F->np * sizeof(double), cudaMemcpyHostToDevice, F->st));
+    return MG_OK;
+}
+
+mg_status upload_scales(mg_forest *F, const std::vector<double> &mult) {
+    set_scales_host(F, mult);
+    return enqueue_scales(F);
+}
+
+mg_status enqueue_problem_sums(mg_forest *F) {
+    k_problem_sums<<<(F->np + 127) / 128, 128, 0, F->st>>>(F->bsum, F->pstart, F->pblk, F->np, F->psum);
+    MG_CUDA(cudaMemcpyAsync(F->psum_h, F->psum, F->np * sizeof(double), cudaMemcpyDeviceToHost, F->st));
+    return MG_OK;
+}
+
+// Level-0 FP64 residual r = f - A u (exchange first); optionally written as FP32 r * scale_p with the FP32
+// correction zeroed; returns ||r_p||^2 (volume-weighted, per problem) to rr when rr is not null.  scale_p (set by
+// upload_scales, mult) is a power of two close to 1 / ||r_p|| so the FP32 values stay near unit size.
 template <int MODE>
-mg_status residual64(mg_forest *F, double *u, const double *f, float *out, double scale, float *zero_out,
-                     double *rr) {
+mg_status residual64(mg_forest *F, double *u, const double *f, float *out, float *zero_out,
+                     const std::vector<double> &mult, std::vector<double> *rr) {
     DevLevel &d = F->L[0];
     exchange<double, MODE>(F, d, u);
-    const int grid = grid_for(d.cells());
+    const int cpb = chunks_per_block(d);
+    MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
     {
-        Prof p(F, P_RESID64, 2);
-        k_residual_norm<MODE><<<grid, kThreads, 0, F->st>>>(u, f, d.c64(), d.ih2_64, d.vol_32, d.g, out,
-                                                            static_cast<float>(scale), F->partial, zero_out);
-        k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
+        Prof p(F, P_RESID64, 1);
+        k_residual_norm<MODE><<<d.g.nb * cpb, kThreads, 0, F->st>>>(u, f, d.c64(), d.ih2_64, d.vol_32, d.g, cpb, out,
+                                                                    F->pscale, d.bprob, F->bsum, zero_out);
     }
     if (rr) {
-        MG_CUDA(cudaMemcpyAsync(F->pinned, F->sums, sizeof(double), cudaMemcpyDeviceToHost, F->st));
-        MG_CUDA(cudaStreamSynchronize(F->st));
-        *rr = F->pinned[0] / (scale * scale);
+        MG_TRY(read_problem_sums(F));
+        rr->resize(F->np);
+        for (int p = 0; p < F->np; ++p) (*rr)[p] = F->psum_h[p] / (mult[p] * mult[p]);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
 
-mg_status residual64_any(mg_forest *F, double *u, const double *f, double scale, double *rr) {
-    if (F->cfg.coeff) return residual64<1>(F, u, f, nullptr, scale, nullptr, rr);
-    return residual64<0>(F, u, f, nullptr, scale, nullptr, rr);
+mg_status residual64_any(mg_forest *F, double *u, const double *f, const std::vector<double> &mult,
+                         std::vector<double> *rr) {
+    if (F->cfg.coeff) return residual64<1>(F, u, f, nullptr, nullptr, mult, rr);
+    return residual64<0>(F, u, f, nullptr, nullptr, mult, rr);
 }
 
 void apply64(mg_forest *F, DevLevel &d, const double *u, double *out) {
@@ -193,48 +243,85 @@ void apply64(mg_forest *F, DevLevel &d, const double *u, double *out) {
         k_apply64<0><<<grid_for(d.cells()), kThreads, 0, F->st>>>(u, d.c64(), d.ih2_64, d.g, out);
 }
 
-// Coarsest-level dense operator (FP64 kernels on unit vectors), inverted on the host, uploaded.
+// Coarsest-level dense operators (FP64 kernels on unit vectors, all problems probed at once), inverted on the host
+// (one block per problem, in parallel threads), uploaded with their transposes.
 mg_status assemble_coarse(mg_forest *F) {
     const int l = static_cast<int>(F->L.size()) - 1;
     DevLevel &d = F->L[l];
+    const HostLevel &hl = F->H.levels[l];
     const int N = static_cast<int>(d.cells());
+    const int cells = d.g.n * d.g.n * d.g.n;
     F->Nc = N;
     if (!F->cmap) {
-        std::vector<int64_t> cmap(N);
+        std::vector<std::vector<int32_t>> blocks(F->np);
+        for (int b = 0; b < d.g.nb; ++b) blocks[hl.keys[b].p].push_back(b);
+        std::vector<int64_t> cmap;
+        std::vector<int32_t> uprob;
+        F->ustart_h.assign(F->np + 1, 0);
+        F->moff_h.assign(F->np + 1, 0);
         const int n = d.g.n;
-        for (int b = 0, m = 0; b < d.g.nb; ++b)
-            for (int z = 0; z < n; ++z)
-                for (int y = 0; y < n; ++y)
-                    for (int x = 0; x < n; ++x) cmap[m++] = b * d.g.bs + off3(x + 1, y + 1, z + 1, d.g.P);
+        for (int p = 0; p < F->np; ++p) {
+            F->ustart_h[p] = static_cast<int64_t>(cmap.size());
+            for (int b : blocks[p])
+                for (int z = 0; z < n; ++z)
+                    for (int y = 0; y < n; ++y)
+                        for (int x = 0; x < n; ++x) {
+                            cmap.push_back(b * d.g.bs + off3(x + 1, y + 1, z + 1, d.g.P));
+                            uprob.push_back(p);
+                        }
+            const int64_t Np = static_cast<int64_t>(blocks[p].size()) * cells;
+            F->moff_h[p + 1] = F->moff_h[p] + Np * Np;
+        }
+        F->ustart_h[F->np] = static_cast<int64_t>(cmap.size());
         MG_TRY(upload(F, &F->cmap, cmap));
-        MG_TRY(dalloc(F, &F->Ainv, static_cast<int64_t>(N) * N));
+        MG_TRY(upload(F, &F->uprob, uprob));
+        MG_TRY(upload(F, &F->ustart, F->ustart_h));
+        MG_TRY(upload(F, &F->moff, F->moff_h));
+        MG_TRY(dalloc(F, &F->Ainv, F->moff_h[F->np]));
+        MG_TRY(dalloc(F, &F->AinvT, F->moff_h[F->np]));
     }
     if (!F->coarse_r) MG_TRY(dalloc(F, &F->coarse_r, d.pool_elems()));
+    int maxN = 0;
+    for (int p = 0; p < F->np; ++p) maxN = std::max<int>(maxN, static_cast<int>(F->ustart_h[p + 1] - F->ustart_h[p]));
     double *r = F->coarse_r, *Adev = F->Ainv;
-    for (int m = 0; m < N; ++m) {
+    for (int m = 0; m < maxN; ++m) {
         MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
-        k_set_unit<<<1, 32, 0, F->st>>>(d.u64, F->cmap, m);
+        k_set_units<<<(F->np + 127) / 128, 128, 0, F->st>>>(d.u64, F->cmap, F->ustart, F->np, m);
         exchange_any64(F, d, d.u64);
         apply64(F, d, d.u64, r);
-        k_gather_column<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, N, Adev, m);
+        k_gather_columns<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, F->uprob, F->ustart, F->moff, N, Adev, m);
     }
     MG_CUDA(cudaGetLastError());
-    std::vector<double> A(static_cast<size_t>(N) * N);
+    std::vector<double> A(static_cast<size_t>(F->moff_h[F->np]));
     MG_CUDA(cudaMemcpyAsync(A.data(), Adev, A.size() * sizeof(double), cudaMemcpyDeviceToHost, F->st));
     MG_CUDA(cudaStreamSynchronize(F->st));
-    if (!invert_dense(A, N)) {
-        set_error("coarsest-level operator is singular");
+    std::vector<double> At(A.size());
+    std::atomic<int> next(0), bad(-1);
+    auto work = [&]() {
+        for (int p = next++; p < F->np; p = next++) {
+            const int Np = static_cast<int>(F->ustart_h[p + 1] - F->ustart_h[p]);
+            std::vector<double> blk(A.begin() + F->moff_h[p], A.begin() + F->moff_h[p + 1]);
+            if (!invert_dense(blk, Np)) {
+                bad = p;
+                continue;
+            }
+            std::copy(blk.begin(), blk.end(), A.begin() + F->moff_h[p]);
+            for (int i = 0; i < Np; ++i)
+                for (int j = 0; j < Np; ++j)
+                    At[F->moff_h[p] + static_cast<int64_t>(j) * Np + i] = blk[static_cast<size_t>(i) * Np + j];
+        }
+    };
+    const int nth = std::max(1, std::min<int>(F->np, static_cast<int>(std::thread::hardware_concurrency())));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+    work();
+    for (auto &t : pool) t.join();
+    if (bad >= 0) {
+        set_error("coarsest-level operator of problem " + std::to_string(bad.load()) + " is singular");
         return MG_ERR_INVALID_ARG;
     }
     MG_CUDA(cudaMemcpyAsync(Adev, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
-    {
-        std::vector<double> At(A.size());
-        for (int i = 0; i < N; ++i)
-            for (int j = 0; j < N; ++j) At[static_cast<size_t>(j) * N + i] = A[static_cast<size_t>(i) * N + j];
-        if (!F->AinvT) MG_TRY(dalloc(F, &F->AinvT, static_cast<int64_t>(N) * N));
-        MG_CUDA(cudaMemcpyAsync(F->AinvT, At.data(), At.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
-        MG_CUDA(cudaStreamSynchronize(F->st));
-    }
+    MG_CUDA(cudaMemcpyAsync(F->AinvT, At.data(), At.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
     MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
     MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
@@ -251,7 +338,7 @@ mg_status build_coefficients(mg_forest *F) {
         exchange_k(F, d);
         k_face_coefs<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.k64, d.ih2_64, d.g, d.tx, d.ty, d.tz,
                                                                         d.kap);
-        k_diag<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.g, d.dg, d.dinv);
+        if (d.dg) k_diag<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.g, d.dg, d.dinv);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -260,7 +347,7 @@ mg_status build_coefficients(mg_forest *F) {
 template <typename T>
 mg_status pack_user(mg_forest *F, DevLevel &d, T *pool, const double *user) {
     Prof p(F, P_LAYOUT, 1);
-    k_pack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(pool, user, d.g);
+    k_pack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(pool, user, d.g, &d == &F->L[0] ? F->leaf_off : nullptr);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -268,7 +355,8 @@ mg_status pack_user(mg_forest *F, DevLevel &d, T *pool, const double *user) {
 template <typename T>
 mg_status unpack_user(mg_forest *F, DevLevel &d, double *user, const T *pool) {
     Prof p(F, P_LAYOUT, 1);
-    k_unpack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(user, pool, d.g);
+    k_unpack<T><<<grid_for(d.cells()), kThreads, 0, F->st>>>(user, pool, d.g,
+                                                             &d == &F->L[0] ? F->leaf_off : nullptr);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -288,26 +376,67 @@ double pow2_near(double x) {
     return std::ldexp(1.0, static_cast<int>(std::lround(std::log2(x))));
 }
 
-// Mixed precision: r64 = f - A u (FP64), written as FP32 r / s; FP32 V-cycle; u += s e.  `iters` outer steps;
-// returns the relative residual measured before the last update when `final_rel` is requested afterwards.
-mg_status mixed_step(mg_forest *F, double scale, double *rr) {
+// Mixed precision, first half of a defect-correction step: r64 = f - A u (FP64), stored as FP32 r * scale_p
+// with the FP32 correction zeroed; per-problem ||r||^2 to rr.
+mg_status mixed_step(mg_forest *F, const std::vector<double> &mult, std::vector<double> *rr) {
     DevLevel &d = F->L[0];
+    MG_TRY(upload_scales(F, mult));
     if (F->cfg.coeff)
-        MG_TRY((residual64<1>(F, d.u64, d.f64, d.f32, scale, d.u32, rr)));
+        MG_TRY((residual64<1>(F, d.u64, d.f64, d.f32, d.u32, mult, rr)));
     else
-        MG_TRY((residual64<0>(F, d.u64, d.f64, d.f32, scale, d.u32, rr)));
+        MG_TRY((residual64<0>(F, d.u64, d.f64, d.f32, d.u32, mult, rr)));
     return MG_OK;
 }
 
-// `cycles` FP32 V-cycles on the scaled residual, then u64 += e32 / mult (mult a power of two: exact).
-mg_status finish_mixed_cycle(mg_forest *F, double inv_mult, int cycles) {
+// The residual half of a defect-correction step without host synchronisation (graph-capturable).
+mg_status enqueue_residual(mg_forest *F) {
+    DevLevel &d = F->L[0];
+    static const std::vector<double> none;
+    if (F->cfg.coeff) return residual64<1>(F, d.u64, d.f64, d.f32, d.u32, none, nullptr);
+    return residual64<0>(F, d.u64, d.f64, d.f32, d.u32, none, nullptr);
+}
+
+// Second half: `cycles` FP32 V-cycles on the scaled residual, then u64 += e32 / scale_p (exact).
+mg_status finish_mixed_cycle(mg_forest *F, int cycles) {
     DevLevel &d = F->L[0];
     for (int i = 0; i < cycles; ++i) vcycle32(F);
     Prof p(F, P_UPDATE, 1);
-    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, inv_mult, d.g);
+    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, F->pinv, d.bprob, d.g);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
+
+// Level-0 FP64 scratch pools (operator application, gradients), allocated on first use.
+mg_status ensure_scratch64(mg_forest *F) {
+    if (!F->s64a) MG_TRY(dalloc(F, &F->s64a, F->L[0].pool_elems()));
+    if (!F->s64b) MG_TRY(dalloc(F, &F->s64b, F->L[0].pool_elems()));
+    return MG_OK;
+}
+
+// FP64 coefficient arrays (scaled faces, diagonal, inverse diagonal) on every level, for the FP64 paths a forest
+// with FP32 cycles does not allocate at creation (adjoint cycles, the debug exchange of intermediate levels).
+mg_status ensure_fp64_coefficients(mg_forest *F) {
+    if (!F->cfg.coeff) return MG_OK;
+    bool added = false;
+    for (DevLevel &d : F->L) {
+        const int64_t pe = d.pool_elems();
+        if (!d.tx) {
+            MG_TRY(dalloc(F, &d.tx, pe));
+            MG_TRY(dalloc(F, &d.ty, pe));
+            MG_TRY(dalloc(F, &d.tz, pe));
+            MG_TRY(dalloc(F, &d.dg, pe));
+            added = true;
+        }
+        if (!d.dinv) {
+            MG_TRY(dalloc(F, &d.dinv, pe));
+            added = true;
+        }
+    }
+    if (added && F->rhs_set) MG_TRY(build_coefficients(F));
+    return MG_OK;
+}
+
+mg_status enqueue_fp32_step(mg_forest *F, int cycles) { return finish_mixed_cycle(F, cycles); }
 
 mg_status check_ready(mg_forest *F) {
     if (!F) {
@@ -321,58 +450,76 @@ mg_status check_ready(mg_forest *F) {
     return MG_OK;
 }
 
-// Runs cycles until rel <= rtol (rtol < 0: exactly max_cycles).  u_dev in/out.
-mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, int *cycles_out, double *rel_out) {
+// Runs cycles until every problem has rel <= rtol (rtol < 0: exactly max_cycles).  u_dev in/out.  Per problem,
+// cycles_out gets the cycle count at which it first met rtol (else the total) and rel_out its final residual.
+mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, int32_t *cycles_out,
+                     double *rel_out) {
     MG_TRY(check_ready(F));
     DevLevel &d = F->L[0];
+    const int np = F->np;
     MG_TRY(pack_user<double>(F, d, d.u64, u_dev));
-    const double fn = F->fnorm > 0.0 ? F->fnorm : 1.0;
+    std::vector<double> fn(np), rel(np, -1.0), mult(np), rr(np, 0.0);
+    std::vector<int32_t> met(np, -1);
+    for (int p = 0; p < np; ++p) {
+        fn[p] = F->fnorm_p[p] > 0.0 ? F->fnorm_p[p] : 1.0;
+        mult[p] = pow2_near(1.0 / fn[p]);
+    }
+    auto update_rel = [&](int done) {
+        bool all = true, finite = true;
+        for (int p = 0; p < np; ++p) {
+            rel[p] = std::sqrt(rr[p]) / fn[p];
+            if (!std::isfinite(rel[p])) finite = false;
+            if (rtol >= 0.0 && rel[p] <= rtol && met[p] < 0) met[p] = done;
+            if (!(rtol >= 0.0 && rel[p] <= rtol)) all = false;
+            mult[p] = pow2_near(1.0 / std::sqrt(rr[p]));
+        }
+        return std::make_pair(all, finite);
+    };
     int done = 0;
-    double rel = -1.0;
-    double mult = pow2_near(1.0 / fn);  // FP32 values of residuals are scaled by a power of two near 1/||r||
+    bool finite = true;
     if (F->cfg.precision == 0) {
-        for (; done < max_cycles; ++done) {
-            if (rtol >= 0.0 && done > 0 && rel <= rtol) break;
+        while (done < max_cycles) {
             vcycle64(F);
-            double rr = 0.0;
-            if (rtol >= 0.0 || rel_out || done + 1 == max_cycles) {
+            ++done;
+            if (rtol >= 0.0 || done == max_cycles) {
+                MG_TRY(upload_scales(F, mult));
                 MG_TRY(residual64_any(F, d.u64, d.f64, mult, &rr));
-                rel = std::sqrt(rr) / fn;
-                mult = pow2_near(1.0 / std::sqrt(rr));
-                if (!std::isfinite(rel)) {
-                    set_error("residual is not finite");
-                    ++done;
-                    break;
-                }
+                auto st = update_rel(done);
+                finite = st.second;
+                if (!finite || st.first) break;
             }
         }
     } else {
-        double rr = 0.0;
         MG_TRY(mixed_step(F, mult, &rr));
-        rel = std::sqrt(rr) / fn;
+        auto st = update_rel(0);
+        finite = st.second;
         const int inner = std::max(1, F->cfg.inner_cycles);
-        while (done < max_cycles) {
-            if (rtol >= 0.0 && rel <= rtol) break;
+        while (finite && done < max_cycles && !st.first) {
             const int m = std::min(inner, max_cycles - done);
-            MG_TRY(finish_mixed_cycle(F, 1.0 / mult, m));
+            MG_TRY(finish_mixed_cycle(F, m));
             done += m;
-            mult = pow2_near(1.0 / std::sqrt(rr));
             MG_TRY(mixed_step(F, mult, &rr));
-            rel = std::sqrt(rr) / fn;
-            if (!std::isfinite(rel)) {
-                set_error("residual is not finite");
-                break;
-            }
+            st = update_rel(done);
+            finite = st.second;
         }
     }
     MG_TRY(unpack_user<double>(F, d, u_dev, d.u64));
     MG_CUDA(cudaStreamSynchronize(F->st));
-    if (cycles_out) *cycles_out = done;
-    if (rel_out) *rel_out = rel;
-    if (!std::isfinite(rel)) return MG_ERR_NOT_CONVERGED;
-    if (rtol >= 0.0 && !(rel <= rtol)) {
-        set_error("relative residual " + fmt_e(rel) + " above rtol after " + std::to_string(done) + " cycles");
+    for (int p = 0; p < np; ++p) {
+        if (cycles_out) cycles_out[p] = met[p] >= 0 ? met[p] : done;
+        if (rel_out) rel_out[p] = rel[p];
+    }
+    if (!finite) {
+        set_error("residual is not finite");
         return MG_ERR_NOT_CONVERGED;
+    }
+    if (rtol >= 0.0) {
+        for (int p = 0; p < np; ++p)
+            if (!(rel[p] <= rtol)) {
+                set_error("problem " + std::to_string(p) + ": relative residual " + fmt_e(rel[p]) +
+                          " above rtol after " + std::to_string(done) + " cycles");
+                return MG_ERR_NOT_CONVERGED;
+            }
     }
     return MG_OK;
 }
@@ -387,14 +534,11 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         set_error("bad coeff / precision / nu1 / nu2 / interface_flux");
         return MG_ERR_INVALID_ARG;
     }
+    const int np = std::max(1, cfg->n_problems);
     std::vector<Key> leaves(cfg->n_leaves);
     for (int i = 0; i < cfg->n_leaves; ++i) {
         const int32_t *r = cfg->leaves + 5 * static_cast<int64_t>(i);
-        if (r[0] != 0) {
-            set_error("leaf problem index must be 0 for a single forest");
-            return MG_ERR_INVALID_ARG;
-        }
-        leaves[i] = Key{r[1], r[2], r[3], r[4]};
+        leaves[i] = Key{r[0], r[1], r[2], r[3], r[4]};
     }
     mg_forest *F = new (std::nothrow) mg_forest();
     if (!F) return MG_ERR_OOM;
@@ -402,8 +546,10 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
     F->cfg.leaves = nullptr;
     if (F->cfg.max_coarse <= 0) F->cfg.max_coarse = 512;
     F->st = static_cast<cudaStream_t>(cfg->stream);
+    F->np = np;
+    F->cfg.n_problems = np;
     std::string err;
-    mg_status st = build_hierarchy(cfg->roots, cfg->n, leaves, F->cfg.max_coarse, F->H, err);
+    mg_status st = build_hierarchy(cfg->roots, cfg->n, np, leaves, F->cfg.max_coarse, F->H, err);
     if (st != MG_OK) {
         set_error(err);
         delete F;
@@ -434,6 +580,22 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
             if ((st = upload(F, &d.fkind, fk)) != MG_OK) return fail(st);
         }
         if ((st = upload(F, &d.segs, h.segs)) != MG_OK) return fail(st);
+        {
+            std::vector<int32_t> bp(h.keys.size());
+            for (size_t b = 0; b < bp.size(); ++b) bp[b] = h.keys[b].p;
+            if ((st = upload(F, &d.bprob, bp)) != MG_OK) return fail(st);
+            std::vector<int32_t> nb6(h.keys.size() * 6, -2);
+            std::vector<FaceItem> itf;
+            for (const FaceItem &fi : h.faces) {
+                int32_t &slot = nb6[static_cast<size_t>(fi.blk) * 6 + 2 * fi.axis + fi.side];
+                if (fi.kind == FK_SAME) slot = fi.nbr;
+                else if (fi.kind == FK_BND) slot = -1;
+                else itf.push_back(fi);
+            }
+            if ((st = upload(F, &d.nbr6, nb6)) != MG_OK) return fail(st);
+            d.nifaces = static_cast<int>(itf.size());
+            if (!itf.empty() && (st = upload(F, &d.ifaces, itf)) != MG_OK) return fail(st);
+        }
         if (!h.to_next.empty() && (st = upload(F, &d.xfer, h.to_next)) != MG_OK) return fail(st);
         std::vector<double> h2(h.h.size()), ih2(h.h.size()), vol(h.h.size());
         std::vector<float> h2f(h.h.size()), ih2f(h.h.size()), volf(h.h.size());
@@ -451,28 +613,52 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         if ((st = upload(F, &d.h2_32, h2f)) != MG_OK) return fail(st);
         if ((st = upload(F, &d.ih2_32, ih2f)) != MG_OK) return fail(st);
         if ((st = upload(F, &d.vol_32, volf)) != MG_OK) return fail(st);
+        // FP32 cycles need FP64 pools only on the finest level (outer residual, solution) and the coarsest (operator
+        // assembly); the FP64 smoother's inverse diagonal only exists for FP64 cycles.  The adjoint and the debug
+        // exchange add the missing FP64 coefficient arrays on first use (ensure_fp64_coefficients).
         const int64_t pe = d.pool_elems();
-        if ((st = dalloc(F, &d.u64, pe)) != MG_OK) return fail(st);
-        if ((st = dalloc(F, &d.f64, pe)) != MG_OK) return fail(st);
-        if (cfg->precision == 1) {
+        const bool mixed = cfg->precision == 1;
+        const bool fp64 = !mixed || l == 0 || l + 1 == nl;
+        if (fp64 && (st = dalloc(F, &d.u64, pe)) != MG_OK) return fail(st);
+        if (fp64 && (st = dalloc(F, &d.f64, pe)) != MG_OK) return fail(st);
+        if (mixed) {
             if ((st = dalloc(F, &d.u32, pe)) != MG_OK) return fail(st);
             if ((st = dalloc(F, &d.f32, pe)) != MG_OK) return fail(st);
         }
         if (cfg->coeff) {
             if ((st = dalloc(F, &d.k64, pe)) != MG_OK) return fail(st);
-            if ((st = dalloc(F, &d.tx, pe)) != MG_OK) return fail(st);
-            if ((st = dalloc(F, &d.ty, pe)) != MG_OK) return fail(st);
-            if ((st = dalloc(F, &d.tz, pe)) != MG_OK) return fail(st);
-            if ((st = dalloc(F, &d.dg, pe)) != MG_OK) return fail(st);
-            if ((st = dalloc(F, &d.dinv, pe)) != MG_OK) return fail(st);
-            if (cfg->precision == 1 && (st = dalloc(F, &d.kap, pe)) != MG_OK) return fail(st);
+            if (fp64) {
+                if ((st = dalloc(F, &d.tx, pe)) != MG_OK) return fail(st);
+                if ((st = dalloc(F, &d.ty, pe)) != MG_OK) return fail(st);
+                if ((st = dalloc(F, &d.tz, pe)) != MG_OK) return fail(st);
+                if ((st = dalloc(F, &d.dg, pe)) != MG_OK) return fail(st);
+            }
+            if (!mixed && (st = dalloc(F, &d.dinv, pe)) != MG_OK) return fail(st);
+            if (mixed && (st = dalloc(F, &d.kap, pe)) != MG_OK) return fail(st);
         }
     }
     if ((st = dalloc(F, &F->partial, 2 * kMaxGrid)) != MG_OK) return fail(st);
     if ((st = dalloc(F, &F->sums, 2)) != MG_OK) return fail(st);
     if ((st = dalloc(F, &F->flag, 1)) != MG_OK) return fail(st);
-    if ((st = dalloc(F, &F->s64a, F->L[0].pool_elems())) != MG_OK) return fail(st);
-    if ((st = dalloc(F, &F->s64b, F->L[0].pool_elems())) != MG_OK) return fail(st);
+    {
+        const HostLevel &h0 = F->H.levels[0];
+        std::vector<int32_t> pstart(np + 1, 0), pblk(h0.keys.size());
+        for (const Key &k : h0.keys) pstart[k.p + 1] += 1;
+        for (int p = 0; p < np; ++p) pstart[p + 1] += pstart[p];
+        std::vector<int32_t> fill(pstart.begin(), pstart.end() - 1);
+        for (size_t b = 0; b < h0.keys.size(); ++b) pblk[fill[h0.keys[b].p]++] = static_cast<int32_t>(b);
+        if ((st = upload(F, &F->pstart, pstart)) != MG_OK) return fail(st);
+        if ((st = upload(F, &F->pblk, pblk)) != MG_OK) return fail(st);
+        if ((st = dalloc(F, &F->bsum, static_cast<int64_t>(h0.keys.size()))) != MG_OK) return fail(st);
+        if ((st = dalloc(F, &F->psum, np)) != MG_OK) return fail(st);
+        if ((st = dalloc(F, &F->pscale, np)) != MG_OK) return fail(st);
+        if ((st = dalloc(F, &F->pinv, np)) != MG_OK) return fail(st);
+        if (cudaMallocHost(&F->psum_h, np * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&F->pscale_h, np * sizeof(float)) != cudaSuccess ||
+            cudaMallocHost(&F->pinv_h, np * sizeof(double)) != cudaSuccess)
+            return fail(MG_ERR_OOM);
+        F->fnorm_p.assign(np, 0.0);
+    }
     if (cudaMallocHost(&F->pinned, 2 * sizeof(double)) != cudaSuccess) return fail(MG_ERR_OOM);
     if (!cfg->coeff && (st = assemble_coarse(F)) != MG_OK) return fail(st);
     if (cudaStreamSynchronize(F->st) != cudaSuccess) {
@@ -504,6 +690,7 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
     DevLevel &d = F->L[0];
     int *bad = F->flag;
     MG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), F->st));
+    if (!F->batch_member)
     k_check_inputs<<<grid_for(d.cells()), kThreads, 0, F->st>>>(f_dev, F->cfg.coeff ? k_dev : nullptr, d.cells(), bad);
     int hbad = 0;
     MG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, F->st));
@@ -518,12 +705,16 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
         MG_TRY(build_coefficients(F));
         MG_TRY(assemble_coarse(F));
     }
-    const int grid = grid_for(d.cells());
-    k_norm64<<<grid, kThreads, 0, F->st>>>(d.f64, d.vol_64, d.g, F->partial);
-    k_sum_partials<<<1, kThreads, 0, F->st>>>(F->partial, grid, F->sums);
-    MG_CUDA(cudaMemcpyAsync(F->pinned, F->sums, sizeof(double), cudaMemcpyDeviceToHost, F->st));
-    MG_CUDA(cudaStreamSynchronize(F->st));
-    F->fnorm = std::sqrt(F->pinned[0]);
+    const int cpb = chunks_per_block(d);
+    MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
+    k_block_norm64<<<d.g.nb * cpb, kThreads, 0, F->st>>>(d.f64, d.vol_64, d.g, cpb, F->bsum);
+    MG_TRY(read_problem_sums(F));
+    double total = 0.0;
+    for (int p = 0; p < F->np; ++p) {
+        F->fnorm_p[p] = std::sqrt(F->psum_h[p]);
+        total += F->psum_h[p];
+    }
+    F->fnorm = std::sqrt(total);
     F->rhs_set = true;
     return MG_OK;
 }
@@ -538,6 +729,7 @@ mg_status apply_op(mg_forest *F, const double *u_dev, double *Au_dev) {
         return MG_ERR_STATE;
     }
     DevLevel &d = F->L[0];
+    MG_TRY(ensure_scratch64(F));
     MG_TRY(pack_user<double>(F, d, F->s64a, u_dev));
     exchange_any64(F, d, F->s64a);
     apply64(F, d, F->s64a, F->s64b);
@@ -562,6 +754,9 @@ void mg_forest_destroy(mg_forest *F) {
     for (void *p : F->allocs) cudaFree(p);
     for (cudaEvent_t e : F->ev_pool) cudaEventDestroy(e);
     if (F->pinned) cudaFreeHost(F->pinned);
+    if (F->psum_h) cudaFreeHost(F->psum_h);
+    if (F->pscale_h) cudaFreeHost(F->pscale_h);
+    if (F->pinv_h) cudaFreeHost(F->pinv_h);
     delete F;
 }
 
@@ -623,6 +818,7 @@ mg_status mg_exchange_level(mg_forest *F, int32_t level, const double *u_dev, do
         set_error("mg_set_rhs (k) has not been called");
         return MG_ERR_STATE;
     }
+    MG_TRY(ensure_fp64_coefficients(F));
     DevLevel &d = F->L[level];
     double *pool = nullptr;
     MG_CUDA(cudaStreamSynchronize(F->st));

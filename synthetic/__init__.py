@@ -8,10 +8,10 @@ multigrid method's arithmetic, and both the CUDA path's tests and the CPU oracle
 from .forests import (uniform_leaves, refine_ball, refine_box, balance_2to1, leaves_array, leaf_keys,
                       count_cells, workload_forest, batch_problems, batch_leaves)
 from .fields import (cell_centres, sin_product, sin_product_rhs, gaussian_bump_with_noise, lognormal_k_rff,
-                     uniform_rhs, sin_target)
+                     uniform_rhs, sin_target, batch_fields)
 
 __all__ = [
     "uniform_leaves", "refine_ball", "refine_box", "balance_2to1", "leaves_array", "leaf_keys", "count_cells",
     "workload_forest", "batch_problems", "batch_leaves", "cell_centres", "sin_product", "sin_product_rhs", "gaussian_bump_with_noise",
-    "lognormal_k_rff", "uniform_rhs", "sin_target",
+    "lognormal_k_rff", "uniform_rhs", "sin_target", "batch_fields",
 ]

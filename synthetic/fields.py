@@ -71,24 +71,26 @@ def gaussian_bump_with_noise(R, n, keys, seed=0, center=(0.5, 0.5, 0.5), sigma=0
     return out + eta
 
 
-def lognormal_k_rff(R, n, keys, seed=0, sigma=1.0, ell=0.1, features=512, device="cpu"):
+def lognormal_k_rff(R, n, keys, seed=0, sigma=1.0, ell=0.1, features=512, device="cpu", dtype=F64):
     """k = exp(g), g a stationary Gaussian random field with covariance sigma^2 exp(-r^2 / (2 ell^2)).
 
     g is drawn by random Fourier features, g(x) = sigma sqrt(2/M) sum_m cos(w_m . x + phi_m), with the M
     frequencies w_m ~ N(0, ell^-2 I) drawn first (shape (M, 3)) and the phases phi_m ~ U(0, 2 pi) second.
-    It can be evaluated at any point, so refined forests sample the same field.
+    It can be evaluated at any point, so refined forests sample the same field.  dtype=torch.float32 evaluates the
+    features in single precision (for very large inputs); the returned field is float64 either way.
     """
     keys = list(keys)
     rng = np.random.default_rng(seed)
     w = torch.from_numpy(rng.normal(0.0, 1.0 / ell, size=(features, 3))).to(device)
     phi = torch.from_numpy(rng.uniform(0.0, 2.0 * math.pi, size=features)).to(device)
+    wd, phid = w.to(dtype), phi.to(dtype)
     amp = sigma * math.sqrt(2.0 / features)
     out = torch.empty((len(keys), n ** 3), dtype=F64, device=device)
     per = max(1, (1 << 20) // n ** 3)
     for sl in _chunks(keys, per):
-        c = cell_centres(R, n, keys, device, sl).reshape(-1, 3)
-        g = amp * torch.cos(c @ w.T + phi).sum(-1)
-        out[sl] = torch.exp(g).reshape(-1, n ** 3)
+        c = cell_centres(R, n, keys, device, sl).reshape(-1, 3).to(dtype)
+        g = amp * torch.cos(c @ wd.T + phid).sum(-1)
+        out[sl] = torch.exp(g.to(F64)).reshape(-1, n ** 3)
     return out
 
 
@@ -105,3 +107,22 @@ def sin_target(R, n, keys, seed=0, device="cpu"):
     c = cell_centres(R, n, keys, device)
     return (torch.sin(m[0] * math.pi * c[..., 0]) * torch.sin(m[1] * math.pi * c[..., 1]) *
             torch.sin(m[2] * math.pi * c[..., 2])).reshape(len(list(keys)), -1)
+
+
+def batch_fields(problems, seed=0, device="cpu", sigma=1.0, ell=0.1):
+    """(f, k) of a batch in its flat layout (problems in order, each leaf n^3 cells): per problem p, k is the
+    log-normal random-Fourier-feature field with seed `seed + p` (features in FP32) and f ~ U(-1, 1) drawn with
+    torch's Philox generator seeded `seed + 100000 + p` on `device`."""
+    total = sum(len(keys) * n ** 3 for n, keys in problems)
+    f = torch.empty(total, dtype=F64, device=device)
+    k = torch.empty(total, dtype=F64, device=device)
+    off = 0
+    for p, (n, keys) in enumerate(problems):
+        cnt = len(keys) * n ** 3
+        k[off:off + cnt] = lognormal_k_rff(1, n, keys, seed=seed + p, sigma=sigma, ell=ell, device=device,
+                                           dtype=torch.float32).reshape(-1)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed + 100000 + p)
+        f[off:off + cnt] = torch.rand(cnt, generator=gen, device=device, dtype=F64) * 2.0 - 1.0
+        off += cnt
+    return f, k

@@ -41,6 +41,7 @@ def _create(lib, R, n, keys):
     cfg.leaves = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     cfg.coeff, cfg.interface_flux, cfg.precision, cfg.nu1, cfg.nu2, cfg.max_coarse = 0, 1, 0, 2, 2, 512
     cfg.inner_cycles = 1
+    cfg.n_problems = 1
     h = ctypes.c_void_p()
     st = lib.mg_forest_create(ctypes.byref(cfg), ctypes.byref(h))
     return st, h, lib.mg_last_error().decode()
