@@ -38,7 +38,7 @@ typedef enum {
     MG_ERR_OOM = 4,           /* device or host allocation failed */
     MG_ERR_CUDA = 5,          /* a CUDA call failed */
     MG_ERR_NOT_CONVERGED = 6, /* residual did not reach rtol within max_cycles, or became non-finite */
-    MG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up (batched persistent kernel) */
+    MG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up (staged smoother's shared-memory copies) */
     MG_ERR_NONFINITE = 8,     /* NaN/Inf in an input field, or k <= 0 */
     MG_ERR_STATE = 9          /* call out of order (e.g. solve before mg_set_rhs) */
 } mg_status;
@@ -136,6 +136,23 @@ mg_status mg_exchange_level_noalloc(mg_forest *forest, int32_t level, const doub
 mg_status mg_profile(mg_forest *forest, int32_t enable);
 mg_status mg_profile_read(mg_forest *forest, int32_t max_families, char *names, double *ms, int64_t *launches,
                           int32_t *n_families);
+
+/* Launch shape of the FP32 smoother on one level (precision 1, block edges 4..128), five int32 {kind, p1..p4}:
+ *   {1, zc, threads, 0, 0}: one thread per zc cells of a z-column (zc 1, 2 or 4), CTAs of 128, 256 or 512 threads;
+ *   {2, TY, TZ, D, R}:      edges 32..128: a CTA per TY rows x TZ planes of a block, the other colour's planes
+ *                           staged in shared memory by bulk copies D planes ahead, R rows per thread.
+ * mg_smoother_shapes lists the shapes offered for a level (5 int32 each, up to max_shapes into shapes, which may
+ * be NULL; *n_shapes receives the count).  The first mg_set_rhs of a forest picks each level's shape by timing
+ * every offered shape on the level's own FP32 pools (levels under 2^18 cells take {1, 1, 256, 0, 0}); the choice
+ * is cached for the process per (device, coefficient mode, n, block count).  mg_set_smoother_shape overrides it.
+ * A shape only changes which thread updates a cell, so every shape gives bit-identical results.
+ * get: all zeros for a level that uses the generic smoother (FP64 solves, n > 128) or is not tuned yet.
+ * set: MG_ERR_INVALID_ARG for a bad level, a shape not offered, or a level without the specialised smoother.
+ * No counterpart in the paper, whose kernels are generated per block size (Sec. 4). */
+mg_status mg_smoother_shapes(const mg_forest *forest, int32_t level, int32_t max_shapes, int32_t *shapes,
+                             int32_t *n_shapes);
+mg_status mg_get_smoother_shape(const mg_forest *forest, int32_t level, int32_t *shape);
+mg_status mg_set_smoother_shape(mg_forest *forest, int32_t level, const int32_t *shape);
 
 /* ---------------------------------------------------------------------------------------------------------------
  * Batches: many independent problems with different block sizes (uneven octree forests), solved together.

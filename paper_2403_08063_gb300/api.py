@@ -141,6 +141,24 @@ class Forest:
         _lib.check(self.lib.mg_exchange_level(self.h, int(level), _ptr(u), _ptr(out)))
         return out.view(nb, n + 2, n + 2, n + 2)
 
+    def smoother_shapes(self, level):
+        """The FP32 smoother launch shapes offered on `level` (5-tuples; empty where it is not used)."""
+        cnt = ctypes.c_int32()
+        _lib.check(self.lib.mg_smoother_shapes(self.h, int(level), 0, None, ctypes.byref(cnt)))
+        buf = (ctypes.c_int32 * (5 * max(1, cnt.value)))()
+        _lib.check(self.lib.mg_smoother_shapes(self.h, int(level), cnt.value, buf, ctypes.byref(cnt)))
+        return [tuple(buf[5 * i:5 * i + 5]) for i in range(cnt.value)]
+
+    def smoother_shape(self, level):
+        """The FP32 smoother launch shape of `level`; (0, 0, 0, 0, 0) where it is not used."""
+        buf = (ctypes.c_int32 * 5)()
+        _lib.check(self.lib.mg_get_smoother_shape(self.h, int(level), buf))
+        return tuple(buf)
+
+    def set_smoother_shape(self, level, shape):
+        buf = (ctypes.c_int32 * 5)(*[int(v) for v in shape])
+        _lib.check(self.lib.mg_set_smoother_shape(self.h, int(level), buf))
+
     # -- accounting --------------------------------------------------------------------------------------
     def profile(self, enable=True):
         _lib.check(self.lib.mg_profile(self.h, int(bool(enable))))

@@ -178,6 +178,7 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
     MG_CUDA(cudaGetLastError());
     MG_TRY(leave(B));
     MG_CUDA(cudaStreamSynchronize(B->st));
+    for (mg_forest *F : B->groups) MG_TRY(check_kernel_waits(F));
     if (!finite) {
         set_error("residual is not finite");
         return MG_ERR_NOT_CONVERGED;

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <string>
 #include <utility>
+#include <array>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -53,6 +54,10 @@ struct DevLevel {
     FaceItem *ifaces = nullptr;  // the C2F faces alone (interface-only exchange)
     int nifaces = 0;
     int8_t *fkind = nullptr;   // per block face (b * 6 + 2 * axis + side): 0 boundary, 1 same, 2 C2F, 3 F2C
+    bool all_halve = false;  // every block of the next level is a halved block of this one
+    // FP32 smoother launch shape (kind, parameters): {1, ZC, threads, 0, 0} k_smooth32, {2, TY, TZ, D, R}
+    // k_smooth32t; kind 0 = not chosen yet
+    std::array<int32_t, 5> s32{0, 0, 0, 0, 0};
     // adjoint work pools (allocated by the first adjoint call)
     double *a_ub = nullptr, *a_fb = nullptr, *a_z = nullptr, *a_tmp = nullptr;
     Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr}; }
@@ -70,7 +75,8 @@ struct mg_forest {
     std::vector<octmg::DevLevel> L;
     std::vector<void *> allocs;
     double *Ainv = nullptr;
-    int64_t *cmap = nullptr;
+    int64_t *cmap = nullptr;    // coarsest unknowns' offsets in the FP64 pools (natural layout)
+    int64_t *cmap32 = nullptr;  // ... and in the colour-split FP32 pools
     int Nc = 0;
     double *partial = nullptr;  // 2 * kMaxGrid
     double *sums = nullptr;     // 2 doubles on the device
@@ -78,6 +84,7 @@ struct mg_forest {
     double *s64a = nullptr, *s64b = nullptr;  // level-0 FP64 scratch pools
     double *coarse_r = nullptr;               // coarsest-level scratch pool (operator assembly)
     int *flag = nullptr;                      // input-check flag
+    int *kerr = nullptr;                      // set by a device wait that gave up (staged smoother)
     double *AinvT = nullptr;                  // transpose of the coarsest inverses (adjoint cycles)
     // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse
     int np = 1;
@@ -97,7 +104,7 @@ struct mg_forest {
     double fnorm = 0.0;
     // per-kernel-family launch counters (always on) and CUDA-event timing (mg_profile)
     bool prof = false;
-    int64_t nlaunch[16] = {};
+    int64_t nlaunch[32] = {};
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> recs;  // (family, index of the start event; stop = +1)
@@ -108,7 +115,7 @@ namespace octmg {
 // Kernel families for launch counting and timing.
 enum ProfCat {
     P_EXCH64 = 0, P_EXCH32, P_SMOOTH64, P_SMOOTH32, P_RESTR64, P_RESTR32, P_PROL64, P_PROL32, P_COARSE64,
-    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_NCAT
+    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_SMOOTH64_L0, P_SMOOTH32_L0, P_NCAT
 };
 template <typename T> constexpr int cat_of(int cat64) { return sizeof(T) == 8 ? cat64 : cat64 + 1; }
 
@@ -153,6 +160,7 @@ void exchange_any64(mg_forest *F, DevLevel &d, double *u);
 // Device allocation owned by the forest (freed by mg_forest_destroy), zero-filled (defined in solver.cu).
 mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
 mg_status check_ready(mg_forest *F);
+mg_status check_kernel_waits(mg_forest *F);
 mg_status ensure_scratch64(mg_forest *F);
 mg_status create(const mg_config *cfg, mg_forest **out);
 mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev);

@@ -49,6 +49,50 @@ __device__ inline int face_off(int axis, int side, int depth, int i1, int i2, in
     return a * axis_stride(axis, P) + (1 + i1) * axis_stride(t1, P) + (1 + i2) * axis_stride(t2, P);
 }
 
+// Padded coordinates of the cell at `depth` from face (axis, side) with tangential interior coordinates (i1, i2).
+__device__ inline void face_xyz(int axis, int side, int depth, int i1, int i2, int n, int &X, int &Y, int &Z) {
+    const int a = side ? (n + 1 - depth) : depth;
+    const int t1 = axis == 0 ? 1 : 0;
+    const int t2 = axis == 2 ? 1 : 2;
+    int c[3];
+    c[axis] = a;
+    c[t1] = 1 + i1;
+    c[t2] = 1 + i2;
+    X = c[0];
+    Y = c[1];
+    Z = c[2];
+}
+
+// Storage of a padded cell (X, Y, Z) of block b.
+//   FP64 pools: natural order, block b at b * bs, x fastest.
+//   FP32 pools: colour-split ("red-black ordered"): a block is two halves holding the cells with X + Y + Z even
+//   (half 0) and odd (half 1); inside a half, row (Y, Z) holds the (n+2)/2 cells of that parity at X / 2, padded
+//   to half_row(P) entries.  A colour half-sweep then reads the other colour's half and writes its own with unit
+//   stride.
+// Row length of one half in the FP32 split layout: the (n+2)/2 cells of a parity, padded to a multiple of 4 floats
+// so that every row, plane and half starts on a 16-byte boundary (bulk-copy granularity).
+__host__ __device__ constexpr int half_row(int P) { return ((P >> 1) + 3) & ~3; }
+
+template <typename T> struct Lay;
+template <> struct Lay<double> {
+    __device__ static int64_t at(const LevelGeom &g, int64_t b, int X, int Y, int Z) {
+        return b * g.bs + off3(X, Y, Z, g.P);
+    }
+};
+template <> struct Lay<float> {
+    __host__ __device__ static int64_t at(const LevelGeom &g, int64_t b, int X, int Y, int Z) {
+        const int P = g.P, hp = half_row(g.P);
+        const int64_t half = static_cast<int64_t>(P) * P * hp;
+        return b * g.bs + ((X + Y + Z) & 1) * half + (static_cast<int64_t>(Z) * P + Y) * hp + (X >> 1);
+    }
+};
+template <typename T>
+__device__ inline int64_t fidx(const LevelGeom &g, int64_t b, int axis, int side, int depth, int i1, int i2) {
+    int X, Y, Z;
+    face_xyz(axis, side, depth, i1, i2, g.n, X, Y, Z);
+    return Lay<T>::at(g, b, X, Y, Z);
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Quadratic coarse-to-fine weights (Sec. 3.3.2).  Lagrange basis through three coarse bases evaluated at the
 // fine-ghost target; distances in coarse cells.
@@ -166,7 +210,7 @@ __device__ inline double apply_at(const double *__restrict__ u, const Coef &cf, 
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, bool KIND_K>
 static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g) {
-    const int n = g.n, P = g.P, lg = g.lg, h = n >> 1;
+    const int n = g.n, lg = g.lg, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -174,18 +218,16 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
         const int r = static_cast<int>(t) & ((1 << (2 * lg)) - 1);
         const int i1 = r & (n - 1), i2 = r >> lg;
         const FaceItem F = items[it];
-        T *ub = u + F.blk * g.bs;
         T val;
         if (F.kind == FK_BND) {
-            const T in = ub[face_off(F.axis, F.side, 1, i1, i2, n, P)];
+            const T in = u[fidx<T>(g, F.blk, F.axis, F.side, 1, i1, i2)];
             val = KIND_K ? in : -in;
         } else if (F.kind == FK_SAME) {
-            val = u[F.nbr * g.bs + face_off(F.axis, 1 - F.side, 1, i1, i2, n, P)];
+            val = u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, i1, i2)];
         } else {
-            const T *uc = u + F.nbr * g.bs;
             const int yc = F.seg1 * h + (i1 >> 1), zc = F.seg2 * h + (i2 >> 1);
             if (KIND_K) {
-                val = uc[face_off(F.axis, 1 - F.side, 1, yc, zc, n, P)];
+                val = u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, yc, zc)];
             } else {
                 const int a1 = i1 & 1, a2 = i2 & 1;
                 const int cy = yc == 0 ? 1 : (yc == n - 1 ? 2 : 0);
@@ -197,9 +239,9 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
                         const int y = yc + c_base[cy][b], z = zc + c_base[cz][c];
-                        T e = w_normal<T>(0) * uc[face_off(F.axis, 1 - F.side, 1, y, z, n, P)];
-                        e = fma(w_normal<T>(1), uc[face_off(F.axis, 1 - F.side, 2, y, z, n, P)], e);
-                        e = fma(w_normal<T>(2), uc[face_off(F.axis, 1 - F.side, 3, y, z, n, P)], e);
+                        T e = w_normal<T>(0) * u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, y, z)];
+                        e = fma(w_normal<T>(1), u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 2, y, z)], e);
+                        e = fma(w_normal<T>(2), u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 3, y, z)], e);
                         accb = fma(w_tang<T>(cy, a1, b), e, accb);
                     }
                     acc = fma(w_tang<T>(cz, a2, c), accb, acc);
@@ -207,7 +249,7 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
                 val = acc;
             }
         }
-        ub[face_off(F.axis, F.side, 0, i1, i2, n, P)] = val;
+        u[fidx<T>(g, F.blk, F.axis, F.side, 0, i1, i2)] = val;
     }
 }
 
@@ -221,7 +263,7 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
 template <typename T, int MODE, bool FLUX>
 static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
                                 LevelGeom g) {
-    const int n = g.n, P = g.P, lgh = g.lg - 1, h = n >> 1;
+    const int n = g.n, lgh = g.lg - 1, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lgh);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -229,7 +271,6 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
         const int r = static_cast<int>(t) & ((1 << (2 * lgh)) - 1);
         const int p = r & (h - 1), q = r >> lgh;
         const SegItem S = items[it];
-        const int64_t cb = S.coarse * g.bs, fb = S.fine * g.bs;
         const int fs = 1 - S.side;
         const int yc = S.s1 * h + p, zc = S.s2 * h + q;
         T val;
@@ -240,26 +281,26 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
 #pragma unroll
                 for (int b = 0; b < 2; ++b)
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) s += u[fb + face_off(S.axis, fs, d, 2 * p + a, 2 * q + b, n, P)];
+                    for (int a = 0; a < 2; ++a) s += u[fidx<T>(g, S.fine, S.axis, fs, d, 2 * p + a, 2 * q + b)];
             val = T(0.125) * s;
         } else {
-            const int64_t gC = cb + face_off(S.axis, S.side, 1, yc, zc, n, P);
-            const int64_t g0c = cb + face_off(S.axis, S.side, 0, yc, zc, n, P);
+            const int64_t gC = fidx<T>(g, S.coarse, S.axis, S.side, 1, yc, zc);
+            const int64_t g0c = fidx<T>(g, S.coarse, S.axis, S.side, 0, yc, zc);
             const T uC = u[gC];
             T flux = T(0);
 #pragma unroll
             for (int b = 0; b < 2; ++b)
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
-                    const int64_t g0 = fb + face_off(S.axis, fs, 0, 2 * p + a, 2 * q + b, n, P);
-                    const int64_t g1 = fb + face_off(S.axis, fs, 1, 2 * p + a, 2 * q + b, n, P);
+                    const int64_t g0 = fidx<T>(g, S.fine, S.axis, fs, 0, 2 * p + a, 2 * q + b);
+                    const int64_t g1 = fidx<T>(g, S.fine, S.axis, fs, 1, 2 * p + a, 2 * q + b);
                     const T Tj = face_coef<T, MODE>(cf, fs ? g0 : g1, fs ? g1 : g0, S.axis);
                     flux = fma(Tj, u[g0] - u[g1], flux);
                 }
             const T Tc = face_coef<T, MODE>(cf, S.side ? g0c : gC, S.side ? gC : g0c, S.axis);
             val = uC - flux / (T(MODE == 1 ? 8 : 2) * Tc);
         }
-        u[cb + face_off(S.axis, S.side, 0, yc, zc, n, P)] = val;
+        u[fidx<T>(g, S.coarse, S.axis, S.side, 0, yc, zc)] = val;
     }
 }
 
@@ -282,23 +323,55 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg - 1);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = static_cast<int>(t & ((n >> 1) - 1));
+        const int j = static_cast<int>(t & ((n >> 1) - 1));
         const int y = static_cast<int>((t >> (lg - 1)) & (n - 1));
         const int z = static_cast<int>((t >> (2 * lg - 1)) & (n - 1));
         const int64_t b = t >> (3 * lg - 1);
-        const int x = 2 * m + ((y + z + colour) & 1);
-        const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
+        const int x = 2 * j + ((y + z + colour) & 1);
         T val;
-        if constexpr (MODE == 1) {
-            val = sten1(u, cf, gi, P, f[gi]) * cf.dinv[gi];
-        } else if constexpr (MODE == 0) {
-            val = fma(h2[b], f[gi], sten0<T>(u, gi, P)) * T(1.0 / 6.0);
+        if constexpr (sizeof(T) == 4) {
+            // colour-split: this colour's cells have padded parity s = colour ^ 1; in row (Y, Z) the cell X = 2m + o
+            // (o = (s + Y + Z) & 1) sits at m of half s, its x-neighbours at m - 1 + o and m + o of half s ^ 1, its
+            // y- and z-neighbours at m in the adjacent rows of half s ^ 1
+            const int hp = half_row(P);
+            const int64_t half = static_cast<int64_t>(P) * P * hp;
+            const int s = colour ^ 1;
+            const int Y = y + 1, Z = z + 1;
+            const int o = (s + Y + Z) & 1;
+            const int m = (x + 1) >> 1;
+            const int64_t row = (static_cast<int64_t>(Z) * P + Y) * hp;
+            const int64_t own = b * g.bs + s * half + row + m;
+            const int64_t oth = b * g.bs + (s ^ 1) * half + row;
+            const int64_t ixm = oth + m - 1 + o, ixp = ixm + 1, iym = oth - hp + m, iyp = oth + hp + m;
+            const int64_t izm = oth - static_cast<int64_t>(P) * hp + m, izp = oth + static_cast<int64_t>(P) * hp + m;
+            if constexpr (MODE == 0) {
+                const float S = ((u[ixm] + u[ixp]) + (u[iym] + u[iyp])) + (u[izm] + u[izp]);
+                val = T(fmaf(float(h2[b]), float(f[own]), S) * (1.0f / 6.0f));
+            } else {
+                const float *kap = cf.kap;
+                const float k0 = kap[own];
+                const float a0 = frcp(k0 + kap[ixm]), a1 = frcp(k0 + kap[ixp]);
+                const float b0 = frcp(k0 + kap[iym]), b1 = frcp(k0 + kap[iyp]);
+                const float c0 = frcp(k0 + kap[izm]), c1 = frcp(k0 + kap[izp]);
+                float sacc = a0 * u[ixm];
+                sacc = fmaf(a1, u[ixp], sacc);
+                sacc = fmaf(b0, u[iym], sacc);
+                sacc = fmaf(b1, u[iyp], sacc);
+                sacc = fmaf(c0, u[izm], sacc);
+                sacc = fmaf(c1, u[izp], sacc);
+                const float D = ((a0 + a1) + (b0 + b1)) + (c0 + c1);
+                val = T(fmaf(float(h2[b]), float(f[own]), 2.0f * sacc) * frcp(2.0f * D));
+            }
+            u[own] = val;
         } else {
-            float S, D;
-            sten2(reinterpret_cast<const float *>(u), cf.kap, gi, P, S, D);
-            val = T(fmaf(float(h2[b]), float(f[gi]), S) * frcp(D));
+            const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
+            if constexpr (MODE == 1) {
+                val = sten1(u, cf, gi, P, f[gi]) * cf.dinv[gi];
+            } else {
+                val = fma(h2[b], f[gi], sten0<T>(u, gi, P)) * T(1.0 / 6.0);
+            }
+            u[gi] = val;
         }
-        u[gi] = val;
         if (nbr6 && (x == 0 || x == n - 1 || y == 0 || y == n - 1 || z == 0 || z == n - 1)) {
             const int c[3] = {x, y, z};
 #pragma unroll
@@ -309,12 +382,408 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
                     const int nb = nbr6[b * 6 + 2 * axis + side];
                     const int i1 = axis == 0 ? y : x, i2 = axis == 2 ? y : z;
                     if (nb >= 0)
-                        u[static_cast<int64_t>(nb) * g.bs + face_off(axis, 1 - side, 0, i1, i2, n, P)] = val;
+                        u[fidx<T>(g, nb, axis, 1 - side, 0, i1, i2)] = val;
                     else if (nb == -1)
-                        u[b * g.bs + face_off(axis, side, 0, i1, i2, n, P)] = -val;
+                        u[fidx<T>(g, b, axis, side, 0, i1, i2)] = -val;
                 }
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// FP32 half-sweep on colour-split blocks with the block edge n = 2^LG fixed at compile time, so that every
+// neighbour of a cell is an immediate offset from a few row pointers and all in-block offsets are 32-bit.
+//
+// Thread (b, j, y, z-group) updates the ZC cells x = 2j + c_z, z = z0 .. z0 + ZC - 1 of one z-column, where
+// c_z = (y + z + colour) & 1.  With H = half_row(P) and row r_z = ((z+1) P + y+1) H of either half, such a cell sits
+// at r_z + j + c_z of its colour's half.  Of the other half it reads r_z + j and r_z + j + 1 (its x-neighbours,
+// whatever c_z), r_z -/+ H + j + c_z (y) and r_(z-/+1) + j + c_z (z).  Because c_(z+-1) = 1 - c_z, the z-neighbours
+// of a column cell are x-neighbour pairs of the adjacent column cells, so the column loads the pairs of its ZC
+// rows, one value in each of the two rows beyond, and the y-neighbours: 4 ZC + 2 values of u and of kappa instead
+// of 6 ZC.  All loads of the column are issued before any store (the other half is not written by the sweep, but
+// the compiler cannot prove it), which keeps 10 ZC + 4 independent loads per thread in flight.
+//
+// Write-through as in k_smooth: a cell on a block face stores its new value into the same-level neighbour's ghost
+// that mirrors it (same half, offset +-n along the axis, i.e. +-n/2, +-n H or +-n P H elements), or -value into
+// its own reflection ghost (the other half, at the neighbour position it read).  Mirrored ghosts belong to the
+// colour being updated, which this half-sweep never reads; a reflection ghost is read only by the cell that writes
+// it, before the write.  x faces concern one lane of a row (j = 0 with c = 0, j = n/2 - 1 with c = 1) and take a
+// short path of their own; y and z faces are uniform over a row.
+// ------------------------------------------------------------------------------------------------------------
+template <int MODE, int LG, int ZC>
+__device__ __forceinline__ void smooth32_column(float *__restrict__ u, const float *__restrict__ f,
+                                                const float *__restrict__ kap, const float *__restrict__ h2,
+                                                int64_t bs, int colour, const int32_t *__restrict__ nbr6,
+                                                int64_t t) {
+    constexpr int n = 1 << LG, NH = n / 2, P = n + 2, HP = half_row(P), PL = P * HP, HALF = P * PL;
+    constexpr int LZ = ZC == 1 ? 0 : (ZC == 2 ? 1 : (ZC == 4 ? 2 : 3));
+    static_assert((1 << LZ) == ZC && ZC <= n, "column length");
+    constexpr int SH = 3 * LG - 1 - LZ;  // log2(columns per block)
+    const int r = static_cast<int>(t) & ((1 << SH) - 1);
+    const int64_t b = t >> SH;
+    const int j = r & (NH - 1);
+    const int y = (r >> (LG - 1)) & (n - 1);
+    const int z0 = (r >> (2 * LG - 1)) << LZ;
+    const int s = colour ^ 1;  // padded parity of this colour's cells
+    const int c0 = (y + z0 + colour) & 1;
+    const int row0 = ((z0 + 1) * P + (y + 1)) * HP + j;  // r_z0 + j, inside a half
+    const int io = (s ^ 1) * HALF + row0;                 // other half at r_z0 + j
+    const int ioc = io + c0;
+    const int iw = s * HALF + row0 + c0;                  // own half, cell z0 (odd dz: -/+ 1)
+    const int64_t base = b * bs;
+    float *ub = u + base;
+    const float *fb = f + base, *kb = kap + base;
+    // ---- loads -------------------------------------------------------------------------------------
+    float xr0[ZC], xr1[ZC], ym[ZC], yp[ZC], fv[ZC];
+    float kx0[ZC], kx1[ZC], kym[ZC], kyp[ZC], k0[ZC];
+    float kzlo = 0.f, kzhi = 0.f;
+    constexpr int odd = (ZC - 1) & 1;  // c of the last cell is c0 ^ odd
+    const float zlo = ub[ioc - PL];
+    const float zhi = ub[(odd ? io + 1 - c0 : ioc) + ZC * PL];
+#pragma unroll
+    for (int dz = 0; dz < ZC; ++dz) {
+        xr0[dz] = ub[io + dz * PL];
+        xr1[dz] = ub[io + dz * PL + 1];
+        const int ic = (dz & 1) ? io + 1 - c0 : ioc;  // other half at r_z + j + c_z
+        ym[dz] = ub[ic + dz * PL - HP];
+        yp[dz] = ub[ic + dz * PL + HP];
+        fv[dz] = __ldg(fb + ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL);
+    }
+    if constexpr (MODE == 2) {
+        kzlo = __ldg(kb + ioc - PL);
+        kzhi = __ldg(kb + (odd ? io + 1 - c0 : ioc) + ZC * PL);
+#pragma unroll
+        for (int dz = 0; dz < ZC; ++dz) {
+            kx0[dz] = __ldg(kb + io + dz * PL);
+            kx1[dz] = __ldg(kb + io + dz * PL + 1);
+            const int ic = (dz & 1) ? io + 1 - c0 : ioc;
+            kym[dz] = __ldg(kb + ic + dz * PL - HP);
+            kyp[dz] = __ldg(kb + ic + dz * PL + HP);
+            k0[dz] = __ldg(kb + ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL);
+        }
+    }
+    const float hb = __ldg(h2 + b);
+    // ---- updates -----------------------------------------------------------------------------------
+    float val[ZC];
+#pragma unroll
+    for (int dz = 0; dz < ZC; ++dz) {
+        const int c = c0 ^ (dz & 1);
+        const float zm = dz == 0 ? zlo : (c ? xr1[dz - 1] : xr0[dz - 1]);
+        const float zp = dz == ZC - 1 ? zhi : (c ? xr1[dz + 1] : xr0[dz + 1]);
+        if constexpr (MODE == 2) {
+            const float kzm = dz == 0 ? kzlo : (c ? kx1[dz - 1] : kx0[dz - 1]);
+            const float kzp = dz == ZC - 1 ? kzhi : (c ? kx1[dz + 1] : kx0[dz + 1]);
+            const float kc = k0[dz];
+            const float a0 = frcp(kc + kx0[dz]), a1 = frcp(kc + kx1[dz]);
+            const float b0 = frcp(kc + kym[dz]), b1 = frcp(kc + kyp[dz]);
+            const float e0 = frcp(kc + kzm), e1 = frcp(kc + kzp);
+            float sacc = a0 * xr0[dz];
+            sacc = fmaf(a1, xr1[dz], sacc);
+            sacc = fmaf(b0, ym[dz], sacc);
+            sacc = fmaf(b1, yp[dz], sacc);
+            sacc = fmaf(e0, zm, sacc);
+            sacc = fmaf(e1, zp, sacc);
+            const float D = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
+            val[dz] = fmaf(hb, fv[dz], 2.0f * sacc) * frcp(2.0f * D);
+        } else {
+            const float S = ((xr0[dz] + xr1[dz]) + (ym[dz] + yp[dz])) + (zm + zp);
+            val[dz] = fmaf(hb, fv[dz], S) * (1.0f / 6.0f);
+        }
+    }
+#pragma unroll
+    for (int dz = 0; dz < ZC; ++dz) ub[((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL] = val[dz];
+    // ---- write-through -----------------------------------------------------------------------------
+    if (!nbr6) return;
+#pragma unroll
+    for (int dz = 0; dz < ZC; ++dz) {
+        const int c = c0 ^ (dz & 1);
+        if ((j == 0 && c == 0) || (j == NH - 1 && c == 1)) {  // x face, side c
+            const int q = row0 + dz * PL + c;                  // the cell inside its half
+            const int nbv = nbr6[b * 6 + c];
+            if (nbv >= 0) u[nbv * bs + s * HALF + q + (c ? -NH : NH)] = val[dz];
+            else if (nbv == -1) ub[(s ^ 1) * HALF + q] = -val[dz];
+        }
+    }
+    if (y == 0 || y == n - 1 || z0 == 0 || z0 + ZC == n) {
+#pragma unroll
+        for (int dz = 0; dz < ZC; ++dz) {
+            const int c = c0 ^ (dz & 1);
+            const int q = row0 + dz * PL + c;
+            const int z = z0 + dz;
+#pragma unroll
+            for (int axis = 1; axis < 3; ++axis) {
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    if ((axis == 1 ? y : z) != (side ? n - 1 : 0)) continue;
+                    const int Dm = axis == 1 ? n * HP : n * PL, E = axis == 1 ? HP : PL;
+                    const int nbv = nbr6[b * 6 + 2 * axis + side];
+                    if (nbv >= 0) u[nbv * bs + s * HALF + q + (side ? -Dm : Dm)] = val[dz];
+                    else if (nbv == -1) ub[(s ^ 1) * HALF + q + (side ? E : -E)] = -val[dz];
+                }
+            }
+        }
+    }
+}
+
+// One column per thread over `total` columns.
+template <int MODE, int LG, int ZC>
+static __global__ void __launch_bounds__(512) k_smooth32(float *__restrict__ u, const float *__restrict__ f,
+                                                         const float *__restrict__ kap, const float *__restrict__ h2,
+                                                         int64_t total, int64_t bs, int colour,
+                                                         const int32_t *__restrict__ nbr6) {
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t < total) smooth32_column<MODE, LG, ZC>(u, f, kap, h2, bs, colour, nbr6, t);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Shared-memory staging with the bulk-copy (TMA) engine: mbarrier helpers.  One thread arms a barrier with the
+// byte count of the copies it issues; every consumer polls the barrier's phase with a bounded wait.
+// ------------------------------------------------------------------------------------------------------------
+__device__ inline uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void mbar_arm(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy completing on `bar`; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ inline void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ inline bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Waits for phase `parity` of `bar` to complete; gives up after about 0.1 s and returns false.
+__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (it > 32) __nanosleep(128);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// FP32 half-sweep with the other colour's planes staged in shared memory by bulk copies (block edge n = 2^LG,
+// colour-split pools with H = half_row(P)).
+//
+// A CTA owns block b, interior rows y0 .. y0 + TY - 1 and planes z0 .. z0 + TZ - 1; thread (j, yl) updates the cells
+// x = 2j + c of rows y0 + yl + i TY/R (i < R) in every plane, marching in z.  Per plane z the CTA needs, of the other half, rows
+// y0 - 1 .. y0 + TY of planes z - 1, z, z + 1 (u, and kappa for variable k) and, of its own half, rows y0 .. y0 + TY - 1
+// of plane z (f, and kappa).  Each such plane segment is one contiguous run of (TY + 2) H or TY H floats, fetched by
+// one bulk copy into a ring of 3 + D (other half) or 1 + D (own half) slots, D planes ahead of the plane being
+// updated; one elected thread issues the copies and arms the slot's mbarrier, every thread waits on it.
+//
+// Per cell the thread reads from shared memory its x-neighbour pair of plane z + 1 (positions j, j + 1 of row yl + 1;
+// the pair of plane z was read one plane earlier and gives the x-neighbours now, that of plane z - 1 the z-minus
+// neighbour at position c), its y-neighbours (rows yl and yl + 2 at j + c) and its own f and kappa: 4 + 4 + 2 shared
+// loads instead of 14.  New values go straight to global memory (the own half is not staged), with the same
+// write-through of block-face cells as k_smooth32.  No staged value is written during the sweep except reflection
+// ghosts, which only the writing cell reads, before it writes.
+//
+// A wait that runs out sets *err and the CTA stops after the current plane (all threads agree through the
+// per-plane __syncthreads_or), after its elected thread has waited, again bounded, for the copies it issued.
+// ------------------------------------------------------------------------------------------------------------
+template <int MODE, int LG, int R>
+static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u, const float *__restrict__ f,
+                                                          const float *__restrict__ kap, const float *__restrict__ h2,
+                                                          int64_t bs, int colour, const int32_t *__restrict__ nbr6,
+                                                          int TY, int TZ, int D, int *__restrict__ err) {
+    constexpr int n = 1 << LG, NH = n / 2, P = n + 2, H = half_row(P), PL = P * H, HALF = P * PL;
+    constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int RO = 3 + D, RW = 1 + D;
+    const int so = (TY + 2) * H, sw = TY * H;  // floats per slot
+    float *ou = reinterpret_cast<float *>(smem_raw);  // other half: u slots, then kappa slots
+    float *ok = ou + RO * so;
+    float *wf = ou + NA * RO * so;                      // own half: f slots, then kappa slots
+    float *wk = wf + RW * sw;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wf + NA * RW * sw);  // RO + RW barriers
+
+    const int nty = n / TY;
+    const int ty = static_cast<int>(blockIdx.x % nty);
+    const int64_t rest = blockIdx.x / nty;
+    const int tz = static_cast<int>(rest % (n / TZ));
+    const int64_t b = rest / (n / TZ);
+    const int y0 = ty * TY, z0 = tz * TZ;
+    const int s = colour ^ 1;
+    const int tid = threadIdx.x;
+    const int TW = TY / R;  // row stride between a thread's rows
+    const int j = tid & (NH - 1), yl0 = tid >> (LG - 1);
+    const int64_t base = b * bs;
+    const float *gou = u + base + (s ^ 1) * HALF, *gok = kap + base + (s ^ 1) * HALF;
+    const float *gwf = f + base + s * HALF, *gwk = kap + base + s * HALF;
+
+    // other-half plane io = padded Z z0 + io (io = 0 .. TZ + 1), rows y0 .. y0 + TY + 1, into slot `sl`
+    const auto issue_oth = [&](int io, int sl) {
+        const int64_t off = (static_cast<int64_t>(z0 + io) * P + y0) * H;
+        mbar_arm(&bar[sl], NA * so * 4);
+        bulk_load(ou + sl * so, gou + off, so * 4, &bar[sl]);
+        if constexpr (MODE == 2) bulk_load(ok + sl * so, gok + off, so * 4, &bar[sl]);
+    };
+    // own-half plane iw = padded Z z0 + 1 + iw (iw = 0 .. TZ - 1), rows y0 + 1 .. y0 + TY
+    const auto issue_own = [&](int iw, int sl) {
+        const int64_t off = (static_cast<int64_t>(z0 + 1 + iw) * P + y0 + 1) * H;
+        mbar_arm(&bar[RO + sl], NA * sw * 4);
+        bulk_load(wf + sl * sw, gwf + off, sw * 4, &bar[RO + sl]);
+        if constexpr (MODE == 2) bulk_load(wk + sl * sw, gwk + off, sw * 4, &bar[RO + sl]);
+    };
+    int n_oth = 0, n_own = 0, iso = 0, isw = 0;  // copies issued and next refill slots (elected thread)
+    if (tid == 0) {
+        for (int i = 0; i < RO + RW; ++i) mbar_init(&bar[i], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (; n_oth < RO && n_oth < TZ + 2; ++n_oth) issue_oth(n_oth, n_oth);
+        for (; n_own < RW && n_own < TZ; ++n_own) issue_own(n_own, n_own);
+    }
+    const float hb = __ldg(h2 + b);
+    int bad = 0;
+    bad |= !mbar_wait(&bar[0], 0);
+    bad |= !mbar_wait(&bar[1], 0);
+    float pm[R][2], pc[R][2], qm[R][2], qc[R][2];  // x-neighbour pairs of planes z - 1 and z (u, kappa)
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int rc = (yl0 + rr * TW + 1) * H + j;
+        pm[rr][0] = ou[rc];
+        pm[rr][1] = ou[rc + 1];
+        pc[rr][0] = ou[so + rc];
+        pc[rr][1] = ou[so + rc + 1];
+        if constexpr (MODE == 2) {
+            qm[rr][0] = ok[rc];
+            qm[rr][1] = ok[rc + 1];
+            qc[rr][0] = ok[so + rc];
+            qc[rr][1] = ok[so + rc + 1];
+        }
+    }
+    // ring positions: plane z + 1 of the other half (slot sn, phase pn), plane z (sc), own plane z (sw_, pw)
+    int sn = 2 % RO, pn = 2 / RO, sc = 1, sw_ = 0, pw = 0;
+    int consumed_oth = 2, consumed_own = 0;
+    for (int k = 0; k < TZ; ++k) {
+        const int z = z0 + k;
+        bad |= !mbar_wait(&bar[sn], pn & 1);
+        bad |= !mbar_wait(&bar[RO + sw_], pw & 1);
+        consumed_oth = k + 3;
+        consumed_own = k + 1;
+        const float *on = ou + sn * so, *oc = ou + sc * so;
+        const float *kn = ok + sn * so, *kc_ = ok + sc * so;
+        const float *fw = wf + sw_ * sw, *kw = wk + sw_ * sw;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            const int yl = yl0 + rr * TW, y = y0 + yl;
+            const int c = (y + z + colour) & 1;
+            const int rc = (yl + 1) * H + j;
+            const float pn0 = on[rc], pn1 = on[rc + 1];
+            const float ym = oc[rc - H + c], yp = oc[rc + H + c];
+            const float fv = fw[yl * H + j + c];
+            const float zm = c ? pm[rr][1] : pm[rr][0], zp = c ? pn1 : pn0;
+            float val;
+            float qn0 = 0.f, qn1 = 0.f;
+            if constexpr (MODE == 2) {
+                qn0 = kn[rc];
+                qn1 = kn[rc + 1];
+                const float kym = kc_[rc - H + c], kyp = kc_[rc + H + c];
+                const float k0 = kw[yl * H + j + c];
+                const float kzm = c ? qm[rr][1] : qm[rr][0], kzp = c ? qn1 : qn0;
+                const float a0 = frcp(k0 + qc[rr][0]), a1 = frcp(k0 + qc[rr][1]);
+                const float b0 = frcp(k0 + kym), b1 = frcp(k0 + kyp);
+                const float e0 = frcp(k0 + kzm), e1 = frcp(k0 + kzp);
+                float sacc = a0 * pc[rr][0];
+                sacc = fmaf(a1, pc[rr][1], sacc);
+                sacc = fmaf(b0, ym, sacc);
+                sacc = fmaf(b1, yp, sacc);
+                sacc = fmaf(e0, zm, sacc);
+                sacc = fmaf(e1, zp, sacc);
+                const float Dn = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
+                val = fmaf(hb, fv, 2.0f * sacc) * frcp(2.0f * Dn);
+            } else {
+                const float S = ((pc[rr][0] + pc[rr][1]) + (ym + yp)) + (zm + zp);
+                val = fmaf(hb, fv, S) * (1.0f / 6.0f);
+            }
+            const int q = ((z + 1) * P + (y + 1)) * H + j + c;  // the cell, in either half
+            u[base + s * HALF + q] = val;
+            if (nbr6) {
+                if ((j == 0 && c == 0) || (j == NH - 1 && c == 1)) {  // x face, side c
+                    const int nbv = nbr6[b * 6 + c];
+                    if (nbv >= 0) u[nbv * bs + s * HALF + q + (c ? -NH : NH)] = val;
+                    else if (nbv == -1) u[base + (s ^ 1) * HALF + q] = -val;
+                }
+                if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
+#pragma unroll
+                    for (int axis = 1; axis < 3; ++axis) {
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            if ((axis == 1 ? y : z) != (side ? n - 1 : 0)) continue;
+                            const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
+                            const int nbv = nbr6[b * 6 + 2 * axis + side];
+                            if (nbv >= 0) u[nbv * bs + s * HALF + q + (side ? -Dm : Dm)] = val;
+                            else if (nbv == -1) u[base + (s ^ 1) * HALF + q + (side ? E : -E)] = -val;
+                        }
+                    }
+                }
+            }
+            pm[rr][0] = pc[rr][0];
+            pm[rr][1] = pc[rr][1];
+            pc[rr][0] = pn0;
+            pc[rr][1] = pn1;
+            if constexpr (MODE == 2) {
+                qm[rr][0] = qc[rr][0];
+                qm[rr][1] = qc[rr][1];
+                qc[rr][0] = qn0;
+                qc[rr][1] = qn1;
+            }
+        }
+        sc = sn;
+        if (++sn == RO) { sn = 0; ++pn; }
+        if (++sw_ == RW) { sw_ = 0; ++pw; }
+        // every thread is done with other-half plane k and own plane k: refill their slots
+        if (__syncthreads_or(bad)) break;
+        if (tid == 0) {
+            if (n_oth < TZ + 2) { issue_oth(n_oth++, iso); if (++iso == RO) iso = 0; }
+            if (n_own < TZ) { issue_own(n_own++, isw); if (++isw == RW) isw = 0; }
+        }
+    }
+    if (bad && tid == 0) {
+        atomicOr(err, 1);
+        // let the copies still in flight land before the CTA's shared memory is released
+        for (int io = consumed_oth; io < n_oth; ++io) mbar_wait(&bar[io % RO], (io / RO) & 1);
+        for (int iw = consumed_own; iw < n_own; ++iw) mbar_wait(&bar[RO + iw % RW], (iw / RW) & 1);
+    }
+}
+
+// Point-form residual at padded cell (X, Y, Z) of block b, any layout (used by the FP32 kernels).
+template <typename T, int MODE>
+__device__ inline T residual_xyz(const T *__restrict__ u, const T *__restrict__ f, const Coef &cf,
+                                 const LevelGeom &g, int64_t b, int X, int Y, int Z, T ih2) {
+    const int64_t i0 = Lay<T>::at(g, b, X, Y, Z);
+    const int64_t nb[6] = {Lay<T>::at(g, b, X - 1, Y, Z), Lay<T>::at(g, b, X + 1, Y, Z),
+                           Lay<T>::at(g, b, X, Y - 1, Z), Lay<T>::at(g, b, X, Y + 1, Z),
+                           Lay<T>::at(g, b, X, Y, Z - 1), Lay<T>::at(g, b, X, Y, Z + 1)};
+    const T u0 = u[i0];
+    if constexpr (MODE == 0) {
+        const T S = ((u[nb[0]] + u[nb[1]]) + (u[nb[2]] + u[nb[3]])) + (u[nb[4]] + u[nb[5]]);
+        return fma(fma(T(-6), u0, S), ih2, f[i0]);
+    } else {
+        const float k0 = cf.kap[i0];
+        float S = 0.0f, D = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float a = frcp(k0 + cf.kap[nb[q]]);
+            S = fmaf(a, float(u[nb[q]]), S);
+            D += a;
+        }
+        return T(fmaf(2.0f * fmaf(-D, float(u0), S), float(ih2), float(f[i0])));
     }
 }
 
@@ -336,11 +805,17 @@ static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__r
         const int Z = static_cast<int>((t >> (2 * lgc)) & (nc - 1));
         const int64_t B = t >> (3 * lgc);
         const XferItem xi = xf[B];
-        const int64_t gcell = B * gc.bs + off3(X + 1, Y + 1, Z + 1, gc.P);
+        const int64_t gcell = Lay<T>::at(gc, B, X + 1, Y + 1, Z + 1);
         uc[gcell] = T(0);
+        const auto res = [&](int64_t bb, int xx, int yy, int zz, T ih2) {
+            if constexpr (sizeof(T) == 4)
+                return residual_xyz<T, MODE>(u, f, cf, gf, bb, xx, yy, zz, ih2);
+            else
+                return residual_at<T, MODE>(u, f, cf, bb * gf.bs + off3(xx, yy, zz, gf.P), gf.P, ih2);
+        };
         if (xi.kind == XF_COPY) {
             const int64_t b = xi.src[0];
-            fc[gcell] = residual_at<T, MODE>(u, f, cf, b * gf.bs + off3(X + 1, Y + 1, Z + 1, gf.P), gf.P, ih2f[b]);
+            fc[gcell] = res(b, X + 1, Y + 1, Z + 1, ih2f[b]);
             continue;
         }
         int64_t b;
@@ -365,10 +840,171 @@ static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__r
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-                for (int a = 0; a < 2; ++a)
-                    s += residual_at<T, MODE>(u, f, cf, b * gf.bs + off3(x0 + a + 1, y0 + bb + 1, z0 + c + 1, gf.P),
-                                              gf.P, ih2);
+                for (int a = 0; a < 2; ++a) s += res(b, x0 + a + 1, y0 + bb + 1, z0 + c + 1, ih2);
         fc[gcell] = T(0.125) * s;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// FP32 residual + restriction for a level whose blocks all halve (fine edge n = 2^LG, coarse n/2), colour-split
+// pools on both sides.  One thread per coarse cell (X, Y, Z): its 8 children are the fine padded cells
+// (2X + i, 2Y + j, 2Z + k), i, j, k in {1, 2}, and the 32 distinct values of u (and of kappa) their 7-point stencils
+// touch lie in the 4^3 box i, j, k in {0..3} without its edges.  In the split layout box cell (i, j, k) sits at
+//     ((i + j + k) & 1) * HALF + (k P + j) H + (i >> 1),   H = half_row(P),
+// from the box's corner offset ((2Z P + 2Y) H + X), so every load is an immediate offset from one pointer; the
+// interior faces of the box are shared by two children and their coefficients are evaluated once.
+// ------------------------------------------------------------------------------------------------------------
+template <int LG>
+struct Box32 {
+    static constexpr int n = 1 << LG, P = n + 2, HP = half_row(P), HALF = P * P * HP;
+    __device__ static constexpr int off(int i, int j, int k) {
+        return ((i + j + k) & 1) * HALF + (k * P + j) * HP + (i >> 1);
+    }
+};
+
+template <int MODE, int LG>
+static __global__ void __launch_bounds__(256) k_residual_restrict32(
+        const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
+        const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
+        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc) {
+    using Bx = Box32<LG>;
+    constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), HALFc = Pc * Pc * HPc;
+    const int64_t total = static_cast<int64_t>(nbc) << (3 * LC);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(t) & ((1 << (3 * LC)) - 1);
+        const int64_t B = t >> (3 * LC);
+        const int X = r & (nc - 1), Y = (r >> LC) & (nc - 1), Z = r >> (2 * LC);
+        const int64_t b = xf[B].src[0];
+        const int64_t corner = b * bsf + (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;
+        const float *ub = u + corner;
+        float U[4][4][4], K[4][4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int out = (i == 0 || i == 3) + (j == 0 || j == 3) + (k == 0 || k == 3);
+                    if (out > 1) continue;
+                    U[k][j][i] = ub[Bx::off(i, j, k)];
+                    if constexpr (MODE == 2) K[k][j][i] = __ldg(kap + corner + Bx::off(i, j, k));
+                }
+        const float ih2 = __ldg(ih2f + b);
+        float sum = 0.0f;
+#pragma unroll
+        for (int k = 1; k < 3; ++k)
+#pragma unroll
+            for (int j = 1; j < 3; ++j)
+#pragma unroll
+                for (int i = 1; i < 3; ++i) {
+                    const float u0 = U[k][j][i];
+                    const float fv = __ldg(f + corner + Bx::off(i, j, k));
+                    const float nbu[6] = {U[k][j][i - 1], U[k][j][i + 1], U[k][j - 1][i],
+                                          U[k][j + 1][i], U[k - 1][j][i], U[k + 1][j][i]};
+                    if constexpr (MODE == 0) {
+                        const float S = ((nbu[0] + nbu[1]) + (nbu[2] + nbu[3])) + (nbu[4] + nbu[5]);
+                        sum += fmaf(fmaf(-6.0f, u0, S), ih2, fv);
+                    } else {
+                        const float k0 = K[k][j][i];
+                        const float nbk[6] = {K[k][j][i - 1], K[k][j][i + 1], K[k][j - 1][i],
+                                              K[k][j + 1][i], K[k - 1][j][i], K[k + 1][j][i]};
+                        float S = 0.0f, D = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            // operands in a fixed order per face (the lower neighbour first), so the two children
+                            // of an interior face evaluate the same expression and it is computed once; the sum
+                            // is the same either way
+                            const float a = (q & 1) ? frcp(k0 + nbk[q]) : frcp(nbk[q] + k0);
+                            S = fmaf(a, nbu[q], S);
+                            D += a;
+                        }
+                        sum += fmaf(2.0f * fmaf(-D, u0, S), ih2, fv);
+                    }
+                }
+        const int Xc = X + 1, Yc = Y + 1, Zc = Z + 1;
+        const auto at = [&](int xx, int yy, int zz) {
+            return B * bsc + ((xx + yy + zz) & 1) * HALFc + (zz * Pc + yy) * HPc + (xx >> 1);
+        };
+        const int64_t gc = at(Xc, Yc, Zc);
+        fc[gc] = 0.125f * sum;
+        uc[gc] = 0.0f;
+        // the coarse correction starts from zero: its face ghosts are zero too, so the level needs no exchange
+        // before its first half-sweep
+        if (X == 0) uc[at(0, Yc, Zc)] = 0.0f;
+        if (X == nc - 1) uc[at(nc + 1, Yc, Zc)] = 0.0f;
+        if (Y == 0) uc[at(Xc, 0, Zc)] = 0.0f;
+        if (Y == nc - 1) uc[at(Xc, nc + 1, Zc)] = 0.0f;
+        if (Z == 0) uc[at(Xc, Yc, 0)] = 0.0f;
+        if (Z == nc - 1) uc[at(Xc, Yc, nc + 1)] = 0.0f;
+    }
+}
+
+// FP32 prolongation + correction for a level whose blocks all halve (fine edge 2^LG): one thread per coarse cell
+// adds 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) to its 8 children, fine offsets as in Box32.  With nbr6 (the
+// fine level's face table, as in k_smooth) every child on a block face also writes its new value through to the
+// same-level neighbour's mirroring ghost, or the reflected value to its own boundary ghost, so that afterwards only
+// refinement-interface ghosts need an exchange.
+template <int LG>
+static __global__ void __launch_bounds__(256) k_prolong32(float *__restrict__ uf, int64_t bsf,
+                                                          const float *__restrict__ ec,
+                                                          const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc,
+                                                          const int32_t *__restrict__ nbr6) {
+    using Bx = Box32<LG>;
+    constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), PLc = Pc * HPc, HALFc = Pc * PLc;
+    const int64_t total = static_cast<int64_t>(nbc) << (3 * LC);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(t) & ((1 << (3 * LC)) - 1);
+        const int64_t B = t >> (3 * LC);
+        const int X = r & (nc - 1), Y = (r >> LC) & (nc - 1), Z = r >> (2 * LC);
+        const int Xc = X + 1, Yc = Y + 1, Zc = Z + 1;
+        const int pc = (Xc + Yc + Zc) & 1;
+        const int row = (Zc * Pc + Yc) * HPc;
+        const float *own = ec + B * bsc + pc * HALFc + row;
+        const float *oth = ec + B * bsc + (pc ^ 1) * HALFc + row;
+        const float e0 = own[Xc >> 1];
+        const float exm = oth[(Xc - 1) >> 1], exp_ = oth[(Xc + 1) >> 1];
+        const float eym = oth[(Xc >> 1) - HPc], eyp = oth[(Xc >> 1) + HPc];
+        const float ezm = oth[(Xc >> 1) - PLc], ezp = oth[(Xc >> 1) + PLc];
+        const float ex[2] = {exm, exp_}, ey[2] = {eym, eyp}, ez[2] = {ezm, ezp};
+        const int64_t b = xf[B].src[0];
+        float *ub = uf + b * bsf + (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;
+        float cur[2][2][2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) cur[c][bb][a] = ub[Bx::off(a + 1, bb + 1, c + 1)];
+        const bool face = nbr6 && (X == 0 || X == nc - 1 || Y == 0 || Y == nc - 1 || Z == 0 || Z == nc - 1);
+        const int corner = (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;  // in-block offset of the box corner
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const float v = cur[c][bb][a] + 0.25f * ((e0 + ex[a]) + (ey[bb] + ez[c]));
+                    ub[Bx::off(a + 1, bb + 1, c + 1)] = v;
+                    if (!face) continue;
+                    constexpr int n = Bx::n, H = Bx::HP, PL = Bx::P * Bx::HP, HALF = Bx::HALF;
+                    const int hs = (a + bb + c + 1) & 1;  // half of the child (its padded coordinate sum's parity)
+                    const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;  // offset inside its half
+                    const int cc[3] = {2 * X + a, 2 * Y + bb, 2 * Z + c};
+#pragma unroll
+                    for (int axis = 0; axis < 3; ++axis) {
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            if (cc[axis] != (side ? n - 1 : 0)) continue;
+                            const int Dm = axis == 0 ? n / 2 : (axis == 1 ? n * H : n * PL);
+                            const int E = axis == 0 ? 0 : (axis == 1 ? H : PL);
+                            const int nbv = nbr6[b * 6 + 2 * axis + side];
+                            if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (side ? -Dm : Dm)] = v;
+                            else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q + (side ? E : -E)] = -v;
+                        }
+                    }
+                }
     }
 }
 
@@ -420,9 +1056,8 @@ static __global__ void k_restrict_field(const T *__restrict__ xf_in, LevelGeom g
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
 static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
-                          const XferItem *__restrict__ xf, LevelGeom gc) {
-    const int lgc = gc.lg, nc = gc.n, Pc = gc.P;
-    const int64_t PPc = static_cast<int64_t>(Pc) * Pc;
+                                 const XferItem *__restrict__ xf, LevelGeom gc) {
+    const int lgc = gc.lg, nc = gc.n;
     const int64_t total = static_cast<int64_t>(gc.nb) << (3 * lgc);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -431,15 +1066,14 @@ static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__re
         const int Z = static_cast<int>((t >> (2 * lgc)) & (nc - 1));
         const int64_t B = t >> (3 * lgc);
         const XferItem xi = xf[B];
-        const int64_t gcell = B * gc.bs + off3(X + 1, Y + 1, Z + 1, Pc);
-        const T e0 = ec[gcell];
+        const T e0 = ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z + 1)];
         if (xi.kind == XF_COPY) {
-            uf[xi.src[0] * gf.bs + off3(X + 1, Y + 1, Z + 1, gf.P)] += e0;
+            uf[Lay<T>::at(gf, xi.src[0], X + 1, Y + 1, Z + 1)] += e0;
             continue;
         }
-        const T ex[2] = {ec[gcell - 1], ec[gcell + 1]};
-        const T ey[2] = {ec[gcell - Pc], ec[gcell + Pc]};
-        const T ez[2] = {ec[gcell - PPc], ec[gcell + PPc]};
+        const T ex[2] = {ec[Lay<T>::at(gc, B, X, Y + 1, Z + 1)], ec[Lay<T>::at(gc, B, X + 2, Y + 1, Z + 1)]};
+        const T ey[2] = {ec[Lay<T>::at(gc, B, X + 1, Y, Z + 1)], ec[Lay<T>::at(gc, B, X + 1, Y + 2, Z + 1)]};
+        const T ez[2] = {ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z)], ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z + 2)]};
         int64_t b;
         int x0, y0, z0;
         if (xi.kind == XF_HALVE) {
@@ -460,10 +1094,9 @@ static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__re
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const int64_t gfc = b * gf.bs + off3(x0 + a + 1, y0 + bb + 1, z0 + c + 1, gf.P);
-                    uf[gfc] += T(0.25) * ((e0 + ex[a]) + (ey[bb] + ez[c]));
-                }
+                for (int a = 0; a < 2; ++a)
+                    uf[Lay<T>::at(gf, b, x0 + a + 1, y0 + bb + 1, z0 + c + 1)] +=
+                        T(0.25) * ((e0 + ex[a]) + (ey[bb] + ez[c]));
     }
 }
 
@@ -515,8 +1148,18 @@ static __global__ void k_residual_norm(const double *__restrict__ u, const doubl
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
         const double r = residual_at<double, MODE>(u, f, cf, gi, P, ihb);
         const float rs = static_cast<float>(r) * scale;
-        if (out) out[gi] = rs;
-        if (zero_out) zero_out[gi] = 0.0f;
+        const int64_t gs = Lay<float>::at(g, b, x + 1, y + 1, z + 1);  // FP32 pools are colour-split
+        if (out) out[gs] = rs;
+        if (zero_out) {
+            zero_out[gs] = 0.0f;
+            // and the face ghosts next to it, so that every ghost of the zeroed correction is current
+            if (x == 0) zero_out[Lay<float>::at(g, b, 0, y + 1, z + 1)] = 0.0f;
+            if (x == n - 1) zero_out[Lay<float>::at(g, b, n + 1, y + 1, z + 1)] = 0.0f;
+            if (y == 0) zero_out[Lay<float>::at(g, b, x + 1, 0, z + 1)] = 0.0f;
+            if (y == n - 1) zero_out[Lay<float>::at(g, b, x + 1, n + 1, z + 1)] = 0.0f;
+            if (z == 0) zero_out[Lay<float>::at(g, b, x + 1, y + 1, 0)] = 0.0f;
+            if (z == n - 1) zero_out[Lay<float>::at(g, b, x + 1, y + 1, n + 1)] = 0.0f;
+        }
         acc = fmaf(rs, rs, acc);
     }
     __shared__ double sm[kThreads / 32];
@@ -676,7 +1319,7 @@ static __global__ void k_update_mixed(double *__restrict__ u, const float *__res
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, g.P);
-        u[gi] = fma(pinv[bprob[b]], static_cast<double>(e[gi]), u[gi]);
+        u[gi] = fma(pinv[bprob[b]], static_cast<double>(e[Lay<float>::at(g, b, x + 1, y + 1, z + 1)]), u[gi]);
     }
 }
 
@@ -702,7 +1345,7 @@ static __global__ void k_face_coefs(const double *__restrict__ k, const double *
         if (ty && Y >= 1 && inX && inZ) ty[gi] = harm(k[gi - P], kc) * s;
         if (tz && Z >= 1 && inX && inY) tz[gi] = harm(k[gi - static_cast<int64_t>(P) * P], kc) * s;
         const bool face_or_interior = (inX && inY) || (inX && inZ) || (inY && inZ);
-        if (kap && face_or_interior && kc > 0.0) kap[gi] = static_cast<float>(1.0 / kc);
+        if (kap && face_or_interior && kc > 0.0) kap[Lay<float>::at(g, b, X, Y, Z)] = static_cast<float>(1.0 / kc);
     }
 }
 

@@ -1,5 +1,8 @@
 // The forest object, the V-cycle driver and the C-ABI entry points (include/octmg.h).
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <atomic>
 #include <thread>
 #include <cmath>
@@ -42,7 +45,8 @@ mg_status upload(mg_forest *F, T **p, const std::vector<T> &v) {
 const char *const kProfNames[P_NCAT] = {"exchange_f64", "exchange_f32", "smooth_f64", "smooth_f32",
                                          "residual_restrict_f64", "residual_restrict_f32", "prolong_f64",
                                          "prolong_f32", "coarse_f64", "coarse_f32", "residual_f64",
-                                         "update_mixed", "layout", "adjoint"};
+                                         "update_mixed", "layout", "adjoint", "smooth_f64_finest",
+                                         "smooth_f32_finest"};
 
 cudaEvent_t next_event(mg_forest *F) {
     if (F->ev_used == F->ev_pool.size()) {
@@ -120,48 +124,245 @@ void exchange_k(mg_forest *F, DevLevel &d) {
                                              F->st>>>(d.k64, Coef{}, d.segs, d.nsegs, d.g);
 }
 
+// FP32 smoothers specialised for block edges 4..128.  Two kernels and their launch shapes (kind, parameters):
+//   {1, ZC, threads, 0, 0}: k_smooth32, one column of ZC in {1, 2, 4} cells per thread, 128 / 256 / 512 threads;
+//   {2, TY, TZ, D, R}:      k_smooth32t (edges 32..128), a CTA per TY rows x TZ planes of a block, other-colour planes
+//                           staged in shared memory D ahead, R rows per thread (threads = n/2 TY / R in 128..512,
+//                           TZ in {16, 32, 64} up to n, D in {2, 4}, R in {1, 2, 4}).
+// A shape only changes which thread updates a cell, never the arithmetic, so every shape gives identical bits.
+using Shape = std::array<int32_t, 5>;
+using Smooth32Fn = void (*)(float *, const float *, const float *, const float *, int64_t, int64_t, int,
+                            const int32_t *);
+#define OCTMG_S32(K, M, L) {K<M, L, 1>, K<M, L, 2>, K<M, L, 4>}
+const Smooth32Fn kSmooth32[2][6][3] = {
+    {OCTMG_S32(k_smooth32, 0, 2), OCTMG_S32(k_smooth32, 0, 3), OCTMG_S32(k_smooth32, 0, 4),
+     OCTMG_S32(k_smooth32, 0, 5), OCTMG_S32(k_smooth32, 0, 6), OCTMG_S32(k_smooth32, 0, 7)},
+    {OCTMG_S32(k_smooth32, 2, 2), OCTMG_S32(k_smooth32, 2, 3), OCTMG_S32(k_smooth32, 2, 4),
+     OCTMG_S32(k_smooth32, 2, 5), OCTMG_S32(k_smooth32, 2, 6), OCTMG_S32(k_smooth32, 2, 7)}};
+using Smooth32tFn = void (*)(float *, const float *, const float *, const float *, int64_t, int, const int32_t *, int,
+                             int, int, int *);
+const Smooth32tFn kSmooth32t[2][3][3] = {
+    {OCTMG_S32(k_smooth32t, 0, 5), OCTMG_S32(k_smooth32t, 0, 6), OCTMG_S32(k_smooth32t, 0, 7)},
+    {OCTMG_S32(k_smooth32t, 2, 5), OCTMG_S32(k_smooth32t, 2, 6), OCTMG_S32(k_smooth32t, 2, 7)}};
+#undef OCTMG_S32
+
+bool smooth32_specialised(const DevLevel &d) { return d.g.lg >= 2 && d.g.lg <= 7; }
+
+size_t smooth32t_smem(int lg, bool var, int TY, int D) {
+    const int P = (1 << lg) + 2, H = half_row(P), NA = var ? 2 : 1;
+    return static_cast<size_t>(4) * NA * ((3 + D) * (TY + 2) * H + (1 + D) * TY * H) + 8 * (4 + 2 * D);
+}
+
+int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
+
+// The shapes a level may use (the tuner's candidates).
+std::vector<Shape> smooth32_shapes(const DevLevel &d, bool var) {
+    std::vector<Shape> v;
+    const int n = d.g.n;
+    for (int zc : {1, 2, 4})
+        for (int th : {128, 256, 512})
+            if (zc <= n) v.push_back({1, zc, th, 0, 0});
+    if (d.g.lg >= 5)
+        for (int R : {1, 2, 4})
+            for (int th : {128, 256, 512})
+                for (int tz : {16, 32, 64})
+                    for (int D : {2, 4}) {
+                        const int TY = th * R / (n / 2);
+                        if (TY >= R && TY <= n && tz <= n && smooth32t_smem(d.g.lg, var, TY, D) <= 200 * 1024)
+                            v.push_back({2, TY, tz, D, R});
+                    }
+    return v;
+}
+
+bool smooth32_shape_ok(const DevLevel &d, bool var, const Shape &sh) {
+    for (const auto &c : smooth32_shapes(d, var))
+        if (c == sh) return true;
+    return false;
+}
+
+void launch_smooth32(mg_forest *F, DevLevel &d, int colour, const Shape &sh, cudaStream_t st) {
+    const int mi = F->cfg.coeff ? 1 : 0;
+    if (sh[0] == 2) {
+        const int TY = sh[1], TZ = sh[2], D = sh[3], R = sh[4], n = d.g.n;
+        const size_t smem = smooth32t_smem(d.g.lg, mi == 1, TY, D);
+        Smooth32tFn fn = kSmooth32t[mi][d.g.lg - 5][ridx(R)];
+        static std::once_flag once[2][3][3];
+        std::call_once(once[mi][d.g.lg - 5][ridx(R)], [&] {
+            cudaFuncSetAttribute(reinterpret_cast<const void *>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+        });
+        const int64_t grid = static_cast<int64_t>(d.g.nb) * (n / TY) * (n / TZ);
+        fn<<<static_cast<unsigned>(grid), (n / 2) * TY / R, smem, st>>>(d.u32, d.f32, d.kap, d.h2_32, d.g.bs, colour,
+                                                                         d.nbr6, TY, TZ, D, F->kerr);
+        return;
+    }
+    const int zc = sh[1], threads = sh[2];
+    const int64_t work = (d.cells() / 2) >> ridx(zc);  // one thread per column of zc cells
+    const int64_t grid = (work + threads - 1) / threads;
+    kSmooth32[mi][d.g.lg - 2][ridx(zc)]<<<static_cast<unsigned>(grid), threads, 0, st>>>(
+        d.u32, d.f32, d.kap, d.h2_32, work, d.g.bs, colour, d.nbr6);
+}
+
+// Reads and clears the device error word of bounded waits.
+mg_status check_kernel_waits(mg_forest *F) {
+    int h = 0;
+    MG_CUDA(cudaMemcpyAsync(&h, F->kerr, sizeof(int), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (h) {
+        MG_CUDA(cudaMemsetAsync(F->kerr, 0, sizeof(int), F->st));
+        set_error("a staged smoother gave up waiting for its shared-memory copies");
+        return MG_ERR_TIMEOUT;
+    }
+    return MG_OK;
+}
+
+// Launch-shape autotuner of the FP32 smoother: on every level with at least 2^18 cells, time both colours of each
+// candidate shape (one untimed pair, then three timed pairs between CUDA events on the forest's stream) and keep
+// the fastest.  It runs on the level's own FP32 pools, whose contents are dead between solves (each correction
+// cycle rewrites f and zeroes u before reading them).  Choices are cached for the process per (device,
+// coefficient mode, n, blocks); smaller levels, and every level while the stream is being captured, take
+// {1, 1, 256, 0}.
+mg_status tune_smooth32(mg_forest *F) {
+    static std::mutex mu;
+    static std::map<std::array<int64_t, 4>, Shape> cache;
+    int dev = 0;
+    MG_CUDA(cudaGetDevice(&dev));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MG_CUDA(cudaStreamIsCapturing(F->st, &cap));
+    const bool var = F->cfg.coeff != 0;
+    for (DevLevel &d : F->L) {
+        if (!smooth32_specialised(d) || !d.u32 || d.s32[0]) continue;
+        if (d.cells() < (int64_t(1) << 18) || cap != cudaStreamCaptureStatusNone) {
+            d.s32 = {1, 1, kThreads, 0, 0};
+            continue;
+        }
+        const std::array<int64_t, 4> key{dev, F->cfg.coeff, d.g.n, d.g.nb};
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                d.s32 = it->second;
+                continue;
+            }
+        }
+        cudaEvent_t e0 = next_event(F), e1 = next_event(F);
+        if (!e0 || !e1) {
+            set_error("cudaEventCreate failed");
+            return MG_ERR_CUDA;
+        }
+        float best = 0.0f;
+        Shape pick{1, 1, kThreads, 0, 0};
+        for (const auto &sh : smooth32_shapes(d, var)) {
+            launch_smooth32(F, d, 0, sh, F->st);
+            launch_smooth32(F, d, 1, sh, F->st);
+            MG_CUDA(cudaEventRecord(e0, F->st));
+            for (int rep = 0; rep < 3; ++rep) {
+                launch_smooth32(F, d, 0, sh, F->st);
+                launch_smooth32(F, d, 1, sh, F->st);
+            }
+            MG_CUDA(cudaEventRecord(e1, F->st));
+            MG_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (best == 0.0f || ms < best) {
+                best = ms;
+                pick = sh;
+            }
+        }
+        F->ev_used -= 2;
+        MG_CUDA(cudaGetLastError());
+        MG_TRY(check_kernel_waits(F));
+        d.s32 = pick;
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = pick;
+    }
+    return MG_OK;
+}
+
+// FP32 residual + restriction and prolongation specialised for levels whose blocks all halve, fine edges 8..128.
+bool transfer32_specialised(const DevLevel &d) { return d.all_halve && d.g.lg >= 3 && d.g.lg <= 7; }
+
+using Restrict32Fn = void (*)(const float *, const float *, const float *, const float *, int64_t, float *, float *,
+                              const XferItem *, int32_t, int64_t);
+const Restrict32Fn kRestrict32[2][5] = {
+    {k_residual_restrict32<0, 3>, k_residual_restrict32<0, 4>, k_residual_restrict32<0, 5>,
+     k_residual_restrict32<0, 6>, k_residual_restrict32<0, 7>},
+    {k_residual_restrict32<2, 3>, k_residual_restrict32<2, 4>, k_residual_restrict32<2, 5>,
+     k_residual_restrict32<2, 6>, k_residual_restrict32<2, 7>}};
+using Prolong32Fn = void (*)(float *, int64_t, const float *, const XferItem *, int32_t, int64_t,
+                             const int32_t *);
+const Prolong32Fn kProlong32[5] = {k_prolong32<3>, k_prolong32<4>, k_prolong32<5>, k_prolong32<6>, k_prolong32<7>};
+
+void launch_residual_restrict32(mg_forest *F, DevLevel &d, DevLevel &c) {
+    kRestrict32[F->cfg.coeff ? 1 : 0][d.g.lg - 3]<<<grid_for(c.cells()), kThreads, 0, F->st>>>(
+        d.u32, d.f32, d.kap, d.ih2_32, d.g.bs, c.f32, c.u32, d.xfer, c.g.nb, c.g.bs);
+}
+
+void launch_prolong32(mg_forest *F, DevLevel &d, DevLevel &c) {
+    kProlong32[d.g.lg - 3]<<<grid_for(c.cells()), kThreads, 0, F->st>>>(d.u32, d.g.bs, c.u32, d.xfer, c.g.nb, c.g.bs,
+                                                                          d.nbr6);
+}
+
 template <typename T, int MODE>
 void smooth(mg_forest *F, DevLevel &d, int colour) {
-    Prof p(F, cat_of<T>(P_SMOOTH64), 1);
+    Prof p(F, &d == &F->L[0] ? cat_of<T>(P_SMOOTH64_L0) : cat_of<T>(P_SMOOTH64), 1);
+    if constexpr (sizeof(T) == 4 && MODE != 1) {
+        if (smooth32_specialised(d)) {
+            launch_smooth32(F, d, colour, d.s32[0] ? d.s32 : Shape{1, 1, kThreads, 0, 0}, F->st);
+            return;
+        }
+    }
     k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d),
                                                                        h2_of<T>(d), d.g, colour, d.nbr6);
 }
 
-// V(nu1, nu2) on level l.  Exchange schedule: a full exchange when the level is entered (its u changed outside
-// the smoother), before each half-sweep and before the restriction only the refinement-interface ghosts (the
-// smoother writes same-level and boundary ghosts through), and a full exchange after the prolongation.
+// V(nu1, nu2) on level l.  Exchange schedule: at level entry a full exchange, unless the ghosts are known to be
+// current (`entry`: ENTRY_FULL, ENTRY_INTERFACE = only refinement-interface ghosts may be stale, ENTRY_NONE = the
+// correction and all its face ghosts were just zeroed); before each later half-sweep and before the restriction
+// only the refinement-interface ghosts (the smoothers write same-level and boundary ghosts through); after the
+// prolongation a full exchange, or only the interface one after a prolongation that writes through.
+enum { ENTRY_FULL = 0, ENTRY_INTERFACE = 1, ENTRY_NONE = 2 };
+
 template <typename T, int MODE>
-void vcycle(mg_forest *F, int l) {
+void vcycle(mg_forest *F, int l, int entry) {
     DevLevel &d = F->L[l];
     const int last = static_cast<int>(F->L.size()) - 1;
     if (l == last) {
         Prof p(F, cat_of<T>(P_COARSE64), 1);
         k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(
-            ufield<T>(d), ffield<T>(d), F->Ainv, F->cmap, F->uprob, F->ustart, F->moff, F->Nc);
+            ufield<T>(d), ffield<T>(d), F->Ainv, sizeof(T) == 4 ? F->cmap32 : F->cmap, F->uprob, F->ustart, F->moff,
+            F->Nc);
         exchange<T, MODE>(F, d, ufield<T>(d));
         return;
     }
-    exchange<T, MODE>(F, d, ufield<T>(d));
+    if (entry != ENTRY_NONE) exchange<T, MODE>(F, d, ufield<T>(d), entry == ENTRY_INTERFACE);
     for (int i = 0; i < F->cfg.nu1; ++i) {
         if (i) exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 0);
         exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 1);
     }
-    exchange<T, MODE>(F, d, ufield<T>(d), true);
+    if (F->cfg.nu1) exchange<T, MODE>(F, d, ufield<T>(d), true);
     DevLevel &c = F->L[l + 1];
+    const bool fast = sizeof(T) == 4 && MODE != 1 && transfer32_specialised(d);
     {
         Prof p(F, cat_of<T>(P_RESTR64), 1);
-        k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
-            ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
+        if (fast)
+            launch_residual_restrict32(F, d, c);
+        else
+            k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
+                ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
     }
-    vcycle<T, MODE>(F, l + 1);
+    vcycle<T, MODE>(F, l + 1, fast ? ENTRY_NONE : ENTRY_FULL);
     if (l + 1 != last) exchange<T, MODE>(F, c, ufield<T>(c), true);
     {
         Prof p(F, cat_of<T>(P_PROL64), 1);
-        k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
+        if (fast)
+            launch_prolong32(F, d, c);
+        else
+            k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
     }
-    exchange<T, MODE>(F, d, ufield<T>(d));
+    exchange<T, MODE>(F, d, ufield<T>(d), fast);
     for (int i = 0; i < F->cfg.nu2; ++i) {
         if (i) exchange<T, MODE>(F, d, ufield<T>(d), true);
         smooth<T, MODE>(F, d, 0);
@@ -255,7 +456,7 @@ mg_status assemble_coarse(mg_forest *F) {
     if (!F->cmap) {
         std::vector<std::vector<int32_t>> blocks(F->np);
         for (int b = 0; b < d.g.nb; ++b) blocks[hl.keys[b].p].push_back(b);
-        std::vector<int64_t> cmap;
+        std::vector<int64_t> cmap, cmap32;
         std::vector<int32_t> uprob;
         F->ustart_h.assign(F->np + 1, 0);
         F->moff_h.assign(F->np + 1, 0);
@@ -267,6 +468,7 @@ mg_status assemble_coarse(mg_forest *F) {
                     for (int y = 0; y < n; ++y)
                         for (int x = 0; x < n; ++x) {
                             cmap.push_back(b * d.g.bs + off3(x + 1, y + 1, z + 1, d.g.P));
+                            cmap32.push_back(Lay<float>::at(d.g, b, x + 1, y + 1, z + 1));
                             uprob.push_back(p);
                         }
             const int64_t Np = static_cast<int64_t>(blocks[p].size()) * cells;
@@ -274,6 +476,7 @@ mg_status assemble_coarse(mg_forest *F) {
         }
         F->ustart_h[F->np] = static_cast<int64_t>(cmap.size());
         MG_TRY(upload(F, &F->cmap, cmap));
+        MG_TRY(upload(F, &F->cmap32, cmap32));
         MG_TRY(upload(F, &F->uprob, uprob));
         MG_TRY(upload(F, &F->ustart, F->ustart_h));
         MG_TRY(upload(F, &F->moff, F->moff_h));
@@ -363,12 +566,14 @@ mg_status unpack_user(mg_forest *F, DevLevel &d, double *user, const T *pool) {
 
 // One FP64 V-cycle on level 0.
 void vcycle64(mg_forest *F) {
-    if (F->cfg.coeff) vcycle<double, 1>(F, 0);
-    else vcycle<double, 0>(F, 0);
+    if (F->cfg.coeff) vcycle<double, 1>(F, 0, ENTRY_FULL);
+    else vcycle<double, 0>(F, 0, ENTRY_FULL);
 }
+// The FP32 correction on level 0 either was just zeroed with its face ghosts (k_residual_norm) or ends a previous
+// FP32 V-cycle whose last half-sweeps wrote its same-level and boundary ghosts through.
 void vcycle32(mg_forest *F) {
-    if (F->cfg.coeff) vcycle<float, 2>(F, 0);
-    else vcycle<float, 0>(F, 0);
+    if (F->cfg.coeff) vcycle<float, 2>(F, 0, ENTRY_INTERFACE);
+    else vcycle<float, 0>(F, 0, ENTRY_INTERFACE);
 }
 
 double pow2_near(double x) {
@@ -505,6 +710,7 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
     }
     MG_TRY(unpack_user<double>(F, d, u_dev, d.u64));
     MG_CUDA(cudaStreamSynchronize(F->st));
+    if (F->cfg.precision == 1) MG_TRY(check_kernel_waits(F));
     for (int p = 0; p < np; ++p) {
         if (cycles_out) cycles_out[p] = met[p] >= 0 ? met[p] : done;
         if (rel_out) rel_out[p] = rel[p];
@@ -568,8 +774,11 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         d.g.n = h.n;
         d.g.lg = ilog2(h.n);
         d.g.P = h.n + 2;
-        const int64_t per = static_cast<int64_t>(d.g.P) * d.g.P * d.g.P;
-        d.g.bs = (per + 31) / 32 * 32;
+        // one stride for both precisions: the natural FP64 block or the padded FP32 split block, whichever is
+        // larger, rounded to 64 elements (every FP32 half, plane and row then starts on a 16-byte boundary)
+        const int64_t per = std::max<int64_t>(static_cast<int64_t>(d.g.P) * d.g.P * d.g.P,
+                                              2 * static_cast<int64_t>(d.g.P) * d.g.P * half_row(d.g.P));
+        d.g.bs = (per + 63) / 64 * 64;
         d.nfaces = static_cast<int>(h.faces.size());
         d.nsegs = static_cast<int>(h.segs.size());
         if ((st = upload(F, &d.faces, h.faces)) != MG_OK) return fail(st);
@@ -597,6 +806,8 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
             if (!itf.empty() && (st = upload(F, &d.ifaces, itf)) != MG_OK) return fail(st);
         }
         if (!h.to_next.empty() && (st = upload(F, &d.xfer, h.to_next)) != MG_OK) return fail(st);
+        d.all_halve = !h.to_next.empty() &&
+                      std::all_of(h.to_next.begin(), h.to_next.end(), [](const XferItem &x) { return x.kind == XF_HALVE; });
         std::vector<double> h2(h.h.size()), ih2(h.h.size()), vol(h.h.size());
         std::vector<float> h2f(h.h.size()), ih2f(h.h.size()), volf(h.h.size());
         for (size_t b = 0; b < h2.size(); ++b) {
@@ -640,6 +851,7 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
     if ((st = dalloc(F, &F->partial, 2 * kMaxGrid)) != MG_OK) return fail(st);
     if ((st = dalloc(F, &F->sums, 2)) != MG_OK) return fail(st);
     if ((st = dalloc(F, &F->flag, 1)) != MG_OK) return fail(st);
+    if ((st = dalloc(F, &F->kerr, 1)) != MG_OK) return fail(st);
     {
         const HostLevel &h0 = F->H.levels[0];
         std::vector<int32_t> pstart(np + 1, 0), pblk(h0.keys.size());
@@ -715,6 +927,7 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
         total += F->psum_h[p];
     }
     F->fnorm = std::sqrt(total);
+    if (F->cfg.precision == 1) MG_TRY(tune_smooth32(F));
     F->rhs_set = true;
     return MG_OK;
 }
@@ -835,6 +1048,51 @@ mg_status mg_exchange_level(mg_forest *F, int32_t level, const double *u_dev, do
         set_error(std::string("exchange_level: ") + cudaGetErrorString(e));
         return MG_ERR_CUDA;
     }
+    return MG_OK;
+}
+
+mg_status mg_get_smoother_shape(const mg_forest *F, int32_t level, int32_t *shape) {
+    if (!F || level < 0 || level >= static_cast<int32_t>(F->L.size()) || !shape) {
+        set_error("null forest or output, or level out of range");
+        return MG_ERR_INVALID_ARG;
+    }
+    const DevLevel &d = F->L[level];
+    const bool used = F->cfg.precision == 1 && smooth32_specialised(d);
+    for (int i = 0; i < 5; ++i) shape[i] = used ? d.s32[i] : 0;
+    return MG_OK;
+}
+
+mg_status mg_set_smoother_shape(mg_forest *F, int32_t level, const int32_t *shape) {
+    if (!F || level < 0 || level >= static_cast<int32_t>(F->L.size()) || !shape) {
+        set_error("null forest or shape, or level out of range");
+        return MG_ERR_INVALID_ARG;
+    }
+    DevLevel &d = F->L[level];
+    if (F->cfg.precision != 1 || !smooth32_specialised(d)) {
+        set_error("level " + std::to_string(level) + " has no specialised FP32 smoother");
+        return MG_ERR_INVALID_ARG;
+    }
+    const Shape sh{shape[0], shape[1], shape[2], shape[3], shape[4]};
+    if (!smooth32_shape_ok(d, F->cfg.coeff != 0, sh)) {
+        set_error("smoother shape not offered for this level (see mg_smoother_shapes)");
+        return MG_ERR_INVALID_ARG;
+    }
+    d.s32 = sh;
+    return MG_OK;
+}
+
+mg_status mg_smoother_shapes(const mg_forest *F, int32_t level, int32_t max_shapes, int32_t *shapes,
+                             int32_t *n_shapes) {
+    if (!F || level < 0 || level >= static_cast<int32_t>(F->L.size()) || !n_shapes || max_shapes < 0) {
+        set_error("null forest or output, or level out of range");
+        return MG_ERR_INVALID_ARG;
+    }
+    const DevLevel &d = F->L[level];
+    std::vector<Shape> v;
+    if (F->cfg.precision == 1 && smooth32_specialised(d)) v = smooth32_shapes(d, F->cfg.coeff != 0);
+    *n_shapes = static_cast<int32_t>(v.size());
+    for (int i = 0; i < static_cast<int>(v.size()) && i < max_shapes && shapes; ++i)
+        for (int k = 0; k < 5; ++k) shapes[5 * i + k] = v[i][k];
     return MG_OK;
 }
 

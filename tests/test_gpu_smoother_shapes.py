@@ -1,0 +1,64 @@
+"""Launch shapes of the FP32 smoother: the column kernel (cells per thread along z, threads per CTA) and the
+kernel whose other-colour planes are staged in shared memory by bulk copies (rows per CTA, planes per CTA, planes
+in flight, rows per thread).
+
+A shape only decides which thread updates which cell of a colour, and the half-sweep's cells are independent, so
+every shape must give the same bits.  Checked on a refined forest with 32^3 blocks (C2F / F2C interfaces, boundary
+reflection and same-level write-through on every level from 32^3 down to 4^3 blocks), for constant and variable
+coefficients.
+"""
+import pytest
+import torch
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.mark.parametrize("coeff", [False, True])
+def test_every_smoother_shape_gives_identical_bits(coeff):
+    from paper_2403_08063_gb300 import Forest
+    R, n, keys = syn.workload_forest("sphere_2x32")
+    dev = torch.device(DEV)
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=31, device=dev)
+    k = syn.lognormal_k_rff(R, n, keys, seed=32, device=dev) if coeff else None
+    F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=2)
+    F.set_rhs(f, k)
+    nlev = len(F.levels())
+    shapes = [F.smoother_shapes(l) for l in range(nlev)]
+    assert all(shapes)
+    # both kernels are offered on the 32^3 level, and the tuner picked an offered shape there
+    assert {s[0] for s in shapes[0]} == {1, 2}
+    assert F.smoother_shape(0) in shapes[0]
+    ref = None
+    for i in range(max(len(s) for s in shapes)):
+        for l in range(nlev):
+            sh = shapes[l][i % len(shapes[l])]
+            F.set_smoother_shape(l, sh)
+            assert F.smoother_shape(l) == sh
+        u = torch.zeros_like(f)
+        F.vcycle(u, 2)
+        if ref is None:
+            ref = u.clone()
+            assert torch.isfinite(ref).all() and ref.abs().max() > 0
+        else:
+            assert torch.equal(u, ref), [shapes[l][i % len(shapes[l])] for l in range(nlev)]
+
+
+def test_smoother_shape_arguments_are_checked():
+    from paper_2403_08063_gb300 import Forest, MGError
+    R, n, keys = syn.workload_forest("uniform_2x4")
+    F = Forest(R, n, keys, precision=1)
+    offered = F.smoother_shapes(0)
+    assert (1, 1, 256, 0, 0) in offered and all(s[0] == 1 for s in offered)  # column kernel only on 4^3 blocks
+    for bad in ((1, 3, 256, 0, 0), (1, 1, 100, 0, 0), (1, 8, 256, 0, 0), (3, 1, 128, 0, 0), (2, 2, 4, 2, 1),
+                (0, 0, 0, 0, 0)):
+        with pytest.raises(MGError):
+            F.set_smoother_shape(0, bad)
+    with pytest.raises(MGError):
+        F.set_smoother_shape(len(F.levels()), (1, 1, 256, 0, 0))
+    F64 = Forest(R, n, keys, precision=0)
+    assert F64.smoother_shape(0) == (0, 0, 0, 0, 0) and F64.smoother_shapes(0) == []
+    with pytest.raises(MGError):
+        F64.set_smoother_shape(0, (1, 1, 256, 0, 0))
