@@ -458,7 +458,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform_8x64_k")
     ap.add_argument("--rtol", type=float, default=1e-10)
-    ap.add_argument("--inner-cycles", type=int, default=3,
+    ap.add_argument("--inner-cycles", type=int, default=4,
                     help="FP32 V-cycles per FP64 defect-correction step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -5,6 +5,8 @@
 // per distinct n, all on one stream, reading and writing the caller's arrays in place through per-leaf offsets.
 // With FP32 cycles, one defect-correction step of every group (m FP32 V-cycles, the FP64 update, the next FP64
 // residual and its per-problem norms) is captured once in a CUDA graph and replayed until every problem meets rtol.
+// Each group runs on a stream of its own, forked from and joined back to the batch stream, so the graph holds one
+// branch per group and the latency-bound launches of small groups overlap the bandwidth-bound ones of large groups.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -21,6 +23,9 @@ struct mg_batch {
     std::vector<mg_forest *> groups;
     std::vector<int32_t> gn;                  // block size per group
     std::vector<std::vector<int32_t>> gprob;  // batch problem ids per group (local id = position)
+    std::vector<cudaStream_t> gst;            // one stream per group (the group forest's stream)
+    std::vector<cudaEvent_t> gev;             // join events, one per group
+    cudaEvent_t ev_fork = nullptr;
     int *flag = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_m = 0;
@@ -43,7 +48,11 @@ void destroy_batch(mg_batch *B) {
     if (!B) return;
     if (B->st) cudaStreamSynchronize(B->st);
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    for (cudaStream_t s : B->gst) cudaStreamSynchronize(s);
     for (mg_forest *F : B->groups) mg_forest_destroy(F);
+    for (cudaEvent_t e : B->gev) cudaEventDestroy(e);
+    for (cudaStream_t s : B->gst) cudaStreamDestroy(s);
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     if (B->flag) cudaFree(B->flag);
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
@@ -63,15 +72,31 @@ mg_status leave(mg_batch *B) {
     return MG_OK;
 }
 
+// Group streams start after the batch stream's work so far (fork) and the batch stream waits for all of them (join).
+mg_status fork(mg_batch *B) {
+    MG_CUDA(cudaEventRecord(B->ev_fork, B->st));
+    for (cudaStream_t s : B->gst) MG_CUDA(cudaStreamWaitEvent(s, B->ev_fork, 0));
+    return MG_OK;
+}
+mg_status join(mg_batch *B) {
+    for (size_t g = 0; g < B->gst.size(); ++g) {
+        MG_CUDA(cudaEventRecord(B->gev[g], B->gst[g]));
+        MG_CUDA(cudaStreamWaitEvent(B->st, B->gev[g], 0));
+    }
+    return MG_OK;
+}
+
 // One FP32 defect-correction step of every group with unconverged problems is enqueued (no synchronisation).
 mg_status enqueue_step(mg_batch *B, int m) {
+    MG_TRY(fork(B));
     for (mg_forest *F : B->groups) {
+        MG_TRY(enqueue_done(F));
         MG_TRY(enqueue_fp32_step(F, m));
         MG_TRY(enqueue_scales(F));
         MG_TRY(enqueue_residual(F));
         MG_TRY(enqueue_problem_sums(F));
     }
-    return MG_OK;
+    return join(B);
 }
 
 bool profiling(const mg_batch *B) {
@@ -91,7 +116,9 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         return MG_ERR_INVALID_ARG;
     }
     MG_TRY(enter(B));
+    MG_TRY(fork(B));
     const size_t G = B->groups.size();
+    for (mg_forest *F : B->groups) reset_done(F);
     std::vector<std::vector<double>> fn(G), mult(G), rel(G), rr(G);
     std::vector<std::vector<int32_t>> met(G);
     for (size_t g = 0; g < G; ++g) {
@@ -112,6 +139,7 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         MG_TRY(enqueue_residual(F));
         MG_TRY(enqueue_problem_sums(F));
     }
+    MG_TRY(join(B));
     int done = 0;
     bool all = false, finite = true;
     const int inner = std::max(1, B->cfg.inner_cycles);
@@ -121,10 +149,14 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         for (size_t g = 0; g < G; ++g) {
             mg_forest *F = B->groups[g];
             for (int p = 0; p < F->np; ++p) {
+                if (F->pdone_h[p]) continue;  // masked out since it met rtol: keeps that residual
                 rr[g][p] = F->psum_h[p] / (mult[g][p] * mult[g][p]);
                 rel[g][p] = std::sqrt(rr[g][p]) / fn[g][p];
                 if (!std::isfinite(rel[g][p])) finite = false;
-                if (rel[g][p] <= rtol && met[g][p] < 0) met[g][p] = done;
+                if (rel[g][p] <= rtol && met[g][p] < 0) {
+                    met[g][p] = done;
+                    F->pdone_h[p] = 1;  // copied to the device at the start of the next step
+                }
                 if (!(rel[g][p] <= rtol)) all = false;
             }
         }
@@ -132,7 +164,8 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         const int m = std::min(inner, max_cycles - done);
         // scales of the next residual; the update of this step still uses the previous ones (device pinv)
         for (size_t g = 0; g < G; ++g) {
-            for (int p = 0; p < B->groups[g]->np; ++p) mult[g][p] = pow2_near(1.0 / std::sqrt(rr[g][p]));
+            for (int p = 0; p < B->groups[g]->np; ++p)
+                if (!B->groups[g]->pdone_h[p]) mult[g][p] = pow2_near(1.0 / std::sqrt(rr[g][p]));
         }
         // the update reads pinv on the device before the captured copies overwrite it: keep host copies of the
         // new scales until the step is enqueued
@@ -165,6 +198,7 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         }
         done += m;
     }
+    MG_TRY(fork(B));
     for (size_t g = 0; g < G; ++g) {
         mg_forest *F = B->groups[g];
         DevLevel &d = F->L[0];
@@ -175,6 +209,8 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
             if (rel_out) rel_out[bp] = rel[g][p];
         }
     }
+    for (mg_forest *F : B->groups) reset_done(F);
+    MG_TRY(join(B));
     MG_CUDA(cudaGetLastError());
     MG_TRY(leave(B));
     MG_CUDA(cudaStreamSynchronize(B->st));
@@ -225,6 +261,7 @@ mg_status mg_batch_create(const mg_config *cfg, const int32_t *problem_n, mg_bat
     if (cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&B->flag, sizeof(int)) != cudaSuccess) {
         set_error("batch stream / event / flag allocation failed");
         return fail(MG_ERR_CUDA);
@@ -260,7 +297,19 @@ mg_status mg_batch_create(const mg_config *cfg, const int32_t *problem_n, mg_bat
         gc.n_leaves = static_cast<int32_t>(goff.size());
         gc.leaves = rows.data();
         gc.n_problems = static_cast<int32_t>(kv.second.size());
-        gc.stream = B->st;
+        cudaStream_t gs = nullptr;
+        cudaEvent_t ge = nullptr;
+        if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) {
+            set_error("group stream creation failed");
+            return fail(MG_ERR_CUDA);
+        }
+        B->gst.push_back(gs);
+        if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) {
+            set_error("group event creation failed");
+            return fail(MG_ERR_CUDA);
+        }
+        B->gev.push_back(ge);
+        gc.stream = gs;
         mg_forest *F = nullptr;
         mg_status st = create(&gc, &F);
         if (st != MG_OK) return fail(st);
@@ -272,9 +321,9 @@ mg_status mg_batch_create(const mg_config *cfg, const int32_t *problem_n, mg_bat
         if ((st = forest_alloc(F, &p, static_cast<int64_t>(goff.size() * sizeof(int64_t)))) != MG_OK) return fail(st);
         F->leaf_off = static_cast<int64_t *>(p);
         // same stream as the zero-fill of the allocation, then wait: the host vector dies at the end of the loop
-        if (cudaMemcpyAsync(F->leaf_off, goff.data(), goff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, B->st) !=
+        if (cudaMemcpyAsync(F->leaf_off, goff.data(), goff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, F->st) !=
                 cudaSuccess ||
-            cudaStreamSynchronize(B->st) != cudaSuccess) {
+            cudaStreamSynchronize(F->st) != cudaSuccess) {
             set_error("leaf offset upload failed");
             return fail(MG_ERR_CUDA);
         }
@@ -301,7 +350,9 @@ mg_status mg_batch_set_rhs(mg_batch *B, const double *f_dev, const double *k_dev
         set_error(hbad & 2 ? "k must be finite and > 0" : "f has a non-finite entry");
         return MG_ERR_NONFINITE;
     }
+    MG_TRY(fork(B));
     for (mg_forest *F : B->groups) MG_TRY(set_rhs(F, f_dev, k_dev));
+    MG_TRY(join(B));
     B->rhs_set = true;
     MG_TRY(leave(B));
     return MG_OK;

@@ -93,6 +93,7 @@ struct mg_forest {
     double *psum = nullptr, *psum_h = nullptr;   // per-problem sums (device, pinned host)
     float *pscale = nullptr, *pscale_h = nullptr;  // per-problem power-of-two residual scale (device, pinned host)
     double *pinv = nullptr, *pinv_h = nullptr;     // its inverse in FP64
+    uint8_t *pdone = nullptr, *pdone_h = nullptr;  // per problem: met rtol in the running solve (device, pinned host)
     int32_t *uprob = nullptr;                    // coarsest unknown -> problem
     int64_t *ustart = nullptr, *moff = nullptr;  // coarsest unknowns / inverse offsets per problem
     std::vector<int64_t> ustart_h, moff_h;
@@ -161,6 +162,8 @@ void exchange_any64(mg_forest *F, DevLevel &d, double *u);
 mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
 mg_status check_ready(mg_forest *F);
 mg_status check_kernel_waits(mg_forest *F);
+void reset_done(mg_forest *F);
+mg_status enqueue_done(mg_forest *F);
 mg_status ensure_scratch64(mg_forest *F);
 mg_status create(const mg_config *cfg, mg_forest **out);
 mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev);

@@ -34,6 +34,14 @@ struct Coef {       // coefficient arrays of one level (unused members are null)
     const float *kap;                        // MODE 2
 };
 
+// Problems of a multi-problem level that have met their tolerance in a batched solve: their blocks are skipped by
+// every kernel of the defect-correction step, so each problem stops where it converged (`done` null: none).
+struct Skip {
+    const int32_t *bprob;  // problem of each block of the level
+    const uint8_t *done;   // per problem
+    __device__ bool operator()(int64_t b) const { return done && done[bprob[b]]; }
+};
+
 __host__ __device__ inline int64_t off3(int X, int Y, int Z, int P) {
     return (static_cast<int64_t>(Z) * P + Y) * P + X;
 }
@@ -124,6 +132,21 @@ template <typename T> __device__ inline T w_tang(int c, int al, int b);
 template <> __device__ inline double w_tang<double>(int c, int al, int b) { return c_wt[c][al][b]; }
 template <> __device__ inline float w_tang<float>(int c, int al, int b) { return c_wt_f[c][al][b]; }
 
+// Global load of data that other CTAs of the same launch may have written earlier (CG = true: through L2 only,
+// as in the persistent tail kernel, whose phases are separated by grid barriers), or a plain load.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// Read-only-for-this-launch data (f of a level), or written by an earlier phase of a persistent launch (CG = true).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldr(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+
 __device__ inline float frcp(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -208,26 +231,27 @@ __device__ inline double apply_at(const double *__restrict__ u, const Coef &cf, 
 // KIND_K = true:  coefficient field k (ghost = k_i at the boundary; fine ghosts inject the covering coarse k).
 // One thread per ghost cell; n is a power of two, so items and cells decode with shifts.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T, bool KIND_K>
-static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g) {
+template <typename T, bool KIND_K, bool CG = false>
+__device__ __forceinline__ void exchange_faces_body(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems,
+                                                    LevelGeom g, Skip skip, int64_t t0, int64_t ts) {
     const int n = g.n, lg = g.lg, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lg);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = t0; t < total; t += ts) {
         const int it = static_cast<int>(t >> (2 * lg));
         const int r = static_cast<int>(t) & ((1 << (2 * lg)) - 1);
         const int i1 = r & (n - 1), i2 = r >> lg;
         const FaceItem F = items[it];
+        if (skip(F.blk)) continue;
         T val;
         if (F.kind == FK_BND) {
-            const T in = u[fidx<T>(g, F.blk, F.axis, F.side, 1, i1, i2)];
+            const T in = ldv<CG>(u + fidx<T>(g, F.blk, F.axis, F.side, 1, i1, i2));
             val = KIND_K ? in : -in;
         } else if (F.kind == FK_SAME) {
-            val = u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, i1, i2)];
+            val = ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, i1, i2));
         } else {
             const int yc = F.seg1 * h + (i1 >> 1), zc = F.seg2 * h + (i2 >> 1);
             if (KIND_K) {
-                val = u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, yc, zc)];
+                val = ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, yc, zc));
             } else {
                 const int a1 = i1 & 1, a2 = i2 & 1;
                 const int cy = yc == 0 ? 1 : (yc == n - 1 ? 2 : 0);
@@ -239,9 +263,9 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
                         const int y = yc + c_base[cy][b], z = zc + c_base[cz][c];
-                        T e = w_normal<T>(0) * u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, y, z)];
-                        e = fma(w_normal<T>(1), u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 2, y, z)], e);
-                        e = fma(w_normal<T>(2), u[fidx<T>(g, F.nbr, F.axis, 1 - F.side, 3, y, z)], e);
+                        T e = w_normal<T>(0) * ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, y, z));
+                        e = fma(w_normal<T>(1), ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 2, y, z)), e);
+                        e = fma(w_normal<T>(2), ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 3, y, z)), e);
                         accb = fma(w_tang<T>(cy, a1, b), e, accb);
                     }
                     acc = fma(w_tang<T>(cz, a2, c), accb, acc);
@@ -253,6 +277,13 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
     }
 }
 
+template <typename T, bool KIND_K>
+static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g,
+                                        Skip skip = Skip{}) {
+    exchange_faces_body<T, KIND_K>(u, items, nitems, g, skip, blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                                   static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Ghost exchange, part 2: coarse ghost segments next to finer neighbours.
 // FLUX = false: F2C mean of the 2x2x2 fine inner cells overlapping each coarse ghost cell (Sec. 3.3.1).
@@ -260,17 +291,17 @@ static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__res
 //               sub-faces j, g_j the fine ghosts (C2F, part 1 must have run), u_j the first fine layer.  With the
 //               1/h^2-scaled coefficients of MODE 1, T_j / (2 T_C) = T~_j / (8 T~_C) since h_C = 2 h_j.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T, int MODE, bool FLUX>
-static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
-                                LevelGeom g) {
+template <typename T, int MODE, bool FLUX, bool CG = false>
+__device__ __forceinline__ void exchange_segs_body(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items,
+                                                   int nitems, LevelGeom g, Skip skip, int64_t t0, int64_t ts) {
     const int n = g.n, lgh = g.lg - 1, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lgh);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = t0; t < total; t += ts) {
         const int it = static_cast<int>(t >> (2 * lgh));
         const int r = static_cast<int>(t) & ((1 << (2 * lgh)) - 1);
         const int p = r & (h - 1), q = r >> lgh;
         const SegItem S = items[it];
+        if (skip(S.coarse)) continue;
         const int fs = 1 - S.side;
         const int yc = S.s1 * h + p, zc = S.s2 * h + q;
         T val;
@@ -281,12 +312,12 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
 #pragma unroll
                 for (int b = 0; b < 2; ++b)
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) s += u[fidx<T>(g, S.fine, S.axis, fs, d, 2 * p + a, 2 * q + b)];
+                    for (int a = 0; a < 2; ++a) s += ldv<CG>(u + fidx<T>(g, S.fine, S.axis, fs, d, 2 * p + a, 2 * q + b));
             val = T(0.125) * s;
         } else {
             const int64_t gC = fidx<T>(g, S.coarse, S.axis, S.side, 1, yc, zc);
             const int64_t g0c = fidx<T>(g, S.coarse, S.axis, S.side, 0, yc, zc);
-            const T uC = u[gC];
+            const T uC = ldv<CG>(u + gC);
             T flux = T(0);
 #pragma unroll
             for (int b = 0; b < 2; ++b)
@@ -295,13 +326,21 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
                     const int64_t g0 = fidx<T>(g, S.fine, S.axis, fs, 0, 2 * p + a, 2 * q + b);
                     const int64_t g1 = fidx<T>(g, S.fine, S.axis, fs, 1, 2 * p + a, 2 * q + b);
                     const T Tj = face_coef<T, MODE>(cf, fs ? g0 : g1, fs ? g1 : g0, S.axis);
-                    flux = fma(Tj, u[g0] - u[g1], flux);
+                    flux = fma(Tj, ldv<CG>(u + g0) - ldv<CG>(u + g1), flux);
                 }
             const T Tc = face_coef<T, MODE>(cf, S.side ? g0c : gC, S.side ? gC : g0c, S.axis);
             val = uC - flux / (T(MODE == 1 ? 8 : 2) * Tc);
         }
         u[fidx<T>(g, S.coarse, S.axis, S.side, 0, yc, zc)] = val;
     }
+}
+
+template <typename T, int MODE, bool FLUX>
+static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
+                                       LevelGeom g, Skip skip = Skip{}) {
+    exchange_segs_body<T, MODE, FLUX>(u, cf, items, nitems, g, skip,
+                                      blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                                      static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -318,7 +357,7 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
 // have the other colour), so the writes cannot race with the reads.
 template <typename T, int MODE>
 static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2,
-                                LevelGeom g, int colour, const int32_t *__restrict__ nbr6) {
+                                LevelGeom g, int colour, const int32_t *__restrict__ nbr6, Skip skip = Skip{}) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg - 1);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -327,6 +366,7 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
         const int y = static_cast<int>((t >> (lg - 1)) & (n - 1));
         const int z = static_cast<int>((t >> (2 * lg - 1)) & (n - 1));
         const int64_t b = t >> (3 * lg - 1);
+        if (skip(b)) continue;
         const int x = 2 * j + ((y + z + colour) & 1);
         T val;
         if constexpr (sizeof(T) == 4) {
@@ -411,17 +451,18 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
 // it, before the write.  x faces concern one lane of a row (j = 0 with c = 0, j = n/2 - 1 with c = 1) and take a
 // short path of their own; y and z faces are uniform over a row.
 // ------------------------------------------------------------------------------------------------------------
-template <int MODE, int LG, int ZC>
+template <int MODE, int LG, int ZC, bool CG = false>
 __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const float *__restrict__ f,
                                                 const float *__restrict__ kap, const float *__restrict__ h2,
                                                 int64_t bs, int colour, const int32_t *__restrict__ nbr6,
-                                                int64_t t) {
+                                                Skip skip, int64_t t) {
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, HP = half_row(P), PL = P * HP, HALF = P * PL;
     constexpr int LZ = ZC == 1 ? 0 : (ZC == 2 ? 1 : (ZC == 4 ? 2 : 3));
     static_assert((1 << LZ) == ZC && ZC <= n, "column length");
     constexpr int SH = 3 * LG - 1 - LZ;  // log2(columns per block)
     const int r = static_cast<int>(t) & ((1 << SH) - 1);
     const int64_t b = t >> SH;
+    if (skip(b)) return;
     const int j = r & (NH - 1);
     const int y = (r >> (LG - 1)) & (n - 1);
     const int z0 = (r >> (2 * LG - 1)) << LZ;
@@ -439,16 +480,16 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
     float kx0[ZC], kx1[ZC], kym[ZC], kyp[ZC], k0[ZC];
     float kzlo = 0.f, kzhi = 0.f;
     constexpr int odd = (ZC - 1) & 1;  // c of the last cell is c0 ^ odd
-    const float zlo = ub[ioc - PL];
-    const float zhi = ub[(odd ? io + 1 - c0 : ioc) + ZC * PL];
+    const float zlo = ldv<CG>(ub + (ioc - PL));
+    const float zhi = ldv<CG>(ub + ((odd ? io + 1 - c0 : ioc) + ZC * PL));
 #pragma unroll
     for (int dz = 0; dz < ZC; ++dz) {
-        xr0[dz] = ub[io + dz * PL];
-        xr1[dz] = ub[io + dz * PL + 1];
+        xr0[dz] = ldv<CG>(ub + (io + dz * PL));
+        xr1[dz] = ldv<CG>(ub + (io + dz * PL + 1));
         const int ic = (dz & 1) ? io + 1 - c0 : ioc;  // other half at r_z + j + c_z
-        ym[dz] = ub[ic + dz * PL - HP];
-        yp[dz] = ub[ic + dz * PL + HP];
-        fv[dz] = __ldg(fb + ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL);
+        ym[dz] = ldv<CG>(ub + (ic + dz * PL - HP));
+        yp[dz] = ldv<CG>(ub + (ic + dz * PL + HP));
+        fv[dz] = ldr<CG>(fb + ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL);
     }
     if constexpr (MODE == 2) {
         kzlo = __ldg(kb + ioc - PL);
@@ -531,9 +572,9 @@ template <int MODE, int LG, int ZC>
 static __global__ void __launch_bounds__(512) k_smooth32(float *__restrict__ u, const float *__restrict__ f,
                                                          const float *__restrict__ kap, const float *__restrict__ h2,
                                                          int64_t total, int64_t bs, int colour,
-                                                         const int32_t *__restrict__ nbr6) {
+                                                         const int32_t *__restrict__ nbr6, Skip skip) {
     const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (t < total) smooth32_column<MODE, LG, ZC>(u, f, kap, h2, bs, colour, nbr6, t);
+    if (t < total) smooth32_column<MODE, LG, ZC>(u, f, kap, h2, bs, colour, nbr6, skip, t);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -598,7 +639,7 @@ template <int MODE, int LG, int R>
 static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u, const float *__restrict__ f,
                                                           const float *__restrict__ kap, const float *__restrict__ h2,
                                                           int64_t bs, int colour, const int32_t *__restrict__ nbr6,
-                                                          int TY, int TZ, int D, int *__restrict__ err) {
+                                                          int TY, int TZ, int D, int *__restrict__ err, Skip skip) {
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, H = half_row(P), PL = P * H, HALF = P * PL;
     constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -615,6 +656,7 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
     const int64_t rest = blockIdx.x / nty;
     const int tz = static_cast<int>(rest % (n / TZ));
     const int64_t b = rest / (n / TZ);
+    if (skip(b)) return;  // uniform over the CTA, before any barrier
     const int y0 = ty * TY, z0 = tz * TZ;
     const int s = colour ^ 1;
     const int tid = threadIdx.x;
@@ -763,27 +805,28 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
 }
 
 // Point-form residual at padded cell (X, Y, Z) of block b, any layout (used by the FP32 kernels).
-template <typename T, int MODE>
+template <typename T, int MODE, bool CG = false>
 __device__ inline T residual_xyz(const T *__restrict__ u, const T *__restrict__ f, const Coef &cf,
                                  const LevelGeom &g, int64_t b, int X, int Y, int Z, T ih2) {
     const int64_t i0 = Lay<T>::at(g, b, X, Y, Z);
     const int64_t nb[6] = {Lay<T>::at(g, b, X - 1, Y, Z), Lay<T>::at(g, b, X + 1, Y, Z),
                            Lay<T>::at(g, b, X, Y - 1, Z), Lay<T>::at(g, b, X, Y + 1, Z),
                            Lay<T>::at(g, b, X, Y, Z - 1), Lay<T>::at(g, b, X, Y, Z + 1)};
-    const T u0 = u[i0];
+    const T u0 = ldv<CG>(u + i0);
     if constexpr (MODE == 0) {
-        const T S = ((u[nb[0]] + u[nb[1]]) + (u[nb[2]] + u[nb[3]])) + (u[nb[4]] + u[nb[5]]);
-        return fma(fma(T(-6), u0, S), ih2, f[i0]);
+        const T S = ((ldv<CG>(u + nb[0]) + ldv<CG>(u + nb[1])) + (ldv<CG>(u + nb[2]) + ldv<CG>(u + nb[3]))) +
+                    (ldv<CG>(u + nb[4]) + ldv<CG>(u + nb[5]));
+        return fma(fma(T(-6), u0, S), ih2, ldv<CG>(f + i0));
     } else {
         const float k0 = cf.kap[i0];
         float S = 0.0f, D = 0.0f;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const float a = frcp(k0 + cf.kap[nb[q]]);
-            S = fmaf(a, float(u[nb[q]]), S);
+            S = fmaf(a, float(ldv<CG>(u + nb[q])), S);
             D += a;
         }
-        return T(fmaf(2.0f * fmaf(-D, float(u0), S), float(ih2), float(f[i0])));
+        return T(fmaf(2.0f * fmaf(-D, float(u0), S), float(ih2), float(ldv<CG>(f + i0))));
     }
 }
 
@@ -792,24 +835,25 @@ __device__ inline T residual_xyz(const T *__restrict__ u, const T *__restrict__ 
 // right-hand side; the coarse solution's interior is zeroed (coarse-grid correction starts from 0).
 // One thread per coarse cell.  ih2f: 1/h^2 per fine block.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T, int MODE>
-static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
-                                    const T *__restrict__ ih2f, LevelGeom gf, T *__restrict__ fc,
-                                    T *__restrict__ uc, const XferItem *__restrict__ xf, LevelGeom gc) {
+template <typename T, int MODE, bool CG = false>
+__device__ __forceinline__ void residual_restrict_body(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
+                                                       const T *__restrict__ ih2f, LevelGeom gf, T *__restrict__ fc,
+                                                       T *__restrict__ uc, const XferItem *__restrict__ xf,
+                                                       LevelGeom gc, Skip skip, int64_t t0, int64_t ts) {
     const int lgc = gc.lg, nc = gc.n;
     const int64_t total = static_cast<int64_t>(gc.nb) << (3 * lgc);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = t0; t < total; t += ts) {
         const int X = static_cast<int>(t & (nc - 1));
         const int Y = static_cast<int>((t >> lgc) & (nc - 1));
         const int Z = static_cast<int>((t >> (2 * lgc)) & (nc - 1));
         const int64_t B = t >> (3 * lgc);
+        if (skip(B)) continue;
         const XferItem xi = xf[B];
         const int64_t gcell = Lay<T>::at(gc, B, X + 1, Y + 1, Z + 1);
         uc[gcell] = T(0);
         const auto res = [&](int64_t bb, int xx, int yy, int zz, T ih2) {
             if constexpr (sizeof(T) == 4)
-                return residual_xyz<T, MODE>(u, f, cf, gf, bb, xx, yy, zz, ih2);
+                return residual_xyz<T, MODE, CG>(u, f, cf, gf, bb, xx, yy, zz, ih2);
             else
                 return residual_at<T, MODE>(u, f, cf, bb * gf.bs + off3(xx, yy, zz, gf.P), gf.P, ih2);
         };
@@ -845,6 +889,16 @@ static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__r
     }
 }
 
+template <typename T, int MODE>
+static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
+                                           const T *__restrict__ ih2f, LevelGeom gf, T *__restrict__ fc,
+                                           T *__restrict__ uc, const XferItem *__restrict__ xf, LevelGeom gc,
+                                           Skip skip = Skip{}) {
+    residual_restrict_body<T, MODE>(u, f, cf, ih2f, gf, fc, uc, xf, gc, skip,
+                                    blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                                    static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // FP32 residual + restriction for a level whose blocks all halve (fine edge n = 2^LG, coarse n/2), colour-split
 // pools on both sides.  One thread per coarse cell (X, Y, Z): its 8 children are the fine padded cells
@@ -862,18 +916,18 @@ struct Box32 {
     }
 };
 
-template <int MODE, int LG>
-static __global__ void __launch_bounds__(256) k_residual_restrict32(
+template <int MODE, int LG, bool CG = false>
+__device__ __forceinline__ void residual_restrict32_body(
         const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
         const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
-        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc) {
+        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip, int64_t t0, int64_t ts) {
     using Bx = Box32<LG>;
     constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), HALFc = Pc * Pc * HPc;
     const int64_t total = static_cast<int64_t>(nbc) << (3 * LC);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = t0; t < total; t += ts) {
         const int r = static_cast<int>(t) & ((1 << (3 * LC)) - 1);
         const int64_t B = t >> (3 * LC);
+        if (skip(B)) continue;  // the coarse level's problem ids
         const int X = r & (nc - 1), Y = (r >> LC) & (nc - 1), Z = r >> (2 * LC);
         const int64_t b = xf[B].src[0];
         const int64_t corner = b * bsf + (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;
@@ -887,7 +941,7 @@ static __global__ void __launch_bounds__(256) k_residual_restrict32(
                 for (int i = 0; i < 4; ++i) {
                     const int out = (i == 0 || i == 3) + (j == 0 || j == 3) + (k == 0 || k == 3);
                     if (out > 1) continue;
-                    U[k][j][i] = ub[Bx::off(i, j, k)];
+                    U[k][j][i] = ldv<CG>(ub + Bx::off(i, j, k));
                     if constexpr (MODE == 2) K[k][j][i] = __ldg(kap + corner + Bx::off(i, j, k));
                 }
         const float ih2 = __ldg(ih2f + b);
@@ -899,7 +953,7 @@ static __global__ void __launch_bounds__(256) k_residual_restrict32(
 #pragma unroll
                 for (int i = 1; i < 3; ++i) {
                     const float u0 = U[k][j][i];
-                    const float fv = __ldg(f + corner + Bx::off(i, j, k));
+                    const float fv = ldr<CG>(f + corner + Bx::off(i, j, k));
                     const float nbu[6] = {U[k][j][i - 1], U[k][j][i + 1], U[k][j - 1][i],
                                           U[k][j + 1][i], U[k - 1][j][i], U[k + 1][j][i]};
                     if constexpr (MODE == 0) {
@@ -940,33 +994,42 @@ static __global__ void __launch_bounds__(256) k_residual_restrict32(
     }
 }
 
+template <int MODE, int LG>
+static __global__ void __launch_bounds__(256) k_residual_restrict32(
+        const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
+        const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
+        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip) {
+    residual_restrict32_body<MODE, LG>(u, f, kap, ih2f, bsf, fc, uc, xf, nbc, bsc, skip,
+                                       blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                                       static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
 // FP32 prolongation + correction for a level whose blocks all halve (fine edge 2^LG): one thread per coarse cell
 // adds 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) to its 8 children, fine offsets as in Box32.  With nbr6 (the
 // fine level's face table, as in k_smooth) every child on a block face also writes its new value through to the
 // same-level neighbour's mirroring ghost, or the reflected value to its own boundary ghost, so that afterwards only
 // refinement-interface ghosts need an exchange.
-template <int LG>
-static __global__ void __launch_bounds__(256) k_prolong32(float *__restrict__ uf, int64_t bsf,
-                                                          const float *__restrict__ ec,
-                                                          const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc,
-                                                          const int32_t *__restrict__ nbr6) {
+template <int LG, bool CG = false>
+__device__ __forceinline__ void prolong32_body(float *__restrict__ uf, int64_t bsf, const float *__restrict__ ec,
+                                               const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc,
+                                               const int32_t *__restrict__ nbr6, Skip skip, int64_t t0, int64_t ts) {
     using Bx = Box32<LG>;
     constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), PLc = Pc * HPc, HALFc = Pc * PLc;
     const int64_t total = static_cast<int64_t>(nbc) << (3 * LC);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = t0; t < total; t += ts) {
         const int r = static_cast<int>(t) & ((1 << (3 * LC)) - 1);
         const int64_t B = t >> (3 * LC);
+        if (skip(B)) continue;
         const int X = r & (nc - 1), Y = (r >> LC) & (nc - 1), Z = r >> (2 * LC);
         const int Xc = X + 1, Yc = Y + 1, Zc = Z + 1;
         const int pc = (Xc + Yc + Zc) & 1;
         const int row = (Zc * Pc + Yc) * HPc;
         const float *own = ec + B * bsc + pc * HALFc + row;
         const float *oth = ec + B * bsc + (pc ^ 1) * HALFc + row;
-        const float e0 = own[Xc >> 1];
-        const float exm = oth[(Xc - 1) >> 1], exp_ = oth[(Xc + 1) >> 1];
-        const float eym = oth[(Xc >> 1) - HPc], eyp = oth[(Xc >> 1) + HPc];
-        const float ezm = oth[(Xc >> 1) - PLc], ezp = oth[(Xc >> 1) + PLc];
+        const float e0 = ldv<CG>(own + (Xc >> 1));
+        const float exm = ldv<CG>(oth + ((Xc - 1) >> 1)), exp_ = ldv<CG>(oth + ((Xc + 1) >> 1));
+        const float eym = ldv<CG>(oth + ((Xc >> 1) - HPc)), eyp = ldv<CG>(oth + ((Xc >> 1) + HPc));
+        const float ezm = ldv<CG>(oth + ((Xc >> 1) - PLc)), ezp = ldv<CG>(oth + ((Xc >> 1) + PLc));
         const float ex[2] = {exm, exp_}, ey[2] = {eym, eyp}, ez[2] = {ezm, ezp};
         const int64_t b = xf[B].src[0];
         float *ub = uf + b * bsf + (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;
@@ -976,7 +1039,7 @@ static __global__ void __launch_bounds__(256) k_prolong32(float *__restrict__ uf
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-                for (int a = 0; a < 2; ++a) cur[c][bb][a] = ub[Bx::off(a + 1, bb + 1, c + 1)];
+                for (int a = 0; a < 2; ++a) cur[c][bb][a] = ldv<CG>(ub + Bx::off(a + 1, bb + 1, c + 1));
         const bool face = nbr6 && (X == 0 || X == nc - 1 || Y == 0 || Y == nc - 1 || Z == 0 || Z == nc - 1);
         const int corner = (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;  // in-block offset of the box corner
 #pragma unroll
@@ -1006,6 +1069,16 @@ static __global__ void __launch_bounds__(256) k_prolong32(float *__restrict__ uf
                     }
                 }
     }
+}
+
+template <int LG>
+static __global__ void __launch_bounds__(256) k_prolong32(float *__restrict__ uf, int64_t bsf,
+                                                          const float *__restrict__ ec,
+                                                          const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc,
+                                                          const int32_t *__restrict__ nbr6, Skip skip) {
+    prolong32_body<LG>(uf, bsf, ec, xf, nbc, bsc, nbr6, skip,
+                       blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                       static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
 
 // Restriction of a plain field (mean of the 8 children; copy for carried-over blocks), e.g. the coefficient k.
@@ -1054,26 +1127,30 @@ static __global__ void k_restrict_field(const T *__restrict__ xf_in, LevelGeom g
 // along axis d (face-neighbour linear interpolation, exact for linear functions; coarse ghosts exchanged).
 // One thread per coarse cell, writing its 8 children.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T>
-static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
-                                 const XferItem *__restrict__ xf, LevelGeom gc) {
+template <typename T, bool CG = false>
+__device__ __forceinline__ void prolong_body(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
+                                             const XferItem *__restrict__ xf, LevelGeom gc, Skip skip, int64_t t0,
+                                             int64_t ts) {
     const int lgc = gc.lg, nc = gc.n;
     const int64_t total = static_cast<int64_t>(gc.nb) << (3 * lgc);
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = t0; t < total; t += ts) {
         const int X = static_cast<int>(t & (nc - 1));
         const int Y = static_cast<int>((t >> lgc) & (nc - 1));
         const int Z = static_cast<int>((t >> (2 * lgc)) & (nc - 1));
         const int64_t B = t >> (3 * lgc);
+        if (skip(B)) continue;
         const XferItem xi = xf[B];
-        const T e0 = ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z + 1)];
+        const T e0 = ldv<CG>(ec + Lay<T>::at(gc, B, X + 1, Y + 1, Z + 1));
         if (xi.kind == XF_COPY) {
-            uf[Lay<T>::at(gf, xi.src[0], X + 1, Y + 1, Z + 1)] += e0;
+            {
+                const int64_t gi = Lay<T>::at(gf, xi.src[0], X + 1, Y + 1, Z + 1);
+                uf[gi] = ldv<CG>(uf + gi) + e0;
+            }
             continue;
         }
-        const T ex[2] = {ec[Lay<T>::at(gc, B, X, Y + 1, Z + 1)], ec[Lay<T>::at(gc, B, X + 2, Y + 1, Z + 1)]};
-        const T ey[2] = {ec[Lay<T>::at(gc, B, X + 1, Y, Z + 1)], ec[Lay<T>::at(gc, B, X + 1, Y + 2, Z + 1)]};
-        const T ez[2] = {ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z)], ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z + 2)]};
+        const T ex[2] = {ldv<CG>(ec + Lay<T>::at(gc, B, X, Y + 1, Z + 1)), ldv<CG>(ec + Lay<T>::at(gc, B, X + 2, Y + 1, Z + 1))};
+        const T ey[2] = {ldv<CG>(ec + Lay<T>::at(gc, B, X + 1, Y, Z + 1)), ldv<CG>(ec + Lay<T>::at(gc, B, X + 1, Y + 2, Z + 1))};
+        const T ez[2] = {ldv<CG>(ec + Lay<T>::at(gc, B, X + 1, Y + 1, Z)), ldv<CG>(ec + Lay<T>::at(gc, B, X + 1, Y + 1, Z + 2))};
         int64_t b;
         int x0, y0, z0;
         if (xi.kind == XF_HALVE) {
@@ -1095,9 +1172,18 @@ static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__re
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
-                    uf[Lay<T>::at(gf, b, x0 + a + 1, y0 + bb + 1, z0 + c + 1)] +=
-                        T(0.25) * ((e0 + ex[a]) + (ey[bb] + ez[c]));
+                {
+                    const int64_t gi = Lay<T>::at(gf, b, x0 + a + 1, y0 + bb + 1, z0 + c + 1);
+                    uf[gi] = ldv<CG>(uf + gi) + T(0.25) * ((e0 + ex[a]) + (ey[bb] + ez[c]));
+                }
     }
+}
+
+template <typename T>
+static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
+                                 const XferItem *__restrict__ xf, LevelGeom gc, Skip skip = Skip{}) {
+    prolong_body<T>(uf, gf, ec, xf, gc, skip, blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                    static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1105,22 +1191,32 @@ static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__re
 // problem p are cmap[ustart[p] .. ustart[p+1]), its inverse is the row-major N_p x N_p matrix at Ainv + moff[p]).
 // One warp per unknown; f gathered from the padded pool through cmap.
 // ------------------------------------------------------------------------------------------------------------
+template <typename T, bool CG = false>
+__device__ __forceinline__ void coarse_solve_row(T *__restrict__ u, const T *__restrict__ f,
+                                                 const double *__restrict__ Ainv, const int64_t *__restrict__ cmap,
+                                                 const int32_t *__restrict__ uprob, const int64_t *__restrict__ ustart,
+                                                 const int64_t *__restrict__ moff, const uint8_t *__restrict__ done,
+                                                 int row_i, int lane) {
+    const int p = uprob[row_i];
+    if (done && done[p]) return;
+    const int64_t base = ustart[p];
+    const int Np = static_cast<int>(ustart[p + 1] - base);
+    const double *row = Ainv + moff[p] + static_cast<int64_t>(row_i - base) * Np;
+    double s = 0.0;
+    for (int j = lane; j < Np; j += 32) s = fma(row[j], static_cast<double>(ldv<CG>(f + cmap[base + j])), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) u[cmap[row_i]] = T(s);
+}
+
 template <typename T>
 static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const double *__restrict__ Ainv,
                                       const int64_t *__restrict__ cmap, const int32_t *__restrict__ uprob,
-                                      const int64_t *__restrict__ ustart, const int64_t *__restrict__ moff, int N) {
+                                      const int64_t *__restrict__ ustart, const int64_t *__restrict__ moff, int N,
+                                      const uint8_t *__restrict__ done = nullptr) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     if (warp >= N) return;
-    const int p = uprob[warp];
-    const int64_t base = ustart[p];
-    const int Np = static_cast<int>(ustart[p + 1] - base);
-    const double *row = Ainv + moff[p] + static_cast<int64_t>(warp - base) * Np;
-    double s = 0.0;
-    for (int j = lane; j < Np; j += 32) s = fma(row[j], static_cast<double>(f[cmap[base + j]]), s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) u[cmap[warp]] = T(s);
+    coarse_solve_row<T>(u, f, Ainv, cmap, uprob, ustart, moff, done, warp, threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1135,9 +1231,10 @@ static __global__ void k_residual_norm(const double *__restrict__ u, const doubl
                                        const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
                                        int cpb, float *__restrict__ out, const float *__restrict__ pscale,
                                        const int32_t *__restrict__ bprob, double *__restrict__ bsum,
-                                       float *__restrict__ zero_out) {
+                                       float *__restrict__ zero_out, Skip skip = Skip{}) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t b = blockIdx.x / cpb;
+    if (skip(b)) return;  // the whole CTA: its block's sum stays 0
     const int chunk = blockIdx.x - static_cast<int>(b * cpb);
     const int per = (1 << (3 * lg)) / cpb;
     const float scale = pscale[bprob[b]];
@@ -1309,7 +1406,7 @@ static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__
 // u64 += e32 / scale_p over the interior (mixed-precision defect correction update; pinv = 1 / scale_p per problem)
 static __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__ e,
                                       const double *__restrict__ pinv, const int32_t *__restrict__ bprob,
-                                      LevelGeom g) {
+                                      LevelGeom g, Skip skip = Skip{}) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -1318,6 +1415,7 @@ static __global__ void k_update_mixed(double *__restrict__ u, const float *__res
         const int y = static_cast<int>((t >> lg) & (n - 1));
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
+        if (skip(b)) continue;
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, g.P);
         u[gi] = fma(pinv[bprob[b]], static_cast<double>(e[Lay<float>::at(g, b, x + 1, y + 1, z + 1)]), u[gi]);
     }

@@ -89,6 +89,9 @@ template <typename T> Coef coef_of(const DevLevel &d);
 template <> Coef coef_of<double>(const DevLevel &d) { return d.c64(); }
 template <> Coef coef_of<float>(const DevLevel &d) { return d.c32(); }
 
+// The done-mask view of a level for its kernels (all problems active outside a solve).
+Skip skip_of(mg_forest *F, const DevLevel &d) { return Skip{d.bprob, F->pdone}; }
+
 // Ghost exchange of a level: every face (full), or only the refinement-interface faces (C2F and F2C), whose
 // ghosts the smoother's write-through does not maintain.
 template <typename T, int MODE>
@@ -99,13 +102,15 @@ void exchange(mg_forest *F, DevLevel &d, T *u, bool interface_only = false) {
     Prof p(F, cat_of<T>(P_EXCH64), (nitems ? 1 : 0) + (d.nsegs ? 1 : 0));
     if (nitems)
         k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(nitems) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
-            u, items, nitems, d.g);
+            u, items, nitems, d.g, skip_of(F, d));
     if (d.nsegs) {
         const int64_t tot = static_cast<int64_t>(d.nsegs) * (d.g.n / 2) * (d.g.n / 2);
         if (F->cfg.interface_flux)
-            k_exchange_segs<T, MODE, true><<<grid_for(tot), kThreads, 0, F->st>>>(u, coef_of<T>(d), d.segs, d.nsegs, d.g);
+            k_exchange_segs<T, MODE, true><<<grid_for(tot), kThreads, 0, F->st>>>(u, coef_of<T>(d), d.segs, d.nsegs, d.g,
+                                                                                skip_of(F, d));
         else
-            k_exchange_segs<T, MODE, false><<<grid_for(tot), kThreads, 0, F->st>>>(u, coef_of<T>(d), d.segs, d.nsegs, d.g);
+            k_exchange_segs<T, MODE, false><<<grid_for(tot), kThreads, 0, F->st>>>(u, coef_of<T>(d), d.segs, d.nsegs,
+                                                                                 d.g, skip_of(F, d));
     }
 }
 
@@ -132,7 +137,7 @@ void exchange_k(mg_forest *F, DevLevel &d) {
 // A shape only changes which thread updates a cell, never the arithmetic, so every shape gives identical bits.
 using Shape = std::array<int32_t, 5>;
 using Smooth32Fn = void (*)(float *, const float *, const float *, const float *, int64_t, int64_t, int,
-                            const int32_t *);
+                            const int32_t *, Skip);
 #define OCTMG_S32(K, M, L) {K<M, L, 1>, K<M, L, 2>, K<M, L, 4>}
 const Smooth32Fn kSmooth32[2][6][3] = {
     {OCTMG_S32(k_smooth32, 0, 2), OCTMG_S32(k_smooth32, 0, 3), OCTMG_S32(k_smooth32, 0, 4),
@@ -140,7 +145,7 @@ const Smooth32Fn kSmooth32[2][6][3] = {
     {OCTMG_S32(k_smooth32, 2, 2), OCTMG_S32(k_smooth32, 2, 3), OCTMG_S32(k_smooth32, 2, 4),
      OCTMG_S32(k_smooth32, 2, 5), OCTMG_S32(k_smooth32, 2, 6), OCTMG_S32(k_smooth32, 2, 7)}};
 using Smooth32tFn = void (*)(float *, const float *, const float *, const float *, int64_t, int, const int32_t *, int,
-                             int, int, int *);
+                             int, int, int *, Skip);
 const Smooth32tFn kSmooth32t[2][3][3] = {
     {OCTMG_S32(k_smooth32t, 0, 5), OCTMG_S32(k_smooth32t, 0, 6), OCTMG_S32(k_smooth32t, 0, 7)},
     {OCTMG_S32(k_smooth32t, 2, 5), OCTMG_S32(k_smooth32t, 2, 6), OCTMG_S32(k_smooth32t, 2, 7)}};
@@ -193,14 +198,14 @@ void launch_smooth32(mg_forest *F, DevLevel &d, int colour, const Shape &sh, cud
         });
         const int64_t grid = static_cast<int64_t>(d.g.nb) * (n / TY) * (n / TZ);
         fn<<<static_cast<unsigned>(grid), (n / 2) * TY / R, smem, st>>>(d.u32, d.f32, d.kap, d.h2_32, d.g.bs, colour,
-                                                                         d.nbr6, TY, TZ, D, F->kerr);
+                                                                         d.nbr6, TY, TZ, D, F->kerr, skip_of(F, d));
         return;
     }
     const int zc = sh[1], threads = sh[2];
     const int64_t work = (d.cells() / 2) >> ridx(zc);  // one thread per column of zc cells
     const int64_t grid = (work + threads - 1) / threads;
     kSmooth32[mi][d.g.lg - 2][ridx(zc)]<<<static_cast<unsigned>(grid), threads, 0, st>>>(
-        d.u32, d.f32, d.kap, d.h2_32, work, d.g.bs, colour, d.nbr6);
+        d.u32, d.f32, d.kap, d.h2_32, work, d.g.bs, colour, d.nbr6, skip_of(F, d));
 }
 
 // Reads and clears the device error word of bounded waits.
@@ -283,24 +288,24 @@ mg_status tune_smooth32(mg_forest *F) {
 bool transfer32_specialised(const DevLevel &d) { return d.all_halve && d.g.lg >= 3 && d.g.lg <= 7; }
 
 using Restrict32Fn = void (*)(const float *, const float *, const float *, const float *, int64_t, float *, float *,
-                              const XferItem *, int32_t, int64_t);
+                              const XferItem *, int32_t, int64_t, Skip);
 const Restrict32Fn kRestrict32[2][5] = {
     {k_residual_restrict32<0, 3>, k_residual_restrict32<0, 4>, k_residual_restrict32<0, 5>,
      k_residual_restrict32<0, 6>, k_residual_restrict32<0, 7>},
     {k_residual_restrict32<2, 3>, k_residual_restrict32<2, 4>, k_residual_restrict32<2, 5>,
      k_residual_restrict32<2, 6>, k_residual_restrict32<2, 7>}};
 using Prolong32Fn = void (*)(float *, int64_t, const float *, const XferItem *, int32_t, int64_t,
-                             const int32_t *);
+                             const int32_t *, Skip);
 const Prolong32Fn kProlong32[5] = {k_prolong32<3>, k_prolong32<4>, k_prolong32<5>, k_prolong32<6>, k_prolong32<7>};
 
 void launch_residual_restrict32(mg_forest *F, DevLevel &d, DevLevel &c) {
     kRestrict32[F->cfg.coeff ? 1 : 0][d.g.lg - 3]<<<grid_for(c.cells()), kThreads, 0, F->st>>>(
-        d.u32, d.f32, d.kap, d.ih2_32, d.g.bs, c.f32, c.u32, d.xfer, c.g.nb, c.g.bs);
+        d.u32, d.f32, d.kap, d.ih2_32, d.g.bs, c.f32, c.u32, d.xfer, c.g.nb, c.g.bs, skip_of(F, c));
 }
 
 void launch_prolong32(mg_forest *F, DevLevel &d, DevLevel &c) {
     kProlong32[d.g.lg - 3]<<<grid_for(c.cells()), kThreads, 0, F->st>>>(d.u32, d.g.bs, c.u32, d.xfer, c.g.nb, c.g.bs,
-                                                                          d.nbr6);
+                                                                          d.nbr6, skip_of(F, c));
 }
 
 template <typename T, int MODE>
@@ -313,7 +318,7 @@ void smooth(mg_forest *F, DevLevel &d, int colour) {
         }
     }
     k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d),
-                                                                       h2_of<T>(d), d.g, colour, d.nbr6);
+                                                                       h2_of<T>(d), d.g, colour, d.nbr6, skip_of(F, d));
 }
 
 // V(nu1, nu2) on level l.  Exchange schedule: at level entry a full exchange, unless the ghosts are known to be
@@ -331,7 +336,7 @@ void vcycle(mg_forest *F, int l, int entry) {
         Prof p(F, cat_of<T>(P_COARSE64), 1);
         k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(
             ufield<T>(d), ffield<T>(d), F->Ainv, sizeof(T) == 4 ? F->cmap32 : F->cmap, F->uprob, F->ustart, F->moff,
-            F->Nc);
+            F->Nc, F->pdone);
         exchange<T, MODE>(F, d, ufield<T>(d));
         return;
     }
@@ -351,7 +356,8 @@ void vcycle(mg_forest *F, int l, int entry) {
             launch_residual_restrict32(F, d, c);
         else
             k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
-                ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g);
+                ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g,
+                skip_of(F, c));
     }
     vcycle<T, MODE>(F, l + 1, fast ? ENTRY_NONE : ENTRY_FULL);
     if (l + 1 != last) exchange<T, MODE>(F, c, ufield<T>(c), true);
@@ -360,7 +366,8 @@ void vcycle(mg_forest *F, int l, int entry) {
         if (fast)
             launch_prolong32(F, d, c);
         else
-            k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g);
+            k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g,
+                                                                      skip_of(F, c));
     }
     exchange<T, MODE>(F, d, ufield<T>(d), fast);
     for (int i = 0; i < F->cfg.nu2; ++i) {
@@ -396,6 +403,19 @@ mg_status enqueue_scales(mg_forest *F) {
     return MG_OK;
 }
 
+// The done-mask to the device (pinned host copy read when the copy runs, also inside a replayed graph).
+mg_status enqueue_done(mg_forest *F) {
+    MG_CUDA(cudaMemcpyAsync(F->pdone, F->pdone_h, F->np, cudaMemcpyHostToDevice, F->st));
+    return MG_OK;
+}
+
+// Clears the per-problem done-mask (host and device): outside a solve no problem is skipped.
+void reset_done(mg_forest *F) {
+    std::memset(F->pdone_h, 0, F->np);
+    cudaMemsetAsync(F->pdone, 0, F->np, F->st);
+}
+
+
 mg_status upload_scales(mg_forest *F, const std::vector<double> &mult) {
     set_scales_host(F, mult);
     return enqueue_scales(F);
@@ -420,7 +440,8 @@ mg_status residual64(mg_forest *F, double *u, const double *f, float *out, float
     {
         Prof p(F, P_RESID64, 1);
         k_residual_norm<MODE><<<d.g.nb * cpb, kThreads, 0, F->st>>>(u, f, d.c64(), d.ih2_64, d.vol_32, d.g, cpb, out,
-                                                                    F->pscale, d.bprob, F->bsum, zero_out);
+                                                                    F->pscale, d.bprob, F->bsum, zero_out,
+                                                                    skip_of(F, d));
     }
     if (rr) {
         MG_TRY(read_problem_sums(F));
@@ -606,7 +627,7 @@ mg_status finish_mixed_cycle(mg_forest *F, int cycles) {
     DevLevel &d = F->L[0];
     for (int i = 0; i < cycles; ++i) vcycle32(F);
     Prof p(F, P_UPDATE, 1);
-    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, F->pinv, d.bprob, d.g);
+    k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, F->pinv, d.bprob, d.g, skip_of(F, d));
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -663,21 +684,30 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
     DevLevel &d = F->L[0];
     const int np = F->np;
     MG_TRY(pack_user<double>(F, d, d.u64, u_dev));
+    reset_done(F);
     std::vector<double> fn(np), rel(np, -1.0), mult(np), rr(np, 0.0);
     std::vector<int32_t> met(np, -1);
     for (int p = 0; p < np; ++p) {
         fn[p] = F->fnorm_p[p] > 0.0 ? F->fnorm_p[p] : 1.0;
         mult[p] = pow2_near(1.0 / fn[p]);
     }
+    // A problem that meets rtol is masked out of every later kernel (its u stays where it converged, its residual
+    // is no longer computed and keeps the value that met rtol).
     auto update_rel = [&](int done) {
-        bool all = true, finite = true;
+        bool all = true, finite = true, changed = false;
         for (int p = 0; p < np; ++p) {
+            if (F->pdone_h[p]) continue;
             rel[p] = std::sqrt(rr[p]) / fn[p];
             if (!std::isfinite(rel[p])) finite = false;
-            if (rtol >= 0.0 && rel[p] <= rtol && met[p] < 0) met[p] = done;
+            if (rtol >= 0.0 && rel[p] <= rtol && met[p] < 0) {
+                met[p] = done;
+                F->pdone_h[p] = 1;
+                changed = true;
+            }
             if (!(rtol >= 0.0 && rel[p] <= rtol)) all = false;
             mult[p] = pow2_near(1.0 / std::sqrt(rr[p]));
         }
+        if (changed && !all) enqueue_done(F);
         return std::make_pair(all, finite);
     };
     int done = 0;
@@ -709,6 +739,7 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
         }
     }
     MG_TRY(unpack_user<double>(F, d, u_dev, d.u64));
+    reset_done(F);
     MG_CUDA(cudaStreamSynchronize(F->st));
     if (F->cfg.precision == 1) MG_TRY(check_kernel_waits(F));
     for (int p = 0; p < np; ++p) {
@@ -865,10 +896,13 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         if ((st = dalloc(F, &F->psum, np)) != MG_OK) return fail(st);
         if ((st = dalloc(F, &F->pscale, np)) != MG_OK) return fail(st);
         if ((st = dalloc(F, &F->pinv, np)) != MG_OK) return fail(st);
+        if ((st = dalloc(F, &F->pdone, np)) != MG_OK) return fail(st);
         if (cudaMallocHost(&F->psum_h, np * sizeof(double)) != cudaSuccess ||
             cudaMallocHost(&F->pscale_h, np * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost(&F->pinv_h, np * sizeof(double)) != cudaSuccess)
+            cudaMallocHost(&F->pinv_h, np * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&F->pdone_h, np) != cudaSuccess)
             return fail(MG_ERR_OOM);
+        std::memset(F->pdone_h, 0, np);
         F->fnorm_p.assign(np, 0.0);
     }
     if (cudaMallocHost(&F->pinned, 2 * sizeof(double)) != cudaSuccess) return fail(MG_ERR_OOM);
@@ -970,6 +1004,7 @@ void mg_forest_destroy(mg_forest *F) {
     if (F->psum_h) cudaFreeHost(F->psum_h);
     if (F->pscale_h) cudaFreeHost(F->pscale_h);
     if (F->pinv_h) cudaFreeHost(F->pinv_h);
+    if (F->pdone_h) cudaFreeHost(F->pdone_h);
     delete F;
 }
 

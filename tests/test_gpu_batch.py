@@ -78,3 +78,40 @@ def test_batch_with_mixed_block_sizes_matches_single_problem_oracle():
         assert ref.rel_residual(got[off:off + cnt].reshape(len(keys), -1), fs[p].reshape(len(keys), -1)) <= 1.05e-8
         off += cnt
     B.close()
+
+
+def test_converged_problems_stop_where_they_would_stop_alone():
+    """Per-problem done-mask: once a problem meets rtol its blocks are skipped by every kernel of the later
+    defect-correction steps, so the batch returns, for each problem, the iterate and the cycle count of a solve of
+    that problem alone (same hierarchy, same inner cycles), although the batch keeps cycling for the slower ones."""
+    from paper_2403_08063_gb300 import Batch, Forest
+    problems = syn.batch_problems(count=6, seed=11, sizes=(8, 16))
+    leaves, ns = syn.batch_leaves(problems)
+    rng = np.random.default_rng(12)
+    fs, ks = [], []
+    for p, (n, keys) in enumerate(problems):
+        fs.append(rng.uniform(-1, 1, size=len(keys) * n ** 3))
+        sigma = 0.2 if p % 2 else 0.6  # different coefficient contrasts: different cycle counts
+        ks.append(syn.lognormal_k_rff(1, n, keys, seed=40 + p, sigma=sigma, ell=0.3).numpy().reshape(-1))
+    f = torch.from_numpy(np.concatenate(fs)).to(DEV)
+    k = torch.from_numpy(np.concatenate(ks)).to(DEV)
+    B = Batch(leaves, ns, coeff=True, inner_cycles=2, max_coarse=64)
+    B.set_rhs(f, k)
+    u = torch.zeros_like(f)
+    cyc, rel = B.solve(u, rtol=1e-9, max_cycles=60)
+    assert max(rel) <= 1e-9
+    assert len(set(cyc)) > 1, cyc  # the problems converge at different cycles
+    off = 0
+    for p, (n, keys) in enumerate(problems):
+        cnt = len(keys) * n ** 3
+        lv = [(0, lev, i, j, kk) for (lev, i, j, kk) in keys]
+        F = Forest(1, n, lv, coeff=True, precision=1, inner_cycles=2, max_coarse=64)
+        F.set_rhs(f[off:off + cnt].clone(), k[off:off + cnt].clone())
+        ua = torch.zeros(cnt, dtype=torch.float64, device=DEV)
+        ca, ra = F.solve(ua, rtol=1e-9, max_cycles=60)
+        assert ca == cyc[p], (p, ca, cyc[p])
+        assert abs(ra - rel[p]) <= 1e-4 * ra  # the squared norm is accumulated in FP32 per thread
+        assert torch.allclose(u[off:off + cnt], ua, rtol=0, atol=1e-12 * float(ua.abs().max()))
+        F.close()
+        off += cnt
+    B.close()
