@@ -251,6 +251,10 @@ def run_ours(args):
     cells = len(keys) * n ** 3
     F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=args.inner_cycles)
     F.set_rhs(f, k)
+    if args.tail != "auto":
+        F.set_tail(int(args.tail))
+    if args.smoother_shape:
+        F.set_smoother_shape(0, [int(v) for v in args.smoother_shape.split(",")])
     levels = F.levels()
     u = torch.zeros_like(f)
 
@@ -264,7 +268,6 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     sampler.start()
-    F.profile(True)
     _barrier(dist)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -280,6 +283,14 @@ def run_ours(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     _barrier(dist)
+    # the same K solves again with a CUDA-event pair around every kernel family (the events add a little time, so
+    # `value` comes from the run above and the per-family times and the roofline from this one)
+    F.profile(True)
+    torch.cuda.nvtx.range_push("mg_profiled")
+    for _ in range(args.steps):
+        step(F)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
     clocks = sampler.stop()
     prof = F.profile_read()
     F.profile(False)
@@ -361,6 +372,8 @@ def run_ours(args):
                        "levels": levels, "coefficient": "log-normal k (sigma 1, ell 0.1)" if coeff else "1",
                        "rhs": WORKLOADS[args.workload][2], "rtol": args.rtol, "cycle": "V(2,2) red-black GS",
                        "inner_cycles": args.inner_cycles,
+                       "smoother_shapes": [list(F.smoother_shape(l)) for l in range(len(levels))],
+                       "persistent_tail_from_level": F.tail_level(),
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"{ws} independent replicas"},
             "cycles_per_solve": cycles, "final_rel_residual": rels[-1],
             "time_to_rtol_s": {"fp32_in_fp64": tmix, "fp64": t64, "speedup": t64 / tmix},
@@ -398,6 +411,8 @@ def run_batch(args):
     cells = f.numel()
     B = Batch(leaves, ns, coeff=True, inner_cycles=args.inner_cycles)
     B.set_rhs(f, k)
+    if args.tail == "-1":
+        B.set_tail_off()
     u = torch.zeros_like(f)
     rtol = 1e-8
 
@@ -436,7 +451,8 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 outer",
             "data": "synthetic",
             "config": {"workload": args.workload, "problems": count, "cells": cells, "groups": B.info()["groups"],
-                       "rtol": rtol, "inner_cycles": args.inner_cycles, "graphs": "one defect-correction step of "
+                       "rtol": rtol, "inner_cycles": args.inner_cycles, "persistent_tail_from_level": B.tail_levels(),
+                       "graphs": "one defect-correction step of "
                        "all groups per graph launch", "l2": "inputs larger than L2 (no flush)"},
             "cycles_per_solve_max": cyc_run, "cycles_per_problem_last": runs[-1][0],
             "worst_rel_residual": max(runs[-1][1]),
@@ -460,6 +476,10 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--inner-cycles", type=int, default=4,
                     help="FP32 V-cycles per FP64 defect-correction step")
+    ap.add_argument("--tail", default="auto",
+                    help="level from which the persistent tail kernel runs the FP32 V-cycle (-1: off; auto: tuned)")
+    ap.add_argument("--smoother-shape", default="",
+                    help="FP32 smoother launch shape of the finest level, e.g. 2,16,16,2,4 (default: tuned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

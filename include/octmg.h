@@ -38,7 +38,7 @@ typedef enum {
     MG_ERR_OOM = 4,           /* device or host allocation failed */
     MG_ERR_CUDA = 5,          /* a CUDA call failed */
     MG_ERR_NOT_CONVERGED = 6, /* residual did not reach rtol within max_cycles, or became non-finite */
-    MG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up (staged smoother's shared-memory copies) */
+    MG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up (staged smoother copies, persistent tail barrier) */
     MG_ERR_NONFINITE = 8,     /* NaN/Inf in an input field, or k <= 0 */
     MG_ERR_STATE = 9          /* call out of order (e.g. solve before mg_set_rhs) */
 } mg_status;
@@ -153,6 +153,17 @@ mg_status mg_smoother_shapes(const mg_forest *forest, int32_t level, int32_t max
                              int32_t *n_shapes);
 mg_status mg_get_smoother_shape(const mg_forest *forest, int32_t level, int32_t *shape);
 mg_status mg_set_smoother_shape(mg_forest *forest, int32_t level, const int32_t *shape);
+
+/* Persistent tail of the FP32 V-cycle (precision 1): from level `level` down to the coarsest and back, every step
+ * (half-sweeps, exchanges, restriction, prolongation, coarsest solve) runs inside one cooperative kernel launch
+ * whose CTAs stay resident and meet at grid barriers, instead of one launch per step.  Results are bit-identical
+ * to the launched V-cycle.  The first mg_set_rhs times V-cycles without the tail and with it from every level
+ * whose own and deeper levels have at most 2^20 cells, and keeps the fastest.  get: -1 when off.  set: -1: off;
+ * MG_ERR_INVALID_ARG for a level with a deeper block edge outside 4..128 or a forest without FP32 cycles.  A grid
+ * barrier that waits too long makes the solve return MG_ERR_TIMEOUT.  No counterpart in the paper, whose cycle
+ * runs level by level with MPI exchanges (Sec. 4). */
+mg_status mg_get_tail(const mg_forest *forest, int32_t *level);
+mg_status mg_set_tail(mg_forest *forest, int32_t level);
 
 /* ---------------------------------------------------------------------------------------------------------------
  * Batches: many independent problems with different block sizes (uneven octree forests), solved together.

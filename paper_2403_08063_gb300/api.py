@@ -141,6 +141,15 @@ class Forest:
         _lib.check(self.lib.mg_exchange_level(self.h, int(level), _ptr(u), _ptr(out)))
         return out.view(nb, n + 2, n + 2, n + 2)
 
+    def tail_level(self):
+        """Level from which the persistent tail kernel runs the FP32 V-cycle (-1: off)."""
+        lv = ctypes.c_int32()
+        _lib.check(self.lib.mg_get_tail(self.h, ctypes.byref(lv)))
+        return lv.value
+
+    def set_tail(self, level):
+        _lib.check(self.lib.mg_set_tail(self.h, int(level)))
+
     def smoother_shapes(self, level):
         """The FP32 smoother launch shapes offered on `level` (5-tuples; empty where it is not used)."""
         cnt = ctypes.c_int32()
@@ -231,6 +240,20 @@ class Batch:
         if st != 0 and (raise_on_failure or st != 6):
             _lib.check(st)
         return list(cyc), list(rel)
+
+    def tail_levels(self):
+        """Per group, the level from which its persistent tail kernel runs the FP32 V-cycle (-1: off)."""
+        out = []
+        for g in range(len(self.info()["groups"])):
+            lv = ctypes.c_int32()
+            _lib.check(self.lib.mg_get_tail(ctypes.c_void_p(self.lib.mg_batch_group(self.h, g)), ctypes.byref(lv)))
+            out.append(lv.value)
+        return out
+
+    def set_tail_off(self):
+        """Runs every group's FP32 V-cycle as separate launches (no persistent tail)."""
+        for g in range(len(self.info()["groups"])):
+            _lib.check(self.lib.mg_set_tail(ctypes.c_void_p(self.lib.mg_batch_group(self.h, g)), -1))
 
     def profile(self, enable=True):
         _lib.check(self.lib.mg_batch_profile(self.h, int(bool(enable))))

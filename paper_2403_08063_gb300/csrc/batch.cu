@@ -29,7 +29,9 @@ struct mg_batch {
     int *flag = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_m = 0;
+    std::vector<int> graph_tails;  // the groups' tail levels when the graph was captured
     bool rhs_set = false;
+    bool tails_tuned = false;
 };
 
 namespace octmg {
@@ -97,6 +99,45 @@ mg_status enqueue_step(mg_batch *B, int m) {
         MG_TRY(enqueue_problem_sums(F));
     }
     return join(B);
+}
+
+// The groups' tail levels were tuned one group at a time; run concurrently, a cooperative tail launch may wait for
+// other groups' kernels to leave the SMs it needs.  So the batch times one defect-correction step of all groups
+// with the tuned tails and with every tail off (one untimed and two timed steps each, on the groups' pools, which
+// are dead between solves) and keeps the faster setting.
+mg_status tune_batch_tails(mg_batch *B) {
+    std::vector<int> tuned;
+    bool any = false;
+    for (mg_forest *F : B->groups) {
+        tuned.push_back(F->tail_level);
+        any = any || F->tail_level >= 0;
+        set_scales_host(F, std::vector<double>(F->np, 1.0));
+    }
+    if (!any) return MG_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    float ms[2] = {0.0f, 0.0f};
+    const int m = std::max(1, B->cfg.inner_cycles);
+    mg_status st = MG_OK;
+    for (int v = 0; v < 2 && st == MG_OK; ++v) {
+        for (size_t g = 0; g < B->groups.size(); ++g) B->groups[g]->tail_level = v ? tuned[g] : -1;
+        if ((st = enqueue_step(B, m)) != MG_OK) break;
+        if (cudaEventRecord(e0, B->st) != cudaSuccess) st = MG_ERR_CUDA;
+        for (int r = 0; r < 2 && st == MG_OK; ++r) st = enqueue_step(B, m);
+        if (st == MG_OK && (cudaEventRecord(e1, B->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess))
+            st = MG_ERR_CUDA;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MG_OK) {
+        if (st == MG_ERR_CUDA) set_error("timing the batch tails failed");
+        return st;
+    }
+    for (size_t g = 0; g < B->groups.size(); ++g) B->groups[g]->tail_level = ms[1] < ms[0] ? tuned[g] : -1;
+    for (mg_forest *F : B->groups) MG_TRY(check_kernel_waits(F));
+    return MG_OK;
 }
 
 bool profiling(const mg_batch *B) {
@@ -170,7 +211,9 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         // the update reads pinv on the device before the captured copies overwrite it: keep host copies of the
         // new scales until the step is enqueued
         if (m == inner && !profiling(B)) {
-            if (!B->graph || B->graph_m != m) {
+            std::vector<int> tails;
+            for (mg_forest *F : B->groups) tails.push_back(F->tail_level);
+            if (!B->graph || B->graph_m != m || B->graph_tails != tails) {
                 if (B->graph) cudaGraphExecDestroy(B->graph);
                 B->graph = nullptr;
                 cudaGraph_t graph = nullptr;
@@ -189,6 +232,7 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
                     return MG_ERR_CUDA;
                 }
                 B->graph_m = m;
+                B->graph_tails = tails;
             }
             for (size_t g = 0; g < G; ++g) set_scales_host(B->groups[g], mult[g]);
             MG_CUDA(cudaGraphLaunch(B->graph, B->st));
@@ -353,6 +397,10 @@ mg_status mg_batch_set_rhs(mg_batch *B, const double *f_dev, const double *k_dev
     MG_TRY(fork(B));
     for (mg_forest *F : B->groups) MG_TRY(set_rhs(F, f_dev, k_dev));
     MG_TRY(join(B));
+    if (!B->tails_tuned && B->cfg.precision == 1) {
+        MG_TRY(tune_batch_tails(B));
+        B->tails_tuned = true;
+    }
     B->rhs_set = true;
     MG_TRY(leave(B));
     return MG_OK;

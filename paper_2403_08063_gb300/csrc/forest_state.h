@@ -66,6 +66,27 @@ struct DevLevel {
     int64_t cells() const { return static_cast<int64_t>(g.nb) << (3 * g.lg); }
 };
 
+// One FP32 level as the persistent tail kernel sees it.
+struct TailLevel {
+    LevelGeom g;
+    float *u, *f;
+    const float *kap, *h2, *ih2;
+    const FaceItem *faces, *ifaces;
+    const SegItem *segs;
+    const XferItem *xfer;  // to the next level
+    const int32_t *nbr6, *bprob;
+    int nfaces, nifaces, nsegs;
+    int fast;  // the transfers to the next level use the specialised kernels (every block halves, edge 8..128)
+};
+
+// One step of the tail's V-cycle; every step is followed by a grid barrier.
+enum TailOp : int32_t {
+    T_SMOOTH0 = 0, T_SMOOTH1, T_FACES_IFACE, T_FACES_FULL, T_SEGS, T_RESTRICT, T_PROLONG, T_COARSE
+};
+struct TailPhase {
+    int32_t op, level;
+};
+
 }  // namespace octmg
 
 struct mg_forest {
@@ -109,6 +130,13 @@ struct mg_forest {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> recs;  // (family, index of the start event; stop = +1)
+    // persistent tail: the FP32 V-cycle from level tail_level down is one cooperative launch (tail_level < 0: off)
+    int tail_level = -1;
+    bool tail_tuned = false;
+    octmg::TailLevel *tail_L = nullptr;  // device copy of the level descriptors
+    octmg::TailPhase *tail_ph = nullptr;  // device phase list
+    int tail_nph = 0, tail_for = -2;      // phases recorded, and for which tail level
+    unsigned *tail_bar = nullptr;          // grid-barrier counter and generation
 };
 
 
@@ -116,7 +144,7 @@ namespace octmg {
 // Kernel families for launch counting and timing.
 enum ProfCat {
     P_EXCH64 = 0, P_EXCH32, P_SMOOTH64, P_SMOOTH32, P_RESTR64, P_RESTR32, P_PROL64, P_PROL32, P_COARSE64,
-    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_SMOOTH64_L0, P_SMOOTH32_L0, P_NCAT
+    P_COARSE32, P_RESID64, P_UPDATE, P_LAYOUT, P_ADJ, P_SMOOTH64_L0, P_SMOOTH32_L0, P_TAIL32, P_NCAT
 };
 template <typename T> constexpr int cat_of(int cat64) { return sizeof(T) == 8 ? cat64 : cat64 + 1; }
 
@@ -162,6 +190,7 @@ void exchange_any64(mg_forest *F, DevLevel &d, double *u);
 mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
 mg_status check_ready(mg_forest *F);
 mg_status check_kernel_waits(mg_forest *F);
+mg_status launch_tail32(mg_forest *F);  // tail.cu
 void reset_done(mg_forest *F);
 mg_status enqueue_done(mg_forest *F);
 mg_status ensure_scratch64(mg_forest *F);

@@ -1040,34 +1040,57 @@ __device__ __forceinline__ void prolong32_body(float *__restrict__ uf, int64_t b
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
                 for (int a = 0; a < 2; ++a) cur[c][bb][a] = ldv<CG>(ub + Bx::off(a + 1, bb + 1, c + 1));
-        const bool face = nbr6 && (X == 0 || X == nc - 1 || Y == 0 || Y == nc - 1 || Z == 0 || Z == nc - 1);
         const int corner = (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;  // in-block offset of the box corner
+        constexpr int n = Bx::n, H = Bx::HP, PL = Bx::P * Bx::HP, HALF = Bx::HALF;
+        float val[2][2][2];
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
-                    const float v = cur[c][bb][a] + 0.25f * ((e0 + ex[a]) + (ey[bb] + ez[c]));
-                    ub[Bx::off(a + 1, bb + 1, c + 1)] = v;
-                    if (!face) continue;
-                    constexpr int n = Bx::n, H = Bx::HP, PL = Bx::P * Bx::HP, HALF = Bx::HALF;
+                    val[c][bb][a] = cur[c][bb][a] + 0.25f * ((e0 + ex[a]) + (ey[bb] + ez[c]));
+                    ub[Bx::off(a + 1, bb + 1, c + 1)] = val[c][bb][a];
+                }
+        if (!nbr6) continue;
+        // x faces: one lane per coarse row (X = 0: children a = 0, X = nc - 1: children a = 1)
+        if (X == 0 || X == nc - 1) {
+            const int a = X == 0 ? 0 : 1;
+            const int nbv = nbr6[b * 6 + a];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb) {
                     const int hs = (a + bb + c + 1) & 1;  // half of the child (its padded coordinate sum's parity)
                     const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;  // offset inside its half
-                    const int cc[3] = {2 * X + a, 2 * Y + bb, 2 * Z + c};
+                    if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (a ? -n / 2 : n / 2)] = val[c][bb][a];
+                    else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q] = -val[c][bb][a];
+                }
+        }
+        // y and z faces: whole coarse rows
+        if (Y == 0 || Y == nc - 1 || Z == 0 || Z == nc - 1) {
 #pragma unroll
-                    for (int axis = 0; axis < 3; ++axis) {
+            for (int c = 0; c < 2; ++c)
 #pragma unroll
-                        for (int side = 0; side < 2; ++side) {
-                            if (cc[axis] != (side ? n - 1 : 0)) continue;
-                            const int Dm = axis == 0 ? n / 2 : (axis == 1 ? n * H : n * PL);
-                            const int E = axis == 0 ? 0 : (axis == 1 ? H : PL);
-                            const int nbv = nbr6[b * 6 + 2 * axis + side];
-                            if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (side ? -Dm : Dm)] = v;
-                            else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q + (side ? E : -E)] = -v;
+                for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        const int hs = (a + bb + c + 1) & 1;
+                        const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;
+                        const int cc[3] = {0, 2 * Y + bb, 2 * Z + c};
+#pragma unroll
+                        for (int axis = 1; axis < 3; ++axis) {
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                if (cc[axis] != (side ? n - 1 : 0)) continue;
+                                const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
+                                const int nbv = nbr6[b * 6 + 2 * axis + side];
+                                if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (side ? -Dm : Dm)] = val[c][bb][a];
+                                else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q + (side ? E : -E)] = -val[c][bb][a];
+                            }
                         }
                     }
-                }
+        }
     }
 }
 

@@ -46,7 +46,7 @@ const char *const kProfNames[P_NCAT] = {"exchange_f64", "exchange_f32", "smooth_
                                          "residual_restrict_f64", "residual_restrict_f32", "prolong_f64",
                                          "prolong_f32", "coarse_f64", "coarse_f32", "residual_f64",
                                          "update_mixed", "layout", "adjoint", "smooth_f64_finest",
-                                         "smooth_f32_finest"};
+                                         "smooth_f32_finest", "tail_f32"};
 
 cudaEvent_t next_event(mg_forest *F) {
     if (F->ev_used == F->ev_pool.size()) {
@@ -328,29 +328,70 @@ void smooth(mg_forest *F, DevLevel &d, int colour) {
 // prolongation a full exchange, or only the interface one after a prolongation that writes through.
 enum { ENTRY_FULL = 0, ENTRY_INTERFACE = 1, ENTRY_NONE = 2 };
 
-template <typename T, int MODE>
-void vcycle(mg_forest *F, int l, int entry) {
-    DevLevel &d = F->L[l];
+// The schedule of V(nu1, nu2) from level l, walked with an executor: LaunchExec launches each step's kernels,
+// RecordExec writes the steps down as the phase list of the persistent tail kernel (tail.cu), so both follow one
+// schedule.
+template <typename T, int MODE, typename E>
+void vcycle_walk(mg_forest *F, int l, int entry, E &ex) {
     const int last = static_cast<int>(F->L.size()) - 1;
+    if (ex.tail(l, entry)) return;
     if (l == last) {
+        ex.coarse(l);
+        ex.exchange(l, false);
+        return;
+    }
+    if (entry != ENTRY_NONE) ex.exchange(l, entry == ENTRY_INTERFACE);
+    for (int i = 0; i < F->cfg.nu1; ++i) {
+        if (i) ex.exchange(l, true);
+        ex.smooth(l, 0);
+        ex.exchange(l, true);
+        ex.smooth(l, 1);
+    }
+    if (F->cfg.nu1) ex.exchange(l, true);
+    const bool fast = sizeof(T) == 4 && MODE != 1 && transfer32_specialised(F->L[l]);
+    ex.restrict_to(l, fast);
+    vcycle_walk<T, MODE>(F, l + 1, fast ? ENTRY_NONE : ENTRY_FULL, ex);
+    if (l + 1 != last) ex.exchange(l + 1, true);
+    ex.prolong_from(l, fast);
+    ex.exchange(l, fast);
+    for (int i = 0; i < F->cfg.nu2; ++i) {
+        if (i) ex.exchange(l, true);
+        ex.smooth(l, 0);
+        ex.exchange(l, true);
+        ex.smooth(l, 1);
+    }
+}
+
+// How level l is entered in an FP32 V-cycle (level 0 from vcycle32, deeper levels from the restriction above).
+int entry32(mg_forest *F, int l) {
+    if (l == 0) return ENTRY_INTERFACE;
+    return transfer32_specialised(F->L[l - 1]) ? ENTRY_NONE : ENTRY_FULL;
+}
+
+template <typename T, int MODE>
+struct LaunchExec {
+    mg_forest *F;
+    bool tail(int l, int entry) {
+        if constexpr (sizeof(T) == 4) {
+            if (F->tail_level >= 0 && l == F->tail_level && F->tail_for == l && entry == entry32(F, l)) {
+                Prof p(F, P_TAIL32, 1);
+                launch_tail32(F);
+                return true;
+            }
+        }
+        return false;
+    }
+    void exchange(int l, bool iface) { octmg::exchange<T, MODE>(F, F->L[l], ufield<T>(F->L[l]), iface); }
+    void smooth(int l, int colour) { octmg::smooth<T, MODE>(F, F->L[l], colour); }
+    void coarse(int l) {
+        DevLevel &d = F->L[l];
         Prof p(F, cat_of<T>(P_COARSE64), 1);
         k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(
             ufield<T>(d), ffield<T>(d), F->Ainv, sizeof(T) == 4 ? F->cmap32 : F->cmap, F->uprob, F->ustart, F->moff,
             F->Nc, F->pdone);
-        exchange<T, MODE>(F, d, ufield<T>(d));
-        return;
     }
-    if (entry != ENTRY_NONE) exchange<T, MODE>(F, d, ufield<T>(d), entry == ENTRY_INTERFACE);
-    for (int i = 0; i < F->cfg.nu1; ++i) {
-        if (i) exchange<T, MODE>(F, d, ufield<T>(d), true);
-        smooth<T, MODE>(F, d, 0);
-        exchange<T, MODE>(F, d, ufield<T>(d), true);
-        smooth<T, MODE>(F, d, 1);
-    }
-    if (F->cfg.nu1) exchange<T, MODE>(F, d, ufield<T>(d), true);
-    DevLevel &c = F->L[l + 1];
-    const bool fast = sizeof(T) == 4 && MODE != 1 && transfer32_specialised(d);
-    {
+    void restrict_to(int l, bool fast) {
+        DevLevel &d = F->L[l], &c = F->L[l + 1];
         Prof p(F, cat_of<T>(P_RESTR64), 1);
         if (fast)
             launch_residual_restrict32(F, d, c);
@@ -359,9 +400,8 @@ void vcycle(mg_forest *F, int l, int entry) {
                 ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g,
                 skip_of(F, c));
     }
-    vcycle<T, MODE>(F, l + 1, fast ? ENTRY_NONE : ENTRY_FULL);
-    if (l + 1 != last) exchange<T, MODE>(F, c, ufield<T>(c), true);
-    {
+    void prolong_from(int l, bool fast) {
+        DevLevel &d = F->L[l], &c = F->L[l + 1];
         Prof p(F, cat_of<T>(P_PROL64), 1);
         if (fast)
             launch_prolong32(F, d, c);
@@ -369,13 +409,60 @@ void vcycle(mg_forest *F, int l, int entry) {
             k_prolong<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer, c.g,
                                                                       skip_of(F, c));
     }
-    exchange<T, MODE>(F, d, ufield<T>(d), fast);
-    for (int i = 0; i < F->cfg.nu2; ++i) {
-        if (i) exchange<T, MODE>(F, d, ufield<T>(d), true);
-        smooth<T, MODE>(F, d, 0);
-        exchange<T, MODE>(F, d, ufield<T>(d), true);
-        smooth<T, MODE>(F, d, 1);
+};
+
+struct RecordExec {
+    mg_forest *F;
+    std::vector<TailPhase> ph;
+    bool tail(int, int) { return false; }
+    void exchange(int l, bool iface) {
+        const DevLevel &d = F->L[l];
+        if ((iface ? d.nifaces : d.nfaces) > 0) ph.push_back({iface ? T_FACES_IFACE : T_FACES_FULL, l});
+        if (d.nsegs > 0) ph.push_back({T_SEGS, l});
     }
+    void smooth(int l, int colour) { ph.push_back({colour ? T_SMOOTH1 : T_SMOOTH0, l}); }
+    void coarse(int l) { ph.push_back({T_COARSE, l}); }
+    void restrict_to(int l, bool) { ph.push_back({T_RESTRICT, l}); }
+    void prolong_from(int l, bool) { ph.push_back({T_PROLONG, l}); }
+};
+
+template <typename T, int MODE>
+void vcycle(mg_forest *F, int l, int entry) {
+    LaunchExec<T, MODE> ex{F};
+    vcycle_walk<T, MODE>(F, l, entry, ex);
+}
+
+// Levels from which the tail kernel can run the rest of an FP32 V-cycle: every deeper level has a specialised
+// column smoother (edge 4..128).
+bool tail_possible(mg_forest *F, int l) {
+    if (F->cfg.precision != 1 || l < 0 || l >= static_cast<int>(F->L.size())) return false;
+    for (int m = l; m < static_cast<int>(F->L.size()); ++m)
+        if (F->L[m].g.lg < 2 || F->L[m].g.lg > 7) return false;
+    return true;
+}
+
+// Records the tail's phase list from level l and uploads it with the level descriptors.
+mg_status record_tail(mg_forest *F, int l) {
+    RecordExec rec{F, {}};
+    if (F->cfg.coeff) vcycle_walk<float, 2>(F, l, entry32(F, l), rec);
+    else vcycle_walk<float, 0>(F, l, entry32(F, l), rec);
+    if (!F->tail_L) {
+        std::vector<TailLevel> tl(F->L.size());
+        for (size_t m = 0; m < F->L.size(); ++m) {
+            const DevLevel &d = F->L[m];
+            tl[m] = TailLevel{d.g, d.u32, d.f32, d.kap, d.h2_32, d.ih2_32, d.faces, d.ifaces, d.segs, d.xfer, d.nbr6,
+                              d.bprob, d.nfaces, d.nifaces, d.nsegs, transfer32_specialised(d) ? 1 : 0};
+        }
+        MG_TRY(upload(F, &F->tail_L, tl));
+        MG_TRY(dalloc(F, &F->tail_bar, 2));
+    }
+    if (static_cast<int>(rec.ph.size()) > F->tail_nph || !F->tail_ph) MG_TRY(dalloc(F, &F->tail_ph, rec.ph.size()));
+    MG_CUDA(cudaMemcpyAsync(F->tail_ph, rec.ph.data(), rec.ph.size() * sizeof(TailPhase), cudaMemcpyHostToDevice,
+                            F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    F->tail_nph = static_cast<int>(rec.ph.size());
+    F->tail_for = l;
+    return MG_OK;
 }
 
 // CTA chunks per block for the per-block reductions: about 2048 cells per CTA.
@@ -595,6 +682,53 @@ void vcycle64(mg_forest *F) {
 void vcycle32(mg_forest *F) {
     if (F->cfg.coeff) vcycle<float, 2>(F, 0, ENTRY_INTERFACE);
     else vcycle<float, 0>(F, 0, ENTRY_INTERFACE);
+}
+
+// Picks the persistent tail's level: every level l whose own and deeper levels have at most 2^20 cells (and
+// specialised smoothers) is a candidate; each candidate and "off" is timed over five FP32 V-cycles (after two
+// untimed ones) on the FP32 pools, which are dead between solves, and the fastest is kept.  Skipped (off) while the
+// stream is being captured.
+mg_status tune_tail(mg_forest *F) {
+    if (F->tail_tuned || F->cfg.precision != 1) return MG_OK;
+    F->tail_tuned = true;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MG_CUDA(cudaStreamIsCapturing(F->st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return MG_OK;
+    const int last = static_cast<int>(F->L.size()) - 1;
+    std::vector<int> cand{-1};
+    for (int l = last - 1; l >= 0; --l) {
+        if (F->L[l].cells() > (int64_t(1) << 20) || !tail_possible(F, l)) break;
+        cand.push_back(l);
+    }
+    if (cand.size() == 1) return MG_OK;
+    cudaEvent_t e0 = next_event(F), e1 = next_event(F);
+    if (!e0 || !e1) {
+        set_error("cudaEventCreate failed");
+        return MG_ERR_CUDA;
+    }
+    float best = 0.0f;
+    int pick = -1;
+    for (int lt : cand) {
+        if (lt >= 0) MG_TRY(record_tail(F, lt));
+        F->tail_level = lt;
+        for (int w = 0; w < 2; ++w) vcycle32(F);
+        MG_CUDA(cudaEventRecord(e0, F->st));
+        for (int w = 0; w < 5; ++w) vcycle32(F);
+        MG_CUDA(cudaEventRecord(e1, F->st));
+        MG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (lt == -1 || ms < best) {
+            best = ms;
+            pick = lt;
+        }
+    }
+    F->ev_used -= 2;
+    MG_CUDA(cudaGetLastError());
+    MG_TRY(check_kernel_waits(F));
+    if (pick >= 0) MG_TRY(record_tail(F, pick));
+    F->tail_level = pick;
+    return MG_OK;
 }
 
 double pow2_near(double x) {
@@ -961,7 +1095,10 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
         total += F->psum_h[p];
     }
     F->fnorm = std::sqrt(total);
-    if (F->cfg.precision == 1) MG_TRY(tune_smooth32(F));
+    if (F->cfg.precision == 1) {
+        MG_TRY(tune_smooth32(F));
+        MG_TRY(tune_tail(F));
+    }
     F->rhs_set = true;
     return MG_OK;
 }
@@ -1113,6 +1250,36 @@ mg_status mg_set_smoother_shape(mg_forest *F, int32_t level, const int32_t *shap
         return MG_ERR_INVALID_ARG;
     }
     d.s32 = sh;
+    return MG_OK;
+}
+
+mg_status mg_get_tail(const mg_forest *F, int32_t *level) {
+    if (!F || !level) {
+        set_error("null forest or output");
+        return MG_ERR_INVALID_ARG;
+    }
+    *level = F->tail_level;
+    return MG_OK;
+}
+
+mg_status mg_set_tail(mg_forest *F, int32_t level) {
+    if (!F) {
+        set_error("null forest");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (level < 0) {
+        F->tail_level = -1;
+        F->tail_tuned = true;
+        return MG_OK;
+    }
+    if (!tail_possible(F, level)) {
+        set_error("no persistent tail from level " + std::to_string(level) +
+                  " (FP32 cycles and block edges 4..128 on every deeper level required)");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_TRY(record_tail(F, level));
+    F->tail_level = level;
+    F->tail_tuned = true;
     return MG_OK;
 }
 

@@ -1,0 +1,198 @@
+// The persistent tail of the FP32 V-cycle: every level from `tail_level` down to the coarsest, and back up to the
+// end of that level's post-smoothing, in one cooperative launch.  The coarse levels of a V-cycle are small (a few
+// thousand to a few hundred thousand cells) and their kernels last a few microseconds each, so launching them one
+// by one is latency-bound; here the CTAs stay resident and walk a phase list recorded from the same schedule as the
+// launched V-cycle (smoothing half-sweeps, interface and full exchanges, restriction, prolongation, coarsest
+// solve), separated by grid barriers.  Every phase runs the same device code as the corresponding kernel (loads of
+// data written by earlier phases go through L2), so results are bit-identical to the launched V-cycle.
+#include "forest_state.h"
+#include "kernels.cuh"
+
+namespace octmg {
+
+constexpr int kTailThreads = 256;
+
+// Grid barrier for a cooperative launch: arrive on a counter, the last CTA resets it and advances the generation,
+// the others wait for the generation to change.  The wait gives up after about half a second, sets *err and
+// returns false (the kernel then stops; the host reports MG_ERR_TIMEOUT).
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g0 = *reinterpret_cast<volatile unsigned *>(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            int it = 0;
+            while (*reinterpret_cast<volatile unsigned *>(gen) == g0) {
+                if (++it > (1 << 22)) {
+                    atomicOr(err, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct TailArgs {
+    const TailLevel *L;
+    const TailPhase *ph;
+    int nph;
+    int flux;  // conservative F2C ghosts
+    const double *Ainv;
+    const int64_t *cmap32;
+    const int32_t *uprob;
+    const int64_t *ustart, *moff;
+    int Nc;
+    const uint8_t *done;
+    unsigned *bar;  // [count, generation]
+    int *err;
+};
+
+template <int MODE, int LG>
+__device__ __forceinline__ void tail_smooth(const TailLevel &d, int colour, Skip skip, int64_t t0, int64_t ts) {
+    const int64_t work = d.g.nb * (int64_t(1) << (3 * LG - 1));
+    for (int64_t t = t0; t < work; t += ts)
+        smooth32_column<MODE, LG, 1, true>(d.u, d.f, d.kap, d.h2, d.g.bs, colour, d.nbr6, skip, t);
+}
+
+template <int MODE, int LG>
+__device__ __forceinline__ void tail_restrict(const TailLevel &d, const TailLevel &c, Skip skip, int64_t t0,
+                                              int64_t ts) {
+    residual_restrict32_body<MODE, LG, true>(d.u, d.f, d.kap, d.ih2, d.g.bs, c.f, c.u, d.xfer, c.g.nb, c.g.bs, skip,
+                                             t0, ts);
+}
+
+template <int LG>
+__device__ __forceinline__ void tail_prolong(const TailLevel &d, const TailLevel &c, Skip skip, int64_t t0,
+                                             int64_t ts) {
+    prolong32_body<LG, true>(d.u, d.g.bs, c.u, d.xfer, c.g.nb, c.g.bs, d.nbr6, skip, t0, ts);
+}
+
+template <int MODE>
+static __global__ void __launch_bounds__(kTailThreads) k_tail32(TailArgs a) {
+    const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t ts = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int p = 0; p < a.nph; ++p) {
+        const TailPhase P = a.ph[p];
+        const TailLevel &d = a.L[P.level];
+        const Skip skip{d.bprob, a.done};
+        const Coef cf{nullptr, nullptr, nullptr, nullptr, nullptr, d.kap};
+        switch (P.op) {
+            case T_SMOOTH0:
+            case T_SMOOTH1: {
+                const int colour = P.op == T_SMOOTH1;
+                switch (d.g.lg) {
+                    case 2: tail_smooth<MODE, 2>(d, colour, skip, t0, ts); break;
+                    case 3: tail_smooth<MODE, 3>(d, colour, skip, t0, ts); break;
+                    case 4: tail_smooth<MODE, 4>(d, colour, skip, t0, ts); break;
+                    case 5: tail_smooth<MODE, 5>(d, colour, skip, t0, ts); break;
+                    case 6: tail_smooth<MODE, 6>(d, colour, skip, t0, ts); break;
+                    default: tail_smooth<MODE, 7>(d, colour, skip, t0, ts); break;
+                }
+                break;
+            }
+            case T_FACES_IFACE:
+                exchange_faces_body<float, false, true>(d.u, d.ifaces, d.nifaces, d.g, skip, t0, ts);
+                break;
+            case T_FACES_FULL:
+                exchange_faces_body<float, false, true>(d.u, d.faces, d.nfaces, d.g, skip, t0, ts);
+                break;
+            case T_SEGS:
+                if (a.flux)
+                    exchange_segs_body<float, MODE, true, true>(d.u, cf, d.segs, d.nsegs, d.g, skip, t0, ts);
+                else
+                    exchange_segs_body<float, MODE, false, true>(d.u, cf, d.segs, d.nsegs, d.g, skip, t0, ts);
+                break;
+            case T_RESTRICT: {
+                const TailLevel &c = a.L[P.level + 1];
+                const Skip cs{c.bprob, a.done};
+                if (d.fast) {
+                    switch (d.g.lg) {
+                        case 3: tail_restrict<MODE, 3>(d, c, cs, t0, ts); break;
+                        case 4: tail_restrict<MODE, 4>(d, c, cs, t0, ts); break;
+                        case 5: tail_restrict<MODE, 5>(d, c, cs, t0, ts); break;
+                        case 6: tail_restrict<MODE, 6>(d, c, cs, t0, ts); break;
+                        default: tail_restrict<MODE, 7>(d, c, cs, t0, ts); break;
+                    }
+                } else {
+                    residual_restrict_body<float, MODE, true>(d.u, d.f, cf, d.ih2, d.g, c.f, c.u, d.xfer, c.g, cs, t0,
+                                                              ts);
+                }
+                break;
+            }
+            case T_PROLONG: {
+                const TailLevel &c = a.L[P.level + 1];
+                const Skip cs{c.bprob, a.done};
+                if (d.fast) {
+                    switch (d.g.lg) {
+                        case 3: tail_prolong<3>(d, c, cs, t0, ts); break;
+                        case 4: tail_prolong<4>(d, c, cs, t0, ts); break;
+                        case 5: tail_prolong<5>(d, c, cs, t0, ts); break;
+                        case 6: tail_prolong<6>(d, c, cs, t0, ts); break;
+                        default: tail_prolong<7>(d, c, cs, t0, ts); break;
+                    }
+                } else {
+                    prolong_body<float, true>(d.u, d.g, c.u, d.xfer, c.g, cs, t0, ts);
+                }
+                break;
+            }
+            default: {  // T_COARSE: one warp per coarsest unknown
+                const int lane = threadIdx.x & 31;
+                const int64_t w0 = t0 >> 5, wn = ts >> 5;
+                for (int64_t w = w0; w < a.Nc; w += wn)
+                    coarse_solve_row<float, true>(d.u, d.f, a.Ainv, a.cmap32, a.uprob, a.ustart, a.moff, a.done,
+                                                  static_cast<int>(w), lane);
+                break;
+            }
+        }
+        if (!grid_barrier(a.bar, a.bar + 1, a.err)) return;
+    }
+}
+
+// Enqueues the recorded tail on the forest's stream (capturable: a memset and a cooperative kernel launch).
+mg_status launch_tail32(mg_forest *F) {
+    const int mi = F->cfg.coeff ? 1 : 0;
+    const void *fn = mi ? reinterpret_cast<const void *>(k_tail32<2>) : reinterpret_cast<const void *>(k_tail32<0>);
+    static int per_sm[2] = {-1, -1}, sms = 0;
+    if (per_sm[mi] < 0) {
+        int dev = 0, v = 0, sm = 0;
+        MG_CUDA(cudaGetDevice(&dev));
+        MG_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, kTailThreads, 0));
+        sms = sm;
+        per_sm[mi] = std::max(1, std::min(v, 2));
+    }
+    // enough CTAs for the largest phase, at most two per SM (all must be resident together)
+    int64_t need = 1;
+    for (int l = F->tail_level; l < static_cast<int>(F->L.size()); ++l)
+        need = std::max<int64_t>(need, (F->L[l].cells() / 2 + kTailThreads - 1) / kTailThreads);
+    const int grid = static_cast<int>(std::min<int64_t>(need, static_cast<int64_t>(per_sm[mi]) * sms));
+    TailArgs a{F->tail_L, F->tail_ph, F->tail_nph, F->cfg.interface_flux, F->Ainv, F->cmap32, F->uprob, F->ustart,
+               F->moff, F->Nc, F->pdone, F->tail_bar, F->kerr};
+    MG_CUDA(cudaMemsetAsync(F->tail_bar, 0, 2 * sizeof(unsigned), F->st));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = F->st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {&a};
+    MG_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    return MG_OK;
+}
+
+}  // namespace octmg
