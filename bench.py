@@ -90,6 +90,14 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launch
     return None, None
 
 
+# DRAM bytes per cell of the level per launch, from one ncu capture of the kernel on the 16.8M-cell case
+# (dram__bytes_read.sum + dram__bytes_write.sum divided by the level's cells), scaled here to the launch's cells
+# (the traffic grows in proportion to the cells).  Kernel and source summary in profiles/.
+_NCU_TRAFFIC_PER_CELL = {
+    "smooth_f32_finest": (188.9e6 / 16777216, "profiles/k_smooth32t_uniform_4x64_k.md"),
+}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -317,8 +325,11 @@ def run_ours(args):
                     "hbm_achieved_gbs": bytes_ / fam_s / 1e9}
         else:
             ach = bytes_ / fam_s / 1e9
+            tr = _NCU_TRAFFIC_PER_CELL.get(fam) if args.workload.startswith("uniform") and coeff else None
             roof = {"kernel": fam, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": None, "peak_source": src}
+                    "traffic": tr[0] * levels[0][0] * levels[0][1] ** 3 if tr else None, "peak_source": src}
+            if tr:
+                roof["traffic_source"] = tr[1] + " (captured on 4^3 blocks of 64^3, scaled by cells)"
         roof["launches"] = prof[fam][1]
         roof["avg_launch_ms"] = prof[fam][0] / max(1, prof[fam][1])
 

@@ -13,28 +13,29 @@ namespace octmg {
 constexpr int kTailThreads = 256;
 
 // Grid barrier for a cooperative launch: arrive on a counter, the last CTA resets it and advances the generation,
-// the others wait for the generation to change.  The wait gives up after about half a second, sets *err and
-// returns false (the kernel then stops; the host reports MG_ERR_TIMEOUT).
+// the others poll the generation (no sleep: a phase of the tail lasts microseconds).  The wait is bounded by the SM
+// clock (2^30 cycles, about half a second): it then sets *err and returns false (the kernel stops; the host
+// reports MG_ERR_TIMEOUT).
 __device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        const unsigned g0 = *reinterpret_cast<volatile unsigned *>(gen);
+        volatile unsigned *vg = gen;
+        const unsigned g0 = *vg;
         __threadfence();
         if (atomicAdd(count, 1u) == gridDim.x - 1) {
             atomicExch(count, 0u);
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
-            int it = 0;
-            while (*reinterpret_cast<volatile unsigned *>(gen) == g0) {
-                if (++it > (1 << 22)) {
+            const long long t0 = clock64();
+            while (*vg == g0) {
+                if (clock64() - t0 > (1LL << 30)) {
                     atomicOr(err, 2);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
