@@ -160,13 +160,19 @@ class ClockSampler:
 
 
 def _dist():
+    """(torch.distributed or None, rank, world size, local rank) from the torchrun environment.  Ranks are
+    independent replicas: the process group only carries the barriers and the max-over-ranks of the timings (NCCL
+    with GPUs, gloo without)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
         return dist, rank, ws, local
     return None, 0, 1, 0
 
@@ -179,7 +185,8 @@ def _barrier(dist):
 def _max_over_ranks(dist, x):
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
