@@ -135,11 +135,12 @@ def workload_forest(name: str):
                       0.25 around the centre, 26-neighbour 2:1 balance (56 level-1 + 64 level-2 blocks).
     'uniform_8x64'    8^3 roots of 64^3 cells (512^3 cells).
     'sphere_4x32'     4^3 roots of 32^3 cells, sphere-refined two levels as above, 26-neighbour balance.
-    Smaller test forests: 'uniform_2x8', 'sphere_2x8', 'sphere_2x16', 'sphere_2x4'.
+    Smaller test forests: 'uniform_2x8', 'uniform_2x32', 'sphere_2x8', 'sphere_2x16', 'sphere_2x4'.
     """
     table = {
         "uniform_2x4": (2, 4, "u"), "uniform_2x8": (2, 8, "u"), "uniform_2x16": (2, 16, "u"),
         "uniform_4x16": (4, 16, "u"), "uniform_8x64": (8, 64, "u"), "uniform_4x64": (4, 64, "u"),
+        "uniform_2x32": (2, 32, "u"),
         "sphere_2x4": (2, 4, "s"), "sphere_2x8": (2, 8, "s"), "sphere_2x16": (2, 16, "s"),
         "sphere_2x32": (2, 32, "s"), "sphere_4x32": (4, 32, "s"), "sphere_4x8": (4, 8, "s"),
     }
