@@ -28,6 +28,12 @@ What it computes
   ``max_coarse`` unknowns, complete sibling octets at the deepest level are merged into their parent (a
   coarsening step the paper does not need, since it smooths on the coarsest level); the coarsest level is solved
   by a dense LU factorisation.
+* The paper's own cycle (Sec. 5), for its accuracy and benchmark experiments: damped Jacobi smoothing (omega
+  = 0.8, one sweep per smoothing step, ghosts frozen at the exchanged values) and damped Jacobi sweeps as the
+  coarsest solver; coarse-to-fine interpolation of order 2 (above), or the Table's lower orders: order 1 linear
+  along the normal (the current coarse cell and the next one inward) and along each orthogonal axis (the
+  neighbour on the fine cell's side, the other one at a coarse block edge), order 0 a copy of the covering coarse
+  cell.  The paper names the lower orders without describing them; these are this project's readings.
 * Stopping: volume-weighted L2 norm sqrt(sum h^3 r^2) of the residual relative to that of f (Sec. 5 says only
   "L2 residual norm"; a normalised norm is the reading that gives the printed kappa near 0.25).
 * Adjoint: A^T applied matrix-free as the transposed stencil followed by the transposed ghost exchange; dL/df =
@@ -69,6 +75,30 @@ NORMAL_TARGET = Fraction(-1, 4)
 NORMAL_W = [float(w) for w in lagrange_weights(NORMAL_NODES, NORMAL_TARGET)]
 
 
+def normal_weights(order):
+    """Weights of the coarse cells 0, 1, .. inward (the -d_comm direction) for the fine ghost at -1/4: the quadratic
+    rule of Sec. 3.3.2 (order 2, bases 0, 1, 2) and the Table's lower orders (order 1: bases 0, 1; order 0: the
+    covering coarse cell alone)."""
+    return [float(w) for w in lagrange_weights(tuple(range(order + 1)), NORMAL_TARGET)]
+
+
+def tangential_nodes_order(yc, n, target, order):
+    """Bases along an orthogonal axis for the given interpolation order.
+
+    Order 2: tangential_nodes.  Order 1 (the paper names the first-order scheme without describing it; reading):
+    the current coarse cell and its neighbour on the target's side, or the neighbour on the other side when that
+    one lies outside the coarse block's interior.  Order 0: the covering coarse cell.
+    """
+    if order == 2:
+        return tangential_nodes(yc, n)
+    if order == 0:
+        return [0]
+    o = -1 if target < 0 else 1
+    if not (0 <= yc + o <= n - 1):
+        o = -o
+    return [0, o]
+
+
 def tangential_nodes(yc, n):
     """Bases along an orthogonal axis for coarse cell yc of a block with n cells on that axis (Sec. 3.3.2).
 
@@ -85,17 +115,17 @@ def tangential_nodes(yc, n):
 
 
 @functools.lru_cache(maxsize=None)
-def _tangential_matrix_cached(n, offset):
-    M = tangential_matrix_uncached(n, offset)
+def _tangential_matrix_cached(n, offset, order):
+    M = tangential_matrix_uncached(n, offset, order)
     M.setflags(write=False)
     return M
 
 
-def tangential_matrix(n, offset):
-    return _tangential_matrix_cached(n, offset)
+def tangential_matrix(n, offset, order=2):
+    return _tangential_matrix_cached(n, offset, order)
 
 
-def tangential_matrix_uncached(n, offset):
+def tangential_matrix_uncached(n, offset, order=2):
     """(n x n) map from the coarse cells of one tangential axis to the n fine ghost cells of a segment.
 
     Fine index yf belongs to coarse cell yc = offset + yf // 2; even yf sits at -1/4 (downwind), odd at +1/4.
@@ -104,7 +134,7 @@ def tangential_matrix_uncached(n, offset):
     for yf in range(n):
         yc = offset + yf // 2
         target = Fraction(-1, 4) if yf % 2 == 0 else Fraction(1, 4)
-        nodes = tangential_nodes(yc, n)
+        nodes = tangential_nodes_order(yc, n, target, order)
         for node, w in zip(nodes, lagrange_weights(nodes, target)):
             M[yf, yc + node] += float(w)
     return M
@@ -218,17 +248,25 @@ class OracleMG:
     """
 
     def __init__(self, R, n, keys, k_user=None, variant="C", nu1=2, nu2=2, max_coarse=512, operator_only=False,
-                 bc=None):
+                 bc=None, c2f_order=2, smoother="rbgs", omega=0.8, coarse_iters=None):
         """operator_only builds the finest level alone (for applying A, A^T and dA/dk; no solver).
 
         bc: None for homogeneous Dirichlet data, else a vectorised g(x, y, z) giving the Dirichlet value at
         boundary face centres of the finest level (Sec. 5, Eq. 2); coarse levels always use g = 0.
+        c2f_order: 2 the paper's quadratic coarse-to-fine scheme, 1 / 0 the lower orders of its Table err_analysis.
+        smoother: 'rbgs' (red-black Gauss-Seidel) or 'jacobi' (damped by omega, the paper's own smoother, Sec. 5;
+        one sweep per smoothing step).  coarse_iters: None for the dense direct coarsest solve, else that many damped
+        Jacobi sweeps from zero on the coarsest level (the paper's coarsest solver, Sec. 5).
         """
         if n < 4 or n & (n - 1):
             raise ValueError("n must be a power of two >= 4")
         check_forest(R, list(keys))
         self.R, self.n, self.variant = R, n, variant
         self.nu1, self.nu2 = nu1, nu2
+        if c2f_order not in (0, 1, 2) or smoother not in ("rbgs", "jacobi"):
+            raise ValueError("c2f_order must be 0, 1 or 2 and smoother 'rbgs' or 'jacobi'")
+        self.c2f_order, self.smoother, self.omega, self.coarse_iters = c2f_order, smoother, omega, coarse_iters
+        self.normal_w = normal_weights(c2f_order)
         self.levels = [Level(R, n, keys)]
         self.transfer = []  # transfer[l]: per coarse block of level l+1, ('halve', b) | ('copy', b) | ('merge', [8 b])
         while self.levels[-1].n > 4 and not operator_only:
@@ -260,7 +298,7 @@ class OracleMG:
                 self.exchange_k(l + 1)
             for l in range(len(self.levels)):
                 self._cache_T(l)
-        if not operator_only:
+        if not operator_only and coarse_iters is None:
             self._factor_coarsest()
 
     # -- hierarchy -------------------------------------------------------------------------------------
@@ -305,9 +343,9 @@ class OracleMG:
     # -- ghost exchange --------------------------------------------------------------------------------
     def _c2f_values(self, Vc, n, seg):
         """Fine ghost face (n x n, [t1, t2]) from the coarse view Vc (Sec. 3.3.2, 3D scheme)."""
-        E = NORMAL_W[0] * Vc[1, 1:-1, 1:-1] + NORMAL_W[1] * Vc[2, 1:-1, 1:-1] + NORMAL_W[2] * Vc[3, 1:-1, 1:-1]
-        M1 = tangential_matrix(n, seg[0] * n // 2)
-        M2 = tangential_matrix(n, seg[1] * n // 2)
+        E = sum(w * Vc[1 + a, 1:-1, 1:-1] for a, w in enumerate(self.normal_w))
+        M1 = tangential_matrix(n, seg[0] * n // 2, self.c2f_order)
+        M2 = tangential_matrix(n, seg[1] * n // 2, self.c2f_order)
         return M1 @ E @ M2.T
 
     def exchange(self, l, U):
@@ -430,10 +468,27 @@ class OracleMG:
         uc = U[:, 1:-1, 1:-1, 1:-1]
         U[:, 1:-1, 1:-1, 1:-1] = np.where(mask, new, uc)
 
+    def jacobi_sweep(self, l, U, F):
+        """Damped Jacobi with ghosts frozen at the exchanged values: u_i <- (1 - w) u_i + w (h^2 f_i + sum_f T_f u_f)
+        / sum_f T_f for every cell at once (the paper's smoother, Sec. 5, omega = 0.8)."""
+        L = self.levels[l]
+        self.exchange(l, U)
+        T = self._T(l)
+        num = (L.h ** 2)[:, None, None, None] * F
+        den = 0.0
+        for Tf, nb in zip(T, _neighbours(U)):
+            num = num + Tf * nb
+            den = den + Tf
+        uc = U[:, 1:-1, 1:-1, 1:-1]
+        U[:, 1:-1, 1:-1, 1:-1] = (1.0 - self.omega) * uc + self.omega * (num / den)
+
     def smooth(self, l, U, F, iters):
         for _ in range(iters):
-            self.half_sweep(l, U, F, 0)
-            self.half_sweep(l, U, F, 1)
+            if self.smoother == "jacobi":
+                self.jacobi_sweep(l, U, F)
+            else:
+                self.half_sweep(l, U, F, 0)
+                self.half_sweep(l, U, F, 1)
 
     # -- transfers -------------------------------------------------------------------------------------
     def _restrict_into(self, l, Xf, Xc_pad):
@@ -493,6 +548,10 @@ class OracleMG:
         l = len(self.levels) - 1
         L = self.levels[l]
         U = L.zeros()
+        if self.coarse_iters is not None:
+            for _ in range(self.coarse_iters):
+                self.jacobi_sweep(l, U, F)
+            return U
         U[:, 1:-1, 1:-1, 1:-1] = scipy.linalg.lu_solve(self.lu, F.reshape(-1)).reshape(F.shape)
         return U
 
@@ -569,6 +628,8 @@ class OracleMG:
         """Transpose of the (linear part of the) ghost exchange, in place on a padded adjoint array G: every ghost
         adjoint is added into the interior cells its ghost value was computed from.  Reverse order of the forward
         exchange: the flux-carrying coarse ghosts (variant C) first, then copies, reflections, C2F and F2C."""
+        if self.c2f_order != 2:
+            raise NotImplementedError("the transposed exchange is written for the quadratic coarse-to-fine scheme")
         L = self.levels[l]
         n = L.n
         h2 = n_half(n)
@@ -676,11 +737,15 @@ class OracleMG:
 
     def vcycle_transposed(self, l, Ubar):
         """M_l^T: the exact transpose of the forward V-cycle map f -> u (zero initial guess) on level l.
+        Written for red-black Gauss-Seidel and the dense coarsest solve.
 
         The forward cycle is a sequence of linear steps (half-sweeps u += Pi_c D^-1 (f - A u), residual,
         restriction, coarse cycle, prolongation); its transpose runs them in reverse with each step transposed.
         A half-sweep's transpose is: z = Pi_c D^-1 ubar; fbar += z; ubar -= A^T z.
         Returns fbar (interior array of level l)."""
+        if self.smoother != "rbgs" or self.coarse_iters is not None:
+            raise NotImplementedError("the transposed cycle is written for red-black Gauss-Seidel and a dense "
+                                      "coarsest solve")
         L = self.levels[l]
         if l == len(self.levels) - 1:
             return scipy.linalg.lu_solve(self.lu, Ubar.reshape(-1), trans=1).reshape(Ubar.shape)
