@@ -39,6 +39,9 @@ WORKLOADS = {
     "uniform_4x64_k": ("uniform_4x64", True, "uniform"),
     "batch_256": ("batch", True, "uniform"),   # 256 single-root problems, n in {16,32,64,128}, 0-2 box refinements
     "batch_32": ("batch", True, "uniform"),    # 32 such problems (smaller case of the same recipe)
+    # the paper's own experiments (Sec. 5 and 6), FP64 with its V(3,3) damped-Jacobi cycle
+    "paper_bench": ("paper_bench", False, "uniform"),  # 22 R^3 blocks of 64^3 (R = 4: 1408 blocks), 100 cycles
+    "paper_table": ("sphere", False, "zero"),           # Table err_analysis: errors for block sizes 16 .. 128
 }
 
 
@@ -485,6 +488,112 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def _sync_time(fn):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def run_paper_bench(args):
+    """The paper's benchmark workload (Sec. 6) on one GPU: R^3 roots refined once, a quarter of them once more
+    (22 R^3 blocks of 64^3, R = 4), V(3,3) damped-Jacobi cycles with 256 coarsest Jacobi sweeps, ghost-only
+    interfaces, FP64.  A step is 20 cycles (the paper times 100).  Reports t_cycle, GLUPS per cycle, the finest-level
+    Jacobi sweep against the paper's 24 B/LUP light-speed model at this GPU's measured bandwidth, and the coarsest
+    solver's share of the cycle (paper: 1.64-5.15 % with generated communication)."""
+    import synthetic as syn
+    from paper_2403_08063_gb300 import Forest
+    dev = torch.device("cuda", 0)
+    R, n = 4, 64
+    keys = syn.paper_benchmark_forest(R)
+    cells = len(keys) * n ** 3
+    f = syn.uniform_rhs(len(keys), n, seed=0).to(dev)
+    F = Forest(R, n, keys, interface_flux=False, precision=0, nu1=3, nu2=3, smoother="jacobi", omega=0.8,
+               coarse_iters=256)
+    F.set_rhs(f)
+    u = torch.zeros_like(f)
+    per_step = 20
+    for _ in range(args.warmup):
+        F.vcycle(u, per_step)
+    sampler = ClockSampler(0)
+    sampler.start()
+    _, t = _sync_time(lambda: [F.vcycle(u, per_step) for _ in range(args.steps)])
+    F.profile(True)
+    F.vcycle(u, per_step)
+    torch.cuda.synchronize()
+    prof = F.profile_read()
+    F.profile(False)
+    clocks = sampler.stop()
+    ncyc = per_step * args.steps
+    tcyc = t / ncyc
+    fin = prof.get("smooth_f64_finest", (0.0, 0))
+    sweep_s = fin[0] / 1e3 / max(1, fin[1])
+    hbm, src = _peaks()
+    prof_total = sum(v[0] for v in prof.values())
+    print(json.dumps({
+        "metric": "t_cycle of V(3,3) damped-Jacobi cycles, the paper's benchmark workload (FP64)",
+        "value": tcyc * 1e3, "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper_bench", "roots": R, "blocks": len(keys), "block": f"{n}^3", "cells": cells,
+                   "levels": F.levels(), "cycle": "V(3,3) damped Jacobi (omega 0.8), 256 coarsest Jacobi sweeps",
+                   "cycles_timed": ncyc, "interfaces": "ghost-only (paper)"},
+        "glups_per_cycle": cells / tcyc / 1e9,
+        "finest_jacobi_sweep": {"ms": sweep_s * 1e3, "glups": cells / sweep_s / 1e9,
+                                "light_speed_model_glups": hbm * 1e9 / 24.0 / 1e9,
+                                "frac_of_model": cells / sweep_s / (hbm * 1e9 / 24.0), "peak_source": src,
+                                "model": "24 B per LUP (the paper's Sec. 6 model: u load + store, f load, FP64)"},
+        "coarse_solve_fraction": prof.get("coarse_f64", (0.0, 0))[0] / prof_total if prof_total else None,
+        "kernel_families_ms_per_20_cycles": {k_: round(v[0], 3) for k_, v in prof.items() if v[1]},
+        "clocks": clocks,
+    }), flush=True)
+
+
+def run_paper_table(args):
+    """Table err_analysis (Sec. 5) on the GPU: -Laplace u = 0 with Dirichlet data u = sin(pi x) sin(pi y)
+    sinh(sqrt(2) pi z) on the 56 + 64 block geometry, the paper's V(3,3) damped-Jacobi cycle with 256 coarsest
+    sweeps and ghost-only interfaces, FP64, solved to a 1e-13 relative residual; L2 (volume-weighted) error against
+    the exact solution for block sizes 16 .. 128 and the three coarse-to-fine variants, with the paper's values."""
+    import numpy as np
+    import synthetic as syn
+    from paper_2403_08063_gb300 import Forest
+    dev = torch.device("cuda", 0)
+    R, _, keys = syn.workload_forest("sphere_2x4")
+    paper = {16: (0.235, 1.067e-2, 3.017e-3), 32: (0.227, 5.255e-3, 7.215e-4), 64: (0.224, 2.611e-3, 1.764e-4),
+             128: (0.222, 1.302e-3, 4.361e-5)}
+    g = lambda x, y, z: np.sin(np.pi * x) * np.sin(np.pi * y) * np.sinh(np.sqrt(2) * np.pi * z)  # noqa: E731
+    rows = {}
+    for n in (16, 32, 64, 128):
+        c = syn.cell_centres(R, n, keys, device=dev).reshape(len(keys), -1, 3)
+        exact = (torch.sin(np.pi * c[..., 0]) * torch.sin(np.pi * c[..., 1]) *
+                 torch.sinh(np.sqrt(2) * np.pi * c[..., 2]))
+        h3 = torch.tensor([(1.0 / (R * 2 ** k[0] * n)) ** 3 for k in keys], dtype=torch.float64, device=dev)
+        for variant in (0, 1, 2):  # second order (the paper's scheme), first order, constant
+            F = Forest(R, n, keys, interface_flux=False, precision=0, nu1=3, nu2=3, smoother="jacobi", omega=0.8,
+                       coarse_iters=256, c2f_variant=variant)
+            f = torch.zeros((len(keys), n ** 3), dtype=torch.float64, device=dev)
+            F.set_rhs(f)
+            F.set_boundary(syn.boundary_values(R, n, keys, g, device=dev))
+            u = torch.zeros_like(f)
+            (cyc, rel), ts = _sync_time(lambda: F.solve(u, rtol=1e-13, max_cycles=80, raise_on_failure=False))
+            err = float(torch.sqrt((h3[:, None] * (u - exact) ** 2).sum()))
+            rows.setdefault(n, {})[("second", "first", "constant")[variant]] = {
+                "error": err, "paper": paper[n][2 - variant], "ratio": err / paper[n][2 - variant], "cycles": cyc,
+                "rel_residual": rel, "solve_s": ts}
+            F.close()
+            del F, u, f
+        torch.cuda.empty_cache()
+    ns = sorted(rows)
+    kappa = {o: [rows[ns[i + 1]][o]["error"] / rows[ns[i]][o]["error"] for i in range(len(ns) - 1)]
+             for o in ("second", "first", "constant")}
+    print(json.dumps({"metric": "L2 error of Table err_analysis (paper's accuracy problem)", "unit": "L2 error",
+                      "workload": "paper_table", "rows": {str(k): v for k, v in rows.items()}, "kappa": kappa,
+                      "paper_kappa": {"second": [0.239, 0.244, 0.247], "first": [0.493, 0.497, 0.499],
+                                      "constant": [0.966, 0.984, 0.992]}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,6 +614,10 @@ def main():
         run_reference(args)
     elif args.workload.startswith("batch"):
         run_batch(args)
+    elif args.workload == "paper_bench":
+        run_paper_bench(args)
+    elif args.workload == "paper_table":
+        run_paper_table(args)
     else:
         run_ours(args)
 

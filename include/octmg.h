@@ -61,6 +61,12 @@ typedef struct {
                                  FP32 resolves about 6 digits per step, so up to ~5 cycles still pay) */
     int32_t n_problems;       /* independent problems sharing R and n, solved together (default 1 when <= 0) */
     void *stream;             /* cudaStream_t, or NULL for the legacy default stream */
+    /* The paper's own cycle and interpolation variants (Sec. 5, Table err_analysis); zero keeps the defaults. */
+    int32_t c2f_variant;      /* coarse-to-fine ghosts: 0 quadratic (Sec. 3.3.2), 1 first order, 2 constant (the
+                                 lower orders of Table err_analysis, not described in the paper: readings) */
+    int32_t smoother;         /* 0 red-black Gauss-Seidel; 1 damped Jacobi, one sweep per smoothing step (FP64) */
+    double omega;             /* Jacobi damping (0.8 when <= 0) */
+    int32_t coarse_iters;     /* 0: dense direct coarsest solve; > 0: that many damped Jacobi sweeps (FP64) */
 } mg_config;
 
 /* Build the forest: validate the leaves, build neighbour and segment tables for every multigrid level, allocate
@@ -83,6 +89,14 @@ mg_status mg_level_keys(const mg_forest *forest, int32_t level, int32_t *keys_ho
  * f_dev: n_leaves * n^3 doubles; k_dev: same size, every entry finite and > 0, or NULL when coeff == 0.
  * Errors: MG_ERR_INVALID_ARG, MG_ERR_NONFINITE, MG_ERR_CUDA. */
 mg_status mg_set_rhs(mg_forest *forest, const double *f_dev, const double *k_dev);
+
+/* Inhomogeneous Dirichlet data g (Sec. 5, Eq. 2) for the finest level: g_dev (device, FP64) holds, per leaf in
+ * leaf order, its 6 faces (face = 2 axis + side, side 1 = the upper face) of n^2 values each, index i2 * n + i1 with
+ * (i1, i2) the interior coordinates along the two other axes in increasing axis order; only faces on the domain
+ * boundary are read.  The boundary ghost becomes 2 g - u (the value g at the face centre).  NULL restores g = 0.
+ * Coarse levels (corrections) keep g = 0.  Relative residuals are then taken against the residual of u = 0.  Used
+ * by FP64 cycles and by the FP64 residual of FP32-in-FP64 solves; the adjoint rejects a forest with g set. */
+mg_status mg_set_boundary(mg_forest *forest, const double *g_dev);
 
 /* Run exactly ncycles V(nu1, nu2) cycles on u_dev (initial guess on entry, iterate on exit; FP64 cycles, or FP32
  * cycles inside FP64 defect correction when precision == 1).  If rel_res_out is not NULL it receives, per problem

@@ -39,6 +39,10 @@ class MGConfig(ctypes.Structure):
         ("inner_cycles", ctypes.c_int32),
         ("n_problems", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("c2f_variant", ctypes.c_int32),
+        ("smoother", ctypes.c_int32),
+        ("omega", ctypes.c_double),
+        ("coarse_iters", ctypes.c_int32),
     ]
 
 
@@ -55,6 +59,7 @@ SIGNATURES = {
     "mg_forest_levels": (I32, [P, IP, IP, IP]),
     "mg_level_keys": (I32, [P, I32, IP]),
     "mg_set_rhs": (I32, [P, P, P]),
+    "mg_set_boundary": (I32, [P, P]),
     "mg_vcycle": (I32, [P, P, I32, DP]),
     "mg_solve": (I32, [P, P, _c.c_double, I32, IP, DP]),
     "mg_adjoint_solve": (I32, [P, P, P, P, P, _c.c_double, I32]),

@@ -31,7 +31,8 @@ class Forest:
     """
 
     def __init__(self, R, n, leaves, coeff=False, interface_flux=True, precision=0, nu1=2, nu2=2, max_coarse=512,
-                 inner_cycles=1, n_problems=None, stream=None):
+                 inner_cycles=1, n_problems=None, stream=None, c2f_variant=0, smoother="rbgs", omega=0.8,
+                 coarse_iters=0):
         self.lib = _lib.load()
         arr = np.asarray(leaves, dtype=np.int32)
         if arr.ndim == 2 and arr.shape[1] == 4:
@@ -47,6 +48,10 @@ class Forest:
         cfg.coeff, cfg.interface_flux, cfg.precision = int(coeff), int(interface_flux), int(precision)
         cfg.nu1, cfg.nu2, cfg.max_coarse = int(nu1), int(nu2), int(max_coarse)
         cfg.inner_cycles = int(inner_cycles)
+        cfg.c2f_variant = int(c2f_variant)
+        cfg.smoother = {"rbgs": 0, "jacobi": 1}[smoother]
+        cfg.omega = float(omega)
+        cfg.coarse_iters = int(coarse_iters)
         self.n_problems = int(n_problems) if n_problems else int(self._leaves[:, 0].max()) + 1
         cfg.n_problems = self.n_problems
         cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -90,6 +95,17 @@ class Forest:
             _dev_f64(k, self.numel, "k")
         _lib.check(self.lib.mg_set_rhs(self.h, _ptr(f), _ptr(k) if self.coeff else None))
         self.version += 1
+
+    def set_boundary(self, g=None):
+        """Dirichlet data on the finest level's boundary faces: g of shape (n_leaves, 6, n^2) (face 2 axis + side,
+        index i2 * n + i1 along the two other axes in increasing order), or None for g = 0."""
+        if g is None:
+            _lib.check(self.lib.mg_set_boundary(self.h, None))
+            self._g = None
+            return
+        _dev_f64(g, self.n_leaves * 6 * self.n ** 2, "g")
+        self._g = g
+        _lib.check(self.lib.mg_set_boundary(self.h, _ptr(g)))
 
     def vcycle(self, u, ncycles=1):
         """ncycles V-cycles on u in place; returns the relative residual (a list with several problems)."""

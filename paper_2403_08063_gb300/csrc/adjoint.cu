@@ -109,10 +109,10 @@ __global__ void k_et_faces(double *__restrict__ G, const FaceItem *__restrict__ 
             const int cz = zc == 0 ? 1 : (zc == n - 1 ? 2 : 0);
             for (int c = 0; c < 3; ++c)
                 for (int bb = 0; bb < 3; ++bb) {
-                    const double wt = w_tang<double>(cz, a2, c) * w_tang<double>(cy, a1, bb) * a;
+                    const double wt = w_tang<double>(0, cz, a2, c) * w_tang<double>(0, cy, a1, bb) * a;
                     const int y = yc + c_base[cy][bb], z = zc + c_base[cz][c];
                     for (int d = 0; d < 3; ++d)
-                        atomicAdd(&G[cbase + face_off(F.axis, 1 - F.side, 1 + d, y, z, n, P)], w_normal<double>(d) * wt);
+                        atomicAdd(&G[cbase + face_off(F.axis, 1 - F.side, 1 + d, y, z, n, P)], w_normal<double>(0, d) * wt);
                 }
         }
     }
@@ -513,6 +513,20 @@ mg_status read_sum(mg_forest *F, int grid, double *out) {
     return MG_OK;
 }
 
+// The transposed operator and cycle are written for the quadratic coarse-to-fine scheme, red-black Gauss-Seidel, the
+// dense coarsest solve and homogeneous boundary data (the k-gradient of a boundary term would need g).
+mg_status adjoint_supported(const mg_forest *F) {
+    if (F->cfg.c2f_variant != 0 || F->cfg.smoother != 0 || F->cfg.coarse_iters != 0) {
+        set_error("the adjoint needs c2f_variant 0, the Gauss-Seidel smoother and the dense coarsest solve");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (F->gb) {
+        set_error("the adjoint needs homogeneous boundary data (mg_set_boundary(forest, NULL))");
+        return MG_ERR_STATE;
+    }
+    return MG_OK;
+}
+
 template <int MODE>
 mg_status adjoint_solve(mg_forest *F, const double *u_dev, const double *dLdu_dev, double *lambda_dev,
                         double *dLdk_dev, double rtol, int max_cycles) {
@@ -585,6 +599,7 @@ extern "C" mg_status mg_apply_transpose(mg_forest *F, const double *y_dev, doubl
         set_error("mg_set_rhs (k) has not been called");
         return MG_ERR_STATE;
     }
+    MG_TRY(adjoint_supported(F));
     MG_TRY(ensure_adjoint_pools(F));
     DevLevel &d = F->L[0];
     MG_CUDA(cudaMemsetAsync(d.a_z, 0, d.pool_elems() * sizeof(double), F->st));
@@ -605,6 +620,7 @@ extern "C" mg_status mg_adjoint_solve(mg_forest *F, const double *u_dev, const d
         return MG_ERR_INVALID_ARG;
     }
     MG_TRY(check_ready(F));
+    MG_TRY(adjoint_supported(F));
     if (F->cfg.coeff) return adjoint_solve<1>(F, u_dev, dLdu_dev, lambda_dev, dLdk_dev, rtol, max_cycles);
     return adjoint_solve<0>(F, u_dev, dLdu_dev, lambda_dev, dLdk_dev, rtol, max_cycles);
 }

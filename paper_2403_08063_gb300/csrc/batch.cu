@@ -164,8 +164,8 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
     std::vector<std::vector<int32_t>> met(G);
     for (size_t g = 0; g < G; ++g) {
         mg_forest *F = B->groups[g];
-        DevLevel &d = F->L[0];
-        k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, u_dev, d.g, F->leaf_off);
+        bool zero_guess = false;
+        MG_TRY(pack_initial_guess(F, u_dev, &zero_guess));
         fn[g].resize(F->np);
         mult[g].resize(F->np);
         rel[g].assign(F->np, -1.0);
@@ -177,7 +177,7 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         }
         set_scales_host(F, mult[g]);
         MG_TRY(enqueue_scales(F));
-        MG_TRY(enqueue_residual(F));
+        MG_TRY(enqueue_residual(F, zero_guess));  // a zero guess needs no operator: r = f
         MG_TRY(enqueue_problem_sums(F));
     }
     MG_TRY(join(B));

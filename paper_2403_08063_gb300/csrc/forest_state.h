@@ -46,6 +46,7 @@ struct DevLevel {
     double *h2_64 = nullptr, *ih2_64 = nullptr, *vol_64 = nullptr;  // per block h^2, 1/h^2, h^3
     float *h2_32 = nullptr, *ih2_32 = nullptr, *vol_32 = nullptr;
     double *u64 = nullptr, *f64 = nullptr;
+    double *u64b = nullptr;  // second FP64 iterate pool (damped Jacobi)
     float *u32 = nullptr, *f32 = nullptr;
     double *k64 = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr, *dg = nullptr, *dinv = nullptr;
     float *kap = nullptr;
@@ -105,6 +106,9 @@ struct mg_forest {
     double *s64a = nullptr, *s64b = nullptr;  // level-0 FP64 scratch pools
     double *coarse_r = nullptr;               // coarsest-level scratch pool (operator assembly)
     int *flag = nullptr;                      // input-check flag
+    double *gb = nullptr;                     // 2 g on the finest level's boundary faces (mg_set_boundary), or null
+    double *gb_pool = nullptr;                // its storage (kept when g is reset to 0)
+    double omega = 0.8;                       // damping of the Jacobi smoother
     int *kerr = nullptr;                      // set by a device wait that gave up (staged smoother)
     double *AinvT = nullptr;                  // transpose of the coarsest inverses (adjoint cycles)
     // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse
@@ -150,13 +154,14 @@ template <typename T> constexpr int cat_of(int cat64) { return sizeof(T) == 8 ? 
 
 cudaEvent_t next_event(mg_forest *F);
 
-// RAII scope around the launches of one kernel family.
+// RAII scope around the launches of one kernel family (a negative family: no accounting).
 struct Prof {
     mg_forest *F;
     int cat;
     size_t start = 0;
     bool on = false;
-    Prof(mg_forest *f, int c, int launches) : F(f), cat(c) {
+    Prof(mg_forest *f, int c, int launches) : F(f), cat(c) {  // c < 0: inside another family's scope, not counted
+        if (c < 0) return;
         F->nlaunch[c] += launches;
         if (F->prof) {
             cudaEvent_t a = next_event(F), b = next_event(F);
@@ -193,13 +198,16 @@ mg_status check_kernel_waits(mg_forest *F);
 mg_status launch_tail32(mg_forest *F);  // tail.cu
 void reset_done(mg_forest *F);
 mg_status enqueue_done(mg_forest *F);
+mg_status reference_norms(mg_forest *F);
 mg_status ensure_scratch64(mg_forest *F);
 mg_status create(const mg_config *cfg, mg_forest **out);
 mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev);
 double pow2_near(double x);
 void set_scales_host(mg_forest *F, const std::vector<double> &mult);
 mg_status enqueue_scales(mg_forest *F);
-mg_status enqueue_residual(mg_forest *F);   // FP64 residual -> FP32 scaled rhs, zeroed correction, per-block sums
+// FP64 residual -> FP32 scaled rhs, zeroed correction, per-block sums (zero_u: u is zero, r = f)
+mg_status enqueue_residual(mg_forest *F, bool zero_u = false);
+mg_status pack_initial_guess(mg_forest *F, const double *u_dev, bool *zero);
 mg_status enqueue_problem_sums(mg_forest *F);  // per-problem sums -> pinned psum_h (no synchronisation)
 mg_status enqueue_fp32_step(mg_forest *F, int cycles);  // `cycles` FP32 V-cycles and the FP64 update
 

@@ -113,24 +113,37 @@ __device__ inline int64_t fidx(const LevelGeom &g, int64_t b, int axis, int side
 //   Upwind neighbour remapped to -2 (case 2, bases {-2, -1, 0}):
 //     (-3, 14, 21) / 32 and (5, -18, 45) / 32.
 // ------------------------------------------------------------------------------------------------------------
-static __constant__ double c_wn[3] = {45.0 / 32, -18.0 / 32, 5.0 / 32};
-static __constant__ double c_wt[3][2][3] = {
-    {{5.0 / 32, 30.0 / 32, -3.0 / 32}, {-3.0 / 32, 30.0 / 32, 5.0 / 32}},
-    {{45.0 / 32, -18.0 / 32, 5.0 / 32}, {21.0 / 32, 14.0 / 32, -3.0 / 32}},
-    {{-3.0 / 32, 14.0 / 32, 21.0 / 32}, {5.0 / 32, -18.0 / 32, 45.0 / 32}}};
+// Variant v of the scheme: 0 the quadratic rule above; 1 first order (linear along the normal through the current
+// cell and the next one inward; along an orthogonal axis through the current cell and the neighbour on the target's
+// side, the other neighbour when that one is outside the coarse block's interior); 2 constant (the covering coarse
+// cell).  The paper names the lower orders (Table err_analysis) without describing them; these are readings.
+//   v = 1 normal (5, -1, 0) / 4; orthogonal case 0: (1, 3, 0) / 4 and (0, 3, 1) / 4, case 1: (5, -1, 0) / 4 and
+//   (3, 1, 0) / 4, case 2: (0, 1, 3) / 4 and (0, -1, 5) / 4.   v = 2: weight 1 on the current cell.
+static __constant__ double c_wn[3][3] = {{45.0 / 32, -18.0 / 32, 5.0 / 32}, {1.25, -0.25, 0.0}, {1.0, 0.0, 0.0}};
+static __constant__ double c_wt[3][3][2][3] = {
+    {{{5.0 / 32, 30.0 / 32, -3.0 / 32}, {-3.0 / 32, 30.0 / 32, 5.0 / 32}},
+     {{45.0 / 32, -18.0 / 32, 5.0 / 32}, {21.0 / 32, 14.0 / 32, -3.0 / 32}},
+     {{-3.0 / 32, 14.0 / 32, 21.0 / 32}, {5.0 / 32, -18.0 / 32, 45.0 / 32}}},
+    {{{0.25, 0.75, 0.0}, {0.0, 0.75, 0.25}}, {{1.25, -0.25, 0.0}, {0.75, 0.25, 0.0}},
+     {{0.0, 0.25, 0.75}, {0.0, -0.25, 1.25}}},
+    {{{0.0, 1.0, 0.0}, {0.0, 1.0, 0.0}}, {{1.0, 0.0, 0.0}, {1.0, 0.0, 0.0}}, {{0.0, 0.0, 1.0}, {0.0, 0.0, 1.0}}}};
 static __constant__ int c_base[3][3] = {{-1, 0, 1}, {0, 1, 2}, {-2, -1, 0}};
-static __constant__ float c_wn_f[3] = {45.0f / 32, -18.0f / 32, 5.0f / 32};
-static __constant__ float c_wt_f[3][2][3] = {
-    {{5.0f / 32, 30.0f / 32, -3.0f / 32}, {-3.0f / 32, 30.0f / 32, 5.0f / 32}},
-    {{45.0f / 32, -18.0f / 32, 5.0f / 32}, {21.0f / 32, 14.0f / 32, -3.0f / 32}},
-    {{-3.0f / 32, 14.0f / 32, 21.0f / 32}, {5.0f / 32, -18.0f / 32, 45.0f / 32}}};
+static __constant__ float c_wn_f[3][3] = {{45.0f / 32, -18.0f / 32, 5.0f / 32}, {1.25f, -0.25f, 0.0f}, {1.0f, 0.0f, 0.0f}};
+static __constant__ float c_wt_f[3][3][2][3] = {
+    {{{5.0f / 32, 30.0f / 32, -3.0f / 32}, {-3.0f / 32, 30.0f / 32, 5.0f / 32}},
+     {{45.0f / 32, -18.0f / 32, 5.0f / 32}, {21.0f / 32, 14.0f / 32, -3.0f / 32}},
+     {{-3.0f / 32, 14.0f / 32, 21.0f / 32}, {5.0f / 32, -18.0f / 32, 45.0f / 32}}},
+    {{{0.25f, 0.75f, 0.0f}, {0.0f, 0.75f, 0.25f}}, {{1.25f, -0.25f, 0.0f}, {0.75f, 0.25f, 0.0f}},
+     {{0.0f, 0.25f, 0.75f}, {0.0f, -0.25f, 1.25f}}},
+    {{{0.0f, 1.0f, 0.0f}, {0.0f, 1.0f, 0.0f}}, {{1.0f, 0.0f, 0.0f}, {1.0f, 0.0f, 0.0f}},
+     {{0.0f, 0.0f, 1.0f}, {0.0f, 0.0f, 1.0f}}}};
 
-template <typename T> __device__ inline T w_normal(int a);
-template <> __device__ inline double w_normal<double>(int a) { return c_wn[a]; }
-template <> __device__ inline float w_normal<float>(int a) { return c_wn_f[a]; }
-template <typename T> __device__ inline T w_tang(int c, int al, int b);
-template <> __device__ inline double w_tang<double>(int c, int al, int b) { return c_wt[c][al][b]; }
-template <> __device__ inline float w_tang<float>(int c, int al, int b) { return c_wt_f[c][al][b]; }
+template <typename T> __device__ inline T w_normal(int v, int a);
+template <> __device__ inline double w_normal<double>(int v, int a) { return c_wn[v][a]; }
+template <> __device__ inline float w_normal<float>(int v, int a) { return c_wn_f[v][a]; }
+template <typename T> __device__ inline T w_tang(int v, int c, int al, int b);
+template <> __device__ inline double w_tang<double>(int v, int c, int al, int b) { return c_wt[v][c][al][b]; }
+template <> __device__ inline float w_tang<float>(int v, int c, int al, int b) { return c_wt_f[v][c][al][b]; }
 
 // Global load of data that other CTAs of the same launch may have written earlier (CG = true: through L2 only,
 // as in the persistent tail kernel, whose phases are separated by grid barriers), or a plain load.
@@ -231,9 +244,12 @@ __device__ inline double apply_at(const double *__restrict__ u, const Coef &cf, 
 // KIND_K = true:  coefficient field k (ghost = k_i at the boundary; fine ghosts inject the covering coarse k).
 // One thread per ghost cell; n is a power of two, so items and cells decode with shifts.
 // ------------------------------------------------------------------------------------------------------------
+// gb (FP64 finest level only, may be null): 2 g on the domain-boundary faces, (b * 6 + face) * n^2 + i2 n + i1, so the
+// reflection ghost is 2 g - u_i (inhomogeneous Dirichlet data, Sec. 5 Eq. 2); c2f: the coarse-to-fine variant.
 template <typename T, bool KIND_K, bool CG = false>
 __device__ __forceinline__ void exchange_faces_body(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems,
-                                                    LevelGeom g, Skip skip, int64_t t0, int64_t ts) {
+                                                    LevelGeom g, Skip skip, int64_t t0, int64_t ts, int c2f = 0,
+                                                    const T *__restrict__ gb = nullptr) {
     const int n = g.n, lg = g.lg, h = n >> 1;
     const int64_t total = static_cast<int64_t>(nitems) << (2 * lg);
     for (int64_t t = t0; t < total; t += ts) {
@@ -245,7 +261,8 @@ __device__ __forceinline__ void exchange_faces_body(T *__restrict__ u, const Fac
         T val;
         if (F.kind == FK_BND) {
             const T in = ldv<CG>(u + fidx<T>(g, F.blk, F.axis, F.side, 1, i1, i2));
-            val = KIND_K ? in : -in;
+            val = KIND_K ? in : (gb ? gb[(static_cast<int64_t>(F.blk) * 6 + 2 * F.axis + F.side) * n * n + i2 * n + i1] - in
+                                     : -in);
         } else if (F.kind == FK_SAME) {
             val = ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, i1, i2));
         } else {
@@ -263,12 +280,12 @@ __device__ __forceinline__ void exchange_faces_body(T *__restrict__ u, const Fac
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
                         const int y = yc + c_base[cy][b], z = zc + c_base[cz][c];
-                        T e = w_normal<T>(0) * ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, y, z));
-                        e = fma(w_normal<T>(1), ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 2, y, z)), e);
-                        e = fma(w_normal<T>(2), ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 3, y, z)), e);
-                        accb = fma(w_tang<T>(cy, a1, b), e, accb);
+                        T e = w_normal<T>(c2f, 0) * ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 1, y, z));
+                        e = fma(w_normal<T>(c2f, 1), ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 2, y, z)), e);
+                        e = fma(w_normal<T>(c2f, 2), ldv<CG>(u + fidx<T>(g, F.nbr, F.axis, 1 - F.side, 3, y, z)), e);
+                        accb = fma(w_tang<T>(c2f, cy, a1, b), e, accb);
                     }
-                    acc = fma(w_tang<T>(cz, a2, c), accb, acc);
+                    acc = fma(w_tang<T>(c2f, cz, a2, c), accb, acc);
                 }
                 val = acc;
             }
@@ -279,9 +296,9 @@ __device__ __forceinline__ void exchange_faces_body(T *__restrict__ u, const Fac
 
 template <typename T, bool KIND_K>
 static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g,
-                                        Skip skip = Skip{}) {
+                                        Skip skip = Skip{}, int c2f = 0, const T *__restrict__ gb = nullptr) {
     exchange_faces_body<T, KIND_K>(u, items, nitems, g, skip, blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
-                                   static_cast<int64_t>(gridDim.x) * blockDim.x);
+                                   static_cast<int64_t>(gridDim.x) * blockDim.x, c2f, gb);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -357,7 +374,8 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
 // have the other colour), so the writes cannot race with the reads.
 template <typename T, int MODE>
 static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef cf, const T *__restrict__ h2,
-                                LevelGeom g, int colour, const int32_t *__restrict__ nbr6, Skip skip = Skip{}) {
+                                LevelGeom g, int colour, const int32_t *__restrict__ nbr6, Skip skip = Skip{},
+                                const T *__restrict__ gb = nullptr) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg - 1);
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -423,11 +441,40 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
                     const int i1 = axis == 0 ? y : x, i2 = axis == 2 ? y : z;
                     if (nb >= 0)
                         u[fidx<T>(g, nb, axis, 1 - side, 0, i1, i2)] = val;
-                    else if (nb == -1)
-                        u[fidx<T>(g, b, axis, side, 0, i1, i2)] = -val;
+                    else if (nb == -1)  // reflection, with the boundary data 2 g where given (gb: finest level)
+                        u[fidx<T>(g, b, axis, side, 0, i1, i2)] =
+                            gb ? gb[(b * 6 + 2 * axis + side) * static_cast<int64_t>(n) * n + i2 * n + i1] - val : -val;
                 }
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Damped Jacobi sweep (the paper's smoother and coarsest solver, Sec. 5), FP64, ghosts as left by the last exchange:
+//     uo_i = (1 - omega) u_i + omega (h^2 f_i + sum_f T_f u_f) / sum_f T_f
+// for every cell of the level at once, into the second pool uo (interior only; its ghosts need an exchange).
+// ------------------------------------------------------------------------------------------------------------
+template <int MODE>
+static __global__ void k_jacobi64(const double *__restrict__ u, double *__restrict__ uo, const double *__restrict__ f,
+                                  Coef cf, const double *__restrict__ h2, LevelGeom g, double omega,
+                                  Skip skip = Skip{}) {
+    const int lg = g.lg, n = g.n, P = g.P;
+    const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t & (n - 1));
+        const int y = static_cast<int>((t >> lg) & (n - 1));
+        const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
+        const int64_t b = t >> (3 * lg);
+        if (skip(b)) continue;
+        const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
+        double nw;
+        if constexpr (MODE == 1)
+            nw = sten1(u, cf, gi, P, f[gi]) * cf.dinv[gi];
+        else
+            nw = fma(h2[b], f[gi], sten0<double>(u, gi, P)) * (1.0 / 6.0);
+        uo[gi] = fma(omega, nw - u[gi], u[gi]);
     }
 }
 
@@ -536,13 +583,15 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
     for (int dz = 0; dz < ZC; ++dz) ub[((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL] = val[dz];
     // ---- write-through -----------------------------------------------------------------------------
     if (!nbr6) return;
+    if (j == 0 || j == NH - 1) {  // x faces: the first and last lane of a row, side 0 / 1, the cells with c == side
+        const int side = j == 0 ? 0 : 1;
+        const int nbv = nbr6[b * 6 + side];
 #pragma unroll
-    for (int dz = 0; dz < ZC; ++dz) {
-        const int c = c0 ^ (dz & 1);
-        if ((j == 0 && c == 0) || (j == NH - 1 && c == 1)) {  // x face, side c
-            const int q = row0 + dz * PL + c;                  // the cell inside its half
-            const int nbv = nbr6[b * 6 + c];
-            if (nbv >= 0) u[nbv * bs + s * HALF + q + (c ? -NH : NH)] = val[dz];
+        for (int dz = 0; dz < ZC; ++dz) {
+            const int c = c0 ^ (dz & 1);
+            if (c != side) continue;
+            const int q = row0 + dz * PL + c;  // the cell inside its half
+            if (nbv >= 0) u[nbv * bs + s * HALF + q + (side ? -NH : NH)] = val[dz];
             else if (nbv == -1) ub[(s ^ 1) * HALF + q] = -val[dz];
         }
     }
@@ -596,21 +645,22 @@ __device__ inline void bulk_load(void *dst, const void *src, uint32_t bytes, uin
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ inline bool mbar_test(uint64_t *bar, uint32_t parity) {
+// One potentially blocking probe of phase `parity`: the thread is suspended in hardware (issuing nothing) until the
+// phase completes or about 20 us pass.
+__device__ inline bool mbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return done != 0;
 }
-// Waits for phase `parity` of `bar` to complete; gives up after about 0.1 s and returns false.
+// Waits for phase `parity` of `bar` to complete; gives up after 2^14 probes (a fraction of a second) and returns
+// false.
 __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 20); ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if (it > 32) __nanosleep(128);
-    }
+    for (int it = 0; it < (1 << 14); ++it)
+        if (mbar_try(bar, parity)) return true;
     return false;
 }
 
@@ -691,6 +741,13 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
         for (; n_own < RW && n_own < TZ; ++n_own) issue_own(n_own, n_own);
     }
     const float hb = __ldg(h2 + b);
+    // write-through targets of this block's faces (the same for the whole CTA), and the x face this lane may touch
+    int nb6[6] = {-2, -2, -2, -2, -2, -2};
+    if (nbr6) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) nb6[q] = __ldg(nbr6 + b * 6 + q);
+    }
+    const int xs = j == 0 ? 0 : (j == NH - 1 ? 1 : -1);
     int bad = 0;
     bad |= !mbar_wait(&bar[0], 0);
     bad |= !mbar_wait(&bar[1], 0);
@@ -755,23 +812,21 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
             }
             const int q = ((z + 1) * P + (y + 1)) * H + j + c;  // the cell, in either half
             u[base + s * HALF + q] = val;
-            if (nbr6) {
-                if ((j == 0 && c == 0) || (j == NH - 1 && c == 1)) {  // x face, side c
-                    const int nbv = nbr6[b * 6 + c];
-                    if (nbv >= 0) u[nbv * bs + s * HALF + q + (c ? -NH : NH)] = val;
-                    else if (nbv == -1) u[base + (s ^ 1) * HALF + q] = -val;
-                }
-                if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
+            if (xs == c) {  // x face, side c (nb6 is -2, nothing to write, without a face table)
+                const int nbv = nb6[c];
+                if (nbv >= 0) u[nbv * bs + s * HALF + q + (c ? -NH : NH)] = val;
+                else if (nbv == -1) u[base + (s ^ 1) * HALF + q] = -val;
+            }
+            if (nbr6 && (y == 0 || y == n - 1 || z == 0 || z == n - 1)) {
 #pragma unroll
-                    for (int axis = 1; axis < 3; ++axis) {
+                for (int axis = 1; axis < 3; ++axis) {
 #pragma unroll
-                        for (int side = 0; side < 2; ++side) {
-                            if ((axis == 1 ? y : z) != (side ? n - 1 : 0)) continue;
-                            const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
-                            const int nbv = nbr6[b * 6 + 2 * axis + side];
-                            if (nbv >= 0) u[nbv * bs + s * HALF + q + (side ? -Dm : Dm)] = val;
-                            else if (nbv == -1) u[base + (s ^ 1) * HALF + q + (side ? E : -E)] = -val;
-                        }
+                    for (int side = 0; side < 2; ++side) {
+                        if ((axis == 1 ? y : z) != (side ? n - 1 : 0)) continue;
+                        const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
+                        const int nbv = nb6[2 * axis + side];
+                        if (nbv >= 0) u[nbv * bs + s * HALF + q + (side ? -Dm : Dm)] = val;
+                        else if (nbv == -1) u[base + (s ^ 1) * HALF + q + (side ? E : -E)] = -val;
                     }
                 }
             }
@@ -1247,9 +1302,10 @@ static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f
 // problem, so the scaling is exact), with the FP32 correction field zeroed, and per-block sums of h^3 (r scale_p)^2.
 // Grid: nb * cpb CTAs, CTA (b, c) covers the c-th of cpb contiguous chunks of block b, so each CTA adds one value
 // to its block's sum.  The squared norm is accumulated in FP32 per thread (it decides convergence and is reported
-// to ~1e-6 relative) and in FP64 across threads.  out / zero_out may be null.
+// to ~1e-6 relative) and in FP64 across threads.  out / zero_out may be null.  ZU: u is known to be zero (a zero
+// initial guess), so r = f without reading u or the operator.
 // ------------------------------------------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, bool ZU = false>
 static __global__ void k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
                                        const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
                                        int cpb, float *__restrict__ out, const float *__restrict__ pscale,
@@ -1266,7 +1322,7 @@ static __global__ void k_residual_norm(const double *__restrict__ u, const doubl
     for (int c = chunk * per + threadIdx.x; c < (chunk + 1) * per; c += blockDim.x) {
         const int x = c & (n - 1), y = (c >> lg) & (n - 1), z = c >> (2 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
-        const double r = residual_at<double, MODE>(u, f, cf, gi, P, ihb);
+        const double r = ZU ? f[gi] : residual_at<double, MODE>(u, f, cf, gi, P, ihb);  // ZU: u = 0, r = f
         const float rs = static_cast<float>(r) * scale;
         const int64_t gs = Lay<float>::at(g, b, x + 1, y + 1, z + 1);  // FP32 pools are colour-split
         if (out) out[gs] = rs;
@@ -1396,9 +1452,10 @@ static __global__ void k_sum_partials(const double *__restrict__ partial, int np
 // Leaf b of the user array starts at element off[b] (or b * n^3 when off is null).
 template <typename T>
 static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ user, LevelGeom g,
-                              const int64_t *__restrict__ off = nullptr) {
+                              const int64_t *__restrict__ off = nullptr, int *__restrict__ nonzero = nullptr) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+    bool any = false;
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int x = static_cast<int>(t & (n - 1));
@@ -1406,8 +1463,11 @@ static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ u
         const int z = static_cast<int>((t >> (2 * lg)) & (n - 1));
         const int64_t b = t >> (3 * lg);
         const int64_t src = off ? off[b] + (t & ((int64_t(1) << (3 * lg)) - 1)) : t;
-        pool[b * g.bs + off3(x + 1, y + 1, z + 1, g.P)] = T(user[src]);
+        const double v = user[src];
+        any = any || v != 0.0;
+        pool[b * g.bs + off3(x + 1, y + 1, z + 1, g.P)] = T(v);
     }
+    if (nonzero && __ballot_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nonzero, 1);
 }
 
 template <typename T>

@@ -95,14 +95,17 @@ Skip skip_of(mg_forest *F, const DevLevel &d) { return Skip{d.bprob, F->pdone}; 
 // Ghost exchange of a level: every face (full), or only the refinement-interface faces (C2F and F2C), whose
 // ghosts the smoother's write-through does not maintain.
 template <typename T, int MODE>
-void exchange(mg_forest *F, DevLevel &d, T *u, bool interface_only = false) {
+void exchange(mg_forest *F, DevLevel &d, T *u, bool interface_only = false, bool prof = true) {
     const FaceItem *items = interface_only ? d.ifaces : d.faces;
     const int nitems = interface_only ? d.nifaces : d.nfaces;
     if (!nitems && !d.nsegs) return;
-    Prof p(F, cat_of<T>(P_EXCH64), (nitems ? 1 : 0) + (d.nsegs ? 1 : 0));
+    Prof p(F, prof ? cat_of<T>(P_EXCH64) : -1, (nitems ? 1 : 0) + (d.nsegs ? 1 : 0));
+    const T *gb = nullptr;  // inhomogeneous Dirichlet data: FP64 finest level only
+    if constexpr (sizeof(T) == 8)
+        if (&d == &F->L[0]) gb = F->gb;
     if (nitems)
         k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(nitems) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
-            u, items, nitems, d.g, skip_of(F, d));
+            u, items, nitems, d.g, skip_of(F, d), F->cfg.c2f_variant, gb);
     if (d.nsegs) {
         const int64_t tot = static_cast<int64_t>(d.nsegs) * (d.g.n / 2) * (d.g.n / 2);
         if (F->cfg.interface_flux)
@@ -317,8 +320,12 @@ void smooth(mg_forest *F, DevLevel &d, int colour) {
             return;
         }
     }
+    const T *gb = nullptr;
+    if constexpr (sizeof(T) == 8)
+        if (&d == &F->L[0]) gb = F->gb;
     k_smooth<T, MODE><<<grid_for(d.cells() / 2), kThreads, 0, F->st>>>(ufield<T>(d), ffield<T>(d), coef_of<T>(d),
-                                                                       h2_of<T>(d), d.g, colour, d.nbr6, skip_of(F, d));
+                                                                       h2_of<T>(d), d.g, colour, d.nbr6, skip_of(F, d),
+                                                                       gb);
 }
 
 // V(nu1, nu2) on level l.  Exchange schedule: at level entry a full exchange, unless the ghosts are known to be
@@ -341,20 +348,31 @@ void vcycle_walk(mg_forest *F, int l, int entry, E &ex) {
         return;
     }
     if (entry != ENTRY_NONE) ex.exchange(l, entry == ENTRY_INTERFACE);
+    const bool jac = F->cfg.smoother == 1;  // damped Jacobi (FP64): no write-through, a full exchange per sweep
     for (int i = 0; i < F->cfg.nu1; ++i) {
+        if (jac) {
+            if (i) ex.exchange(l, false);
+            ex.jacobi(l);
+            continue;
+        }
         if (i) ex.exchange(l, true);
         ex.smooth(l, 0);
         ex.exchange(l, true);
         ex.smooth(l, 1);
     }
-    if (F->cfg.nu1) ex.exchange(l, true);
+    if (F->cfg.nu1) ex.exchange(l, !jac);
     const bool fast = sizeof(T) == 4 && MODE != 1 && transfer32_specialised(F->L[l]);
     ex.restrict_to(l, fast);
     vcycle_walk<T, MODE>(F, l + 1, fast ? ENTRY_NONE : ENTRY_FULL, ex);
-    if (l + 1 != last) ex.exchange(l + 1, true);
+    if (l + 1 != last) ex.exchange(l + 1, !jac);  // Jacobi sweeps write no ghosts through
     ex.prolong_from(l, fast);
     ex.exchange(l, fast);
     for (int i = 0; i < F->cfg.nu2; ++i) {
+        if (jac) {
+            if (i) ex.exchange(l, false);
+            ex.jacobi(l);
+            continue;
+        }
         if (i) ex.exchange(l, true);
         ex.smooth(l, 0);
         ex.exchange(l, true);
@@ -383,8 +401,26 @@ struct LaunchExec {
     }
     void exchange(int l, bool iface) { octmg::exchange<T, MODE>(F, F->L[l], ufield<T>(F->L[l]), iface); }
     void smooth(int l, int colour) { octmg::smooth<T, MODE>(F, F->L[l], colour); }
+    void jacobi(int l, bool prof = true) {
+        if constexpr (sizeof(T) == 8) {
+            DevLevel &d = F->L[l];
+            Prof p(F, prof ? cat_of<T>(l == 0 ? P_SMOOTH64_L0 : P_SMOOTH64) : -1, 1);
+            k_jacobi64<MODE><<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u64b, d.f64, d.c64(), d.h2_64, d.g,
+                                                                          F->omega, skip_of(F, d));
+            std::swap(d.u64, d.u64b);  // the new iterate; its ghosts are refreshed by the next exchange
+        }
+    }
     void coarse(int l) {
         DevLevel &d = F->L[l];
+        if (F->cfg.coarse_iters > 0) {  // damped Jacobi sweeps from zero (the paper's coarsest solver)
+            const DevLevel &d = F->L[l];
+            Prof p(F, cat_of<T>(P_COARSE64), F->cfg.coarse_iters * (1 + (d.nfaces > 0) + (d.nsegs > 0)));
+            for (int it = 0; it < F->cfg.coarse_iters; ++it) {
+                octmg::exchange<T, MODE>(F, F->L[l], ufield<T>(F->L[l]), false, false);
+                jacobi(l, false);
+            }
+            return;
+        }
         Prof p(F, cat_of<T>(P_COARSE64), 1);
         k_coarse_solve<T><<<(F->Nc * 32 + kThreads - 1) / kThreads, kThreads, 0, F->st>>>(
             ufield<T>(d), ffield<T>(d), F->Ainv, sizeof(T) == 4 ? F->cmap32 : F->cmap, F->uprob, F->ustart, F->moff,
@@ -421,6 +457,7 @@ struct RecordExec {
         if (d.nsegs > 0) ph.push_back({T_SEGS, l});
     }
     void smooth(int l, int colour) { ph.push_back({colour ? T_SMOOTH1 : T_SMOOTH0, l}); }
+    void jacobi(int) {}  // FP64 only; the tail runs FP32 cycles
     void coarse(int l) { ph.push_back({T_COARSE, l}); }
     void restrict_to(int l, bool) { ph.push_back({T_RESTRICT, l}); }
     void prolong_from(int l, bool) { ph.push_back({T_PROLONG, l}); }
@@ -519,16 +556,21 @@ mg_status enqueue_problem_sums(mg_forest *F) {
 // upload_scales, mult) is a power of two close to 1 / ||r_p|| so the FP32 values stay near unit size.
 template <int MODE>
 mg_status residual64(mg_forest *F, double *u, const double *f, float *out, float *zero_out,
-                     const std::vector<double> &mult, std::vector<double> *rr) {
+                     const std::vector<double> &mult, std::vector<double> *rr, bool zero_u = false) {
     DevLevel &d = F->L[0];
-    exchange<double, MODE>(F, d, u);
+    if (!zero_u) exchange<double, MODE>(F, d, u);
     const int cpb = chunks_per_block(d);
     MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
     {
         Prof p(F, P_RESID64, 1);
-        k_residual_norm<MODE><<<d.g.nb * cpb, kThreads, 0, F->st>>>(u, f, d.c64(), d.ih2_64, d.vol_32, d.g, cpb, out,
-                                                                    F->pscale, d.bprob, F->bsum, zero_out,
-                                                                    skip_of(F, d));
+        if (zero_u)
+            k_residual_norm<MODE, true><<<d.g.nb * cpb, kThreads, 0, F->st>>>(
+                u, f, d.c64(), d.ih2_64, d.vol_32, d.g, cpb, out, F->pscale, d.bprob, F->bsum, zero_out,
+                skip_of(F, d));
+        else
+            k_residual_norm<MODE><<<d.g.nb * cpb, kThreads, 0, F->st>>>(u, f, d.c64(), d.ih2_64, d.vol_32, d.g, cpb,
+                                                                        out, F->pscale, d.bprob, F->bsum, zero_out,
+                                                                        skip_of(F, d));
     }
     if (rr) {
         MG_TRY(read_problem_sums(F));
@@ -738,22 +780,37 @@ double pow2_near(double x) {
 
 // Mixed precision, first half of a defect-correction step: r64 = f - A u (FP64), stored as FP32 r * scale_p
 // with the FP32 correction zeroed; per-problem ||r||^2 to rr.
-mg_status mixed_step(mg_forest *F, const std::vector<double> &mult, std::vector<double> *rr) {
+mg_status mixed_step(mg_forest *F, const std::vector<double> &mult, std::vector<double> *rr, bool zero_u) {
     DevLevel &d = F->L[0];
     MG_TRY(upload_scales(F, mult));
     if (F->cfg.coeff)
-        MG_TRY((residual64<1>(F, d.u64, d.f64, d.f32, d.u32, mult, rr)));
+        MG_TRY((residual64<1>(F, d.u64, d.f64, d.f32, d.u32, mult, rr, zero_u)));
     else
-        MG_TRY((residual64<0>(F, d.u64, d.f64, d.f32, d.u32, mult, rr)));
+        MG_TRY((residual64<0>(F, d.u64, d.f64, d.f32, d.u32, mult, rr, zero_u)));
     return MG_OK;
 }
 
 // The residual half of a defect-correction step without host synchronisation (graph-capturable).
-mg_status enqueue_residual(mg_forest *F) {
+mg_status enqueue_residual(mg_forest *F, bool zero_u) {
     DevLevel &d = F->L[0];
     static const std::vector<double> none;
-    if (F->cfg.coeff) return residual64<1>(F, d.u64, d.f64, d.f32, d.u32, none, nullptr);
-    return residual64<0>(F, d.u64, d.f64, d.f32, d.u32, none, nullptr);
+    if (F->cfg.coeff) return residual64<1>(F, d.u64, d.f64, d.f32, d.u32, none, nullptr, zero_u);
+    return residual64<0>(F, d.u64, d.f64, d.f32, d.u32, none, nullptr, zero_u);
+}
+
+// Packs the caller's u into the level-0 FP64 pool and reports whether it is all zero (one read-back).
+mg_status pack_initial_guess(mg_forest *F, const double *u_dev, bool *zero) {
+    DevLevel &d = F->L[0];
+    MG_CUDA(cudaMemsetAsync(F->flag, 0, sizeof(int), F->st));
+    {
+        Prof p(F, P_LAYOUT, 1);
+        k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, u_dev, d.g, F->leaf_off, F->flag);
+    }
+    int h = 1;
+    MG_CUDA(cudaMemcpyAsync(&h, F->flag, sizeof(int), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    *zero = h == 0;
+    return MG_OK;
 }
 
 // Second half: `cycles` FP32 V-cycles on the scaled residual, then u64 += e32 / scale_p (exact).
@@ -817,7 +874,8 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
     MG_TRY(check_ready(F));
     DevLevel &d = F->L[0];
     const int np = F->np;
-    MG_TRY(pack_user<double>(F, d, d.u64, u_dev));
+    bool zero_guess = false;
+    MG_TRY(pack_initial_guess(F, u_dev, &zero_guess));
     reset_done(F);
     std::vector<double> fn(np), rel(np, -1.0), mult(np), rr(np, 0.0);
     std::vector<int32_t> met(np, -1);
@@ -859,7 +917,7 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
             }
         }
     } else {
-        MG_TRY(mixed_step(F, mult, &rr));
+        MG_TRY(mixed_step(F, mult, &rr, zero_guess && !F->gb));  // a zero guess (g = 0) needs no operator: r = f
         auto st = update_rel(0);
         finite = st.second;
         const int inner = std::max(1, F->cfg.inner_cycles);
@@ -867,7 +925,7 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
             const int m = std::min(inner, max_cycles - done);
             MG_TRY(finish_mixed_cycle(F, m));
             done += m;
-            MG_TRY(mixed_step(F, mult, &rr));
+            MG_TRY(mixed_step(F, mult, &rr, false));
             st = update_rel(done);
             finite = st.second;
         }
@@ -905,6 +963,15 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         set_error("bad coeff / precision / nu1 / nu2 / interface_flux");
         return MG_ERR_INVALID_ARG;
     }
+    if (cfg->c2f_variant < 0 || cfg->c2f_variant > 2 || cfg->smoother < 0 || cfg->smoother > 1 ||
+        cfg->coarse_iters < 0 || !(cfg->omega < 2.0) || std::isnan(cfg->omega)) {
+        set_error("bad c2f_variant (0..2) / smoother (0, 1) / coarse_iters (>= 0) / omega (< 2)");
+        return MG_ERR_INVALID_ARG;
+    }
+    if ((cfg->smoother == 1 || cfg->coarse_iters > 0) && cfg->precision != 0) {
+        set_error("the damped Jacobi smoother and coarsest solver run FP64 cycles (precision 0)");
+        return MG_ERR_INVALID_ARG;
+    }
     const int np = std::max(1, cfg->n_problems);
     std::vector<Key> leaves(cfg->n_leaves);
     for (int i = 0; i < cfg->n_leaves; ++i) {
@@ -917,6 +984,7 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
     F->cfg.leaves = nullptr;
     if (F->cfg.max_coarse <= 0) F->cfg.max_coarse = 512;
     F->st = static_cast<cudaStream_t>(cfg->stream);
+    F->omega = cfg->omega > 0.0 ? cfg->omega : 0.8;
     F->np = np;
     F->cfg.n_problems = np;
     std::string err;
@@ -997,6 +1065,8 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         const bool fp64 = !mixed || l == 0 || l + 1 == nl;
         if (fp64 && (st = dalloc(F, &d.u64, pe)) != MG_OK) return fail(st);
         if (fp64 && (st = dalloc(F, &d.f64, pe)) != MG_OK) return fail(st);
+        const bool jacobi_level = cfg->smoother == 1 || (cfg->coarse_iters > 0 && l + 1 == nl);
+        if (jacobi_level && (st = dalloc(F, &d.u64b, pe)) != MG_OK) return fail(st);
         if (mixed) {
             if ((st = dalloc(F, &d.u32, pe)) != MG_OK) return fail(st);
             if ((st = dalloc(F, &d.f32, pe)) != MG_OK) return fail(st);
@@ -1058,6 +1128,39 @@ __global__ void k_check_inputs(const double *__restrict__ f, const double *__res
     }
 }
 
+// Per-problem reference norms of relative residuals: ||f|| (volume-weighted) with g = 0, else the norm of the residual
+// of u = 0, i.e. of f plus the boundary data's contribution.
+mg_status reference_norms(mg_forest *F) {
+    DevLevel &d = F->L[0];
+    std::vector<double> sums(F->np, 0.0);
+    if (!F->gb) {
+        const int cpb = chunks_per_block(d);
+        MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
+        k_block_norm64<<<d.g.nb * cpb, kThreads, 0, F->st>>>(d.f64, d.vol_64, d.g, cpb, F->bsum);
+        MG_TRY(read_problem_sums(F));
+        for (int p = 0; p < F->np; ++p) sums[p] = F->psum_h[p];
+    } else {
+        MG_TRY(ensure_scratch64(F));
+        MG_CUDA(cudaMemsetAsync(F->s64a, 0, d.pool_elems() * sizeof(double), F->st));
+        const std::vector<double> ones(F->np, 1.0);
+        MG_TRY(upload_scales(F, ones));
+        MG_TRY(residual64_any(F, F->s64a, d.f64, ones, &sums));
+    }
+    double total = 0.0;
+    for (int p = 0; p < F->np; ++p) {
+        F->fnorm_p[p] = std::sqrt(sums[p]);
+        total += sums[p];
+    }
+    F->fnorm = std::sqrt(total);
+    return MG_OK;
+}
+
+__global__ void k_twice(double *__restrict__ out, const double *__restrict__ in, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] = 2.0 * in[i];
+}
+
 mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
     if (!F || !f_dev) {
         set_error("null forest or f");
@@ -1085,16 +1188,7 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
         MG_TRY(build_coefficients(F));
         MG_TRY(assemble_coarse(F));
     }
-    const int cpb = chunks_per_block(d);
-    MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
-    k_block_norm64<<<d.g.nb * cpb, kThreads, 0, F->st>>>(d.f64, d.vol_64, d.g, cpb, F->bsum);
-    MG_TRY(read_problem_sums(F));
-    double total = 0.0;
-    for (int p = 0; p < F->np; ++p) {
-        F->fnorm_p[p] = std::sqrt(F->psum_h[p]);
-        total += F->psum_h[p];
-    }
-    F->fnorm = std::sqrt(total);
+    MG_TRY(reference_norms(F));
     if (F->cfg.precision == 1) {
         MG_TRY(tune_smooth32(F));
         MG_TRY(tune_tail(F));
@@ -1250,6 +1344,34 @@ mg_status mg_set_smoother_shape(mg_forest *F, int32_t level, const int32_t *shap
         return MG_ERR_INVALID_ARG;
     }
     d.s32 = sh;
+    return MG_OK;
+}
+
+mg_status mg_set_boundary(mg_forest *F, const double *g_dev) {
+    if (!F) {
+        set_error("null forest");
+        return MG_ERR_INVALID_ARG;
+    }
+    DevLevel &d = F->L[0];
+    if (!g_dev) {
+        F->gb = nullptr;
+    } else {
+        const int64_t cnt = static_cast<int64_t>(d.g.nb) * 6 * d.g.n * d.g.n;
+        if (!F->gb_pool) MG_TRY(dalloc(F, &F->gb_pool, cnt));
+        MG_CUDA(cudaMemsetAsync(F->flag, 0, sizeof(int), F->st));
+        k_check_inputs<<<grid_for(cnt), kThreads, 0, F->st>>>(g_dev, nullptr, cnt, F->flag);
+        int hbad = 0;
+        MG_CUDA(cudaMemcpyAsync(&hbad, F->flag, sizeof(int), cudaMemcpyDeviceToHost, F->st));
+        MG_CUDA(cudaStreamSynchronize(F->st));
+        if (hbad) {
+            set_error("g has a non-finite entry");
+            return MG_ERR_NONFINITE;
+        }
+        k_twice<<<grid_for(cnt), kThreads, 0, F->st>>>(F->gb_pool, g_dev, cnt);
+        F->gb = F->gb_pool;
+    }
+    if (F->rhs_set) MG_TRY(reference_norms(F));
+    MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
 }
 

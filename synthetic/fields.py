@@ -126,3 +126,26 @@ def batch_fields(problems, seed=0, device="cpu", sigma=1.0, ell=0.1):
         f[off:off + cnt] = torch.rand(cnt, generator=gen, device=device, dtype=F64) * 2.0 - 1.0
         off += cnt
     return f, k
+
+
+def boundary_values(R, n, keys, g, device="cpu"):
+    """Dirichlet data at the face centres of every leaf face, shape (n_leaves, 6, n^2) float64: face 2 axis + side
+    (side 1 the upper face), entry i2 * n + i1 at interior coordinates (i1, i2) along the two other axes in
+    increasing axis order.  g is a vectorised function of (x, y, z); faces inside the domain get values too (they
+    are ignored by the solver)."""
+    keys = list(keys)
+    out = np.empty((len(keys), 6, n * n))
+    t = (np.arange(n) + 0.5) / n
+    for b, (lev, i, j, k) in enumerate(keys):
+        ext = 1.0 / (R * 2.0 ** lev)
+        org = np.array([i, j, k], dtype=np.float64) * ext
+        for axis in range(3):
+            t1, t2 = [d for d in range(3) if d != axis]
+            i2g, i1g = np.meshgrid(t, t, indexing="ij")  # [i2][i1]
+            X = [None, None, None]
+            X[t1] = org[t1] + i1g * ext
+            X[t2] = org[t2] + i2g * ext
+            for side in range(2):
+                X[axis] = np.full_like(i1g, org[axis] + side * ext)
+                out[b, 2 * axis + side] = np.asarray(g(X[0], X[1], X[2]), dtype=np.float64).reshape(-1)
+    return torch.from_numpy(out).to(device)

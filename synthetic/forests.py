@@ -152,6 +152,22 @@ def workload_forest(name: str):
     return R, n, keys
 
 
+def paper_benchmark_forest(R):
+    """The paper's benchmark geometry (Sec. 6) for R^3 root blocks: every root refined once, then the quarter of the
+    level-1 blocks with x < 1/2 and y < 1/2 refined once more (22 R^3 leaves; 2:1 balanced by construction).
+    Returns leaf keys (level, i, j, k)."""
+    keys = []
+    m = 2 * R
+    for k in range(m):
+        for j in range(m):
+            for i in range(m):
+                if i < R and j < R:
+                    keys += [(2, 2 * i + a, 2 * j + b, 2 * k + c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+                else:
+                    keys.append((1, i, j, k))
+    return keys
+
+
 def batch_problems(count=256, seed=0, sizes=(16, 32, 64, 128), max_depth=2, box=(0.1, 0.4)):
     """Independent single-root problems: per problem (drawn in this order) the block size n from ``sizes``, the
     refinement depth from {0..max_depth}, box sides U(box) per axis, and the box corner uniform so the box fits;
