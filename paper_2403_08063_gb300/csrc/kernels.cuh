@@ -1,8 +1,9 @@
 // Device kernels of the octree-block multigrid (arXiv 2403.08063), written for sm_103a.
 //
-// Storage: every block of a level is a padded (n+2)^3 array, x fastest (padded coordinate = interior + 1), one
-// ghost layer per face (Sec. 3.3: one layer suffices for the quadratic C2F / linear F2C schemes).  The blocks of
-// a level are contiguous with a stride `bs` (elements) rounded up to 256 bytes.
+// Storage: every block of a level is a padded (n+2)^3 array (padded coordinate = interior + 1), one ghost layer
+// per face (Sec. 3.3: one layer suffices for the quadratic C2F / linear F2C schemes); FP64 pools keep it x-fastest,
+// FP32 pools split it by colour (see Lay below).  The blocks of a level are contiguous with one stride `bs`
+// (elements) for both precisions: the larger of the two block sizes, rounded up to 64 elements.
 //
 // Coefficient modes (template parameter MODE):
 //   0  constant coefficient, -Laplace: every face coefficient T_f = 1;
@@ -13,6 +14,7 @@
 //   2  variable k in FP32: kap[idx] = 1/k with ghosts; T_f = 2 / (kap_i + kap_nb) evaluated with rcp.approx.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "octmg_internal.h"
@@ -551,7 +553,7 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
             k0[dz] = __ldg(kb + ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL);
         }
     }
-    const float hb = __ldg(h2 + b);
+    const float hb = __ldg(h2 + b), hh = 0.5f * hb;  // T_f = 2 / (kap_i + kap_f): its 2 cancels against h^2 / 2
     // ---- updates -----------------------------------------------------------------------------------
     float val[ZC];
 #pragma unroll
@@ -573,7 +575,7 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
             sacc = fmaf(e0, zm, sacc);
             sacc = fmaf(e1, zp, sacc);
             const float D = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
-            val[dz] = fmaf(hb, fv[dz], 2.0f * sacc) * frcp(2.0f * D);
+            val[dz] = fmaf(hh, fv[dz], sacc) * frcp(D);
         } else {
             const float S = ((xr0[dz] + xr1[dz]) + (ym[dz] + yp[dz])) + (zm + zp);
             val[dz] = fmaf(hb, fv[dz], S) * (1.0f / 6.0f);
@@ -668,19 +670,28 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // FP32 half-sweep with the other colour's planes staged in shared memory by bulk copies (block edge n = 2^LG,
 // colour-split pools with H = half_row(P)).
 //
-// A CTA owns block b, interior rows y0 .. y0 + TY - 1 and planes z0 .. z0 + TZ - 1; thread (j, yl) updates the cells
-// x = 2j + c of rows y0 + yl + i TY/R (i < R) in every plane, marching in z.  Per plane z the CTA needs, of the other half, rows
-// y0 - 1 .. y0 + TY of planes z - 1, z, z + 1 (u, and kappa for variable k) and, of its own half, rows y0 .. y0 + TY - 1
-// of plane z (f, and kappa).  Each such plane segment is one contiguous run of (TY + 2) H or TY H floats, fetched by
-// one bulk copy into a ring of 3 + D (other half) or 1 + D (own half) slots, D planes ahead of the plane being
-// updated; one elected thread issues the copies and arms the slot's mbarrier, every thread waits on it.
+// A CTA owns block b, interior rows y0 .. y0 + TY - 1 and planes z0 .. z0 + TZ - 1 and marches in z.  Thread (j, yl)
+// updates the cells at position j + C of rows y0 + yl + i TW (i < R, TW = TY / R) in every plane, where
+// C = (y + z + colour) & 1.  TY, TW and z0 are even, so C is the same for all rows of a thread, and lanes are mapped
+// to rows so that it is the same for every lane of a warp: a warp covers one row (n >= 64) or two rows two apart
+// (n = 32).  Each plane then runs one of two bodies with C a compile-time constant, without per-cell selects.
+//
+// Per plane z the CTA needs, of the other half, rows y0 - 1 .. y0 + TY of planes z - 1, z, z + 1 (u, and kappa for
+// variable k) and, of its own half, rows y0 .. y0 + TY - 1 of plane z (f, and kappa).  Each plane segment is one
+// contiguous run of (TY + 2) H or TY H floats, fetched by one bulk copy.  The other half's planes z0 - 1 and z0 come
+// first, on barrier 0; after that, group g = {other plane z0 + g + 1, own plane z0 + g} completes on one of D + 1
+// group barriers, so each plane costs one wait.  Groups run D + 1 planes ahead of the plane being updated, in rings
+// of D + 2 (other half) and D + 1 (own half) slots; one elected thread issues the copies and arms the barriers.  Group
+// D reuses the slot of plane z0 - 1, so it is issued only after every thread has moved that plane into registers.
 //
 // Per cell the thread reads from shared memory its x-neighbour pair of plane z + 1 (positions j, j + 1 of row yl + 1;
 // the pair of plane z was read one plane earlier and gives the x-neighbours now, that of plane z - 1 the z-minus
-// neighbour at position c), its y-neighbours (rows yl and yl + 2 at j + c) and its own f and kappa: 4 + 4 + 2 shared
-// loads instead of 14.  New values go straight to global memory (the own half is not staged), with the same
-// write-through of block-face cells as k_smooth32.  No staged value is written during the sweep except reflection
-// ghosts, which only the writing cell reads, before it writes.
+// neighbour at position C), its y-neighbours (rows yl and yl + 2 at j + C) and its own f and kappa: 4 + 4 + 2 shared
+// loads instead of 14.  New values go straight to global memory (the own half is not staged).  Write-through of
+// block-face cells as in k_smooth32, with the target of every face this thread can touch resolved before the
+// march: the x face of lanes j = 0 (side 0, cells with C = 0) and j = n/2 - 1 (side 1, C = 1), the y face of the
+// thread's row y = 0 or n - 1, and the z faces of planes 0 and n - 1 (uniform over the CTA).  No staged value is
+// written during the sweep except reflection ghosts, which only the writing cell reads, before it writes.
 //
 // A wait that runs out sets *err and the CTA stops after the current plane (all threads agree through the
 // per-plane __syncthreads_or), after its elected thread has waited, again bounded, for the copies it issued.
@@ -693,13 +704,12 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, H = half_row(P), PL = P * H, HALF = P * PL;
     constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int RO = 3 + D, RW = 1 + D;
-    const int so = (TY + 2) * H, sw = TY * H;  // floats per slot
-    float *ou = reinterpret_cast<float *>(smem_raw);  // other half: u slots, then kappa slots
-    float *ok = ou + RO * so;
-    float *wf = ou + NA * RO * so;                      // own half: f slots, then kappa slots
-    float *wk = wf + RW * sw;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(wf + NA * RW * sw);  // RO + RW barriers
+    const int RO = 2 + D, RW = 1 + D, G = 1 + D;
+    const int so = (TY + 2) * H, sw = TY * H;  // floats per plane segment
+    // other-half slot i: u at ou + i NA so, kappa after it; own-half slot i: f at wf + i NA sw, kappa after it
+    float *ou = reinterpret_cast<float *>(smem_raw);
+    float *wf = ou + NA * RO * so;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wf + NA * RW * sw);  // bar[0]: planes z0 - 1, z0; bar[1 + g % G]
 
     const int nty = n / TY;
     const int ty = static_cast<int>(blockIdx.x % nty);
@@ -710,152 +720,165 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
     const int y0 = ty * TY, z0 = tz * TZ;
     const int s = colour ^ 1;
     const int tid = threadIdx.x;
-    const int TW = TY / R;  // row stride between a thread's rows
-    const int j = tid & (NH - 1), yl0 = tid >> (LG - 1);
+    const int TW = TY / R;
+    const int j = tid & (NH - 1);
+    int yl0 = tid >> (LG - 1);
+    if constexpr (NH < 32) yl0 = (yl0 & ~3) | ((yl0 & 1) << 1) | ((yl0 >> 1) & 1);  // a warp's two rows: same parity
     const int64_t base = b * bs;
     const float *gou = u + base + (s ^ 1) * HALF, *gok = kap + base + (s ^ 1) * HALF;
     const float *gwf = f + base + s * HALF, *gwk = kap + base + s * HALF;
 
-    // other-half plane io = padded Z z0 + io (io = 0 .. TZ + 1), rows y0 .. y0 + TY + 1, into slot `sl`
-    const auto issue_oth = [&](int io, int sl) {
-        const int64_t off = (static_cast<int64_t>(z0 + io) * P + y0) * H;
-        mbar_arm(&bar[sl], NA * so * 4);
-        bulk_load(ou + sl * so, gou + off, so * 4, &bar[sl]);
-        if constexpr (MODE == 2) bulk_load(ok + sl * so, gok + off, so * 4, &bar[sl]);
+    const auto issue_first = [&]() {  // other-half planes z0 - 1 and z0 (padded Z z0, z0 + 1) into slots 0, 1
+        mbar_arm(&bar[0], 2 * NA * so * 4);
+        for (int io = 0; io < 2; ++io) {
+            const int64_t off = (static_cast<int64_t>(z0 + io) * P + y0) * H;
+            bulk_load(ou + io * NA * so, gou + off, so * 4, &bar[0]);
+            if constexpr (MODE == 2) bulk_load(ou + io * NA * so + so, gok + off, so * 4, &bar[0]);
+        }
     };
-    // own-half plane iw = padded Z z0 + 1 + iw (iw = 0 .. TZ - 1), rows y0 + 1 .. y0 + TY
-    const auto issue_own = [&](int iw, int sl) {
-        const int64_t off = (static_cast<int64_t>(z0 + 1 + iw) * P + y0 + 1) * H;
-        mbar_arm(&bar[RO + sl], NA * sw * 4);
-        bulk_load(wf + sl * sw, gwf + off, sw * 4, &bar[RO + sl]);
-        if constexpr (MODE == 2) bulk_load(wk + sl * sw, gwk + off, sw * 4, &bar[RO + sl]);
+    const auto issue_group = [&](int g) {  // other plane z0 + g + 1 (padded z0 + g + 2), own plane z0 + g
+        uint64_t *bg = &bar[1 + g % G];
+        mbar_arm(bg, NA * (so + sw) * 4);
+        const int64_t oo = (static_cast<int64_t>(z0 + g + 2) * P + y0) * H;
+        float *d0 = ou + ((g + 2) % RO) * NA * so;
+        bulk_load(d0, gou + oo, so * 4, bg);
+        if constexpr (MODE == 2) bulk_load(d0 + so, gok + oo, so * 4, bg);
+        const int64_t ow = (static_cast<int64_t>(z0 + 1 + g) * P + y0 + 1) * H;
+        float *d1 = wf + (g % RW) * NA * sw;
+        bulk_load(d1, gwf + ow, sw * 4, bg);
+        if constexpr (MODE == 2) bulk_load(d1 + sw, gwk + ow, sw * 4, bg);
     };
-    int n_oth = 0, n_own = 0, iso = 0, isw = 0;  // copies issued and next refill slots (elected thread)
+    int n_iss = 0;  // groups issued (elected thread)
     if (tid == 0) {
-        for (int i = 0; i < RO + RW; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < 1 + G; ++i) mbar_init(&bar[i], 1);
         mbar_init_fence();
     }
     __syncthreads();
-    if (tid == 0) {
-        for (; n_oth < RO && n_oth < TZ + 2; ++n_oth) issue_oth(n_oth, n_oth);
-        for (; n_own < RW && n_own < TZ; ++n_own) issue_own(n_own, n_own);
+    if (tid == 0) {  // group D would land in the slot of plane z0 - 1: it follows once that plane is in registers
+        issue_first();
+        for (; n_iss < G - 1 && n_iss < TZ; ++n_iss) issue_group(n_iss);
     }
-    const float hb = __ldg(h2 + b);
-    // write-through targets of this block's faces (the same for the whole CTA), and the x face this lane may touch
-    int nb6[6] = {-2, -2, -2, -2, -2, -2};
+    const float hb = __ldg(h2 + b), hh = 0.5f * hb;
+
+    // write-through targets, as pointers p with the target of the cell at index q (in its half) at p[q]
+    float *us = u + base + s * HALF;
+    float *xw = nullptr, *yw = nullptr, *zlo = nullptr, *zhi = nullptr;
+    float xsg = 1.f, ysg = 1.f, zlsg = 1.f, zhsg = 1.f;
+    const int xs = j == 0 ? 0 : 1;  // x face side of lanes j = 0 and j = n/2 - 1
+    int yr = -1;                    // which of the thread's rows lies on a y face
     if (nbr6) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) nb6[q] = __ldg(nbr6 + b * 6 + q);
-    }
-    const int xs = j == 0 ? 0 : (j == NH - 1 ? 1 : -1);
-    int bad = 0;
-    bad |= !mbar_wait(&bar[0], 0);
-    bad |= !mbar_wait(&bar[1], 0);
-    float pm[R][2], pc[R][2], qm[R][2], qc[R][2];  // x-neighbour pairs of planes z - 1 and z (u, kappa)
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int rc = (yl0 + rr * TW + 1) * H + j;
-        pm[rr][0] = ou[rc];
-        pm[rr][1] = ou[rc + 1];
-        pc[rr][0] = ou[so + rc];
-        pc[rr][1] = ou[so + rc + 1];
-        if constexpr (MODE == 2) {
-            qm[rr][0] = ok[rc];
-            qm[rr][1] = ok[rc + 1];
-            qc[rr][0] = ok[so + rc];
-            qc[rr][1] = ok[so + rc + 1];
-        }
-    }
-    // ring positions: plane z + 1 of the other half (slot sn, phase pn), plane z (sc), own plane z (sw_, pw)
-    int sn = 2 % RO, pn = 2 / RO, sc = 1, sw_ = 0, pw = 0;
-    int consumed_oth = 2, consumed_own = 0;
-    for (int k = 0; k < TZ; ++k) {
-        const int z = z0 + k;
-        bad |= !mbar_wait(&bar[sn], pn & 1);
-        bad |= !mbar_wait(&bar[RO + sw_], pw & 1);
-        consumed_oth = k + 3;
-        consumed_own = k + 1;
-        const float *on = ou + sn * so, *oc = ou + sc * so;
-        const float *kn = ok + sn * so, *kc_ = ok + sc * so;
-        const float *fw = wf + sw_ * sw, *kw = wk + sw_ * sw;
+        const auto target = [&](int q6, int nb_off, int refl_off, float *&p, float &sg) {
+            const int nbv = __ldg(nbr6 + b * 6 + q6);
+            if (nbv >= 0) p = u + nbv * bs + s * HALF + nb_off;
+            else if (nbv == -1) { p = u + base + (s ^ 1) * HALF + refl_off; sg = -1.f; }
+        };
+        if (j == 0 || j == NH - 1) target(xs, xs ? -NH : NH, 0, xw, xsg);
 #pragma unroll
         for (int rr = 0; rr < R; ++rr) {
-            const int yl = yl0 + rr * TW, y = y0 + yl;
-            const int c = (y + z + colour) & 1;
-            const int rc = (yl + 1) * H + j;
-            const float pn0 = on[rc], pn1 = on[rc + 1];
-            const float ym = oc[rc - H + c], yp = oc[rc + H + c];
-            const float fv = fw[yl * H + j + c];
-            const float zm = c ? pm[rr][1] : pm[rr][0], zp = c ? pn1 : pn0;
-            float val;
-            float qn0 = 0.f, qn1 = 0.f;
-            if constexpr (MODE == 2) {
-                qn0 = kn[rc];
-                qn1 = kn[rc + 1];
-                const float kym = kc_[rc - H + c], kyp = kc_[rc + H + c];
-                const float k0 = kw[yl * H + j + c];
-                const float kzm = c ? qm[rr][1] : qm[rr][0], kzp = c ? qn1 : qn0;
-                const float a0 = frcp(k0 + qc[rr][0]), a1 = frcp(k0 + qc[rr][1]);
-                const float b0 = frcp(k0 + kym), b1 = frcp(k0 + kyp);
-                const float e0 = frcp(k0 + kzm), e1 = frcp(k0 + kzp);
-                float sacc = a0 * pc[rr][0];
-                sacc = fmaf(a1, pc[rr][1], sacc);
-                sacc = fmaf(b0, ym, sacc);
-                sacc = fmaf(b1, yp, sacc);
-                sacc = fmaf(e0, zm, sacc);
-                sacc = fmaf(e1, zp, sacc);
-                const float Dn = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
-                val = fmaf(hb, fv, 2.0f * sacc) * frcp(2.0f * Dn);
-            } else {
-                const float S = ((pc[rr][0] + pc[rr][1]) + (ym + yp)) + (zm + zp);
-                val = fmaf(hb, fv, S) * (1.0f / 6.0f);
-            }
-            const int q = ((z + 1) * P + (y + 1)) * H + j + c;  // the cell, in either half
-            u[base + s * HALF + q] = val;
-            if (xs == c) {  // x face, side c (nb6 is -2, nothing to write, without a face table)
-                const int nbv = nb6[c];
-                if (nbv >= 0) u[nbv * bs + s * HALF + q + (c ? -NH : NH)] = val;
-                else if (nbv == -1) u[base + (s ^ 1) * HALF + q] = -val;
-            }
-            if (nbr6 && (y == 0 || y == n - 1 || z == 0 || z == n - 1)) {
+            const int y = y0 + yl0 + rr * TW;
+            if (y == 0) { target(2, n * H, -H, yw, ysg); yr = rr; }
+            if (y == n - 1) { target(3, -n * H, H, yw, ysg); yr = rr; }
+        }
+        if (!yw) yr = -1;
+        if (z0 == 0) target(4, n * PL, -PL, zlo, zlsg);
+        if (z0 + TZ == n) target(5, -n * PL, PL, zhi, zhsg);
+    }
+
+    int bad = !mbar_wait(&bar[0], 0);
+    const int cpar = (yl0 + colour) & 1;  // C of plane z0 (y0, TW and z0 are even)
+    const int ro0 = (yl0 + 1) * H + j, rstep = TW * H;  // row yl + 1 of an other-half slot, position j
+    const int qo0 = ((z0 + 1) * P + y0 + yl0 + 1) * H + j, qstep = TW * H;  // the cell at plane z0, C = 0
+    float pc[R][2], qc[R][2], zmu[R], zmk[R];  // x-neighbour pair of the current plane, z-minus neighbour (u, kappa)
 #pragma unroll
-                for (int axis = 1; axis < 3; ++axis) {
+    for (int rr = 0; rr < R; ++rr) {
+        const int ro = ro0 + rr * rstep;
+        zmu[rr] = ou[ro + cpar];
+        pc[rr][0] = ou[NA * so + ro];
+        pc[rr][1] = ou[NA * so + ro + 1];
+        if constexpr (MODE == 2) {
+            zmk[rr] = ou[so + ro + cpar];
+            qc[rr][0] = ou[NA * so + so + ro];
+            qc[rr][1] = ou[NA * so + so + ro + 1];
+        } else {
+            zmk[rr] = qc[rr][0] = qc[rr][1] = 0.f;
+        }
+    }
+    // ring positions: other-half slots of planes z + 1 and z, own-half slot and group barrier of plane z
+    int on_s = 2 % RO, oc_s = 1, w_s = 0, g_s = 0, g_ph = 0;
+    int k = 0;
+    if (!__syncthreads_or(bad)) {
+        if (tid == 0 && n_iss < TZ) issue_group(n_iss++);
+        for (; k < TZ; ++k) {
+            bad |= !mbar_wait(&bar[1 + g_s], g_ph);
+            const float *on = ou + on_s * NA * so, *oc = ou + oc_s * NA * so, *fw = wf + w_s * NA * sw;
+            const float *kn = on + so, *kc = oc + so, *kw = fw + sw;
+            const int z = z0 + k;
+            float *zw = z == 0 ? zlo : (z == n - 1 ? zhi : nullptr);
+            const float zsg = z == 0 ? zlsg : zhsg;
+            const int qz = qo0 + k * PL;
+            const auto plane = [&](auto Cc) {
+                constexpr int C = decltype(Cc)::value;
 #pragma unroll
-                    for (int side = 0; side < 2; ++side) {
-                        if ((axis == 1 ? y : z) != (side ? n - 1 : 0)) continue;
-                        const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
-                        const int nbv = nb6[2 * axis + side];
-                        if (nbv >= 0) u[nbv * bs + s * HALF + q + (side ? -Dm : Dm)] = val;
-                        else if (nbv == -1) u[base + (s ^ 1) * HALF + q + (side ? E : -E)] = -val;
+                for (int rr = 0; rr < R; ++rr) {
+                    const int ro = ro0 + rr * rstep;
+                    const float pn0 = on[ro], pn1 = on[ro + 1];
+                    const float ym = oc[ro - H + C], yp = oc[ro + H + C];
+                    const float fv = fw[ro - H + C];
+                    const float zp = C ? pn1 : pn0;
+                    float val;
+                    float qn0 = 0.f, qn1 = 0.f;
+                    if constexpr (MODE == 2) {
+                        qn0 = kn[ro];
+                        qn1 = kn[ro + 1];
+                        const float kym = kc[ro - H + C], kyp = kc[ro + H + C];
+                        const float k0 = kw[ro - H + C];
+                        const float kzp = C ? qn1 : qn0;
+                        const float a0 = frcp(k0 + qc[rr][0]), a1 = frcp(k0 + qc[rr][1]);
+                        const float b0 = frcp(k0 + kym), b1 = frcp(k0 + kyp);
+                        const float e0 = frcp(k0 + zmk[rr]), e1 = frcp(k0 + kzp);
+                        float sacc = a0 * pc[rr][0];
+                        sacc = fmaf(a1, pc[rr][1], sacc);
+                        sacc = fmaf(b0, ym, sacc);
+                        sacc = fmaf(b1, yp, sacc);
+                        sacc = fmaf(e0, zmu[rr], sacc);
+                        sacc = fmaf(e1, zp, sacc);
+                        const float Dn = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
+                        val = fmaf(hh, fv, sacc) * frcp(Dn);
+                    } else {
+                        const float S = ((pc[rr][0] + pc[rr][1]) + (ym + yp)) + (zmu[rr] + zp);
+                        val = fmaf(hb, fv, S) * (1.0f / 6.0f);
+                    }
+                    const int q = qz + rr * qstep + C;
+                    us[q] = val;
+                    if (xs == C && xw) xw[q] = xsg * val;
+                    if (yr == rr) yw[q] = ysg * val;
+                    if (zw) zw[q] = zsg * val;
+                    zmu[rr] = pc[rr][1 - C];
+                    pc[rr][0] = pn0;
+                    pc[rr][1] = pn1;
+                    if constexpr (MODE == 2) {
+                        zmk[rr] = qc[rr][1 - C];
+                        qc[rr][0] = qn0;
+                        qc[rr][1] = qn1;
                     }
                 }
-            }
-            pm[rr][0] = pc[rr][0];
-            pm[rr][1] = pc[rr][1];
-            pc[rr][0] = pn0;
-            pc[rr][1] = pn1;
-            if constexpr (MODE == 2) {
-                qm[rr][0] = qc[rr][0];
-                qm[rr][1] = qc[rr][1];
-                qc[rr][0] = qn0;
-                qc[rr][1] = qn1;
-            }
-        }
-        sc = sn;
-        if (++sn == RO) { sn = 0; ++pn; }
-        if (++sw_ == RW) { sw_ = 0; ++pw; }
-        // every thread is done with other-half plane k and own plane k: refill their slots
-        if (__syncthreads_or(bad)) break;
-        if (tid == 0) {
-            if (n_oth < TZ + 2) { issue_oth(n_oth++, iso); if (++iso == RO) iso = 0; }
-            if (n_own < TZ) { issue_own(n_own++, isw); if (++isw == RW) isw = 0; }
+            };
+            if ((cpar + k) & 1) plane(std::integral_constant<int, 1>{});
+            else plane(std::integral_constant<int, 0>{});
+            oc_s = on_s;
+            if (++on_s == RO) on_s = 0;
+            if (++w_s == RW) w_s = 0;
+            if (++g_s == G) { g_s = 0; g_ph ^= 1; }
+            // every thread is done with the slots of group k and other-half plane z: group k + G may refill them
+            if (__syncthreads_or(bad)) break;
+            if (tid == 0 && n_iss < TZ) issue_group(n_iss++);
         }
     }
     if (bad && tid == 0) {
         atomicOr(err, 1);
         // let the copies still in flight land before the CTA's shared memory is released
-        for (int io = consumed_oth; io < n_oth; ++io) mbar_wait(&bar[io % RO], (io / RO) & 1);
-        for (int iw = consumed_own; iw < n_own; ++iw) mbar_wait(&bar[RO + iw % RW], (iw / RW) & 1);
+        mbar_wait(&bar[0], 0);
+        for (int g = k; g < n_iss; ++g) mbar_wait(&bar[1 + g % G], (g / G) & 1);
     }
 }
 

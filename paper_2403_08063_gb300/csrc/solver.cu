@@ -158,7 +158,7 @@ bool smooth32_specialised(const DevLevel &d) { return d.g.lg >= 2 && d.g.lg <= 7
 
 size_t smooth32t_smem(int lg, bool var, int TY, int D) {
     const int P = (1 << lg) + 2, H = half_row(P), NA = var ? 2 : 1;
-    return static_cast<size_t>(4) * NA * ((3 + D) * (TY + 2) * H + (1 + D) * TY * H) + 8 * (4 + 2 * D);
+    return static_cast<size_t>(4) * NA * ((2 + D) * (TY + 2) * H + (1 + D) * TY * H) + 8 * (2 + D);
 }
 
 int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
