@@ -168,6 +168,33 @@ __device__ inline float frcp(float x) {
     return r;
 }
 
+// Conversions between binary64 and binary32 with an exact power-of-two scale, written on the IEEE 754 bit fields
+// (1 sign bit; 11 / 8 exponent bits with bias 1023 / 127; 52 / 23 fraction bits) so that they run on the integer
+// pipes: the hardware conversion instructions between the two formats issue on the FP64 pipe, the bottleneck of
+// the FP64 residual on this GPU.  Results below the binary32 normal range flush to a signed zero (binary32
+// subnormals are not produced or read); the scale exponent is |sexp| <= 126.
+// round_to_nearest_even(r * 2^sexp) as binary32
+__device__ __forceinline__ float f64_to_f32_pow2(double r, int sexp) {
+    const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(r));
+    const uint32_t sign = static_cast<uint32_t>(bits >> 32) & 0x80000000u;
+    const int e = static_cast<int>((bits >> 52) & 0x7ff) - 1023 + 127 + sexp;  // binary32 biased exponent
+    const uint32_t m = static_cast<uint32_t>(bits >> 29) & 0x7fffffu;          // the 23 kept fraction bits
+    const uint32_t rest = static_cast<uint32_t>(bits) & 0x1fffffffu;           // the 29 dropped ones
+    const uint32_t up = (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(((sign | (static_cast<uint32_t>(e) << 23)) | m) + up);  // a carry rounds up the exponent
+}
+// x * 2^pexp as binary64 (exact)
+__device__ __forceinline__ double f32_to_f64_pow2(float x, int pexp) {
+    const uint32_t bits = __float_as_uint(x);
+    const uint64_t sign = static_cast<uint64_t>(bits & 0x80000000u) << 32;
+    const int e = static_cast<int>((bits >> 23) & 0xff);
+    if (e == 0) return __longlong_as_double(static_cast<long long>(sign));
+    const uint64_t ed = e == 255 ? 0x7ffull : static_cast<uint64_t>(e - 127 + 1023 + pexp);
+    return __longlong_as_double(static_cast<long long>(sign | (ed << 52) | (static_cast<uint64_t>(bits & 0x7fffffu) << 29)));
+}
+
 // Face coefficient of the face between depth 0 and depth 1 of a block face, stored (MODE 1) or evaluated (MODE 2)
 // at the cell with the larger padded coordinate along the axis: `loc`; `other` is the cell across the face.
 template <typename T, int MODE>
@@ -1339,14 +1366,14 @@ static __global__ void k_residual_norm(const double *__restrict__ u, const doubl
     if (skip(b)) return;  // the whole CTA: its block's sum stays 0
     const int chunk = blockIdx.x - static_cast<int>(b * cpb);
     const int per = (1 << (3 * lg)) / cpb;
-    const float scale = pscale[bprob[b]];
+    const int sexp = static_cast<int>((__float_as_uint(pscale[bprob[b]]) >> 23) & 0xff) - 127;  // scale = 2^sexp
     const double ihb = MODE == 1 ? 0.0 : ih2[b];
     float acc = 0.0f;
     for (int c = chunk * per + threadIdx.x; c < (chunk + 1) * per; c += blockDim.x) {
         const int x = c & (n - 1), y = (c >> lg) & (n - 1), z = c >> (2 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
         const double r = ZU ? f[gi] : residual_at<double, MODE>(u, f, cf, gi, P, ihb);  // ZU: u = 0, r = f
-        const float rs = static_cast<float>(r) * scale;
+        const float rs = f64_to_f32_pow2(r, sexp);
         const int64_t gs = Lay<float>::at(g, b, x + 1, y + 1, z + 1);  // FP32 pools are colour-split
         if (out) out[gs] = rs;
         if (zero_out) {
@@ -1523,7 +1550,8 @@ static __global__ void k_update_mixed(double *__restrict__ u, const float *__res
         const int64_t b = t >> (3 * lg);
         if (skip(b)) continue;
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, g.P);
-        u[gi] = fma(pinv[bprob[b]], static_cast<double>(e[Lay<float>::at(g, b, x + 1, y + 1, z + 1)]), u[gi]);
+        const int pexp = static_cast<int>((static_cast<uint64_t>(__double_as_longlong(pinv[bprob[b]])) >> 52) & 0x7ff) - 1023;
+        u[gi] += f32_to_f64_pow2(e[Lay<float>::at(g, b, x + 1, y + 1, z + 1)], pexp);  // pinv = 2^pexp: exact
     }
 }
 

@@ -773,9 +773,11 @@ mg_status tune_tail(mg_forest *F) {
     return MG_OK;
 }
 
+// The power of two nearest to x, kept inside the binary32 normal range (the kernels apply it on exponent bits).
 double pow2_near(double x) {
     if (!(x > 0.0) || !std::isfinite(x)) return 1.0;
-    return std::ldexp(1.0, static_cast<int>(std::lround(std::log2(x))));
+    const long e = std::lround(std::log2(x));
+    return std::ldexp(1.0, static_cast<int>(std::min(126L, std::max(-126L, e))));
 }
 
 // Mixed precision, first half of a defect-correction step: r64 = f - A u (FP64), stored as FP32 r * scale_p
