@@ -668,6 +668,10 @@ __device__ inline void mbar_init_fence() { asm volatile("fence.mbarrier_init.rel
 __device__ inline void mbar_arm(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// plain arrival (release) of one thread on `bar`
+__device__ inline void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // global -> shared bulk copy completing on `bar`; both addresses 16-byte aligned, bytes a multiple of 16
 __device__ inline void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -707,9 +711,12 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // variable k) and, of its own half, rows y0 .. y0 + TY - 1 of plane z (f, and kappa).  Each plane segment is one
 // contiguous run of (TY + 2) H or TY H floats, fetched by one bulk copy.  The other half's planes z0 - 1 and z0 come
 // first, on barrier 0; after that, group g = {other plane z0 + g + 1, own plane z0 + g} completes on one of D + 1
-// group barriers, so each plane costs one wait.  Groups run D + 1 planes ahead of the plane being updated, in rings
-// of D + 2 (other half) and D + 1 (own half) slots; one elected thread issues the copies and arms the barriers.  Group
-// D reuses the slot of plane z0 - 1, so it is issued only after every thread has moved that plane into registers.
+// "full" group barriers, so each plane costs one wait.  Groups run D + 1 planes ahead of the plane being updated, in
+// rings of D + 2 (other half) and D + 1 (own half) slots.  The copies are issued by one thread of an extra producer
+// warp (the CTA's last): group g reuses the slots of group g - D - 1, and the producer issues it once every consumer
+// warp has arrived on that group's "empty" barrier (lane 0, after the warp's last read of the slots); group D reuses
+// the slot of plane z0 - 1 and waits for every warp to have moved that plane into registers.  Consumer warps are
+// never synchronised with each other: a warp runs ahead until it needs a group that has not landed.
 //
 // Per cell the thread reads from shared memory its x-neighbour pair of plane z + 1 (positions j, j + 1 of row yl + 1;
 // the pair of plane z was read one plane earlier and gives the x-neighbours now, that of plane z - 1 the z-minus
@@ -720,11 +727,12 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // thread's row y = 0 or n - 1, and the z faces of planes 0 and n - 1 (uniform over the CTA).  No staged value is
 // written during the sweep except reflection ghosts, which only the writing cell reads, before it writes.
 //
-// A wait that runs out sets *err and the CTA stops after the current plane (all threads agree through the
-// per-plane __syncthreads_or), after its elected thread has waited, again bounded, for the copies it issued.
+// Every wait is bounded.  A consumer warp whose wait runs out (its lanes agree by a vote) sets *err and stops; the
+// producer stops when an empty barrier is not reached in time, sets *err, and before it exits waits, again bounded,
+// for the copies it issued, so no copy lands in released shared memory.
 // ------------------------------------------------------------------------------------------------------------
 template <int MODE, int LG, int R>
-static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u, const float *__restrict__ f,
+static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u, const float *__restrict__ f,
                                                           const float *__restrict__ kap, const float *__restrict__ h2,
                                                           int64_t bs, int colour, const int32_t *__restrict__ nbr6,
                                                           int TY, int TZ, int D, int *__restrict__ err, Skip skip) {
@@ -736,7 +744,10 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
     // other-half slot i: u at ou + i NA so, kappa after it; own-half slot i: f at wf + i NA sw, kappa after it
     float *ou = reinterpret_cast<float *>(smem_raw);
     float *wf = ou + NA * RO * so;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(wf + NA * RW * sw);  // bar[0]: planes z0 - 1, z0; bar[1 + g % G]
+    // full barriers: bar[0] planes z0 - 1, z0; bar[1 + g % G] group g.  Empty barriers (all consumer warps are done
+    // with the slots): ebar[g % G] group g, ibar planes z0 - 1, z0 moved into registers
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wf + NA * RW * sw);
+    uint64_t *ebar = bar + 1 + G, *ibar = ebar + G;
 
     const int nty = n / TY;
     const int ty = static_cast<int>(blockIdx.x % nty);
@@ -775,15 +786,32 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
         bulk_load(d1, gwf + ow, sw * 4, bg);
         if constexpr (MODE == 2) bulk_load(d1 + sw, gwk + ow, sw * 4, bg);
     };
-    int n_iss = 0;  // groups issued (elected thread)
+    const int nthc = blockDim.x - 32, ncw = nthc >> 5;  // consumer threads and warps; the last warp produces
     if (tid == 0) {
         for (int i = 0; i < 1 + G; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < G + 1; ++i) mbar_init(&ebar[i], ncw);
         mbar_init_fence();
     }
     __syncthreads();
-    if (tid == 0) {  // group D would land in the slot of plane z0 - 1: it follows once that plane is in registers
-        issue_first();
-        for (; n_iss < G - 1 && n_iss < TZ; ++n_iss) issue_group(n_iss);
+    if (tid >= nthc) {
+        if (tid == nthc) {
+            // group g reuses the slots of group g - G (other half: the plane that was `oc` at plane g - G); group
+            // G - 1 the slot of plane z0 - 1
+            issue_first();
+            int g = 0;
+            for (; g < G - 1 && g < TZ; ++g) issue_group(g);
+            bool ok = true;
+            while (g < TZ) {
+                ok = g == G - 1 ? mbar_wait(ibar, 0) : mbar_wait(&ebar[(g - G) % G], ((g - G) / G) & 1);
+                if (!ok) break;
+                issue_group(g++);
+            }
+            if (!ok) atomicOr(err, 1);
+            // the copies still in flight land before the CTA's shared memory can be released
+            mbar_wait(&bar[0], 0);
+            for (int q = g > G ? g - G : 0; q < g; ++q) mbar_wait(&bar[1 + q % G], (q / G) & 1);
+        }
+        return;
     }
     const float hb = __ldg(h2 + b), hh = 0.5f * hb;
 
@@ -811,7 +839,7 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
         if (z0 + TZ == n) target(5, -n * PL, PL, zhi, zhsg);
     }
 
-    int bad = !mbar_wait(&bar[0], 0);
+    int bad = __any_sync(0xffffffffu, !mbar_wait(&bar[0], 0));
     const int cpar = (yl0 + colour) & 1;  // C of plane z0 (y0, TW and z0 are even)
     const int ro0 = (yl0 + 1) * H + j, rstep = TW * H;  // row yl + 1 of an other-half slot, position j
     const int qo0 = ((z0 + 1) * P + y0 + yl0 + 1) * H + j, qstep = TW * H;  // the cell at plane z0, C = 0
@@ -830,13 +858,14 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
             zmk[rr] = qc[rr][0] = qc[rr][1] = 0.f;
         }
     }
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(ibar);
     // ring positions: other-half slots of planes z + 1 and z, own-half slot and group barrier of plane z
     int on_s = 2 % RO, oc_s = 1, w_s = 0, g_s = 0, g_ph = 0;
-    int k = 0;
-    if (!__syncthreads_or(bad)) {
-        if (tid == 0 && n_iss < TZ) issue_group(n_iss++);
-        for (; k < TZ; ++k) {
-            bad |= !mbar_wait(&bar[1 + g_s], g_ph);
+    if (!bad) {
+        for (int k = 0; k < TZ; ++k) {
+            bad = __any_sync(0xffffffffu, !mbar_wait(&bar[1 + g_s], g_ph));
+            if (bad) break;
             const float *on = ou + on_s * NA * so, *oc = ou + oc_s * NA * so, *fw = wf + w_s * NA * sw;
             const float *kn = on + so, *kc = oc + so, *kw = fw + sw;
             const int z = z0 + k;
@@ -892,21 +921,16 @@ static __global__ void __launch_bounds__(512) k_smooth32t(float *__restrict__ u,
             };
             if ((cpar + k) & 1) plane(std::integral_constant<int, 1>{});
             else plane(std::integral_constant<int, 0>{});
+            // this warp is done with the slots of group k and other-half plane z: group k + G may refill them
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&ebar[g_s]);
             oc_s = on_s;
             if (++on_s == RO) on_s = 0;
             if (++w_s == RW) w_s = 0;
             if (++g_s == G) { g_s = 0; g_ph ^= 1; }
-            // every thread is done with the slots of group k and other-half plane z: group k + G may refill them
-            if (__syncthreads_or(bad)) break;
-            if (tid == 0 && n_iss < TZ) issue_group(n_iss++);
         }
     }
-    if (bad && tid == 0) {
-        atomicOr(err, 1);
-        // let the copies still in flight land before the CTA's shared memory is released
-        mbar_wait(&bar[0], 0);
-        for (int g = k; g < n_iss; ++g) mbar_wait(&bar[1 + g % G], (g / G) & 1);
-    }
+    if (bad && (tid & 31) == 0) atomicOr(err, 1);
 }
 
 // Point-form residual at padded cell (X, Y, Z) of block b, any layout (used by the FP32 kernels).

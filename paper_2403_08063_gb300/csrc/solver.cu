@@ -135,8 +135,9 @@ void exchange_k(mg_forest *F, DevLevel &d) {
 // FP32 smoothers specialised for block edges 4..128.  Two kernels and their launch shapes (kind, parameters):
 //   {1, ZC, threads, 0, 0}: k_smooth32, one column of ZC in {1, 2, 4} cells per thread, 128 / 256 / 512 threads;
 //   {2, TY, TZ, D, R}:      k_smooth32t (edges 32..128), a CTA per TY rows x TZ planes of a block, other-colour planes
-//                           staged in shared memory D ahead, R rows per thread (threads = n/2 TY / R in 128..512,
-//                           TZ in {16, 32, 64} up to n, D in {2, 4}, R in {1, 2, 4}).
+//                           staged in shared memory D + 1 ahead, R rows per thread (consumer threads = n/2 TY / R in
+//                           128..512, plus one producer warp,
+//                           TZ in {8, 16, 32, 64} up to n, D in {2, 4}, R in {1, 2, 4}).
 // A shape only changes which thread updates a cell, never the arithmetic, so every shape gives identical bits.
 using Shape = std::array<int32_t, 5>;
 using Smooth32Fn = void (*)(float *, const float *, const float *, const float *, int64_t, int64_t, int,
@@ -158,7 +159,7 @@ bool smooth32_specialised(const DevLevel &d) { return d.g.lg >= 2 && d.g.lg <= 7
 
 size_t smooth32t_smem(int lg, bool var, int TY, int D) {
     const int P = (1 << lg) + 2, H = half_row(P), NA = var ? 2 : 1;
-    return static_cast<size_t>(4) * NA * ((2 + D) * (TY + 2) * H + (1 + D) * TY * H) + 8 * (2 + D);
+    return static_cast<size_t>(4) * NA * ((2 + D) * (TY + 2) * H + (1 + D) * TY * H) + 8 * (4 + 2 * D);
 }
 
 int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
@@ -173,7 +174,7 @@ std::vector<Shape> smooth32_shapes(const DevLevel &d, bool var) {
     if (d.g.lg >= 5)
         for (int R : {1, 2, 4})
             for (int th : {128, 256, 512})
-                for (int tz : {16, 32, 64})
+                for (int tz : {8, 16, 32, 64})
                     for (int D : {2, 4}) {
                         const int TY = th * R / (n / 2);
                         if (TY >= R && TY <= n && tz <= n && smooth32t_smem(d.g.lg, var, TY, D) <= 200 * 1024)
@@ -200,7 +201,7 @@ void launch_smooth32(mg_forest *F, DevLevel &d, int colour, const Shape &sh, cud
                                  200 * 1024);
         });
         const int64_t grid = static_cast<int64_t>(d.g.nb) * (n / TY) * (n / TZ);
-        fn<<<static_cast<unsigned>(grid), (n / 2) * TY / R, smem, st>>>(d.u32, d.f32, d.kap, d.h2_32, d.g.bs, colour,
+        fn<<<static_cast<unsigned>(grid), (n / 2) * TY / R + 32, smem, st>>>(d.u32, d.f32, d.kap, d.h2_32, d.g.bs, colour,
                                                                          d.nbr6, TY, TZ, D, F->kerr, skip_of(F, d));
         return;
     }
@@ -302,7 +303,9 @@ using Prolong32Fn = void (*)(float *, int64_t, const float *, const XferItem *, 
 const Prolong32Fn kProlong32[5] = {k_prolong32<3>, k_prolong32<4>, k_prolong32<5>, k_prolong32<6>, k_prolong32<7>};
 
 void launch_residual_restrict32(mg_forest *F, DevLevel &d, DevLevel &c) {
-    kRestrict32[F->cfg.coeff ? 1 : 0][d.g.lg - 3]<<<grid_for(c.cells()), kThreads, 0, F->st>>>(
+    // one coarse cell per thread (no grid-stride loop): its load chain xf -> fine block -> 64 loads is latency-bound
+    const auto grid = static_cast<unsigned>((c.cells() + kThreads - 1) / kThreads);
+    kRestrict32[F->cfg.coeff ? 1 : 0][d.g.lg - 3]<<<grid, kThreads, 0, F->st>>>(
         d.u32, d.f32, d.kap, d.ih2_32, d.g.bs, c.f32, c.u32, d.xfer, c.g.nb, c.g.bs, skip_of(F, c));
 }
 
