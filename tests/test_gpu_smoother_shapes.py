@@ -4,8 +4,8 @@ in flight, rows per thread).
 
 A shape only decides which thread updates which cell of a colour, and the half-sweep's cells are independent, so
 every shape must give the same bits.  Checked on a refined forest with 32^3 blocks (C2F / F2C interfaces, boundary
-reflection and same-level write-through on every level from 32^3 down to 4^3 blocks), for constant and variable
-coefficients.
+reflection and same-level write-through on every level from 32^3 down to 4^3 blocks) and on a uniform forest of
+32^3 blocks (no interface: only write-through ghosts), for constant and variable coefficients.
 """
 import pytest
 import torch
@@ -17,9 +17,10 @@ DEV = "cuda:0"
 
 
 @pytest.mark.parametrize("coeff", [False, True])
-def test_every_smoother_shape_gives_identical_bits(coeff):
+@pytest.mark.parametrize("workload", ["sphere_2x32", "uniform_2x32"])
+def test_every_smoother_shape_gives_identical_bits(coeff, workload):
     from paper_2403_08063_gb300 import Forest
-    R, n, keys = syn.workload_forest("sphere_2x32")
+    R, n, keys = syn.workload_forest(workload)
     dev = torch.device(DEV)
     f = syn.gaussian_bump_with_noise(R, n, keys, seed=31, device=dev)
     k = syn.lognormal_k_rff(R, n, keys, seed=32, device=dev) if coeff else None
