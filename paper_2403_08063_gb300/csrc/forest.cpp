@@ -287,43 +287,4 @@ mg_status build_hierarchy(int32_t R, int32_t n, int32_t n_problems, const std::v
     return MG_OK;
 }
 
-bool invert_dense(std::vector<double> &A, int N) {
-    std::vector<double> I(static_cast<size_t>(N) * N, 0.0);
-    for (int i = 0; i < N; ++i) I[static_cast<size_t>(i) * N + i] = 1.0;
-    for (int c = 0; c < N; ++c) {
-        int piv = c;
-        double best = std::fabs(A[static_cast<size_t>(c) * N + c]);
-        for (int r = c + 1; r < N; ++r) {
-            double v = std::fabs(A[static_cast<size_t>(r) * N + c]);
-            if (v > best) {
-                best = v;
-                piv = r;
-            }
-        }
-        if (!(best > 0.0)) return false;
-        if (piv != c) {
-            for (int j = 0; j < N; ++j) {
-                std::swap(A[static_cast<size_t>(c) * N + j], A[static_cast<size_t>(piv) * N + j]);
-                std::swap(I[static_cast<size_t>(c) * N + j], I[static_cast<size_t>(piv) * N + j]);
-            }
-        }
-        double inv = 1.0 / A[static_cast<size_t>(c) * N + c];
-        for (int j = 0; j < N; ++j) {
-            A[static_cast<size_t>(c) * N + j] *= inv;
-            I[static_cast<size_t>(c) * N + j] *= inv;
-        }
-        for (int r = 0; r < N; ++r) {
-            if (r == c) continue;
-            double fct = A[static_cast<size_t>(r) * N + c];
-            if (fct == 0.0) continue;
-            for (int j = 0; j < N; ++j) {
-                A[static_cast<size_t>(r) * N + j] -= fct * A[static_cast<size_t>(c) * N + j];
-                I[static_cast<size_t>(r) * N + j] -= fct * I[static_cast<size_t>(c) * N + j];
-            }
-        }
-    }
-    A.swap(I);
-    return true;
-}
-
 }  // namespace octmg

@@ -111,6 +111,12 @@ struct mg_forest {
     double omega = 0.8;                       // damping of the Jacobi smoother
     int *kerr = nullptr;                      // set by a device wait that gave up (staged smoother)
     double *AinvT = nullptr;                  // transpose of the coarsest inverses (adjoint cycles)
+    int32_t *gj_piv = nullptr, *gj_src = nullptr;  // device Gauss-Jordan: pivot rows, column permutation
+    double *gj_pinv = nullptr;                 // and the current pivot's reciprocal, per problem
+    cudaGraphExec_t coarse_graph = nullptr;    // recorded coarsest-level probe + inversion (assemble_coarse)
+    int coarse_runs = 0;                       // calls of assemble_coarse so far
+    bool coarse_nograph = false;               // its recording failed: launched directly
+    cudaStream_t cap_st = nullptr;             // private stream the recording is made on
     // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse
     int np = 1;
     int32_t *pstart = nullptr, *pblk = nullptr;  // level-0 blocks of problem p: pblk[pstart[p] .. pstart[p+1])

@@ -1596,12 +1596,32 @@ static __global__ void k_face_coefs(const double *__restrict__ k, const double *
         const int64_t gi = b * g.bs + r;
         const double kc = k[gi], s = ih2[b];
         const bool inY = Y >= 1 && Y <= n, inZ = Z >= 1 && Z <= n, inX = X >= 1 && X <= n;
-        const auto harm = [](double a, double c) { return 2.0 * a * c / (a + c); };
-        if (tx && X >= 1 && inY && inZ) tx[gi] = harm(k[gi - 1], kc) * s;
-        if (ty && Y >= 1 && inX && inZ) ty[gi] = harm(k[gi - P], kc) * s;
-        if (tz && Z >= 1 && inX && inY) tz[gi] = harm(k[gi - static_cast<int64_t>(P) * P], kc) * s;
+        const bool wx = tx && X >= 1 && inY && inZ, wy = ty && Y >= 1 && inX && inZ, wz = tz && Z >= 1 && inX && inY;
+        if (wx || wy || wz) {
+            // harmonic means 2 k_a k_c / (k_a + k_c) of the three lower faces with one FP64 division: the reciprocals
+            // of the three sums from the reciprocal of their product (batch inversion), unless the product leaves
+            // the normal range, then one division each
+            const double ka = wx ? k[gi - 1] : kc, kb = wy ? k[gi - P] : kc;
+            const double kd = wz ? k[gi - static_cast<int64_t>(P) * P] : kc;
+            const double sa = ka + kc, sb = kb + kc, sd = kd + kc, sab = sa * sb, prod = sab * sd;
+            double ra, rb, rd;
+            if (isfinite(prod) && prod > 2.2250738585072014e-308) {
+                const double ip = 1.0 / prod, iab = ip * sd;
+                ra = iab * sb;
+                rb = iab * sa;
+                rd = ip * sab;
+            } else {
+                ra = 1.0 / sa;
+                rb = 1.0 / sb;
+                rd = 1.0 / sd;
+            }
+            if (wx) tx[gi] = 2.0 * ka * kc * ra * s;
+            if (wy) ty[gi] = 2.0 * kb * kc * rb * s;
+            if (wz) tz[gi] = 2.0 * kd * kc * rd * s;
+        }
         const bool face_or_interior = (inX && inY) || (inX && inZ) || (inY && inZ);
-        if (kap && face_or_interior && kc > 0.0) kap[Lay<float>::at(g, b, X, Y, Z)] = static_cast<float>(1.0 / kc);
+        // 1/k for the FP32 cycles: FP32 accuracy suffices (binary32 conversion on exponent bits, FP32 division)
+        if (kap && face_or_interior && kc > 0.0) kap[Lay<float>::at(g, b, X, Y, Z)] = 1.0f / f64_to_f32_pow2(kc, 0);
     }
 }
 
@@ -1627,11 +1647,121 @@ static __global__ void k_diag(const double *__restrict__ tx, const double *__res
 }  // namespace octmg
 
 namespace octmg {
-// Unit entry m of every problem with more than m coarsest unknowns.
+// Unit entry m of every problem with more than m coarsest unknowns, and entry m - 1 cleared again (the interior is
+// otherwise zero; the exchange rewrites every ghost from it).
 static __global__ void k_set_units(double *__restrict__ u, const int64_t *__restrict__ cmap,
                                    const int64_t *__restrict__ ustart, int np, int m) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < np && ustart[p] + m < ustart[p + 1]) u[cmap[ustart[p] + m]] = 1.0;
+    if (p >= np) return;
+    if (m > 0 && ustart[p] + m - 1 < ustart[p + 1]) u[cmap[ustart[p] + m - 1]] = 0.0;
+    if (ustart[p] + m < ustart[p + 1]) u[cmap[ustart[p] + m]] = 1.0;
+}
+// Gauss-Jordan inversion of every problem's coarsest block (row-major N_p x N_p at moff[p]) on the device, in place
+// with partial pivoting, one column c per step (two launches), reading one buffer and writing the other:
+//   pivot: q = the row r >= c with the largest |a[r][c]| (the first on ties), v = 1 / a[q][c];
+//   step:  rows c and q exchanged, then  a'[c][j] = a[c][j] v (j != c), a'[c][c] = v,
+//          a'[r][j] = a[r][j] - a[r][c] a'[c][j] (r != c, j != c), a'[r][c] = -a[r][c] v.
+// After N steps the buffer holds (P A)^{-1} = A^{-1} P^T for the row exchanges P; A^{-1} follows by exchanging the
+// columns back in reverse order.  Problems with fewer unknowns than c copy their block through.
+// One warp per problem; a zero (or non-finite) pivot sets *bad.
+static __global__ void k_gj_pivot(const double *__restrict__ A, const int64_t *__restrict__ moff,
+                                  const int64_t *__restrict__ ustart, int np, int c, int32_t *__restrict__ piv,
+                                  double *__restrict__ pinv, int maxN, int *__restrict__ bad) {
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (p >= np) return;
+    const int N = static_cast<int>(ustart[p + 1] - ustart[p]);
+    if (c >= N) return;
+    const double *a = A + moff[p];
+    double best = -1.0;
+    int row = N;
+    for (int r = c + lane; r < N; r += 32) {
+        const double v = fabs(a[static_cast<int64_t>(r) * N + c]);
+        if (v > best) { best = v; row = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int orow = __shfl_xor_sync(0xffffffffu, row, o);
+        if (ob > best || (ob == best && orow < row)) { best = ob; row = orow; }
+    }
+    if (lane == 0) {
+        if (!(best > 0.0) || !isfinite(best) || row >= N) {
+            atomicOr(bad, 1);
+            row = c;
+        }
+        piv[static_cast<int64_t>(p) * maxN + c] = row;
+        pinv[p] = 1.0 / a[static_cast<int64_t>(row) * N + c];
+    }
+}
+static __global__ void k_gj_step(const double *__restrict__ A, double *__restrict__ B, const int64_t *__restrict__ moff,
+                                 const int64_t *__restrict__ ustart, int c, const int32_t *__restrict__ piv,
+                                 const double *__restrict__ pinv, int maxN) {
+    const int p = blockIdx.y;
+    const int N = static_cast<int>(ustart[p + 1] - ustart[p]);
+    const int64_t NN = static_cast<int64_t>(N) * N;
+    const double *a = A + moff[p];
+    double *b = B + moff[p];
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < NN;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (c >= N) {
+            b[e] = a[e];
+            continue;
+        }
+        const int r = static_cast<int>(e / N), j = static_cast<int>(e - static_cast<int64_t>(r) * N);
+        const int q = piv[static_cast<int64_t>(p) * maxN + c];
+        const double v = pinv[p];
+        const int sr = r == c ? q : (r == q ? c : r);  // row r of the exchanged matrix
+        const double *arow = a + static_cast<int64_t>(sr) * N, *prow = a + static_cast<int64_t>(q) * N;
+        double out;
+        if (r == c) {
+            out = j == c ? v : prow[j] * v;
+        } else {
+            const double fr = arow[c];
+            out = j == c ? -fr * v : fma(-fr, prow[j] * v, arow[j]);
+        }
+        b[e] = out;
+    }
+}
+// A^{-1} from the eliminated buffer R: the column exchanges undone (src = composed inverse permutation per problem,
+// src[k] the column of R that becomes column k), written to X; and its transpose to R afterwards (k_gj_transpose).
+static __global__ void k_gj_unpermute(const double *__restrict__ R, double *__restrict__ X,
+                                      const int64_t *__restrict__ moff, const int64_t *__restrict__ ustart,
+                                      const int32_t *__restrict__ src, int maxN) {
+    const int p = blockIdx.y;
+    const int N = static_cast<int>(ustart[p + 1] - ustart[p]);
+    const int64_t NN = static_cast<int64_t>(N) * N;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < NN;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(e / N), k = static_cast<int>(e - static_cast<int64_t>(r) * N);
+        X[moff[p] + e] = R[moff[p] + static_cast<int64_t>(r) * N + src[static_cast<int64_t>(p) * maxN + k]];
+    }
+}
+static __global__ void k_gj_transpose(const double *__restrict__ X, double *__restrict__ T,
+                                      const int64_t *__restrict__ moff, const int64_t *__restrict__ ustart) {
+    const int p = blockIdx.y;
+    const int N = static_cast<int>(ustart[p + 1] - ustart[p]);
+    const int64_t NN = static_cast<int64_t>(N) * N;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < NN;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(e / N), k = static_cast<int>(e - static_cast<int64_t>(r) * N);
+        T[moff[p] + static_cast<int64_t>(k) * N + r] = X[moff[p] + e];
+    }
+}
+// The inverse column permutation of every problem from its pivot rows (one thread per problem): exchanges undone in
+// reverse order, src[k] = the eliminated column that holds column k of A^{-1}.
+static __global__ void k_gj_perm(const int32_t *__restrict__ piv, const int64_t *__restrict__ ustart, int np,
+                                 int32_t *__restrict__ src, int maxN) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int N = static_cast<int>(ustart[p + 1] - ustart[p]);
+    int32_t *s = src + static_cast<int64_t>(p) * maxN;
+    const int32_t *pv = piv + static_cast<int64_t>(p) * maxN;
+    for (int k = 0; k < N; ++k) s[k] = k;
+    for (int c = N - 1; c >= 0; --c) {
+        const int q = pv[c], t = s[c];
+        s[c] = s[q];
+        s[q] = t;
+    }
 }
 // Column m of every problem's block: A_p[i, m] = (A e_m)[cmap[ustart[p] + i]].
 static __global__ void k_gather_columns(const double *__restrict__ r, const int64_t *__restrict__ cmap,

@@ -68,9 +68,6 @@ struct HostHierarchy {
 mg_status build_hierarchy(int32_t R, int32_t n, int32_t n_problems, const std::vector<Key> &leaves,
                           int32_t max_coarse, HostHierarchy &out, std::string &err);
 
-// Dense inverse by Gauss-Jordan elimination with partial pivoting (row-major, in place); false if singular.
-bool invert_dense(std::vector<double> &A, int N);
-
 void set_error(const std::string &msg);
 
 }  // namespace octmg

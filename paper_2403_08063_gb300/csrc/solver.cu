@@ -3,8 +3,6 @@
 #include <array>
 #include <map>
 #include <mutex>
-#include <atomic>
-#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -597,8 +595,38 @@ void apply64(mg_forest *F, DevLevel &d, const double *u, double *out) {
         k_apply64<0><<<grid_for(d.cells()), kThreads, 0, F->st>>>(u, d.c64(), d.ih2_64, d.g, out);
 }
 
-// Coarsest-level dense operators (FP64 kernels on unit vectors, all problems probed at once), inverted on the host
-// (one block per problem, in parallel threads), uploaded with their transposes.
+// The device part of assemble_coarse: the columns A e_m of every problem's coarsest operator (FP64 kernels on unit
+// vectors, all problems probed at once), then Gauss-Jordan on the device into Ainv and AinvT (transposes).
+void enqueue_coarse_inverse(mg_forest *F, DevLevel &d, int N, int maxN) {
+    double *r = F->coarse_r;
+    // the columns go to the buffer that makes the eliminated matrix end up in AinvT after maxN steps
+    double *Adev = maxN % 2 == 0 ? F->AinvT : F->Ainv;
+    cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st);
+    for (int m = 0; m < maxN; ++m) {
+        k_set_units<<<(F->np + 127) / 128, 128, 0, F->st>>>(d.u64, F->cmap, F->ustart, F->np, m);
+        exchange_any64(F, d, d.u64);
+        apply64(F, d, d.u64, r);
+        k_gather_columns<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, F->uprob, F->ustart, F->moff, N, Adev, m);
+    }
+    cudaMemsetAsync(F->flag, 0, sizeof(int), F->st);
+    const dim3 grid(static_cast<unsigned>(std::min<int64_t>(1024, (static_cast<int64_t>(maxN) * maxN + 255) / 256)),
+                    static_cast<unsigned>(F->np));
+    double *X = Adev, *Y = Adev == F->Ainv ? F->AinvT : F->Ainv;
+    for (int c = 0; c < maxN; ++c) {
+        k_gj_pivot<<<(F->np * 32 + 255) / 256, 256, 0, F->st>>>(X, F->moff, F->ustart, F->np, c, F->gj_piv,
+                                                                F->gj_pinv, maxN, F->flag);
+        k_gj_step<<<grid, 256, 0, F->st>>>(X, Y, F->moff, F->ustart, c, F->gj_piv, F->gj_pinv, maxN);
+        std::swap(X, Y);
+    }
+    k_gj_perm<<<(F->np + 127) / 128, 128, 0, F->st>>>(F->gj_piv, F->ustart, F->np, F->gj_src, maxN);
+    k_gj_unpermute<<<grid, 256, 0, F->st>>>(F->AinvT, F->Ainv, F->moff, F->ustart, F->gj_src, maxN);
+    k_gj_transpose<<<grid, 256, 0, F->st>>>(F->Ainv, F->AinvT, F->moff, F->ustart);
+    cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st);
+}
+
+// Coarsest-level dense operators and their inverses (and transposes), every problem's block at once.  The device
+// part is a few thousand small launches; outside a stream capture it is recorded as a CUDA graph at the second call
+// and replayed by later ones (the pointers it uses never change).
 mg_status assemble_coarse(mg_forest *F) {
     const int l = static_cast<int>(F->L.size()) - 1;
     DevLevel &d = F->L[l];
@@ -639,47 +667,63 @@ mg_status assemble_coarse(mg_forest *F) {
     if (!F->coarse_r) MG_TRY(dalloc(F, &F->coarse_r, d.pool_elems()));
     int maxN = 0;
     for (int p = 0; p < F->np; ++p) maxN = std::max<int>(maxN, static_cast<int>(F->ustart_h[p + 1] - F->ustart_h[p]));
-    double *r = F->coarse_r, *Adev = F->Ainv;
-    for (int m = 0; m < maxN; ++m) {
-        MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
-        k_set_units<<<(F->np + 127) / 128, 128, 0, F->st>>>(d.u64, F->cmap, F->ustart, F->np, m);
-        exchange_any64(F, d, d.u64);
-        apply64(F, d, d.u64, r);
-        k_gather_columns<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, F->uprob, F->ustart, F->moff, N, Adev, m);
+    if (!F->gj_piv) {
+        MG_TRY(dalloc(F, &F->gj_piv, static_cast<int64_t>(F->np) * maxN));
+        MG_TRY(dalloc(F, &F->gj_src, static_cast<int64_t>(F->np) * maxN));
+        MG_TRY(dalloc(F, &F->gj_pinv, F->np));
     }
-    MG_CUDA(cudaGetLastError());
-    std::vector<double> A(static_cast<size_t>(F->moff_h[F->np]));
-    MG_CUDA(cudaMemcpyAsync(A.data(), Adev, A.size() * sizeof(double), cudaMemcpyDeviceToHost, F->st));
-    MG_CUDA(cudaStreamSynchronize(F->st));
-    std::vector<double> At(A.size());
-    std::atomic<int> next(0), bad(-1);
-    auto work = [&]() {
-        for (int p = next++; p < F->np; p = next++) {
-            const int Np = static_cast<int>(F->ustart_h[p + 1] - F->ustart_h[p]);
-            std::vector<double> blk(A.begin() + F->moff_h[p], A.begin() + F->moff_h[p + 1]);
-            if (!invert_dense(blk, Np)) {
-                bad = p;
-                continue;
-            }
-            std::copy(blk.begin(), blk.end(), A.begin() + F->moff_h[p]);
-            for (int i = 0; i < Np; ++i)
-                for (int j = 0; j < Np; ++j)
-                    At[F->moff_h[p] + static_cast<int64_t>(j) * Np + i] = blk[static_cast<size_t>(i) * Np + j];
+    // the probe must see the homogeneous operator: no boundary data, no profiling events inside a recorded graph
+    double *const gb = F->gb;
+    const bool prof = F->prof;
+    F->gb = nullptr;
+    F->prof = false;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(F->st, &cap);
+    // recorded from the second call on (the first one loads every kernel the sequence uses, which a capture does not
+    // allow); a recording that fails is abandoned for good and the sequence launched directly
+    if (ce == cudaSuccess && cap == cudaStreamCaptureStatusNone && F->coarse_runs++ > 0 && !F->coarse_graph &&
+        !F->coarse_nograph) {
+        // recorded on a private stream (the forest's stream may be the legacy default stream, which cannot be
+        // captured); the graph is then launched on the forest's stream
+        cudaGraph_t graph = nullptr;
+        cudaError_t e1 = F->cap_st ? cudaSuccess : cudaStreamCreateWithFlags(&F->cap_st, cudaStreamNonBlocking);
+        if (e1 == cudaSuccess) e1 = cudaStreamBeginCapture(F->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e1 == cudaSuccess) {
+            cudaStream_t own = F->st;
+            F->st = F->cap_st;
+            enqueue_coarse_inverse(F, d, N, maxN);
+            F->st = own;
+            e1 = cudaStreamEndCapture(F->cap_st, &graph);
         }
-    };
-    const int nth = std::max(1, std::min<int>(F->np, static_cast<int>(std::thread::hardware_concurrency())));
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nth; ++t) pool.emplace_back(work);
-    work();
-    for (auto &t : pool) t.join();
-    if (bad >= 0) {
-        set_error("coarsest-level operator of problem " + std::to_string(bad.load()) + " is singular");
+        if (e1 == cudaSuccess && graph) e1 = cudaGraphInstantiate(&F->coarse_graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e1 != cudaSuccess || !F->coarse_graph) {
+            F->coarse_graph = nullptr;
+            F->coarse_nograph = true;
+            cudaGetLastError();
+        }
+    }
+    if (ce == cudaSuccess) {
+        if (F->coarse_graph && cap == cudaStreamCaptureStatusNone) {
+            ce = cudaGraphLaunch(F->coarse_graph, F->st);
+        } else {
+            enqueue_coarse_inverse(F, d, N, maxN);
+            ce = cudaGetLastError();
+        }
+    }
+    F->gb = gb;
+    F->prof = prof;
+    if (ce != cudaSuccess) {
+        set_error(std::string("coarsest-level inverse: ") + cudaGetErrorString(ce));
+        return MG_ERR_CUDA;
+    }
+    int hbad = 0;
+    MG_CUDA(cudaMemcpyAsync(&hbad, F->flag, sizeof(int), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (hbad) {
+        set_error("a coarsest-level operator is singular");
         return MG_ERR_INVALID_ARG;
     }
-    MG_CUDA(cudaMemcpyAsync(Adev, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
-    MG_CUDA(cudaMemcpyAsync(F->AinvT, At.data(), At.size() * sizeof(double), cudaMemcpyHostToDevice, F->st));
-    MG_CUDA(cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st));
-    MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
 }
 
@@ -1241,6 +1285,8 @@ void mg_forest_destroy(mg_forest *F) {
     if (F->pscale_h) cudaFreeHost(F->pscale_h);
     if (F->pinv_h) cudaFreeHost(F->pinv_h);
     if (F->pdone_h) cudaFreeHost(F->pdone_h);
+    if (F->coarse_graph) cudaGraphExecDestroy(F->coarse_graph);
+    if (F->cap_st) cudaStreamDestroy(F->cap_st);
     delete F;
 }
 
