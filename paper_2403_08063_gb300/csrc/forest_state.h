@@ -117,6 +117,8 @@ struct mg_forest {
     int coarse_runs = 0;                       // calls of assemble_coarse so far
     bool coarse_nograph = false;               // its recording failed: launched directly
     cudaStream_t cap_st = nullptr;             // private stream the recording is made on
+    int8_t *pcol = nullptr;                    // colour probe (interface-free coarsest level): colour per unknown
+    int32_t *pnbu = nullptr;                   // and the unknowns of its 7-point neighbourhood (-1: outside)
     // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse
     int np = 1;
     int32_t *pstart = nullptr, *pblk = nullptr;  // level-0 blocks of problem p: pblk[pstart[p] .. pstart[p+1])

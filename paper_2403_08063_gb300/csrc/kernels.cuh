@@ -1763,6 +1763,32 @@ static __global__ void k_gj_perm(const int32_t *__restrict__ piv, const int64_t 
         s[q] = t;
     }
 }
+// Colour probe of a coarsest level without refinement interfaces (its operator couples a cell only with its six face
+// neighbours, across block faces through same-level ghosts): u = 1 on every unknown of colour C (global cell
+// coordinates mod 3 per axis, 27 colours), 0 elsewhere.  Then row i of A u is A[i, m] for the one unknown m of colour
+// C among i and its six neighbours (nbu: their unknown indices, -1 outside the domain), or 0.
+static __global__ void k_set_colour(double *__restrict__ u, const int64_t *__restrict__ cmap,
+                                    const int8_t *__restrict__ col, int N, int C) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) u[cmap[i]] = col[i] == C ? 1.0 : 0.0;
+}
+static __global__ void k_gather_colour(const double *__restrict__ r, const int64_t *__restrict__ cmap,
+                                       const int32_t *__restrict__ uprob, const int64_t *__restrict__ ustart,
+                                       const int64_t *__restrict__ moff, const int8_t *__restrict__ col,
+                                       const int32_t *__restrict__ nbu, int N, double *__restrict__ A, int C) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = uprob[i];
+    const int64_t base = ustart[p], Np = ustart[p + 1] - base;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const int m = nbu[static_cast<int64_t>(i) * 7 + q];
+        if (m >= 0 && col[m] == C) {
+            A[moff[p] + (i - base) * Np + (m - base)] = r[cmap[i]];
+            return;
+        }
+    }
+}
 // Column m of every problem's block: A_p[i, m] = (A e_m)[cmap[ustart[p] + i]].
 static __global__ void k_gather_columns(const double *__restrict__ r, const int64_t *__restrict__ cmap,
                                         const int32_t *__restrict__ uprob, const int64_t *__restrict__ ustart,

@@ -602,11 +602,23 @@ void enqueue_coarse_inverse(mg_forest *F, DevLevel &d, int N, int maxN) {
     // the columns go to the buffer that makes the eliminated matrix end up in AinvT after maxN steps
     double *Adev = maxN % 2 == 0 ? F->AinvT : F->Ainv;
     cudaMemsetAsync(d.u64, 0, d.pool_elems() * sizeof(double), F->st);
-    for (int m = 0; m < maxN; ++m) {
-        k_set_units<<<(F->np + 127) / 128, 128, 0, F->st>>>(d.u64, F->cmap, F->ustart, F->np, m);
-        exchange_any64(F, d, d.u64);
-        apply64(F, d, d.u64, r);
-        k_gather_columns<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, F->uprob, F->ustart, F->moff, N, Adev, m);
+    if (F->pcol) {  // no refinement interface: 27 colour probes
+        cudaMemsetAsync(Adev, 0, F->moff_h[F->np] * sizeof(double), F->st);
+        for (int C = 0; C < 27; ++C) {
+            k_set_colour<<<(N + 255) / 256, 256, 0, F->st>>>(d.u64, F->cmap, F->pcol, N, C);
+            exchange_any64(F, d, d.u64);
+            apply64(F, d, d.u64, r);
+            k_gather_colour<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, F->uprob, F->ustart, F->moff, F->pcol,
+                                                                F->pnbu, N, Adev, C);
+        }
+    } else {  // one unit vector per column
+        for (int m = 0; m < maxN; ++m) {
+            k_set_units<<<(F->np + 127) / 128, 128, 0, F->st>>>(d.u64, F->cmap, F->ustart, F->np, m);
+            exchange_any64(F, d, d.u64);
+            apply64(F, d, d.u64, r);
+            k_gather_columns<<<(N + 255) / 256, 256, 0, F->st>>>(r, F->cmap, F->uprob, F->ustart, F->moff, N, Adev,
+                                                                 m);
+        }
     }
     cudaMemsetAsync(F->flag, 0, sizeof(int), F->st);
     const dim3 grid(static_cast<unsigned>(std::min<int64_t>(1024, (static_cast<int64_t>(maxN) * maxN + 255) / 256)),
@@ -663,6 +675,56 @@ mg_status assemble_coarse(mg_forest *F) {
         MG_TRY(upload(F, &F->moff, F->moff_h));
         MG_TRY(dalloc(F, &F->Ainv, F->moff_h[F->np]));
         MG_TRY(dalloc(F, &F->AinvT, F->moff_h[F->np]));
+        if (d.nifaces == 0 && d.nsegs == 0) {
+            // colours and the 7-point neighbourhoods of the unknowns for the colour probe; every block of a problem
+            // is then at one refinement level (face neighbours share it), so key * n + local is a global coordinate
+            std::vector<int64_t> first(d.g.nb, -1);  // unknown index of each block's first cell
+            for (int p = 0; p < F->np; ++p) {
+                int64_t at = F->ustart_h[p];
+                for (int b : blocks[p]) {
+                    first[b] = at;
+                    at += cells;
+                }
+            }
+            std::vector<int32_t> nb6(static_cast<size_t>(d.g.nb) * 6, -2);
+            for (const FaceItem &fi : hl.faces)
+                nb6[static_cast<size_t>(fi.blk) * 6 + 2 * fi.axis + fi.side] =
+                    fi.kind == FK_SAME ? fi.nbr : (fi.kind == FK_BND ? -1 : -2);
+            std::vector<int8_t> col(N);
+            std::vector<int32_t> nbu(static_cast<size_t>(N) * 7, -1);
+            bool ok = true;
+            for (int b = 0; b < d.g.nb && ok; ++b) {
+                const Key &kb = hl.keys[b];
+                for (int z = 0; z < n; ++z)
+                    for (int y = 0; y < n; ++y)
+                        for (int x = 0; x < n; ++x) {
+                            const int64_t i = first[b] + (static_cast<int64_t>(z) * n + y) * n + x;
+                            const int64_t gx = static_cast<int64_t>(kb.i) * n + x, gy = static_cast<int64_t>(kb.j) * n + y,
+                                          gz = static_cast<int64_t>(kb.k) * n + z;
+                            col[i] = static_cast<int8_t>(gx % 3 + 3 * (gy % 3) + 9 * (gz % 3));
+                            nbu[i * 7] = static_cast<int32_t>(i);
+                            const int c[3] = {x, y, z};
+                            for (int axis = 0; axis < 3; ++axis)
+                                for (int side = 0; side < 2; ++side) {
+                                    int cc[3] = {c[0], c[1], c[2]};
+                                    cc[axis] += side ? 1 : -1;
+                                    int bb = b;
+                                    if (cc[axis] < 0 || cc[axis] >= n) {
+                                        bb = nb6[static_cast<size_t>(b) * 6 + 2 * axis + side];
+                                        if (bb == -2) ok = false;
+                                        if (bb < 0) continue;
+                                        cc[axis] = side ? 0 : n - 1;
+                                    }
+                                    nbu[i * 7 + 1 + 2 * axis + side] =
+                                        static_cast<int32_t>(first[bb] + (static_cast<int64_t>(cc[2]) * n + cc[1]) * n + cc[0]);
+                                }
+                        }
+            }
+            if (ok && N < (int64_t(1) << 31)) {
+                MG_TRY(upload(F, &F->pcol, col));
+                MG_TRY(upload(F, &F->pnbu, nbu));
+            }
+        }
     }
     if (!F->coarse_r) MG_TRY(dalloc(F, &F->coarse_r, d.pool_elems()));
     int maxN = 0;
