@@ -882,7 +882,7 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
                     const float fv = fw[ro - H + C];
                     const float zp = C ? pn1 : pn0;
                     float val;
-                    float qn0 = 0.f, qn1 = 0.f;
+                    [[maybe_unused]] float qn0 = 0.f, qn1 = 0.f;  // kappa pair of plane z + 1 (MODE 2)
                     if constexpr (MODE == 2) {
                         qn0 = kn[ro];
                         qn1 = kn[ro + 1];
