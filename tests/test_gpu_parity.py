@@ -115,6 +115,54 @@ def test_small_uniform_ten_cycles_manufactured():
     assert 2.5e-4 < err < 3.2e-4  # discretisation error of the 32^3 grid
 
 
+@pytest.mark.parametrize("coeff,variant", [(False, "C"), (True, "C"), (True, "P")])
+def test_coarsest_level_with_interfaces_matches_oracle(coeff, variant):
+    """A coarsest level that keeps refinement interfaces: one root, seven level-1 blocks and the eight level-2 blocks
+    of the eighth octant (n = 8), with max_coarse = 960 so that the 15 blocks of 4^3 are the coarsest level.  Its
+    dense operator is then probed one unknown at a time through the C2F / F2C exchange (a coarsest level without
+    interfaces is probed by colour classes instead); 4 FP64 V(2,2) cycles match the oracle's to 1e-10."""
+    keys = [(1, i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1) if (i, j, k) != (0, 0, 0)]
+    keys += [(2, i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    R, n = 1, 8
+    k = syn.lognormal_k_rff(R, n, keys, seed=41) if coeff else None
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=42)
+    F = _forest(R, n, keys, coeff=coeff, interface_flux=variant == "C", max_coarse=960)
+    assert F.levels() == [(15, 8), (15, 4)]
+    F.set_rhs(f.to(DEV), k.to(DEV) if coeff else None)
+    u = torch.zeros_like(f, device=DEV)
+    F.vcycle(u, 4)
+    ref = OracleMG(R, n, keys, k_user=None if k is None else k.numpy(), variant=variant, max_coarse=960)
+    u_ref, _ = ref.solve(f.numpy(), cycles=4)
+    got = u.cpu().numpy()
+    assert np.linalg.norm(got - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+
+
+@pytest.mark.parametrize("forest", ["sphere_2x8", "mixed_coarsest"])
+def test_repeated_set_rhs_gives_the_same_cycles(forest):
+    """mg_set_rhs records the coarsest-level probe and inversion as a CUDA graph at its second call and replays it
+    afterwards: the V-cycles after the first and the third call with the same k give identical bits (colour probe on
+    sphere_2x8's uniform coarsest level, column probe on a coarsest level with interfaces)."""
+    if forest == "mixed_coarsest":
+        keys = [(1, i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1) if (i, j, k) != (0, 0, 0)]
+        keys += [(2, i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+        R, n, mc = 1, 8, 960
+    else:
+        R, n, keys = syn.workload_forest(forest)
+        mc = 512
+    k1 = syn.lognormal_k_rff(R, n, keys, seed=51).to(DEV)
+    k2 = syn.lognormal_k_rff(R, n, keys, seed=52).to(DEV)
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=53).to(DEV)
+    F = _forest(R, n, keys, coeff=True, max_coarse=mc)
+    runs = []
+    for kk in (k1, k2, k1):
+        F.set_rhs(f, kk)
+        u = torch.zeros_like(f)
+        F.vcycle(u, 2)
+        runs.append(u.clone())
+    assert torch.isfinite(runs[0]).all() and not torch.equal(runs[0], runs[1])
+    assert torch.equal(runs[0], runs[2])
+
+
 @pytest.mark.parametrize("coeff", [False, True])
 def test_refined_solve_to_1e10_property(coeff):
     """Refined forest (56 + 64 blocks of 16^3): the GPU solve's residual, recomputed by the oracle, is <= 1e-10."""
