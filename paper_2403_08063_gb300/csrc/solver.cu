@@ -101,7 +101,10 @@ void exchange(mg_forest *F, DevLevel &d, T *u, bool interface_only = false, bool
     const T *gb = nullptr;  // inhomogeneous Dirichlet data: FP64 finest level only
     if constexpr (sizeof(T) == 8)
         if (&d == &F->L[0]) gb = F->gb;
-    if (nitems)
+    if (nitems && interface_only)  // C2F faces only: one thread per coarse source cell
+        k_exchange_c2f<T><<<grid_for(static_cast<int64_t>(nitems) * (d.g.n / 2) * (d.g.n / 2)), kThreads, 0, F->st>>>(
+            u, items, nitems, d.g, skip_of(F, d), F->cfg.c2f_variant);
+    else if (nitems)
         k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(nitems) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
             u, items, nitems, d.g, skip_of(F, d), F->cfg.c2f_variant, gb);
     if (d.nsegs) {
