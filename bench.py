@@ -463,7 +463,9 @@ def run_batch(args):
     value = cells * sum(cyc_run) / t / 1e9 * ws
     # kernel families from one profiled solve (graphs off while profiling)
     B.profile(True)
+    torch.cuda.nvtx.range_push("mg_batch_profiled")
     step()
+    torch.cuda.nvtx.range_pop()
     prof = B.profile_read()
     B.profile(False)
     if rank == 0:
