@@ -179,6 +179,14 @@ mg_status mg_set_smoother_shape(mg_forest *forest, int32_t level, const int32_t 
 mg_status mg_get_tail(const mg_forest *forest, int32_t *level);
 mg_status mg_set_tail(mg_forest *forest, int32_t level);
 
+/* Self-test of the bounded waits that keep a kernel from hanging when an expected event never comes: launches one
+ * CTA on the forest's stream that waits for something nothing provides, which = 0 an mbarrier phase (the wait of the
+ * staged smoother's shared-memory copies, bounded by 2^14 probes), which = 1 a grid barrier expecting one CTA more
+ * than the grid has (the persistent tail's, bounded by 2^30 SM clock cycles), and reads the error word.  Expected
+ * result: MG_ERR_TIMEOUT after at most about a second, with the context still usable; MG_ERR_INVALID_ARG for
+ * another `which`.  Synchronises the stream. */
+mg_status mg_selftest_waits(mg_forest *forest, int32_t which);
+
 /* ---------------------------------------------------------------------------------------------------------------
  * Batches: many independent problems with different block sizes (uneven octree forests), solved together.
  * Every problem is its own forest over [0,1]^3 with cfg->roots root blocks per axis; its leaves are the rows of

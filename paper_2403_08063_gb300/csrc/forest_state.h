@@ -204,6 +204,7 @@ mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
 mg_status check_ready(mg_forest *F);
 mg_status check_kernel_waits(mg_forest *F);
 mg_status launch_tail32(mg_forest *F);  // tail.cu
+mg_status launch_selftest_wait(mg_forest *F, int which);  // tail.cu (F->tail_bar allocated)
 void reset_done(mg_forest *F);
 mg_status enqueue_done(mg_forest *F);
 mg_status reference_norms(mg_forest *F);

@@ -220,7 +220,8 @@ mg_status check_kernel_waits(mg_forest *F) {
     MG_CUDA(cudaStreamSynchronize(F->st));
     if (h) {
         MG_CUDA(cudaMemsetAsync(F->kerr, 0, sizeof(int), F->st));
-        set_error("a staged smoother gave up waiting for its shared-memory copies");
+        set_error(h & 1 ? "a staged smoother gave up waiting for its shared-memory copies"
+                        : "the persistent tail kernel gave up waiting at a grid barrier");
         return MG_ERR_TIMEOUT;
     }
     return MG_OK;
@@ -1489,6 +1490,16 @@ mg_status mg_set_boundary(mg_forest *F, const double *g_dev) {
     if (F->rhs_set) MG_TRY(reference_norms(F));
     MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
+}
+
+mg_status mg_selftest_waits(mg_forest *F, int32_t which) {
+    if (!F || (which != 0 && which != 1)) {
+        set_error("mg_selftest_waits: null forest or which not in {0, 1}");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (!F->tail_bar) MG_TRY(dalloc(F, &F->tail_bar, 2));
+    MG_TRY(launch_selftest_wait(F, which));
+    return check_kernel_waits(F);
 }
 
 mg_status mg_get_tail(const mg_forest *F, int32_t *level) {

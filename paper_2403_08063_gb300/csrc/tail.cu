@@ -16,7 +16,7 @@ constexpr int kTailThreads = 256;
 // the others poll the generation (no sleep: a phase of the tail lasts microseconds).  The wait is bounded by the SM
 // clock (2^30 cycles, about half a second): it then sets *err and returns false (the kernel stops; the host
 // reports MG_ERR_TIMEOUT).
-__device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err) {
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err, unsigned expected) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -24,7 +24,7 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err) {
         volatile unsigned *vg = gen;
         const unsigned g0 = *vg;
         __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(count, 1u) == expected - 1) {
             atomicExch(count, 0u);
             __threadfence();
             atomicAdd(gen, 1u);
@@ -156,7 +156,7 @@ static __global__ void __launch_bounds__(kTailThreads) k_tail32(TailArgs a) {
                 break;
             }
         }
-        if (!grid_barrier(a.bar, a.bar + 1, a.err)) return;
+        if (!grid_barrier(a.bar, a.bar + 1, a.err, gridDim.x)) return;
     }
 }
 
@@ -193,6 +193,31 @@ mg_status launch_tail32(mg_forest *F) {
     cfg.numAttrs = 1;
     void *args[] = {&a};
     MG_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    return MG_OK;
+}
+
+// Self-test of the bounded waits (mg_selftest_waits): one CTA waits for something that never happens and must give up
+// with its error bit set.  which = 0: an mbarrier phase that no thread or copy completes (the wait of the staged
+// smoother's copies, bit 1); which = 1: a grid barrier that expects one more CTA than the grid has (the persistent
+// tail's, bit 2).
+static __global__ void k_selftest_wait(int which, unsigned *bar, int *err) {
+    __shared__ uint64_t mb;
+    if (which == 0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&mb, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && !mbar_wait(&mb, 0)) atomicOr(err, 1);
+    } else {
+        grid_barrier(bar, bar + 1, err, gridDim.x + 1);
+    }
+}
+
+mg_status launch_selftest_wait(mg_forest *F, int which) {
+    MG_CUDA(cudaMemsetAsync(F->tail_bar, 0, 2 * sizeof(unsigned), F->st));
+    k_selftest_wait<<<1, 32, 0, F->st>>>(which, F->tail_bar, F->kerr);
+    MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
 
