@@ -112,6 +112,16 @@ mg_status mg_vcycle(mg_forest *forest, double *u_dev, int32_t ncycles, double *r
 mg_status mg_solve(mg_forest *forest, double *u_dev, double rtol, int32_t max_cycles, int32_t *cycles_out,
                    double *rel_res_out);
 
+/* mg_set_rhs + mg_solve from host buffers (user layout, FP64, n_leaves * n^3 each): f_host, k_host (NULL when
+ * coeff == 0), u0_host the initial guess (NULL: zero), u_host receives the solution (may be the same buffer as
+ * u0_host).  The library copies into device staging buffers of its own (allocated at the first call, kept by the
+ * forest): k first on the forest's stream, where its set-up (coefficient pyramid, coarsest inverse) starts while f
+ * and the initial guess cross on a second stream; the solve then runs as mg_solve and u is copied back.  Page-locked
+ * host buffers let the copies run at full bandwidth and overlap; pageable ones work too.  Returns when u_host holds
+ * the result (or on error).  Errors as mg_set_rhs and mg_solve; MG_ERR_STATE for a forest of a batch. */
+mg_status mg_solve_host(mg_forest *forest, const double *f_host, const double *k_host, const double *u0_host,
+                        double *u_host, double rtol, int32_t max_cycles, int32_t *cycles_out, double *rel_res_out);
+
 /* Adjoint of the converged solve for L = 1/2 sum_i (u_i - u_t,i)^2: given u_dev (the forward solution) and
  * dLdu_dev = u - u_t, solve A^T lambda = dL/du by defect correction with the transposed V-cycle, write lambda
  * (= dL/df) to lambda_dev and, when dLdk_dev is not NULL and coeff == 1, dL/dk = -lambda^T (dA/dk) u.

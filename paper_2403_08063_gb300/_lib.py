@@ -62,6 +62,7 @@ SIGNATURES = {
     "mg_set_boundary": (I32, [P, P]),
     "mg_vcycle": (I32, [P, P, I32, DP]),
     "mg_solve": (I32, [P, P, _c.c_double, I32, IP, DP]),
+    "mg_solve_host": (I32, [P, P, P, P, P, _c.c_double, I32, IP, DP]),
     "mg_adjoint_solve": (I32, [P, P, P, P, P, _c.c_double, I32]),
     "mg_apply": (I32, [P, P, P]),
     "mg_apply_transpose": (I32, [P, P, P]),

@@ -15,6 +15,14 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _host_f64(t, numel, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != F64:
+        raise TypeError(f"{name} must be a CPU float64 tensor")
+    if t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with {numel} elements")
+    return t
+
+
 def _dev_f64(t, numel, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != F64:
         raise TypeError(f"{name} must be a CUDA float64 tensor")
@@ -127,6 +135,29 @@ class Forest:
         if self.n_problems == 1:
             return cyc[0], rel[0]
         return list(cyc), list(rel)
+
+    def solve_host(self, f, k=None, u=None, u0=None, rtol=1e-10, max_cycles=100, raise_on_failure=True):
+        """mg_set_rhs + mg_solve from CPU float64 tensors (page-locked ones give the fastest copies): f, k (coeff),
+        u0 the initial guess (None: zero); the solution is written into u (allocated when None, may be u0).
+
+        Returns (u, cycles, rel), with lists of cycles and rel for several problems."""
+        _host_f64(f, self.numel, "f")
+        if k is not None:
+            _host_f64(k, self.numel, "k")
+        if u0 is not None:
+            _host_f64(u0, self.numel, "u0")
+        if u is None:
+            u = torch.empty_like(f)
+        _host_f64(u, self.numel, "u")
+        cyc = (ctypes.c_int32 * self.n_problems)()
+        rel = (ctypes.c_double * self.n_problems)()
+        st = self.lib.mg_solve_host(self.h, _ptr(f), _ptr(k), _ptr(u0), _ptr(u), float(rtol), int(max_cycles), cyc,
+                                    rel)
+        if st != 0 and (raise_on_failure or st != 6):
+            _lib.check(st)
+        if self.n_problems == 1:
+            return u, cyc[0], rel[0]
+        return u, list(cyc), list(rel)
 
     def apply(self, u):
         _dev_f64(u, self.numel, "u")

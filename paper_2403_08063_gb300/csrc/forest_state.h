@@ -116,7 +116,9 @@ struct mg_forest {
     cudaGraphExec_t coarse_graph = nullptr;    // recorded coarsest-level probe + inversion (assemble_coarse)
     int coarse_runs = 0;                       // calls of assemble_coarse so far
     bool coarse_nograph = false;               // its recording failed: launched directly
-    cudaStream_t cap_st = nullptr;             // private stream the recording is made on
+    cudaStream_t cap_st = nullptr;             // private stream: graph recording, host-input copies
+    double *hst_f = nullptr, *hst_k = nullptr, *hst_u = nullptr;  // mg_solve_host staging buffers (user layout)
+    cudaEvent_t hst_ev = nullptr;              // orders the staging copies against the forest's stream
     int8_t *pcol = nullptr;                    // colour probe (interface-free coarsest level): colour per unknown
     int32_t *pnbu = nullptr;                   // and the unknowns of its 7-point neighbourhood (-1: outside)
     // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse

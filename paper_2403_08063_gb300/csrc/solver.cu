@@ -1238,7 +1238,7 @@ __global__ void k_check_inputs(const double *__restrict__ f, const double *__res
                                int *__restrict__ bad) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        if (!isfinite(f[i])) atomicOr(bad, 1);
+        if (f && !isfinite(f[i])) atomicOr(bad, 1);
         if (k && !(isfinite(k[i]) && k[i] > 0.0)) atomicOr(bad, 2);
     }
 }
@@ -1276,6 +1276,41 @@ __global__ void k_twice(double *__restrict__ out, const double *__restrict__ in,
         out[i] = 2.0 * in[i];
 }
 
+// Finite f and finite positive k (either may be null), read back on the host.
+mg_status check_inputs(mg_forest *F, const double *f_dev, const double *k_dev) {
+    if (F->batch_member) return MG_OK;  // the batch checks its whole fields once
+    DevLevel &d = F->L[0];
+    MG_CUDA(cudaMemsetAsync(F->flag, 0, sizeof(int), F->st));
+    k_check_inputs<<<grid_for(d.cells()), kThreads, 0, F->st>>>(f_dev, k_dev, d.cells(), F->flag);
+    int hbad = 0;
+    MG_CUDA(cudaMemcpyAsync(&hbad, F->flag, sizeof(int), cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
+    if (hbad) {
+        set_error(hbad & 2 ? "k must be finite and > 0" : "f has a non-finite entry");
+        return MG_ERR_NONFINITE;
+    }
+    return MG_OK;
+}
+
+// The k part of mg_set_rhs: coefficient pyramid and coarsest inverse (inputs already checked).
+mg_status set_rhs_k(mg_forest *F, const double *k_dev) {
+    MG_TRY(pack_user<double>(F, F->L[0], F->L[0].k64, k_dev));
+    MG_TRY(build_coefficients(F));
+    return assemble_coarse(F);
+}
+
+// The f part: the right-hand side, its reference norms and (first call) the launch-shape and tail tuning.
+mg_status set_rhs_f(mg_forest *F, const double *f_dev) {
+    MG_TRY(pack_user<double>(F, F->L[0], F->L[0].f64, f_dev));
+    MG_TRY(reference_norms(F));
+    if (F->cfg.precision == 1) {
+        MG_TRY(tune_smooth32(F));
+        MG_TRY(tune_tail(F));
+    }
+    F->rhs_set = true;
+    return MG_OK;
+}
+
 mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
     if (!F || !f_dev) {
         set_error("null forest or f");
@@ -1285,30 +1320,55 @@ mg_status set_rhs(mg_forest *F, const double *f_dev, const double *k_dev) {
         set_error("coeff == 1 needs k");
         return MG_ERR_INVALID_ARG;
     }
-    DevLevel &d = F->L[0];
-    int *bad = F->flag;
-    MG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), F->st));
-    if (!F->batch_member)
-    k_check_inputs<<<grid_for(d.cells()), kThreads, 0, F->st>>>(f_dev, F->cfg.coeff ? k_dev : nullptr, d.cells(), bad);
-    int hbad = 0;
-    MG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, F->st));
-    MG_CUDA(cudaStreamSynchronize(F->st));
-    if (hbad) {
-        set_error(hbad & 2 ? "k must be finite and > 0" : "f has a non-finite entry");
-        return MG_ERR_NONFINITE;
+    MG_TRY(check_inputs(F, f_dev, F->cfg.coeff ? k_dev : nullptr));
+    if (F->cfg.coeff) MG_TRY(set_rhs_k(F, k_dev));
+    return set_rhs_f(F, f_dev);
+}
+
+// mg_solve_host: inputs from host buffers through device staging buffers.  k goes first on the forest's stream and
+// its set-up (coefficient pyramid, coarsest inverse) runs while f and the initial guess cross on the private copy
+// stream; the forest's stream waits for them before the f part.  u comes back on the forest's stream.
+mg_status solve_host(mg_forest *F, const double *f_host, const double *k_host, const double *u0_host,
+                     double *u_host, double rtol, int32_t max_cycles, int32_t *cycles_out, double *rel_out) {
+    if (!F || !f_host || !u_host || (F->cfg.coeff && !k_host) || max_cycles < 0 || !(rtol >= 0.0)) {
+        set_error("mg_solve_host: null forest, f or u, k missing with coeff == 1, or bad rtol / max_cycles");
+        return MG_ERR_INVALID_ARG;
     }
-    MG_TRY(pack_user<double>(F, d, d.f64, f_dev));
+    if (F->batch_member) {
+        set_error("mg_solve_host: not for a batch member forest");
+        return MG_ERR_STATE;
+    }
+    const int64_t cells = F->L[0].cells();
+    const size_t bytes = static_cast<size_t>(cells) * sizeof(double);
+    if (!F->hst_f) {
+        MG_TRY(dalloc(F, &F->hst_f, cells, false));
+        MG_TRY(dalloc(F, &F->hst_u, cells, false));
+        if (F->cfg.coeff) MG_TRY(dalloc(F, &F->hst_k, cells, false));
+    }
+    if (!F->cap_st) MG_CUDA(cudaStreamCreateWithFlags(&F->cap_st, cudaStreamNonBlocking));
+    if (!F->hst_ev) MG_CUDA(cudaEventCreateWithFlags(&F->hst_ev, cudaEventDisableTiming));
+    // the copy stream must not overtake work still queued on the forest's stream that uses the staging buffers
+    MG_CUDA(cudaEventRecord(F->hst_ev, F->st));
+    MG_CUDA(cudaStreamWaitEvent(F->cap_st, F->hst_ev, 0));
+    if (F->cfg.coeff) MG_CUDA(cudaMemcpyAsync(F->hst_k, k_host, bytes, cudaMemcpyHostToDevice, F->st));
+    MG_CUDA(cudaMemcpyAsync(F->hst_f, f_host, bytes, cudaMemcpyHostToDevice, F->cap_st));
+    if (u0_host) MG_CUDA(cudaMemcpyAsync(F->hst_u, u0_host, bytes, cudaMemcpyHostToDevice, F->cap_st));
+    else MG_CUDA(cudaMemsetAsync(F->hst_u, 0, bytes, F->cap_st));
+    MG_CUDA(cudaEventRecord(F->hst_ev, F->cap_st));
     if (F->cfg.coeff) {
-        MG_TRY(pack_user<double>(F, d, d.k64, k_dev));
-        MG_TRY(build_coefficients(F));
-        MG_TRY(assemble_coarse(F));
+        mg_status st = check_inputs(F, nullptr, F->hst_k);
+        if (st == MG_OK) st = set_rhs_k(F, F->hst_k);
+        if (st != MG_OK) {
+            cudaStreamSynchronize(F->cap_st);  // the staging copies still read the caller's buffers
+            return st;
+        }
     }
-    MG_TRY(reference_norms(F));
-    if (F->cfg.precision == 1) {
-        MG_TRY(tune_smooth32(F));
-        MG_TRY(tune_tail(F));
-    }
-    F->rhs_set = true;
+    MG_CUDA(cudaStreamWaitEvent(F->st, F->hst_ev, 0));
+    MG_TRY(check_inputs(F, F->hst_f, nullptr));
+    MG_TRY(set_rhs_f(F, F->hst_f));
+    MG_TRY(run_cycles(F, F->hst_u, rtol, max_cycles, cycles_out, rel_out));
+    MG_CUDA(cudaMemcpyAsync(u_host, F->hst_u, bytes, cudaMemcpyDeviceToHost, F->st));
+    MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
 }
 
@@ -1353,6 +1413,7 @@ void mg_forest_destroy(mg_forest *F) {
     if (F->pdone_h) cudaFreeHost(F->pdone_h);
     if (F->coarse_graph) cudaGraphExecDestroy(F->coarse_graph);
     if (F->cap_st) cudaStreamDestroy(F->cap_st);
+    if (F->hst_ev) cudaEventDestroy(F->hst_ev);
     delete F;
 }
 
@@ -1401,6 +1462,11 @@ mg_status mg_solve(mg_forest *F, double *u_dev, double rtol, int32_t max_cycles,
         return MG_ERR_INVALID_ARG;
     }
     return run_cycles(F, u_dev, rtol, max_cycles, cycles_out, rel_res_out);
+}
+
+mg_status mg_solve_host(mg_forest *F, const double *f_host, const double *k_host, const double *u0_host,
+                        double *u_host, double rtol, int32_t max_cycles, int32_t *cycles_out, double *rel_res_out) {
+    return solve_host(F, f_host, k_host, u0_host, u_host, rtol, max_cycles, cycles_out, rel_res_out);
 }
 
 mg_status mg_apply(mg_forest *F, const double *u_dev, double *Au_dev) { return apply_op(F, u_dev, Au_dev); }
