@@ -76,12 +76,12 @@ __device__ inline void face_xyz(int axis, int side, int depth, int i1, int i2, i
 // Storage of a padded cell (X, Y, Z) of block b.
 //   FP64 pools: natural order, block b at b * bs, x fastest.
 //   FP32 pools: colour-split ("red-black ordered"): a block is two halves holding the cells with X + Y + Z even
-//   (half 0) and odd (half 1); inside a half, row (Y, Z) holds the (n+2)/2 cells of that parity at X / 2, padded
-//   to half_row(P) entries.  A colour half-sweep then reads the other colour's half and writes its own with unit
-//   stride.
-// Row length of one half in the FP32 split layout: the (n+2)/2 cells of a parity, padded to a multiple of 4 floats
-// so that every row, plane and half starts on a 16-byte boundary (bulk-copy granularity).
-__host__ __device__ constexpr int half_row(int P) { return ((P >> 1) + 3) & ~3; }
+//   (half 0) and odd (half 1); inside a half, row (Y, Z) holds the (n+2)/2 cells of that parity at X / 2, with no
+//   padding between rows.  A colour half-sweep then reads the other colour's half and writes its own with unit
+//   stride.  Every half and block starts on a 16-byte boundary (P^2 is a multiple of 4); rows and planes in general
+//   do not, so bulk copies of row runs are widened to 16-byte bounds (k_smooth32t).
+// Row length of one half in the FP32 split layout: the (n+2)/2 cells of a parity.
+__host__ __device__ constexpr int half_row(int P) { return P >> 1; }
 
 template <typename T> struct Lay;
 template <> struct Lay<double> {
@@ -792,7 +792,9 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
     constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int RO = 2 + D, RW = 1 + D, G = 1 + D;
-    const int so = (TY + 2) * H, sw = TY * H;  // floats per plane segment
+    // a plane segment is a run of (TY + 2) H (other half) or TY H (own half) floats; it is copied from the 16-byte
+    // boundary at or below its start, so it lands e = (start & 3) floats into its slot, and slots have room for that
+    const int lo = (TY + 2) * H, lw = TY * H, so = (lo + 6) & ~3, sw = (lw + 6) & ~3;
     // other-half slot i: u at ou + i NA so, kappa after it; own-half slot i: f at wf + i NA sw, kappa after it
     float *ou = reinterpret_cast<float *>(smem_raw);
     float *wf = ou + NA * RO * so;
@@ -818,25 +820,34 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
     const float *gou = u + base + (s ^ 1) * HALF, *gok = kap + base + (s ^ 1) * HALF;
     const float *gwf = f + base + s * HALF, *gwk = kap + base + s * HALF;
 
+    // start (floats, within a half) of the other-half segment of padded plane Zp and of the own-half one
+    const auto off_o = [&](int Zp) { return (Zp * P + y0) * H; };
+    const auto off_w = [&](int Zp) { return (Zp * P + y0 + 1) * H; };
+    const auto bytes_of = [](int off, int len) { return static_cast<uint32_t>(((off & 3) + len + 3) & ~3) * 4; };
+    const auto copy = [](float *dst, const float *half, int off, uint32_t bytes, uint64_t *b) {
+        bulk_load(dst, half + (off & ~3), bytes, b);
+    };
     const auto issue_first = [&]() {  // other-half planes z0 - 1 and z0 (padded Z z0, z0 + 1) into slots 0, 1
-        mbar_arm(&bar[0], 2 * NA * so * 4);
+        const uint32_t b0 = bytes_of(off_o(z0), lo), b1 = bytes_of(off_o(z0 + 1), lo);
+        mbar_arm(&bar[0], NA * (b0 + b1));
         for (int io = 0; io < 2; ++io) {
-            const int64_t off = (static_cast<int64_t>(z0 + io) * P + y0) * H;
-            bulk_load(ou + io * NA * so, gou + off, so * 4, &bar[0]);
-            if constexpr (MODE == 2) bulk_load(ou + io * NA * so + so, gok + off, so * 4, &bar[0]);
+            const int off = off_o(z0 + io);
+            const uint32_t bb = io ? b1 : b0;
+            copy(ou + io * NA * so, gou, off, bb, &bar[0]);
+            if constexpr (MODE == 2) copy(ou + io * NA * so + so, gok, off, bb, &bar[0]);
         }
     };
     const auto issue_group = [&](int g) {  // other plane z0 + g + 1 (padded z0 + g + 2), own plane z0 + g
         uint64_t *bg = &bar[1 + g % G];
-        mbar_arm(bg, NA * (so + sw) * 4);
-        const int64_t oo = (static_cast<int64_t>(z0 + g + 2) * P + y0) * H;
+        const int oo = off_o(z0 + g + 2), ow = off_w(z0 + 1 + g);
+        const uint32_t bo = bytes_of(oo, lo), bw = bytes_of(ow, lw);
+        mbar_arm(bg, NA * (bo + bw));
         float *d0 = ou + ((g + 2) % RO) * NA * so;
-        bulk_load(d0, gou + oo, so * 4, bg);
-        if constexpr (MODE == 2) bulk_load(d0 + so, gok + oo, so * 4, bg);
-        const int64_t ow = (static_cast<int64_t>(z0 + 1 + g) * P + y0 + 1) * H;
+        copy(d0, gou, oo, bo, bg);
+        if constexpr (MODE == 2) copy(d0 + so, gok, oo, bo, bg);
         float *d1 = wf + (g % RW) * NA * sw;
-        bulk_load(d1, gwf + ow, sw * 4, bg);
-        if constexpr (MODE == 2) bulk_load(d1 + sw, gwk + ow, sw * 4, bg);
+        copy(d1, gwf, ow, bw, bg);
+        if constexpr (MODE == 2) copy(d1 + sw, gwk, ow, bw, bg);
     };
     const int nthc = blockDim.x - 32, ncw = nthc >> 5;  // consumer threads and warps; the last warp produces
     if (tid == 0) {
@@ -899,13 +910,14 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
         const int ro = ro0 + rr * rstep;
-        zmu[rr] = ou[ro + cpar];
-        pc[rr][0] = ou[NA * so + ro];
-        pc[rr][1] = ou[NA * so + ro + 1];
+        const int e0 = off_o(z0) & 3, e1 = off_o(z0 + 1) & 3;  // slot offsets of planes z0 - 1 and z0
+        zmu[rr] = ou[e0 + ro + cpar];
+        pc[rr][0] = ou[NA * so + e1 + ro];
+        pc[rr][1] = ou[NA * so + e1 + ro + 1];
         if constexpr (MODE == 2) {
-            zmk[rr] = ou[so + ro + cpar];
-            qc[rr][0] = ou[NA * so + so + ro];
-            qc[rr][1] = ou[NA * so + so + ro + 1];
+            zmk[rr] = ou[so + e0 + ro + cpar];
+            qc[rr][0] = ou[NA * so + so + e1 + ro];
+            qc[rr][1] = ou[NA * so + so + e1 + ro + 1];
         } else {
             zmk[rr] = qc[rr][0] = qc[rr][1] = 0.f;
         }
@@ -918,7 +930,9 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
         for (int k = 0; k < TZ; ++k) {
             bad = __any_sync(0xffffffffu, !mbar_wait(&bar[1 + g_s], g_ph));
             if (bad) break;
-            const float *on = ou + on_s * NA * so, *oc = ou + oc_s * NA * so, *fw = wf + w_s * NA * sw;
+            const float *on = ou + on_s * NA * so + (off_o(z0 + k + 2) & 3);
+            const float *oc = ou + oc_s * NA * so + (off_o(z0 + k + 1) & 3);
+            const float *fw = wf + w_s * NA * sw + (off_w(z0 + k + 1) & 3);
             const float *kn = on + so, *kc = oc + so, *kw = fw + sw;
             const int z = z0 + k;
             float *zw = z == 0 ? zlo : (z == n - 1 ? zhi : nullptr);

@@ -160,7 +160,8 @@ bool smooth32_specialised(const DevLevel &d) { return d.g.lg >= 2 && d.g.lg <= 7
 
 size_t smooth32t_smem(int lg, bool var, int TY, int D) {
     const int P = (1 << lg) + 2, H = half_row(P), NA = var ? 2 : 1;
-    return static_cast<size_t>(4) * NA * ((2 + D) * (TY + 2) * H + (1 + D) * TY * H) + 8 * (4 + 2 * D);
+    const int so = ((TY + 2) * H + 6) & ~3, sw = (TY * H + 6) & ~3;  // slots with room for 16-byte widening
+    return static_cast<size_t>(4) * NA * ((2 + D) * so + (1 + D) * sw) + 8 * (4 + 2 * D);
 }
 
 int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
@@ -1122,8 +1123,9 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         d.g.n = h.n;
         d.g.lg = ilog2(h.n);
         d.g.P = h.n + 2;
-        // one stride for both precisions: the natural FP64 block or the padded FP32 split block, whichever is
-        // larger, rounded to 64 elements (every FP32 half, plane and row then starts on a 16-byte boundary)
+        // one stride for both precisions: the natural FP64 block or the FP32 split block (the same size), rounded
+        // to 64 elements, so every block and FP32 half starts on a 16-byte boundary and a bulk copy widened to
+        // 16-byte bounds at the end of the last block stays inside the pool
         const int64_t per = std::max<int64_t>(static_cast<int64_t>(d.g.P) * d.g.P * d.g.P,
                                               2 * static_cast<int64_t>(d.g.P) * d.g.P * half_row(d.g.P));
         d.g.bs = (per + 63) / 64 * 64;
