@@ -97,7 +97,7 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launch
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the level's cells), scaled here to the launch's cells
 # (the traffic grows in proportion to the cells).  Kernel and source summary in profiles/.
 _NCU_TRAFFIC_PER_CELL = {
-    "smooth_f32_finest": (187.1e6 / 16777216, "profiles/k_smooth32t_uniform_4x64_k.md"),
+    "smooth_f32_finest": (164.7e6 / 16777216, "profiles/k_smooth32t_uniform_4x64_k.md"),
 }
 
 
