@@ -4,8 +4,9 @@
 uniform forests; (d) a uniformly refined forest reproduces the exact single-grid solve (DST-II); (e) flux
 conservation of the conservative interface variant; (f) dense direct solve on tiny forests; plus C2F
 triquadratic exactness in all nine remap cases (Sec. 3.3.2), F2C multilinear exactness (Sec. 3.3.1), transfer
-operators on linear functions, the transposed operator (dot-product test), and the adjoint gradients against
-finite differences of dense solves.
+operators on linear functions, the transposed operator (dot-product test), the adjoint gradients against
+finite differences of dense solves, harmonic-mean faces exact through a material jump, and constant k reducing
+to the -Laplace cycle.
 """
 import math
 
@@ -198,6 +199,54 @@ def test_b_kappa_variable_coefficient():
         errs.append(vw_norm(leaf_h(R, n, keys), us - u))
     kap = errs[2] / errs[1]
     assert 0.2 < kap < 0.3, errs
+
+
+def _layered(axis, k1, k2):
+    """k = k1 below the plane coord[axis] = 1/2, k2 above it; phi continuous, piecewise linear in coord[axis] with
+    the same flux k phi' = 1 on both sides: the exact solution of -div(k grad u) = 0 through a material jump."""
+    def phi(x, y, z):
+        t = (x, y, z)[axis]
+        return np.where(t <= 0.5, t / k1, 0.5 / k1 + (t - 0.5) / k2)
+    def kf(x, y, z):
+        return np.where((x, y, z)[axis] < 0.5, k1, k2)
+    return phi, kf
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("k1,k2", [(1.0, 10.0), (3.0, 0.25)])
+def test_a_harmonic_faces_exact_through_a_material_jump(axis, k1, k2, monkeypatch):
+    """Two-point flux with harmonic-mean faces is exact for a piecewise-linear, flux-continuous u when the jump
+    lies on a cell face: A u = 0 in every cell, with the Dirichlet data u itself.  An arithmetic face mean fails."""
+    import oracle.octree_mg as om
+    R, n = 2, 8
+    keys = syn.uniform_leaves(R)
+    c = syn.cell_centres(R, n, keys).numpy().reshape(len(keys), -1, 3)
+    phi, kf = _layered(axis, k1, k2)
+    u = phi(c[..., 0], c[..., 1], c[..., 2])
+    k = kf(c[..., 0], c[..., 1], c[..., 2])
+    scale = 1.0 / (0.5 / n)  # |T (u_i - u_j)| / h^2 = flux / h
+    Au = OracleMG(R, n, keys, k_user=k, operator_only=True, bc=phi).apply_A(u)
+    assert np.abs(Au).max() <= 1e-12 * scale
+    monkeypatch.setattr(om, "harmonic", lambda a, b: 0.5 * (a + b))
+    Au_arith = OracleMG(R, n, keys, k_user=k, operator_only=True, bc=phi).apply_A(u)
+    assert np.abs(Au_arith).max() > 0.1 * scale
+
+
+@pytest.mark.parametrize("variant", ["C", "P"])
+def test_constant_k_reduces_to_the_laplace_cycle(variant):
+    """k = c everywhere: every level's operator is c times the -Laplace one (face means, coarse averages and ghost
+    k all give c), and red-black Gauss-Seidel, the transfers and the dense coarsest solve commute with that
+    scaling, so V-cycles on (A_k, c f) give the -Laplace V-cycles' iterates on (A, f)."""
+    R, n, keys = 2, 8, one_refined_root()
+    c = 2.5
+    rng = np.random.default_rng(8)
+    f = rng.uniform(-1.0, 1.0, size=(len(keys), n ** 3))
+    mk = OracleMG(R, n, keys, k_user=np.full((len(keys), n ** 3), c), variant=variant)
+    m1 = OracleMG(R, n, keys, variant=variant)
+    assert len(mk.levels) == len(m1.levels) >= 3
+    uk, _ = mk.solve(c * f, cycles=3)
+    u1, _ = m1.solve(f, cycles=3)
+    assert np.abs(uk - u1).max() <= 1e-13 * np.abs(u1).max()
 
 
 # ---------------------------------------------------------------- (c) symmetry on uniform forests
