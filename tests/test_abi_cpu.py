@@ -1,5 +1,6 @@
-"""The C ABI on a machine without a GPU: the library loads, exports every declared symbol, and rejects invalid
-forests on the host before touching the device."""
+"""The C ABI on a machine without a GPU: the library loads, exports every declared symbol, the ctypes binding
+agrees with the header (argument kinds, the config struct's layout), and invalid forests are rejected on the host
+before the device is touched."""
 import ctypes
 import os
 import re
@@ -72,3 +73,64 @@ def test_rejects_holes_and_overlaps(lib):
 def test_rejects_bad_arguments(lib):
     h = ctypes.c_void_p()
     assert lib.mg_forest_create(None, ctypes.byref(h)) == 1
+
+
+def _prototypes():
+    text = open(os.path.join(ROOT, "include", "octmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w\s\*]*?)\s*\b(mg_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+        params = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        out[name] = (ret.split()[-1] if "*" not in ret else "*", params)
+    return out
+
+
+def _c_kind(decl):
+    if "*" in decl:
+        return "ptr"
+    for word, kind in (("double", "f64"), ("int64_t", "i64"), ("int32_t", "i32"), ("mg_status", "i32")):
+        if re.search(rf"\b{word}\b", decl):
+            return kind
+    raise AssertionError(f"unknown C type in {decl!r}")
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    return {ctypes.c_int32: "i32", ctypes.c_int64: "i64", ctypes.c_double: "f64"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype in the header and its ctypes declaration agree in arity and in the kind of every argument
+    and result (pointer, int32, int64, double), so no call marshals an argument into the wrong register."""
+    from paper_2403_08063_gb300 import _lib
+    protos = _prototypes()
+    assert set(protos) == set(_lib.SIGNATURES)
+    for name, (ret, params) in protos.items():
+        res, args = _lib.SIGNATURES[name]
+        want_ret = "void" if ret == "void" else ("ptr" if ret == "*" else _c_kind(ret))
+        assert _ctypes_kind(res) == want_ret, name
+        assert [_c_kind(p) for p in params] == [_ctypes_kind(a) for a in args], name
+
+
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of mg_config has the C compiler's field offsets and size (a mismatch would let the library
+    read the caller's fields at the wrong places)."""
+    import shutil
+    import subprocess
+    from paper_2403_08063_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in _lib.MGConfig._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"octmg.h\"\nint main(void) {\n"
+                   + "".join(f'    printf("%zu\\n", offsetof(mg_config, {f}));\n' for f in fields)
+                   + '    printf("%zu\\n", sizeof(mg_config));\n    return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [getattr(_lib.MGConfig, f).offset for f in fields] + [ctypes.sizeof(_lib.MGConfig)]
+    assert got == want, list(zip(fields + ["sizeof"], got, want))
