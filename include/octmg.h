@@ -142,7 +142,7 @@ mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_de
 
 /* mg_exchange_level without device allocation.  The paper has no counterpart: this serves callers that cannot
  * call cudaMalloc at the time they need the exchange (during a CUDA stream capture, when all device memory is owned
- * by a caching allocator, or in loops that must not enter the driver's allocator).  Same arguments, result and
+ * by a caching allocator, or in loops that must not enter CUDA's device allocator).  Same arguments, result and
  * errors as mg_exchange_level, but the level's padded scratch pool is a static device array of 524,288 doubles
  * (4 MiB) inside the library, which every GPU that loads the library holds until the process exits; a level whose
  * pool (nb * (n+2)^3 rounded up to 32 doubles per block) is larger is rejected with MG_ERR_INVALID_ARG and a

@@ -4,7 +4,7 @@
 // afterwards.  Callers that cannot allocate device memory at that point -- code running while a CUDA stream capture
 // is in progress (allocation is not a stream operation and breaks or invalidates the capture), applications whose
 // device memory is entirely handed to a caching allocator or pre-reserved at start-up, or real-time loops that
-// must not hit the driver's allocator -- use this variant.  Its scratch pool is the file-scope device array below,
+// must not enter CUDA's device allocator -- use this variant.  Its scratch pool is the file-scope device array below,
 // of a fixed size; every GPU that loads the library holds that array until the process exits.
 #include <mutex>
 

@@ -1,7 +1,7 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI.
 
 Tolerances: single operator applications and exchanges agree to rounding (1e-13 relative); FP64 iterates after a
-fixed number of V-cycles to 1e-10 relative L2 (the spec FP64 bar); converged solves are compared by the
+fixed number of V-cycles to 1e-10 relative L2 (the FP64 parity bar); converged solves are compared by the
 oracle's own residual of the GPU solution; mixed-precision results state their error against the FP64 oracle.
 """
 import numpy as np
