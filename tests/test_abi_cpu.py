@@ -134,3 +134,47 @@ def test_config_struct_layout_matches_the_header(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     want = [getattr(_lib.MGConfig, f).offset for f in fields] + [ctypes.sizeof(_lib.MGConfig)]
     assert got == want, list(zip(fields + ["sizeof"], got, want))
+
+
+def _create_rows(lib, rows, R=2, n=8, **fields):
+    """mg_forest_create with leaf rows (problem, level, i, j, k) and config fields overridden."""
+    from paper_2403_08063_gb300 import _lib
+    arr = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, 5)
+    cfg = _lib.MGConfig()
+    cfg.roots, cfg.n, cfg.n_leaves = R, n, len(arr)
+    cfg.leaves = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    cfg.coeff, cfg.interface_flux, cfg.precision, cfg.nu1, cfg.nu2, cfg.max_coarse = 0, 1, 0, 2, 2, 512
+    cfg.inner_cycles, cfg.n_problems = 1, 1
+    for name, value in fields.items():
+        setattr(cfg, name, value)
+    h = ctypes.c_void_p()
+    st = lib.mg_forest_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert h.value is None
+    return st, lib.mg_last_error().decode()
+
+
+_ROOTS = [(0, 0, i, j, k) for k in range(2) for j in range(2) for i in range(2)]
+
+
+@pytest.mark.parametrize("rows,fields,status,text", [
+    (_ROOTS, {"n_leaves": 0}, 1, "null config"),
+    (_ROOTS, {"coeff": 2}, 1, "bad coeff"),
+    (_ROOTS, {"nu1": 0, "nu2": 0}, 1, "nu1"),
+    (_ROOTS, {"interface_flux": -1}, 1, "interface_flux"),
+    (_ROOTS, {"c2f_variant": 3}, 1, "c2f_variant"),
+    (_ROOTS, {"omega": 2.5}, 1, "omega"),
+    (_ROOTS, {"omega": float("nan")}, 1, "omega"),
+    (_ROOTS, {"coarse_iters": -1}, 1, "coarse_iters"),
+    (_ROOTS, {"smoother": 1, "precision": 1}, 1, "damped Jacobi"),
+    (_ROOTS, {"roots": 0}, 1, "roots must be"),
+    (_ROOTS, {"n": 2048}, 3, "4..1024"),
+    (_ROOTS[:-1] + [(1, 0, 1, 1, 1)], {}, 1, "problem index"),
+    (_ROOTS[:-1] + [(0, 0, 2, 1, 1)], {}, 2, "outside the domain"),
+    (_ROOTS + [_ROOTS[3]], {}, 2, "duplicate"),
+    (_ROOTS, {"n_problems": 2}, 2, "(problem 1)"),
+    ([(0, 20, 0, 0, 0)], {}, 1, "too deep"),
+])
+def test_host_checks_reject_each_bad_config(lib, rows, fields, status, text):
+    """Every config and leaf check runs on the host before any device call, with its own status and message."""
+    st, msg = _create_rows(lib, rows, **fields)
+    assert st == status and text in msg, (st, msg)
