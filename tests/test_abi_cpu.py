@@ -178,3 +178,17 @@ def test_host_checks_reject_each_bad_config(lib, rows, fields, status, text):
     """Every config and leaf check runs on the host before any device call, with its own status and message."""
     st, msg = _create_rows(lib, rows, **fields)
     assert st == status and text in msg, (st, msg)
+
+
+def test_batch_host_checks(lib):
+    from paper_2403_08063_gb300 import _lib
+    rows = np.ascontiguousarray([(p, 0, 0, 0, 0) for p in range(3)], dtype=np.int32)
+    cfg = _lib.MGConfig()
+    cfg.roots, cfg.n, cfg.n_leaves, cfg.n_problems = 1, 8, 3, 3
+    cfg.coeff, cfg.interface_flux, cfg.precision, cfg.nu1, cfg.nu2 = 1, 1, 1, 2, 2
+    h = ctypes.c_void_p()
+    assert lib.mg_batch_create(ctypes.byref(cfg), None, ctypes.byref(h)) == 1  # no leaves
+    cfg.leaves = rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    pn = np.ascontiguousarray([8, 6, 16], dtype=np.int32)
+    st = lib.mg_batch_create(ctypes.byref(cfg), pn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h))
+    assert st == 3 and "problem 1" in lib.mg_last_error().decode() and h.value is None
