@@ -192,3 +192,21 @@ def test_batch_host_checks(lib):
     pn = np.ascontiguousarray([8, 6, 16], dtype=np.int32)
     st = lib.mg_batch_create(ctypes.byref(cfg), pn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h))
     assert st == 3 and "problem 1" in lib.mg_last_error().decode() and h.value is None
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library the binding raises instead of computing anything."""
+    from paper_2403_08063_gb300 import _lib
+    monkeypatch.setattr(_lib, "_LIB", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load(str(tmp_path / "libocmg.so"))
+
+
+def test_product_code_never_touches_the_oracle():
+    """The package and the header name neither the oracle module nor its functions."""
+    pkg = os.path.join(ROOT, "paper_2403_08063_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, name)).read()
+                assert not re.search(r"\boracle\b|octree_mg|OracleMG", text), name
