@@ -116,12 +116,14 @@ def tangential_nodes(yc, n):
 
 @functools.lru_cache(maxsize=None)
 def _tangential_matrix_cached(n, offset, order):
+    """Read-only cached copy of tangential_matrix_uncached (Sec. 3.3.2)."""
     M = tangential_matrix_uncached(n, offset, order)
     M.setflags(write=False)
     return M
 
 
 def tangential_matrix(n, offset, order=2):
+    """The C2F tangential interpolation matrix of one axis (Sec. 3.3.2), cached."""
     return _tangential_matrix_cached(n, offset, order)
 
 
@@ -141,6 +143,8 @@ def tangential_matrix_uncached(n, offset, order=2):
 
 
 def harmonic(a, b):
+    """Face coefficient between cells with k = a and k = b: the harmonic mean (this project's reading for the
+    variable coefficients that Sec. 8 leaves to future work)."""
     return 2.0 * a * b / (a + b)
 
 
@@ -164,6 +168,7 @@ class Level:
     """One multigrid level: a list of blocks (level, i, j, k) all holding n^3 cells."""
 
     def __init__(self, R, n, keys):
+        """Blocks of one level of the forest (Sec. 2: octree blocks over R^3 roots), with their face neighbours."""
         self.R, self.n, self.keys = R, n, list(keys)
         self.index = {key: b for b, key in enumerate(self.keys)}
         self.nb = len(self.keys)
@@ -173,11 +178,14 @@ class Level:
         self.T = None  # cached face coefficients (6 arrays (nb, n, n, n)) for variable k
 
     def blocks_per_axis(self, lev):
+        """R 2^lev: blocks per axis at refinement level lev (Sec. 2)."""
         m = self.R * 2.0 ** lev
         assert m == int(m) and m >= 1, "level below the root grid"
         return int(m)
 
     def _face(self, key, axis, side):
+        """Neighbour relation across one block face (Sec. 3.1): boundary, same level, coarser (C2F, with the
+        segment of the coarse face) or finer (F2C, the four fine blocks and their segments)."""
         lev = key[0]
         idx = list(key[1:])
         m = self.blocks_per_axis(lev)
@@ -206,10 +214,12 @@ class Level:
         return ("f2c", segs)
 
     def zeros(self):
+        """A zero field with one ghost layer per block (Sec. 3.3: one ghost layer)."""
         n = self.n
         return np.zeros((self.nb, n + 2, n + 2, n + 2))
 
     def colour_mask(self, c):
+        """Interior cells of colour c, (x + y + z) mod 2 of the block-local index (red-black ordering)."""
         n = self.n
         z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
         return ((x + y + z) % 2) == c
@@ -303,6 +313,8 @@ class OracleMG:
 
     # -- hierarchy -------------------------------------------------------------------------------------
     def _merge_deepest(self, L):
+        """Merge complete sibling octets of 4^3 blocks at the deepest level into their parent (a coarsening step
+        below Sec. 5's block-local coarsening, used when the coarsest level is too large for a dense solve)."""
         deepest = max(key[0] for key in L.keys)
         m_parent = L.R * 2.0 ** (deepest - 1)
         if m_parent != int(m_parent) or m_parent < 1:
@@ -331,6 +343,7 @@ class OracleMG:
 
     # -- layout ----------------------------------------------------------------------------------------
     def to_pad(self, x_user, level=0):
+        """User layout (leaf-major, n^3 per leaf, x fastest) -> blocks with a zero ghost layer."""
         L = self.levels[level]
         n = L.n
         U = L.zeros()
@@ -338,6 +351,7 @@ class OracleMG:
         return U
 
     def from_pad(self, U):
+        """Blocks with ghosts -> user layout (interior only)."""
         return U[:, 1:-1, 1:-1, 1:-1].reshape(U.shape[0], -1).copy()
 
     # -- ghost exchange --------------------------------------------------------------------------------
@@ -430,6 +444,7 @@ class OracleMG:
                             Vf[1:3, 1:-1, 1:-1].reshape(2, h2, 2, h2, 2).mean(axis=(0, 2, 4))
 
     def _cache_T(self, l):
+        """Face coefficients T_f of level l from its ghost-filled k (Sec. 5, Eq. 1 with a per-cell k)."""
         L = self.levels[l]
         K = L.kpad
         kc = K[:, 1:-1, 1:-1, 1:-1]
@@ -437,6 +452,7 @@ class OracleMG:
 
     # -- stencil ---------------------------------------------------------------------------------------
     def _T(self, l):
+        """The six face-coefficient arrays of level l (1 for -Laplace)."""
         return self.levels[l].T if self.coeff else [1.0] * 6
 
     def apply_padded(self, l, U):
@@ -450,6 +466,7 @@ class OracleMG:
         return acc / (L.h ** 2)[:, None, None, None]
 
     def residual(self, l, U, F):
+        """r = f - A u on level l after a ghost exchange (Sec. 5, Eq. 1-2)."""
         self.exchange(l, U)
         return F - self.apply_padded(l, U)
 
@@ -483,6 +500,8 @@ class OracleMG:
         U[:, 1:-1, 1:-1, 1:-1] = (1.0 - self.omega) * uc + self.omega * (num / den)
 
     def smooth(self, l, U, F, iters):
+        """iters smoothing steps (Sec. 5): red-black Gauss-Seidel, or the paper's damped Jacobi, each after an
+        exchange."""
         for _ in range(iters):
             if self.smoother == "jacobi":
                 self.jacobi_sweep(l, U, F)
@@ -530,6 +549,8 @@ class OracleMG:
 
     # -- coarsest solve --------------------------------------------------------------------------------
     def _factor_coarsest(self):
+        """Dense LU of the coarsest level's operator, assembled column by column (this project's direct coarsest
+        solver; the paper's is damped Jacobi, Sec. 5, available through coarse_iters)."""
         l = len(self.levels) - 1
         L = self.levels[l]
         N = L.nb * L.n ** 3
@@ -545,6 +566,7 @@ class OracleMG:
         self.lu = scipy.linalg.lu_factor(A)
 
     def coarse_solve(self, F):
+        """Coarsest-level solve: dense LU, or coarse_iters damped Jacobi sweeps from zero (Sec. 5)."""
         l = len(self.levels) - 1
         L = self.levels[l]
         U = L.zeros()
@@ -557,6 +579,8 @@ class OracleMG:
 
     # -- cycle -----------------------------------------------------------------------------------------
     def vcycle(self, l, U, F):
+        """One V(nu1, nu2) cycle from level l (Sec. 5): smooth, restrict the residual, recurse, prolongate and
+        correct, smooth."""
         if l == len(self.levels) - 1:
             U[...] = self.coarse_solve(F)
             return
@@ -572,6 +596,7 @@ class OracleMG:
         self.smooth(l, U, F, self.nu2)
 
     def norm(self, l, X):
+        """Volume-weighted L2 norm sqrt(sum h^3 x^2) (Sec. 5's L2 norm, in the reading that gives its kappa)."""
         L = self.levels[l]
         return float(np.sqrt(np.sum((L.h ** 3)[:, None, None, None] * X ** 2)))
 
@@ -596,11 +621,13 @@ class OracleMG:
 
     # -- plain operator in user layout -----------------------------------------------------------------
     def apply_A(self, u_user, level=0):
+        """A u in user layout (Sec. 5, Eq. 1-2), ghosts from the exchange of Sec. 3."""
         U = self.to_pad(u_user, level)
         self.exchange(level, U)
         return self.apply_padded(level, U).reshape(U.shape[0], -1)
 
     def rel_residual(self, u_user, f_user):
+        """||f - A u|| / ||f|| in the volume-weighted norm (Sec. 5)."""
         F = self.to_pad(f_user)[:, 1:-1, 1:-1, 1:-1]
         U = self.to_pad(u_user)
         return self.norm(0, self.residual(0, U, F)) / self.norm(0, F)
@@ -733,6 +760,7 @@ class OracleMG:
         return Eb[:, 1:-1, 1:-1, 1:-1].copy()
 
     def _smooth_steps(self, nu):
+        """Colour order of nu red-black Gauss-Seidel iterations (red first)."""
         return [c for _ in range(nu) for c in (0, 1)]
 
     def vcycle_transposed(self, l, Ubar):
@@ -870,6 +898,7 @@ class OracleMG:
 
 
 def n_half(n):
+    """Coarse cells along a block edge covered by one coarse-fine segment (Sec. 3.3: a fine face covers half)."""
     return n // 2
 
 
@@ -900,6 +929,7 @@ def _neighbour_slices():
 
 
 def _neighbours(U):
+    """The six face-neighbour views of every interior cell of padded blocks U (the 7-point stencil)."""
     return [U[(slice(None),) + sl] for sl in _neighbour_slices()]
 
 
