@@ -78,14 +78,19 @@ mg_status mg_forest_create(const mg_config *cfg, mg_forest **out);
 void mg_forest_destroy(mg_forest *forest);
 
 /* Number of multigrid levels, and (optionally) per level the block count and block edge (host arrays of
- * n_levels entries, either may be NULL).  Level 0 is the finest. */
+ * n_levels entries, either may be NULL).  Level 0 is the finest; each coarser level halves every block's edge
+ * (block-local coarsening, Sec. 5) down to 4^3, then merges complete sibling octets while the coarsest level has
+ * more than max_coarse unknowns (this library's addition for a dense coarsest solve). */
 mg_status mg_forest_levels(const mg_forest *forest, int32_t *n_levels, int32_t *nb_per_level, int32_t *n_per_level);
 
-/* Block keys (level, i, j, k) of multigrid level `level`, in the level's block order (keys_host: 4 * nb int32). */
+/* Block keys (level, i, j, k) of multigrid level `level`, in the level's block order (keys_host: 4 * nb int32);
+ * (level, i, j, k) names the octree block of edge 1 / (R 2^level) at (i, j, k) (Sec. 2). */
 mg_status mg_level_keys(const mg_forest *forest, int32_t level, int32_t *keys_host);
 
-/* Copy the right-hand side f (and, for coeff == 1, the coefficient k) into the forest; for coeff == 1 also build
- * the coefficient pyramid (k of a coarse cell = mean of its 8 children) and the coarsest-level inverse.
+/* Copy the right-hand side f of -div(k grad u) = f (Sec. 5, Eq. 1; a per-cell k is the variable coefficient that
+ * Sec. 8 names as future work) and, for coeff == 1, the coefficient k into the forest; for coeff == 1 also build
+ * the face coefficients (harmonic means of the two cells' k), the coefficient pyramid (k of a coarse cell = mean
+ * of its 8 children) and the coarsest-level inverse.
  * f_dev: n_leaves * n^3 doubles; k_dev: same size, every entry finite and > 0, or NULL when coeff == 0.
  * Errors: MG_ERR_INVALID_ARG, MG_ERR_NONFINITE, MG_ERR_CUDA. */
 mg_status mg_set_rhs(mg_forest *forest, const double *f_dev, const double *k_dev);
@@ -98,14 +103,15 @@ mg_status mg_set_rhs(mg_forest *forest, const double *f_dev, const double *k_dev
  * by FP64 cycles and by the FP64 residual of FP32-in-FP64 solves; the adjoint rejects a forest with g set. */
 mg_status mg_set_boundary(mg_forest *forest, const double *g_dev);
 
-/* Run exactly ncycles V(nu1, nu2) cycles on u_dev (initial guess on entry, iterate on exit; FP64 cycles, or FP32
- * cycles inside FP64 defect correction when precision == 1).  If rel_res_out is not NULL it receives, per problem
+/* Run exactly ncycles V(nu1, nu2) cycles (Sec. 5: smoothing with the ghosts refreshed before every half-sweep
+ * (Sec. 3), residual, 8:1 restriction, coarser levels, prolongation and correction) on u_dev (initial guess on
+ * entry, iterate on exit; FP64 cycles, or FP32 cycles inside FP64 defect correction when precision == 1).  If rel_res_out is not NULL it receives, per problem
  * (n_problems doubles), ||f - A u|| / ||f|| after the last cycle (volume-weighted L2 norm sqrt(sum h^3 r^2) over that
  * problem's cells).  Requires mg_set_rhs. */
 mg_status mg_vcycle(mg_forest *forest, double *u_dev, int32_t ncycles, double *rel_res_out);
 
-/* Cycle from the initial guess in u_dev until every problem has ||f - A u|| / ||f|| <= rtol, or max_cycles cycles
- * ran.  cycles_out / rel_res_out (host arrays of n_problems entries, may be NULL) receive per problem the number of
+/* Cycle from the initial guess in u_dev until every problem has ||f - A u|| / ||f|| <= rtol (the relative L2
+ * residual criterion of Sec. 5, volume-weighted), or max_cycles cycles ran.  cycles_out / rel_res_out (host arrays of n_problems entries, may be NULL) receive per problem the number of
  * cycles after which it first met rtol (or the total) and its final relative residual.  All problems keep cycling
  * until the last one converges.  Returns MG_ERR_NOT_CONVERGED (u_dev still holds the last iterate) when a problem
  * does not reach rtol. */
@@ -122,7 +128,8 @@ mg_status mg_solve(mg_forest *forest, double *u_dev, double rtol, int32_t max_cy
 mg_status mg_solve_host(mg_forest *forest, const double *f_host, const double *k_host, const double *u0_host,
                         double *u_host, double rtol, int32_t max_cycles, int32_t *cycles_out, double *rel_res_out);
 
-/* Adjoint of the converged solve for L = 1/2 sum_i (u_i - u_t,i)^2: given u_dev (the forward solution) and
+/* Adjoint of the converged solve (this library's extension; the paper has no adjoint) for
+ * L = 1/2 sum_i (u_i - u_t,i)^2: given u_dev (the forward solution) and
  * dLdu_dev = u - u_t, solve A^T lambda = dL/du by defect correction with the transposed V-cycle, write lambda
  * (= dL/df) to lambda_dev and, when dLdk_dev is not NULL and coeff == 1, dL/dk = -lambda^T (dA/dk) u.
  * All arrays n_leaves * n^3 doubles on the device.  With several problems, rtol applies to the norm over all of
@@ -130,13 +137,14 @@ mg_status mg_solve_host(mg_forest *forest, const double *f_host, const double *k
 mg_status mg_adjoint_solve(mg_forest *forest, const double *u_dev, const double *dLdu_dev, double *lambda_dev,
                            double *dLdk_dev, double rtol, int32_t max_cycles);
 
-/* The finest-level operator: Au_dev = A u_dev (ghosts filled by the full exchange, homogeneous Dirichlet data),
- * and its transpose ATy_dev = A^T y_dev.  Requires mg_set_rhs when coeff == 1. */
+/* The finest-level operator of Sec. 5, Eq. 1-2: Au_dev = A u_dev (ghosts filled by the full exchange of Sec. 3,
+ * homogeneous Dirichlet data), and its transpose ATy_dev = A^T y_dev.  Requires mg_set_rhs when coeff == 1. */
 mg_status mg_apply(mg_forest *forest, const double *u_dev, double *Au_dev);
 mg_status mg_apply_transpose(mg_forest *forest, const double *y_dev, double *ATy_dev);
 
-/* Debug view of one exchange: copy u_dev (user layout of level `level`, nb_level * n_level^3 doubles) into the
- * level's FP64 pool, run that level's ghost exchange, and copy the whole padded pool (nb_level * (n_level+2)^3
+/* Debug view of one exchange (Sec. 3.1 same level, Sec. 3.3.2 coarse to fine, Sec. 3.3.1 fine to coarse, and the
+ * Dirichlet reflection at the domain boundary): copy u_dev (user layout of level `level`, nb_level * n_level^3
+ * doubles) into the level's FP64 pool, run that level's ghost exchange, and copy the whole padded pool (nb_level * (n_level+2)^3
  * doubles, block-major, x fastest) to padded_dev. */
 mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
 
@@ -152,7 +160,7 @@ mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_de
  * its work on the forest's stream and synchronises that stream before returning. */
 mg_status mg_exchange_level_noalloc(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
 
-/* Kernel accounting.  Launch counters per kernel family always run; mg_profile(forest, 1) clears them and starts
+/* Kernel accounting (no counterpart in the paper).  Launch counters per kernel family always run; mg_profile(forest, 1) clears them and starts
  * recording a CUDA-event pair on the forest's stream around every family's launches, mg_profile(forest, 0) stops.
  * mg_profile_read synchronises the stream and, for up to max_families families, writes the family name (32 bytes
  * each, NUL-terminated) into names, the summed event time in milliseconds into ms and the launch count into
@@ -189,7 +197,7 @@ mg_status mg_set_smoother_shape(mg_forest *forest, int32_t level, const int32_t 
 mg_status mg_get_tail(const mg_forest *forest, int32_t *level);
 mg_status mg_set_tail(mg_forest *forest, int32_t level);
 
-/* Self-test of the bounded waits that keep a kernel from hanging when an expected event never comes: launches one
+/* Self-test (no counterpart in the paper) of the bounded waits that keep a kernel from hanging when an expected event never comes: launches one
  * CTA on the forest's stream that waits for something nothing provides, which = 0 an mbarrier phase (the wait of the
  * staged smoother's shared-memory copies, bounded by 2^14 probes), which = 1 a grid barrier expecting one CTA more
  * than the grid has (the persistent tail's, bounded by 2^30 SM clock cycles), and reads the error word.  Expected
