@@ -323,6 +323,8 @@ __device__ __forceinline__ void exchange_faces_body(T *__restrict__ u, const Fac
     }
 }
 
+// Every block face's ghost layer of a level, one thread per ghost cell: same-level copy (Sec. 3.1), quadratic
+// coarse-to-fine extrapolation (Sec. 3.3.2) and the Dirichlet reflection at the domain boundary (Sec. 5, Eq. 2).
 template <typename T, bool KIND_K>
 static __global__ void k_exchange_faces(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g,
                                         Skip skip = Skip{}, int c2f = 0, const T *__restrict__ gb = nullptr) {
@@ -375,6 +377,7 @@ __device__ __forceinline__ void exchange_c2f_body(T *__restrict__ u, const FaceI
     }
 }
 
+// Coarse-to-fine ghosts of refinement interfaces only (Sec. 3.3.2), one thread per coarse source cell.
 template <typename T>
 static __global__ void k_exchange_c2f(T *__restrict__ u, const FaceItem *__restrict__ items, int nitems, LevelGeom g,
                                       Skip skip, int c2f) {
@@ -433,6 +436,8 @@ __device__ __forceinline__ void exchange_segs_body(T *__restrict__ u, Coef cf, c
     }
 }
 
+// Fine-to-coarse ghosts (Sec. 3.3.1: mean of the 2 x 2 x 2 fine cells over a coarse ghost), or with FLUX the
+// conservative coarse ghost whose flux is the sum of the four fine sub-face fluxes (this library's reading).
 template <typename T, int MODE, bool FLUX>
 static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem *__restrict__ items, int nitems,
                                        LevelGeom g, Skip skip = Skip{}) {
@@ -442,7 +447,8 @@ static __global__ void k_exchange_segs(T *__restrict__ u, Coef cf, const SegItem
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Red-black Gauss-Seidel half-sweep of one colour ((x+y+z) mod 2 of the block-local interior index; red = 0):
+// Red-black Gauss-Seidel half-sweep (the smoother of the problem statement; Sec. 5 smooths with damped Jacobi) of
+// one colour ((x+y+z) mod 2 of the block-local interior index; red = 0):
 //     u_i = (h^2 f_i + sum_f T_f u_f) / sum_f T_f
 // over every block of the level, ghosts as left by the last exchange.  One thread per updated cell.
 // h2 is h^2 per block in the field's precision (unused in MODE 1, whose coefficients carry 1/h^2).
@@ -697,7 +703,8 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
     }
 }
 
-// One column per thread over `total` columns.
+// FP32 red-black Gauss-Seidel half-sweep on colour-split blocks of edge 2^LG, one column per thread over `total`
+// columns (the update of k_smooth, Sec. 5 operator).
 template <int MODE, int LG, int ZC>
 static __global__ void __launch_bounds__(512) k_smooth32(float *__restrict__ u, const float *__restrict__ f,
                                                          const float *__restrict__ kap, const float *__restrict__ h2,
@@ -1084,6 +1091,8 @@ __device__ __forceinline__ void residual_restrict_body(const T *__restrict__ u, 
     }
 }
 
+// Residual r = f - A u (Sec. 5, Eq. 1) restricted 8:1 to the coarse right-hand side (mean of the 8 children, the
+// block-local coarsening of Sec. 5), coarse correction zeroed.
 template <typename T, int MODE>
 static __global__ void k_residual_restrict(const T *__restrict__ u, const T *__restrict__ f, Coef cf,
                                            const T *__restrict__ ih2f, LevelGeom gf, T *__restrict__ fc,
@@ -1397,6 +1406,8 @@ __device__ __forceinline__ void prolong_body(T *__restrict__ uf, LevelGeom gf, c
     }
 }
 
+// Prolongation and correction u_f += P e_c, P the face-neighbour linear cell-centred interpolation (the paper
+// inherits its transfers and does not state them; this is the library's reading).
 template <typename T>
 static __global__ void k_prolong(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
                                  const XferItem *__restrict__ xf, LevelGeom gc, Skip skip = Skip{}) {
@@ -1427,6 +1438,8 @@ __device__ __forceinline__ void coarse_solve_row(T *__restrict__ u, const T *__r
     if (lane == 0) u[cmap[row_i]] = T(s);
 }
 
+// Coarsest-level solve u = A^-1 f by the dense FP64 inverse, one warp per row (this library's direct coarsest
+// solver; Sec. 5's is damped Jacobi, run by the Jacobi kernels when coarse_iters > 0).
 template <typename T>
 static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f, const double *__restrict__ Ainv,
                                       const int64_t *__restrict__ cmap, const int32_t *__restrict__ uprob,
@@ -1438,7 +1451,7 @@ static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// FP64 residual over the finest level, r = f - A u, written as FP32 r * scale_p (scale_p a power of two per
+// FP64 residual over the finest level, r = f - A u (Sec. 5, Eq. 1), written as FP32 r * scale_p (scale_p a power of two per
 // problem, so the scaling is exact), with the FP32 correction field zeroed, and per-block sums of h^3 (r scale_p)^2.
 // Grid: nb * cpb CTAs, CTA (b, c) covers the c-th of cpb contiguous chunks of block b, so each CTA adds one value
 // to its block's sum.  The squared norm is accumulated in FP32 per thread (it decides convergence and is reported
@@ -1626,7 +1639,8 @@ static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__
     }
 }
 
-// u64 += e32 / scale_p over the interior (mixed-precision defect correction update; pinv = 1 / scale_p per problem)
+// u64 += e32 / scale_p over the interior (mixed-precision defect correction update, an extension the paper does not
+// have; pinv = 1 / scale_p per problem)
 static __global__ void k_update_mixed(double *__restrict__ u, const float *__restrict__ e,
                                       const double *__restrict__ pinv, const int32_t *__restrict__ bprob,
                                       LevelGeom g, Skip skip = Skip{}) {
@@ -1645,7 +1659,8 @@ static __global__ void k_update_mixed(double *__restrict__ u, const float *__res
     }
 }
 
-// Face coefficients of a level from k with ghosts: MODE 1 arrays (harmonic mean times the block's 1/h^2) and
+// Face coefficients of a level from k with ghosts (variable coefficients: future work in Sec. 8; harmonic-mean
+// reading): MODE 1 arrays (harmonic mean times the block's 1/h^2) and
 // 1/k for FP32 (MODE 2).  tx at padded (X, Y, Z) is the face between X-1 and X, for X in 1..n+1 and interior
 // Y, Z (same for ty, tz).
 static __global__ void k_face_coefs(const double *__restrict__ k, const double *__restrict__ ih2, LevelGeom g,
