@@ -1,5 +1,6 @@
 // Adjoint of the octree-block multigrid solve (FP64): the transposed operator, the exact transpose of the forward
-// V-cycle, the adjoint solve by defect correction, and dL/dk.
+// V-cycle, the adjoint solve by defect correction, and dL/dk.  The paper has no adjoint; every step here is the
+// transpose of a forward step that cites its passage.
 //
 // A = S E: E fills ghosts from interiors (reflection, copy, C2F extrapolation of Sec. 3.3.2, F2C mean of Sec. 3.3.1
 // or the conservative flux ghost), S is the 7-point stencil.  A^T = E^T S^T: S^T y is the stencil applied to y with

@@ -4,7 +4,8 @@
 // by one is latency-bound; here the CTAs stay resident and walk a phase list recorded from the same schedule as the
 // launched V-cycle (smoothing half-sweeps, interface and full exchanges, restriction, prolongation, coarsest
 // solve), separated by grid barriers.  Every phase runs the same device code as the corresponding kernel (loads of
-// data written by earlier phases go through L2), so results are bit-identical to the launched V-cycle.
+// data written by earlier phases go through L2), so results are bit-identical to the launched V-cycle.  No
+// counterpart in the paper, whose generated code runs the cycle level by level (Sec. 4).
 #include "forest_state.h"
 #include "kernels.cuh"
 
