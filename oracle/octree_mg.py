@@ -38,11 +38,16 @@ What it computes
   "L2 residual norm"; a normalised norm is the reading that gives the printed kappa near 0.25).
 * Adjoint: A^T applied matrix-free as the transposed stencil followed by the transposed ghost exchange; dL/df =
   lambda and dL/dk = -lambda^T (dA/dk) u for L = 1/2 sum (u - u_t)^2.
+* Mixed precision (not in the paper, which computes in FP64): ``OracleMG.with_dtype(np.float32)`` is a copy whose
+  level fields, face coefficients and cycle arithmetic are FP32 while its set-up (hierarchy, FP64 coefficient
+  pyramid, LU factors of the FP64 coarsest operator) stays FP64; ``mixed_solve`` runs such FP32 V-cycles inside FP64
+  defect correction, so that the error an FP32 cycle should have can be stated against the FP64 oracle.
 
 User layout: leaf-major in the order of the leaf list, each leaf n^3 interior cells with x fastest.
 """
 from __future__ import annotations
 
+import copy
 import functools
 from fractions import Fraction
 
@@ -167,6 +172,8 @@ def face_view(a, axis, side):
 class Level:
     """One multigrid level: a list of blocks (level, i, j, k) all holding n^3 cells."""
 
+    dtype = np.dtype(np.float64)  # working precision of the level's fields (OracleMG.with_dtype changes it)
+
     def __init__(self, R, n, keys):
         """Blocks of one level of the forest (Sec. 2: octree blocks over R^3 roots), with their face neighbours."""
         self.R, self.n, self.keys = R, n, list(keys)
@@ -216,7 +223,7 @@ class Level:
     def zeros(self):
         """A zero field with one ghost layer per block (Sec. 3.3: one ghost layer)."""
         n = self.n
-        return np.zeros((self.nb, n + 2, n + 2, n + 2))
+        return np.zeros((self.nb, n + 2, n + 2, n + 2), dtype=self.dtype)
 
     def colour_mask(self, c):
         """Interior cells of colour c, (x + y + z) mod 2 of the block-local index (red-black ordering)."""
@@ -256,6 +263,8 @@ class OracleMG:
     R: root blocks per axis; n: cells per block edge on the finest level (power of two, >= 4);
     keys: leaf list (level, i, j, k); k_user: None for -Laplace, else (n_leaves, n^3) coefficient values.
     """
+
+    dtype = np.dtype(np.float64)  # working precision of the cycles (with_dtype makes an FP32 copy)
 
     def __init__(self, R, n, keys, k_user=None, variant="C", nu1=2, nu2=2, max_coarse=512, operator_only=False,
                  bc=None, c2f_order=2, smoother="rbgs", omega=0.8, coarse_iters=None):
@@ -354,12 +363,36 @@ class OracleMG:
         """Blocks with ghosts -> user layout (interior only)."""
         return U[:, 1:-1, 1:-1, 1:-1].reshape(U.shape[0], -1).copy()
 
+    def with_dtype(self, dtype):
+        """A copy of this oracle whose cycles compute in ``dtype``: level fields, ghost exchange, smoother,
+        residual, transfers and face coefficients (the harmonic means of the FP64 k pyramid rounded to dtype).  The
+        set-up stays this oracle's: hierarchy, FP64 k pyramid and the LU factors of the FP64 coarsest operator, whose
+        solves run in FP64 on the rounded right-hand side and are stored in dtype.  np.float32 gives the FP32
+        V-cycles of the mixed-precision solve (not in the paper; its FP64 cycle is this oracle's default)."""
+        other = copy.copy(self)
+        other.dtype = np.dtype(dtype)
+        other.levels = []
+        for L in self.levels:
+            M = copy.copy(L)
+            M.dtype = other.dtype
+            if L.kpad is not None:
+                M.kpad = L.kpad.astype(other.dtype)
+            other.levels.append(M)
+        if self.coeff:
+            for l in range(len(other.levels)):
+                other._cache_T(l)
+        return other
+
+    def _h2(self, l):
+        """h^2 of every block of level l in the working precision, broadcast over a block's cells."""
+        return (self.levels[l].h ** 2).astype(self.dtype)[:, None, None, None]
+
     # -- ghost exchange --------------------------------------------------------------------------------
     def _c2f_values(self, Vc, n, seg):
         """Fine ghost face (n x n, [t1, t2]) from the coarse view Vc (Sec. 3.3.2, 3D scheme)."""
         E = sum(w * Vc[1 + a, 1:-1, 1:-1] for a, w in enumerate(self.normal_w))
-        M1 = tangential_matrix(n, seg[0] * n // 2, self.c2f_order)
-        M2 = tangential_matrix(n, seg[1] * n // 2, self.c2f_order)
+        M1 = tangential_matrix(n, seg[0] * n // 2, self.c2f_order).astype(self.dtype)
+        M2 = tangential_matrix(n, seg[1] * n // 2, self.c2f_order).astype(self.dtype)
         return M1 @ E @ M2.T
 
     def exchange(self, l, U):
@@ -463,7 +496,7 @@ class OracleMG:
         acc = np.zeros_like(uc)
         for Tf, nb in zip(T, _neighbours(U)):
             acc += Tf * (uc - nb)
-        return acc / (L.h ** 2)[:, None, None, None]
+        return acc / self._h2(l)
 
     def residual(self, l, U, F):
         """r = f - A u on level l after a ghost exchange (Sec. 5, Eq. 1-2)."""
@@ -475,7 +508,7 @@ class OracleMG:
         L = self.levels[l]
         self.exchange(l, U)
         T = self._T(l)
-        num = (L.h ** 2)[:, None, None, None] * F
+        num = self._h2(l) * F
         den = 0.0
         for Tf, nb in zip(T, _neighbours(U)):
             num = num + Tf * nb
@@ -488,10 +521,9 @@ class OracleMG:
     def jacobi_sweep(self, l, U, F):
         """Damped Jacobi with ghosts frozen at the exchanged values: u_i <- (1 - w) u_i + w (h^2 f_i + sum_f T_f u_f)
         / sum_f T_f for every cell at once (the paper's smoother, Sec. 5, omega = 0.8)."""
-        L = self.levels[l]
         self.exchange(l, U)
         T = self._T(l)
-        num = (L.h ** 2)[:, None, None, None] * F
+        num = self._h2(l) * F
         den = 0.0
         for Tf, nb in zip(T, _neighbours(U)):
             num = num + Tf * nb
@@ -531,7 +563,7 @@ class OracleMG:
             if tr[0] == "copy":
                 Uf[tr[1], 1:-1, 1:-1, 1:-1] += E[1:-1, 1:-1, 1:-1]
                 continue
-            P = np.zeros((2 * nc,) * 3)
+            P = np.zeros((2 * nc,) * 3, dtype=E.dtype)
             c = E[1:-1, 1:-1, 1:-1]
             for sz in (0, 1):
                 for sy in (0, 1):
@@ -892,6 +924,44 @@ class OracleMG:
         return grad.reshape(L.nb, -1)
 
 
+def pow2_near(x):
+    """The power of two nearest to x > 0 in the log scale (2^round(log2 x)); scaling by it is exact in binary
+    floating point."""
+    return float(2.0 ** np.round(np.log2(x)))
+
+
+def mixed_solve(mg64, f_user, steps, inner=1, mg32=None, u0_user=None):
+    """FP32 V-cycles inside FP64 defect correction (the mixed-precision solve; the paper itself computes in FP64).
+
+    Every step: r = f - A u in FP64 (the finest operator with its exchange); s = pow2_near(1 / ||r||) with the
+    volume-weighted norm; rhs = FP32(s r); ``inner`` V-cycles of the FP32 copy mg32 (default
+    mg64.with_dtype(np.float32)) on A e = rhs from e = 0; u += e / s in FP64.  Because s is a power of two the
+    scaling adds no rounding, and with an FP64 copy in place of mg32 a step equals ``inner`` FP64 V-cycles on u.
+    Returns (u_user, [||f - A u|| / ||f|| after every step]).
+    """
+    if mg32 is None:
+        mg32 = mg64.with_dtype(np.float32)
+    L0 = mg64.levels[0]
+    F = mg64.to_pad(f_user)[:, 1:-1, 1:-1, 1:-1].copy()
+    U = mg64.to_pad(u0_user) if u0_user is not None else L0.zeros()
+    fn = mg64.norm(0, mg64.residual(0, L0.zeros(), F))
+    hist = []
+    for _ in range(steps):
+        r = mg64.residual(0, U, F)
+        rn = mg64.norm(0, r)
+        if rn == 0.0:
+            hist.append(0.0)
+            break
+        s = pow2_near(1.0 / rn)
+        rhs = (s * r).astype(mg32.dtype)
+        E = mg32.levels[0].zeros()
+        for _ in range(inner):
+            mg32.vcycle(0, E, rhs)
+        U[:, 1:-1, 1:-1, 1:-1] += E[:, 1:-1, 1:-1, 1:-1].astype(np.float64) / s
+        hist.append(mg64.norm(0, mg64.residual(0, U, F)) / fn)
+    return mg64.from_pad(U), hist
+
+
 # ----------------------------------------------------------------------------------------------------------
 # small helpers
 # ----------------------------------------------------------------------------------------------------------
@@ -943,7 +1013,7 @@ def _interior_view(a, axis, side, padded=False):
 def _assemble_octets(children):
     """8 child blocks (n^3 each, octant order x fastest) -> one (2n)^3 array."""
     n = children[0].shape[0]
-    out = np.zeros((2 * n,) * 3)
+    out = np.zeros((2 * n,) * 3, dtype=children[0].dtype)
     for o, c in enumerate(children):
         a, b, cc = o % 2, (o // 2) % 2, o // 4
         out[cc * n:(cc + 1) * n, b * n:(b + 1) * n, a * n:(a + 1) * n] = c

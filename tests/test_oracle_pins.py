@@ -566,3 +566,167 @@ def test_paper_cycle_converges():
     f = np.random.default_rng(10).normal(size=(len(keys), n ** 3))
     u, hist = mg.solve(f, cycles=30)
     assert hist[-1] < 1e-8, hist[-5:]
+
+
+# ---------------------------------------------------------------- red-black Gauss-Seidel, ghost k, FP32 cycles
+
+
+def _global_colour(R, n, keys, c):
+    """Cells of colour c by the parity of their global index on their own refinement level (red = even), computed
+    from the leaf coordinates alone."""
+    out = []
+    t = np.arange(n)
+    z, y, x = np.meshgrid(t, t, t, indexing="ij")
+    for (lev, i, j, k) in keys:
+        out.append((((i * n + x) + (j * n + y) + (k * n + z)) % 2 == c).reshape(-1))
+    return np.concatenate(out)
+
+
+def _textbook_rbgs(A, D, colours, u, f):
+    """One red-black Gauss-Seidel iteration in matrix form: every cell of one colour at once takes
+    u_i + (f - A u)_i / D_i (D the stencil's diagonal sum_f T_f / h^2, ghosts as functions of the current u),
+    red first, then black from the updated u."""
+    for m in colours:
+        u = u + np.where(m, (f - A @ u) / D, 0.0)
+    return u
+
+
+@pytest.mark.parametrize("variant", ["C", "P"])
+def test_rbgs_iteration_is_the_textbook_update_refined(variant):
+    """OracleMG.smooth (two half-sweeps, an exchange before each) against the red-black update written with the
+    dense composite operator, constant k (D = 6 / h^2), on a forest with coarse-fine faces: a wrong colour order,
+    a colour defined by local instead of global parity, a black sweep reading the ghosts exchanged before the red
+    one, or a dropped h^2 f term fails it."""
+    R, n = 2, 4
+    keys = one_refined_root(R)
+    mg = OracleMG(R, n, keys, variant=variant)
+    A = _dense_operator(OracleMG(R, n, keys, variant=variant, operator_only=True))
+    rng = np.random.default_rng(81)
+    u = rng.normal(size=(len(keys), n ** 3))
+    f = rng.normal(size=(len(keys), n ** 3))
+    D = np.repeat(6.0 / leaf_h(R, n, keys) ** 2, n ** 3)
+    red, black = _global_colour(R, n, keys, 0), _global_colour(R, n, keys, 1)
+    want = _textbook_rbgs(A, D, (red, black), u.reshape(-1), f.reshape(-1))
+    U = mg.to_pad(u)
+    F = mg.to_pad(f)[:, 1:-1, 1:-1, 1:-1].copy()
+    mg.smooth(0, U, F, 1)
+    np.testing.assert_allclose(mg.from_pad(U).reshape(-1), want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_rbgs_iteration_is_the_textbook_update_variable_k():
+    """The same with a random k on a uniform forest; D_i = sum_f T_f / h^2 with T_f the harmonic mean of the two
+    cells' k (the cell's own k on a domain face) is computed here on the global grid, independently of the
+    oracle's ghost-k exchange and face-coefficient cache."""
+    R, n = 2, 4
+    keys = syn.uniform_leaves(R)
+    N = R * n
+    rng = np.random.default_rng(82)
+    Kg = np.exp(rng.normal(size=(N, N, N)))  # [z, y, x] on the global grid
+    k_user = np.stack([Kg[c * n:(c + 1) * n, b * n:(b + 1) * n, a * n:(a + 1) * n].reshape(-1)
+                       for (_, a, b, c) in keys])
+    mg = OracleMG(R, n, keys, k_user=k_user)
+    A = _dense_operator(OracleMG(R, n, keys, k_user=k_user, operator_only=True))
+    Tsum = np.zeros_like(Kg)
+    for ax in range(3):
+        for sh in (-1, 1):
+            nb = np.roll(Kg, sh, axis=ax)
+            edge = [slice(None)] * 3
+            edge[ax] = 0 if sh == 1 else N - 1  # the rolled-in value came from the opposite face
+            nb[tuple(edge)] = Kg[tuple(edge)]
+            Tsum += 2.0 * Kg * nb / (Kg + nb)
+    h = 1.0 / N
+    D = np.stack([Tsum[c * n:(c + 1) * n, b * n:(b + 1) * n, a * n:(a + 1) * n].reshape(-1)
+                  for (_, a, b, c) in keys]).reshape(-1) / h ** 2
+    u = rng.normal(size=(len(keys), n ** 3))
+    f = rng.normal(size=(len(keys), n ** 3))
+    red, black = _global_colour(R, n, keys, 0), _global_colour(R, n, keys, 1)
+    want = _textbook_rbgs(A, D, (red, black), u.reshape(-1), f.reshape(-1))
+    U = mg.to_pad(u)
+    F = mg.to_pad(f)[:, 1:-1, 1:-1, 1:-1].copy()
+    mg.smooth(0, U, F, 1)
+    np.testing.assert_allclose(mg.from_pad(U).reshape(-1), want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_ghost_k_samples_a_field_constant_on_coarse_cells(n):
+    """k constant on the cells of the coarse blocks' grid (edge 1 / (R n)) with independent random values, so it
+    jumps across every refinement interface: every face ghost k inside the domain must equal the field at the
+    ghost's centre (the fine ghost injects the coarse cell it lies in; the coarse ghost averages 8 fine cells of
+    one coarse cell), and a domain-face ghost equals its cell's k.  A ghost taking its own cell's k, the wrong
+    coarse cell or the wrong fine layers fails it."""
+    R = 2
+    keys = one_refined_root(R)
+    M = R * n
+    V = np.exp(np.random.default_rng(83).normal(size=(M, M, M)))  # [ix, iy, iz] of the coarse cells
+    field = lambda x, y, z: V[np.floor(x * M).astype(int), np.floor(y * M).astype(int),  # noqa: E731
+                              np.floor(z * M).astype(int)]
+    c = syn.cell_centres(R, n, keys).numpy()
+    k_user = field(c[..., 0], c[..., 1], c[..., 2]).reshape(len(keys), -1)
+    mg = OracleMG(R, n, keys, k_user=k_user, operator_only=True)
+    L = mg.levels[0]
+    checked = {"inside": 0, "interface": 0, "boundary": 0}
+    for b, key in enumerate(L.keys):
+        x, y, z = padded_centres(R, n, key)
+        for f in range(6):
+            axis, side = f // 2, f % 2
+            G = face_view(L.kpad[b], axis, side)[0, 1:-1, 1:-1]
+            I = face_view(L.kpad[b], axis, side)[1, 1:-1, 1:-1]
+            X = [face_view(a, axis, side)[0, 1:-1, 1:-1] for a in (x, y, z)]
+            if L.faces[b][f][0] == "bnd":
+                np.testing.assert_array_equal(G, I)
+                checked["boundary"] += 1
+                continue
+            np.testing.assert_allclose(G, field(*X), rtol=1e-14, atol=0)
+            checked["inside"] += 1
+            checked["interface"] += L.faces[b][f][0] in ("c2f", "f2c")
+    assert checked["interface"] >= 6 and checked["boundary"] > 0
+
+
+def test_fp32_copy_computes_in_fp32():
+    """with_dtype(np.float32): fields and face coefficients are FP32, and one V-cycle lands within FP32 rounding
+    of the FP64 cycle (relative L2 between 1e-9 and 1e-5: far above FP64 rounding, far below any wrong step)."""
+    from oracle.octree_mg import OracleMG as O
+    R, n, keys = syn.workload_forest("sphere_2x4")
+    k = syn.lognormal_k_rff(R, n, keys, seed=84).numpy()
+    f = np.random.default_rng(85).normal(size=(len(keys), n ** 3))
+    mg = O(R, n, keys, k_user=k)
+    m32 = mg.with_dtype(np.float32)
+    assert m32.levels[0].zeros().dtype == np.float32 and m32.levels[1].T[0].dtype == np.float32
+    assert mg.levels[0].zeros().dtype == np.float64 and mg.levels[1].T[0].dtype == np.float64
+    u64, _ = mg.solve(f, cycles=1)
+    E = m32.levels[0].zeros()
+    m32.vcycle(0, E, m32.to_pad(f)[:, 1:-1, 1:-1, 1:-1].astype(np.float32))
+    assert E.dtype == np.float32
+    rel = np.linalg.norm(m32.from_pad(E) - u64) / np.linalg.norm(u64)
+    assert 1e-9 < rel < 1e-5, rel
+
+
+@pytest.mark.parametrize("inner", [1, 3])
+def test_mixed_solve_with_an_fp64_copy_is_plain_vcycles(inner):
+    """Defect correction is exact algebra: with an FP64 copy as the inner solver, s steps of `inner` cycles give
+    the iterate of s * inner FP64 V-cycles (the V-cycle is affine, u <- u + M (f - A u), and the power-of-two
+    residual scale is exact), on a refined variable-k forest."""
+    from oracle.octree_mg import mixed_solve
+    R, n, keys = syn.workload_forest("sphere_2x4")
+    k = syn.lognormal_k_rff(R, n, keys, seed=86).numpy()
+    f = np.random.default_rng(87).normal(size=(len(keys), n ** 3))
+    mg = OracleMG(R, n, keys, k_user=k)
+    u_mix, _ = mixed_solve(mg, f, steps=2, inner=inner, mg32=mg.with_dtype(np.float64))
+    u_ref, _ = mg.solve(f, cycles=2 * inner)
+    assert np.linalg.norm(u_mix - u_ref) <= 1e-13 * np.linalg.norm(u_ref)
+
+
+def test_mixed_solve_reaches_fp64_accuracy():
+    """FP32 cycles inside FP64 defect correction reach a 1e-12 relative residual and the FP64 solution (dense
+    solve of the composite operator) to 1e-10, although each FP32 cycle only resolves ~7 digits."""
+    from oracle.octree_mg import mixed_solve
+    R, n = 2, 4
+    keys = one_refined_root(R)
+    k = syn.lognormal_k_rff(R, n, keys, seed=88).numpy()
+    f = np.random.default_rng(89).normal(size=(len(keys), n ** 3))
+    mg = OracleMG(R, n, keys, k_user=k)
+    u, hist = mixed_solve(mg, f, steps=8, inner=2)
+    assert hist[-1] < 1e-12, hist
+    A = _dense_operator(OracleMG(R, n, keys, k_user=k, operator_only=True))
+    x = np.linalg.solve(A, f.reshape(-1))
+    assert np.linalg.norm(u.reshape(-1) - x) <= 1e-10 * np.linalg.norm(x)
