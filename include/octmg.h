@@ -186,6 +186,25 @@ mg_status mg_smoother_shapes(const mg_forest *forest, int32_t level, int32_t max
 mg_status mg_get_smoother_shape(const mg_forest *forest, int32_t level, int32_t *shape);
 mg_status mg_set_smoother_shape(mg_forest *forest, int32_t level, const int32_t *shape);
 
+/* Bulk-copy plan of the staged FP32 smoother (k_smooth32t), computed on the host by the same code the kernel's
+ * producer thread runs; no GPU is needed.  No counterpart in the paper: it lets a test check every shared-memory copy
+ * of the kernel against the rules of cp.async.bulk without running it.  For block edge 2^lg (lg 5..7), coefficient
+ * mode coeff (0 constant, 1 variable k) and half-sweep colour `colour`, *n_shapes receives the number of staged
+ * shapes ({2, TY, TZ, D, R}) offered; for the one with index shape_index (none: *n_records = 0) shape receives it
+ * (5 int32, may be NULL), *smem_bytes the dynamic shared memory a CTA is launched with and *block_bytes the block
+ * stride of an FP32 pool (either may be NULL), and records (max_records x 10 int64, may be NULL) every mbarrier arm and
+ * bulk copy that the CTAs of one block issue, in issue order per CTA:
+ *   {tile (tz * n / TY + ty), kind (0 arm, 1 copy), barrier (0 first planes, 1 + g % (D + 1) group g),
+ *    group g (-1: first planes), dst (bytes from the start of dynamic shared memory; -1 for an arm),
+ *    array (0 other-half u, 1 other-half kappa, 2 own-half f, 3 own-half kappa; -1), src (bytes from the start of
+ *    the block in the pool; -1), bytes (armed or copied), lead (floats from the copy's start to the wanted plane
+ *    segment; -1), len (floats of the wanted segment; -1)}.
+ * *n_records receives the total (records beyond max_records are counted, not written).  MG_ERR_INVALID_ARG for a
+ * bad lg, coeff, colour or a null count pointer. */
+mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t shape_index, int32_t *shape,
+                              int32_t *n_shapes, int64_t *smem_bytes, int64_t *block_bytes, int64_t max_records,
+                              int64_t *records, int64_t *n_records);
+
 /* Persistent tail of the FP32 V-cycle (precision 1): from level `level` down to the coarsest and back, every step
  * (half-sweeps, exchanges, restriction, prolongation, coarsest solve) runs inside one cooperative kernel launch
  * whose CTAs stay resident and meet at grid barriers, instead of one launch per step.  Results are bit-identical

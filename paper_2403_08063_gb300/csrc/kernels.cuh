@@ -83,6 +83,14 @@ __device__ inline void face_xyz(int axis, int side, int depth, int i1, int i2, i
 // Row length of one half in the FP32 split layout: the (n+2)/2 cells of a parity.
 __host__ __device__ constexpr int half_row(int P) { return P >> 1; }
 
+// Block stride of a level's pools, in elements: one stride for both precisions, the natural FP64 block or the FP32
+// split block (the same size), rounded to 64 elements, so every block and FP32 half starts on a 16-byte boundary and
+// a bulk copy widened to 16-byte bounds at the end of the last block stays inside the pool.
+__host__ __device__ constexpr int64_t block_stride(int P) {
+    const int64_t nat = static_cast<int64_t>(P) * P * P, split = 2 * static_cast<int64_t>(P) * P * half_row(P);
+    return ((nat > split ? nat : split) + 63) / 64 * 64;
+}
+
 template <typename T> struct Lay;
 template <> struct Lay<double> {
     __device__ static int64_t at(const LevelGeom &g, int64_t b, int X, int Y, int Z) {
@@ -757,6 +765,92 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // ------------------------------------------------------------------------------------------------------------
+// Copy plan of the staged half-sweep below (k_smooth32t), shared by the kernel's producer thread, the launch code
+// (dynamic shared-memory size) and the host-side enumerator that checks every copy against the bulk-copy rules.
+//
+// Shared memory, in floats from the start: RO = D + 2 other-half slots of so floats (u; with variable k, kappa
+// after it), then RW = D + 1 own-half slots of sw floats (f; kappa after it), then 2 G + 2 mbarriers (G = D + 1).
+// A plane segment of len floats starting at float off of its half is copied from off & ~3 (the 16-byte boundary
+// at or below it), (off & 3) + len floats rounded up to a multiple of 4, so it lands off & 3 floats into its slot.
+// ------------------------------------------------------------------------------------------------------------
+struct S32tPlan {
+    int P, H, NA, RO, RW, G;  // padded edge, half-row length, staged arrays per half, ring sizes, group barriers
+    int lo, lw, so, sw;       // other / own segment lengths and slot strides (floats)
+};
+__host__ __device__ __forceinline__ S32tPlan s32t_plan(int lg, bool var, int TY, int D) {
+    S32tPlan p;
+    p.P = (1 << lg) + 2;
+    p.H = half_row(p.P);
+    p.NA = var ? 2 : 1;
+    p.RO = 2 + D;
+    p.RW = 1 + D;
+    p.G = 1 + D;
+    p.lo = (TY + 2) * p.H;
+    p.lw = TY * p.H;
+    p.so = (p.lo + 6) & ~3;  // room for the widening to 16-byte bounds
+    p.sw = (p.lw + 6) & ~3;
+    return p;
+}
+__host__ __device__ __forceinline__ int s32t_other_slot(const S32tPlan &p, int i) { return i * p.NA * p.so; }
+__host__ __device__ __forceinline__ int s32t_own_slot(const S32tPlan &p, int i) {
+    return p.NA * p.RO * p.so + i * p.NA * p.sw;
+}
+__host__ __device__ __forceinline__ int s32t_bar_floats(const S32tPlan &p) { return p.NA * (p.RO * p.so + p.RW * p.sw); }
+__host__ __device__ __forceinline__ size_t s32t_smem_bytes(const S32tPlan &p) {
+    return static_cast<size_t>(4) * s32t_bar_floats(p) + static_cast<size_t>(8) * (2 * p.G + 2);
+}
+// start (floats, within a half) of the other-half segment of padded plane Zp (rows y0 - 1 .. y0 + TY) and of the
+// own-half one (rows y0 .. y0 + TY - 1)
+__host__ __device__ __forceinline__ int s32t_off_other(const S32tPlan &p, int Zp, int y0) { return (Zp * p.P + y0) * p.H; }
+__host__ __device__ __forceinline__ int s32t_off_own(const S32tPlan &p, int Zp, int y0) { return (Zp * p.P + y0 + 1) * p.H; }
+__host__ __device__ __forceinline__ uint32_t s32t_bytes(int off, int len) {
+    return static_cast<uint32_t>(((off & 3) + len + 3) & ~3) * 4;
+}
+// The copies of one CTA.  sink.arm(bar, bytes) arms barrier `bar` (0: the first planes; 1 + g % G: group g) with
+// the bytes that will complete it; sink.copy(dst, array, src, lead, bytes, bar) copies `bytes` from float `src` of
+// `array` (0 other-half u, 1 other-half kappa, 2 own-half f, 3 own-half kappa) to shared float `dst`, the wanted
+// segment starting `lead` floats into the copy.
+// First: other-half padded planes z0 and z0 + 1 (planes z0 - 1 and z0) into other slots 0 and 1.
+template <class Sink>
+__host__ __device__ __forceinline__ void s32t_issue_first(const S32tPlan &p, int z0, int y0, Sink &&sink) {
+    const int o0 = s32t_off_other(p, z0, y0), o1 = s32t_off_other(p, z0 + 1, y0);
+    const uint32_t b0 = s32t_bytes(o0, p.lo), b1 = s32t_bytes(o1, p.lo);
+    sink.arm(0, p.NA * (b0 + b1));
+    for (int io = 0; io < 2; ++io) {
+        const int off = io ? o1 : o0;
+        const uint32_t bb = io ? b1 : b0;
+        const int d = s32t_other_slot(p, io);
+        sink.copy(d, 0, off & ~3, off & 3, bb, 0);
+        if (p.NA == 2) sink.copy(d + p.so, 1, off & ~3, off & 3, bb, 0);
+    }
+}
+// Group g: other-half padded plane z0 + g + 2 (plane z0 + g + 1) into other slot (g + 2) % RO, own-half padded
+// plane z0 + g + 1 (plane z0 + g) into own slot g % RW.
+template <class Sink>
+__host__ __device__ __forceinline__ void s32t_issue_group(const S32tPlan &p, int z0, int y0, int g, Sink &&sink) {
+    const int bi = 1 + g % p.G;
+    const int oo = s32t_off_other(p, z0 + g + 2, y0), ow = s32t_off_own(p, z0 + 1 + g, y0);
+    const uint32_t bo = s32t_bytes(oo, p.lo), bw = s32t_bytes(ow, p.lw);
+    sink.arm(bi, p.NA * (bo + bw));
+    const int d0 = s32t_other_slot(p, (g + 2) % p.RO), d1 = s32t_own_slot(p, g % p.RW);
+    sink.copy(d0, 0, oo & ~3, oo & 3, bo, bi);
+    if (p.NA == 2) sink.copy(d0 + p.so, 1, oo & ~3, oo & 3, bo, bi);
+    sink.copy(d1, 2, ow & ~3, ow & 3, bw, bi);
+    if (p.NA == 2) sink.copy(d1 + p.sw, 3, ow & ~3, ow & 3, bw, bi);
+}
+// The kernel's sink: arms the CTA's mbarriers and issues the bulk copies.
+struct S32tDeviceSink {
+    float *smem;
+    const float *ou, *ok, *wf, *wk;  // other-half u, kappa; own-half f, kappa (the block's halves)
+    uint64_t *bar;
+    __device__ __forceinline__ void arm(int bi, uint32_t bytes) const { mbar_arm(&bar[bi], bytes); }
+    __device__ __forceinline__ void copy(int dst, int array, int off, int, uint32_t bytes, int bi) const {
+        const float *src = array == 0 ? ou : (array == 1 ? ok : (array == 2 ? wf : wk));
+        bulk_load(smem + dst, src + off, bytes, &bar[bi]);
+    }
+};
+
+// ------------------------------------------------------------------------------------------------------------
 // FP32 half-sweep with the other colour's planes staged in shared memory by bulk copies (block edge n = 2^LG,
 // colour-split pools with H = half_row(P)).
 //
@@ -798,16 +892,15 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, H = half_row(P), PL = P * H, HALF = P * PL;
     constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int RO = 2 + D, RW = 1 + D, G = 1 + D;
-    // a plane segment is a run of (TY + 2) H (other half) or TY H (own half) floats; it is copied from the 16-byte
-    // boundary at or below its start, so it lands e = (start & 3) floats into its slot, and slots have room for that
-    const int lo = (TY + 2) * H, lw = TY * H, so = (lo + 6) & ~3, sw = (lw + 6) & ~3;
+    const S32tPlan plan = s32t_plan(LG, MODE == 2, TY, D);
+    const int RO = plan.RO, RW = plan.RW, G = plan.G;
+    const int so = plan.so, sw = plan.sw;
     // other-half slot i: u at ou + i NA so, kappa after it; own-half slot i: f at wf + i NA sw, kappa after it
     float *ou = reinterpret_cast<float *>(smem_raw);
-    float *wf = ou + NA * RO * so;
+    float *wf = ou + s32t_own_slot(plan, 0);
     // full barriers: bar[0] planes z0 - 1, z0; bar[1 + g % G] group g.  Empty barriers (all consumer warps are done
     // with the slots): ebar[g % G] group g, ibar planes z0 - 1, z0 moved into registers
-    uint64_t *bar = reinterpret_cast<uint64_t *>(wf + NA * RW * sw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ou + s32t_bar_floats(plan));
     uint64_t *ebar = bar + 1 + G, *ibar = ebar + G;
 
     const int nty = n / TY;
@@ -827,35 +920,12 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
     const float *gou = u + base + (s ^ 1) * HALF, *gok = kap + base + (s ^ 1) * HALF;
     const float *gwf = f + base + s * HALF, *gwk = kap + base + s * HALF;
 
-    // start (floats, within a half) of the other-half segment of padded plane Zp and of the own-half one
-    const auto off_o = [&](int Zp) { return (Zp * P + y0) * H; };
-    const auto off_w = [&](int Zp) { return (Zp * P + y0 + 1) * H; };
-    const auto bytes_of = [](int off, int len) { return static_cast<uint32_t>(((off & 3) + len + 3) & ~3) * 4; };
-    const auto copy = [](float *dst, const float *half, int off, uint32_t bytes, uint64_t *b) {
-        bulk_load(dst, half + (off & ~3), bytes, b);
-    };
-    const auto issue_first = [&]() {  // other-half planes z0 - 1 and z0 (padded Z z0, z0 + 1) into slots 0, 1
-        const uint32_t b0 = bytes_of(off_o(z0), lo), b1 = bytes_of(off_o(z0 + 1), lo);
-        mbar_arm(&bar[0], NA * (b0 + b1));
-        for (int io = 0; io < 2; ++io) {
-            const int off = off_o(z0 + io);
-            const uint32_t bb = io ? b1 : b0;
-            copy(ou + io * NA * so, gou, off, bb, &bar[0]);
-            if constexpr (MODE == 2) copy(ou + io * NA * so + so, gok, off, bb, &bar[0]);
-        }
-    };
-    const auto issue_group = [&](int g) {  // other plane z0 + g + 1 (padded z0 + g + 2), own plane z0 + g
-        uint64_t *bg = &bar[1 + g % G];
-        const int oo = off_o(z0 + g + 2), ow = off_w(z0 + 1 + g);
-        const uint32_t bo = bytes_of(oo, lo), bw = bytes_of(ow, lw);
-        mbar_arm(bg, NA * (bo + bw));
-        float *d0 = ou + ((g + 2) % RO) * NA * so;
-        copy(d0, gou, oo, bo, bg);
-        if constexpr (MODE == 2) copy(d0 + so, gok, oo, bo, bg);
-        float *d1 = wf + (g % RW) * NA * sw;
-        copy(d1, gwf, ow, bw, bg);
-        if constexpr (MODE == 2) copy(d1 + sw, gwk, ow, bw, bg);
-    };
+    const auto off_o = [&](int Zp) { return s32t_off_other(plan, Zp, y0); };
+    const auto off_w = [&](int Zp) { return s32t_off_own(plan, Zp, y0); };
+    // the producer's copies, as planned by s32t_issue_first / s32t_issue_group
+    const S32tDeviceSink sink{ou, gou, gok, gwf, gwk, bar};
+    const auto issue_first = [&]() { s32t_issue_first(plan, z0, y0, sink); };
+    const auto issue_group = [&](int g) { s32t_issue_group(plan, z0, y0, g, sink); };
     const int nthc = blockDim.x - 32, ncw = nthc >> 5;  // consumer threads and warps; the last warp produces
     if (tid == 0) {
         for (int i = 0; i < 1 + G; ++i) mbar_init(&bar[i], 1);

@@ -158,11 +158,7 @@ const Smooth32tFn kSmooth32t[2][3][3] = {
 
 bool smooth32_specialised(const DevLevel &d) { return d.g.lg >= 2 && d.g.lg <= 7; }
 
-size_t smooth32t_smem(int lg, bool var, int TY, int D) {
-    const int P = (1 << lg) + 2, H = half_row(P), NA = var ? 2 : 1;
-    const int so = ((TY + 2) * H + 6) & ~3, sw = (TY * H + 6) & ~3;  // slots with room for 16-byte widening
-    return static_cast<size_t>(4) * NA * ((2 + D) * so + (1 + D) * sw) + 8 * (4 + 2 * D);
-}
+size_t smooth32t_smem(int lg, bool var, int TY, int D) { return s32t_smem_bytes(s32t_plan(lg, var, TY, D)); }
 
 int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
 
@@ -1123,12 +1119,7 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         d.g.n = h.n;
         d.g.lg = ilog2(h.n);
         d.g.P = h.n + 2;
-        // one stride for both precisions: the natural FP64 block or the FP32 split block (the same size), rounded
-        // to 64 elements, so every block and FP32 half starts on a 16-byte boundary and a bulk copy widened to
-        // 16-byte bounds at the end of the last block stays inside the pool
-        const int64_t per = std::max<int64_t>(static_cast<int64_t>(d.g.P) * d.g.P * d.g.P,
-                                              2 * static_cast<int64_t>(d.g.P) * d.g.P * half_row(d.g.P));
-        d.g.bs = (per + 63) / 64 * 64;
+        d.g.bs = block_stride(d.g.P);
         d.nfaces = static_cast<int>(h.faces.size());
         d.nsegs = static_cast<int>(h.segs.size());
         if ((st = upload(F, &d.faces, h.faces)) != MG_OK) return fail(st);
@@ -1612,6 +1603,66 @@ mg_status mg_smoother_shapes(const mg_forest *F, int32_t level, int32_t max_shap
     *n_shapes = static_cast<int32_t>(v.size());
     for (int i = 0; i < static_cast<int>(v.size()) && i < max_shapes && shapes; ++i)
         for (int k = 0; k < 5; ++k) shapes[5 * i + k] = v[i][k];
+    return MG_OK;
+}
+
+mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t shape_index, int32_t *shape,
+                              int32_t *n_shapes, int64_t *smem_bytes, int64_t *block_bytes, int64_t max_records,
+                              int64_t *records, int64_t *n_records) {
+    if (lg < 5 || lg > 7 || coeff < 0 || coeff > 1 || colour < 0 || colour > 1 || shape_index < 0 || !n_shapes ||
+        !n_records || max_records < 0) {
+        set_error("mg_staged_copy_plan: lg 5..7, coeff and colour 0 or 1, shape_index >= 0, outputs not null");
+        return MG_ERR_INVALID_ARG;
+    }
+    DevLevel d;
+    d.g.n = 1 << lg;
+    d.g.lg = lg;
+    d.g.P = d.g.n + 2;
+    std::vector<Shape> staged;
+    for (const Shape &sh : smooth32_shapes(d, coeff != 0))
+        if (sh[0] == 2) staged.push_back(sh);
+    *n_shapes = static_cast<int32_t>(staged.size());
+    *n_records = 0;
+    if (shape_index >= static_cast<int32_t>(staged.size())) return MG_OK;
+    const Shape sh = staged[shape_index];
+    if (shape)
+        for (int k = 0; k < 5; ++k) shape[k] = sh[k];
+    const int TY = sh[1], TZ = sh[2], D = sh[3], n = d.g.n;
+    const S32tPlan plan = s32t_plan(lg, coeff != 0, TY, D);
+    const int64_t half = static_cast<int64_t>(plan.P) * plan.P * plan.H;
+    const int64_t bs = block_stride(d.g.P);
+    if (smem_bytes) *smem_bytes = static_cast<int64_t>(smooth32t_smem(lg, coeff != 0, TY, D));
+    if (block_bytes) *block_bytes = 4 * bs;
+    // the kernel's halves: the colour being updated is stored in half s = colour ^ 1, the other one in half colour
+    const int64_t own = (colour ^ 1) * half, other = static_cast<int64_t>(colour) * half;
+    struct HostSink {
+        int64_t *rec, cap, *cnt, tile, group, other, own;
+        const S32tPlan *p;
+        void put(const int64_t (&v)[10]) {
+            if (*cnt < cap && rec)
+                for (int i = 0; i < 10; ++i) rec[10 * *cnt + i] = v[i];
+            ++*cnt;
+        }
+        void arm(int bi, uint32_t bytes) { put({tile, 0, bi, group, -1, -1, -1, static_cast<int64_t>(bytes), -1, -1}); }
+        void copy(int dst, int array, int off, int lead, uint32_t bytes, int bi) {
+            const int64_t src = (array < 2 ? other : own) + off;
+            const int len = array < 2 ? p->lo : p->lw;
+            put({tile, 1, bi, group, 4 * static_cast<int64_t>(dst), array, 4 * src, static_cast<int64_t>(bytes), lead,
+                 len});
+        }
+    };
+    HostSink sink{records, max_records, n_records, 0, -1, other, own, &plan};
+    for (int tz = 0; tz < n / TZ; ++tz)
+        for (int ty = 0; ty < n / TY; ++ty) {
+            sink.tile = static_cast<int64_t>(tz) * (n / TY) + ty;
+            const int y0 = ty * TY, z0 = tz * TZ;
+            sink.group = -1;
+            s32t_issue_first(plan, z0, y0, sink);
+            for (int g = 0; g < TZ; ++g) {
+                sink.group = g;
+                s32t_issue_group(plan, z0, y0, g, sink);
+            }
+        }
     return MG_OK;
 }
 
