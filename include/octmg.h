@@ -148,16 +148,20 @@ mg_status mg_apply_transpose(mg_forest *forest, const double *y_dev, double *ATy
  * doubles, block-major, x fastest) to padded_dev. */
 mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
 
-/* mg_exchange_level without device allocation.  The paper has no counterpart: this serves callers that cannot
- * call cudaMalloc at the time they need the exchange (during a CUDA stream capture, when all device memory is owned
- * by a caching allocator, or in loops that must not enter CUDA's device allocator).  Same arguments, result and
- * errors as mg_exchange_level, but the level's padded scratch pool is a static device array of 524,288 doubles
- * (4 MiB) inside the library, which every GPU that loads the library holds until the process exits; a level whose
- * pool (nb * (n+2)^3 rounded up to 32 doubles per block) is larger is rejected with MG_ERR_INVALID_ARG and a
- * message.  The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  All calls share the array: calls whose work overlaps on the GPU (other
- * streams, other threads, other forests) race on it.  The call clears the part of the array it uses, enqueues
- * its work on the forest's stream and synchronises that stream before returning. */
+/* mg_exchange_level without device allocation.  The paper has no counterpart: this serves callers that cannot let
+ * a library call cudaMalloc when they need the exchange -- applications whose device memory is entirely owned by a
+ * caching allocator or reserved at start-up, and loops with a latency budget that must not enter CUDA's device
+ * allocator.  Same arguments and result as mg_exchange_level, but the level's padded scratch pool is a static
+ * device array of 524,288 doubles (4 MiB) inside the library, which every GPU that loads the library holds until
+ * the process exits; a level whose pool (nb * (n+2)^3 rounded up to 32 doubles per block) is larger is rejected
+ * with MG_ERR_INVALID_ARG and a message.  Nothing else is allocated either: on a variable-k forest with FP32
+ * cycles (precision 1) and conservative interfaces, the FP64 face coefficients that the fine-to-coarse ghosts
+ * need are created by the first mg_exchange_level, mg_apply or mg_adjoint_solve call; before that, a level with
+ * fine-to-coarse ghosts returns MG_ERR_STATE.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it.  All calls share the array and it keeps the last call's contents (each
+ * call clears the part it uses): calls whose work overlaps on the GPU (other streams, other threads, other
+ * forests) race on it.  The call enqueues its work on the forest's stream and synchronises that stream before
+ * returning. */
 mg_status mg_exchange_level_noalloc(mg_forest *forest, int32_t level, const double *u_dev, double *padded_dev);
 
 /* Kernel accounting (no counterpart in the paper).  Launch counters per kernel family always run; mg_profile(forest, 1) clears them and starts

@@ -1,11 +1,13 @@
 // mg_exchange_level_noalloc: the one-level ghost exchange of mg_exchange_level without any device allocation.
 //
 // mg_exchange_level allocates (cudaMalloc) a padded scratch pool for the level on every call and frees it
-// afterwards.  Callers that cannot allocate device memory at that point -- code running while a CUDA stream capture
-// is in progress (allocation is not a stream operation and breaks or invalidates the capture), applications whose
-// device memory is entirely handed to a caching allocator or pre-reserved at start-up, or real-time loops that
-// must not enter CUDA's device allocator -- use this variant.  Its scratch pool is the file-scope device array below,
-// of a fixed size; every GPU that loads the library holds that array until the process exits.
+// afterwards.  Some callers cannot let a library allocate device memory at that point: applications whose device
+// memory is entirely handed to a caching allocator or reserved at start-up (a cudaMalloc then fails or steals
+// from the pool), and loops with a latency budget that must not enter CUDA's device allocator (cudaMalloc and
+// cudaFree can synchronise the device and take unbounded time).  They use this variant.  Its scratch pool is the
+// file-scope device array below, of a fixed size; every GPU that loads the library holds that array until the
+// process exits.  The call allocates nothing else either: on a forest whose FP64 face coefficients do not exist
+// yet (variable k with FP32 cycles creates them on first use) it returns MG_ERR_STATE instead of creating them.
 #include <mutex>
 
 #include "forest_state.h"
@@ -55,8 +57,15 @@ extern "C" mg_status mg_exchange_level_noalloc(mg_forest *F, int32_t level, cons
         set_error("mg_set_rhs (k) has not been called");
         return MG_ERR_STATE;
     }
-    MG_TRY(ensure_fp64_coefficients(F));
     DevLevel &d = F->L[level];
+    // The conservative fine-to-coarse ghosts of a variable-k forest read the level's FP64 face coefficients.  A
+    // forest with FP32 cycles creates those arrays lazily (cudaMalloc), which this entry point must not do.
+    if (F->cfg.coeff && F->cfg.interface_flux && d.nsegs && (!d.tx || !d.ty || !d.tz)) {
+        set_error("mg_exchange_level_noalloc: the FP64 face coefficients of level " + std::to_string(level) +
+                  " do not exist yet (a variable-k forest with FP32 cycles creates them on first use, which "
+                  "allocates); call mg_exchange_level, mg_apply or mg_adjoint_solve once first");
+        return MG_ERR_STATE;
+    }
     const int64_t need = d.pool_elems();
     if (need > kScratchElems) {
         set_error("mg_exchange_level_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
