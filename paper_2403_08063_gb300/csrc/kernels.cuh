@@ -176,6 +176,17 @@ __device__ inline float frcp(float x) {
     return r;
 }
 
+// t / 6 for the constant-coefficient FP32 smoothers.  Multiplying by the binary32 value of 1/6, which is 3.0e-8
+// (relative) too large, biases every update the same way, and the bias accumulates over the sweeps of a cycle
+// (the FP32 V-cycle landed 17x further from the FP64 cycle than a plain FP32 evaluation).  Splitting 1/6 into a
+// head and a tail that sum to it within 2^-48 and rounding once in an FMA gives t / 6 to within about half an ulp
+// with no bias.
+__device__ __forceinline__ float div6(float t) {
+    constexpr float hi = 1.0f / 6.0f;
+    constexpr float lo = static_cast<float>(1.0 / 6.0 - static_cast<double>(1.0f / 6.0f));
+    return fmaf(t, hi, t * lo);
+}
+
 // Conversions between binary64 and binary32 with an exact power-of-two scale, written on the IEEE 754 bit fields
 // (1 sign bit; 11 / 8 exponent bits with bias 1023 / 127; 52 / 23 fraction bits) so that they run on the integer
 // pipes: the hardware conversion instructions between the two formats issue on the FP64 pipe, the bottleneck of
@@ -499,7 +510,7 @@ static __global__ void k_smooth(T *__restrict__ u, const T *__restrict__ f, Coef
             const int64_t izm = oth - static_cast<int64_t>(P) * hp + m, izp = oth + static_cast<int64_t>(P) * hp + m;
             if constexpr (MODE == 0) {
                 const float S = ((u[ixm] + u[ixp]) + (u[iym] + u[iyp])) + (u[izm] + u[izp]);
-                val = T(fmaf(float(h2[b]), float(f[own]), S) * (1.0f / 6.0f));
+                val = T(div6(fmaf(float(h2[b]), float(f[own]), S)));
             } else {
                 const float *kap = cf.kap;
                 const float k0 = kap[own];
@@ -671,7 +682,7 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
             val[dz] = fmaf(hh, fv[dz], sacc) * frcp(D);
         } else {
             const float S = ((xr0[dz] + xr1[dz]) + (ym[dz] + yp[dz])) + (zm + zp);
-            val[dz] = fmaf(hb, fv[dz], S) * (1.0f / 6.0f);
+            val[dz] = div6(fmaf(hb, fv[dz], S));
         }
     }
 #pragma unroll
@@ -1045,7 +1056,7 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
                         val = fmaf(hh, fv, sacc) * frcp(Dn);
                     } else {
                         const float S = ((pc[rr][0] + pc[rr][1]) + (ym + yp)) + (zmu[rr] + zp);
-                        val = fmaf(hb, fv, S) * (1.0f / 6.0f);
+                        val = div6(fmaf(hb, fv, S));
                     }
                     const int q = qz + rr * qstep + C;
                     us[q] = val;
