@@ -64,9 +64,8 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launch
     """Algorithmic bytes and FP64 flops of one family over the timed region.
 
     Per cell of the level a launch sweeps:
-      smooth_f32      10 B   (one colour half-sweep on colour-split FP32 blocks: the other colour's u, 2 B; this
-                             colour's f, 2 B; 1/k of both colours, 4 B; this colour's u written, 2 B.  6 B for
-                             constant k)
+      smooth_f32       8 B   (half of a full red-black iteration's u, f, k read and u written, 4 B each; 6 B for
+                             constant k.  The two-launch schedule itself moves 10 B: see _SCHEDULE_BYTES_HALF_SWEEP)
       smooth_f64      12 B   (24 B/cell RBGS iteration for -Laplace in FP64: u, f, u)
       residual_f64    32 B   (u, f, k read as FP64; r written as FP32; FP32 correction zeroed) and 27 FP64 flops
                              (stencil 11, diagonal 5, residual 4, scaling 1, two volume-weighted norms 6)
@@ -74,7 +73,7 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launch
     """
     cells = [nb * n ** 3 for nb, n in levels]
     sweeps = 2 * (nu1 + nu2)
-    f32b = 10 if coeff else 6
+    f32b = _ALG_BYTES_HALF_SWEEP[bool(coeff)]
     if fam == "smooth_f32_finest":
         return cells[0] * f32b * launches, 0.0
     if fam == "smooth_f64_finest":
@@ -95,11 +94,23 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launch
 
 # DRAM bytes per cell of the level per launch, from one ncu capture of the kernel on the 16.8M-cell case
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the level's cells), scaled here to the launch's cells
-# (the traffic grows in proportion to the cells).  Kernel and source summary in profiles/.
+# (the traffic grows in proportion to the cells).
 _NCU_TRAFFIC_PER_CELL = {
-    "smooth_f32_finest": (164.7e6 / 16777216, "profiles/k_smooth32t_uniform_4x64_k.md"),
+    "smooth_f32_finest": (164.7e6 / 16777216, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                          "k_smooth32t<2,6,4> launch on 4^3 roots of 64^3 cells (16,777,216 cells, log-normal k), "
+                          "scaled by cells"),
 }
 
+# Algorithmic bytes of the FP32 red-black smoother per cell: a full iteration reads u, f and k and writes u once,
+# 4 B each, 16 B per cell (12 B with constant k), i.e. 8 (6) B per one-colour launch.  The two-launch schedule moves
+# 10 B per launch with variable k (the other colour's u, this colour's f, both colours' 1/k, this colour's u written)
+# and the same 6 B with constant k.
+_ALG_BYTES_HALF_SWEEP = {True: 8.0, False: 6.0}
+_SCHEDULE_BYTES_HALF_SWEEP = {True: 10.0, False: 6.0}
+# Bytes per finest cell per V(2,2) cycle (FP32 cycles, variable k, levels summed with the 8/7 geometric factor):
+# the unfused model with one FP64 outer residual per cycle, and the minimum of one fused down- and up-pass per level.
+_CYCLE_BYTES_MIXED = 78.0
+_CYCLE_BYTES_ALG_MIN = 37.7
 
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 
@@ -213,6 +224,29 @@ ORACLE_SAMPLE = ("uniform_2x64", "2^3 roots of 64^3 cells (2,097,152 cells) of t
                  "U(-1,1) f), FP64 V(2,2) cycles of the numpy oracle; cores = process CPU time / wall time")
 
 
+def _host_cpu():
+    """The host's logical CPU count and CPU model (/proc/cpuinfo, else lscpu, else the machine name)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith(("model name", "vendor id")):
+                    model = (model + " / " if model else "") + line.split(":", 1)[1].strip()
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def _cores(cpu_s, wall_s):
     """Host cores the timed oracle loop kept busy: process CPU time (all threads) over wall time, at least 1."""
     return max(1, round(cpu_s / wall_s))
@@ -253,7 +287,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample": ORACLE_SAMPLE[0]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": ORACLE_SAMPLE[1]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": ORACLE_SAMPLE[1],
+                         **_host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -273,7 +308,7 @@ def cpu_baseline(budget_s=12.0):
     dt = time.perf_counter() - t0
     cores = _cores(time.process_time() - c0, dt)
     return {"value": cells * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{ORACLE_SAMPLE[1]}; {n} cycles in {dt:.1f} s"}
+            "sample": f"{ORACLE_SAMPLE[1]}; {n} cycles in {dt:.1f} s", **_host_cpu()}
 
 
 # ------------------------------------------------------------------------------------------------------------
@@ -358,9 +393,17 @@ def run_ours(args):
             tr = _NCU_TRAFFIC_PER_CELL.get(fam) if args.workload.startswith("uniform") and coeff else None
             roof = {"kernel": fam, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": tr[0] * levels[0][0] * levels[0][1] ** 3 if tr else None, "peak_source": src,
+                    "algorithmic_bytes_per_cell": _ALG_BYTES_HALF_SWEEP[coeff] if fam.startswith("smooth_f32")
+                    else None,
                     "frac_of_nominal": ach / HBM_NOMINAL_GBS, "nominal_peak": HBM_NOMINAL_GBS}
+            if fam.startswith("smooth_f32"):
+                sched = _SCHEDULE_BYTES_HALF_SWEEP[coeff] / _ALG_BYTES_HALF_SWEEP[coeff]
+                roof["schedule_bytes_per_cell"] = _SCHEDULE_BYTES_HALF_SWEEP[coeff]
+                roof["frac_schedule_bytes"] = ach * sched / hbm
+                roof["schedule_over_algorithmic"] = sched
             if tr:
-                roof["traffic_source"] = tr[1] + " (captured on 4^3 blocks of 64^3, scaled by cells)"
+                roof["traffic_source"] = tr[1]
+                roof["traffic_bytes_per_cell"] = tr[0]
         roof["launches"] = prof[fam][1]
         roof["avg_launch_ms"] = prof[fam][0] / max(1, prof[fam][1])
 
@@ -425,6 +468,15 @@ def run_ours(args):
             "time_to_rtol_s": {"fp32_in_fp64": tmix, "fp64": t64, "speedup": t64 / tmix},
             "fp64_cycles_per_solve": cyc64, "fp64_glups_per_cycle": cells * statistics.mean(cyc64) / t64 / 1e9,
             "roofline": roof,
+            "cycle_roofline": {
+                "glups": value, "peak_gbs": hbm, "peak_source": src,
+                "bytes_per_cell_cycle": _CYCLE_BYTES_MIXED,
+                "achieved_gbs": value * _CYCLE_BYTES_MIXED, "frac": value * _CYCLE_BYTES_MIXED / hbm,
+                "alg_min_bytes_per_cell_cycle": _CYCLE_BYTES_ALG_MIN,
+                "achieved_gbs_alg_min": value * _CYCLE_BYTES_ALG_MIN,
+                "frac_alg_min": value * _CYCLE_BYTES_ALG_MIN / hbm,
+                "models": "78 B: FP32 V(2,2) with four smoother passes, residual+restriction and prolongation per "
+                          "level plus one FP64 residual per cycle; 37.7 B: one fused down- and up-pass per level"},
             "setup_ms": {"mg_set_rhs": round(setup_ms, 3), "in_value": False},
             "smoother_finest": _smoother_report(prof, cells),
             "kernel_families_ms": {k_: round(v[0], 3) for k_, v in prof.items() if v[1]},
@@ -438,12 +490,179 @@ def run_ours(args):
             "clocks": clocks,
         }
     F.close()
+    del F64
+    if rank == 0 and ws == 1 and not getattr(args, "no_other_configs", False):
+        torch.cuda.empty_cache()
+        out["other_configs"] = run_other_configs(dev)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------------------
+# the other configurations of the benchmark set, each timed with its own clock record (rank 0, N = 1)
+# ------------------------------------------------------------------------------------------------------------
+def _timed(fn, reps):
+    """Mean seconds of reps calls of fn, CUDA events on the current stream around them (synchronised)."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = [fn() for _ in range(reps)]
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3 / reps
+
+
+def _cfg_small(dev):
+    """2^3 roots of 16^3 (32,768 cells), -Laplace with the sin-product right-hand side, FP64 V(2,2), exactly 10
+    cycles: launch-latency-bound, reported as microseconds per cycle."""
+    import synthetic as syn
+    from paper_2403_08063_gb300 import Forest
+    R, n, keys = syn.workload_forest("uniform_2x16")
+    f = syn.sin_product_rhs(R, n, keys).to(dev)
+    F = Forest(R, n, keys, precision=0)
+    F.set_rhs(f)
+    u = torch.zeros_like(f)
+
+    def run():
+        u.zero_()
+        return F.vcycle(u, 10)
+
+    for _ in range(3):
+        run()
+    rels, t = _timed(run, 20)
+    ue = syn.sin_product(R, n, keys).to(dev)
+    err = float(torch.sqrt(((u - ue) ** 2).sum() / (R * n) ** 3))
+    F.close()
+    cells = len(keys) * n ** 3
+    return {"workload": "uniform_2x16 (2^3 roots of 16^3, sin-product f)", "cells": cells, "dtype": "f64",
+            "cycles": 10, "us_per_cycle": t / 10 * 1e6, "glups_per_cycle": cells * 10 / t / 1e9,
+            "rel_residual_after_10": rels[-1], "l2_error_vs_exact": err,
+            "timing": "20 repetitions of 10 cycles from u = 0 (each ends with the residual and the copy of u)"}
+
+
+def _cfg_refined(dev):
+    """The refined 56 + 64 block forest of 32^3 blocks (3,932,160 cells), Gaussian bump plus noise, solved to
+    1e-10 in FP64 (and with FP32 cycles inside FP64 defect correction for comparison)."""
+    import synthetic as syn
+    from paper_2403_08063_gb300 import Forest
+    R, n, keys = syn.workload_forest("sphere_2x32")
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=1, device=dev)
+    cells = len(keys) * n ** 3
+    res = {"workload": "sphere_2x32 (56 + 64 blocks of 32^3, bump + noise f)", "cells": cells, "rtol": 1e-10}
+    for name, prec, inner in (("fp64", 0, 1), ("fp32_in_fp64", 1, 4)):
+        F = Forest(R, n, keys, precision=prec, inner_cycles=inner)
+        F.set_rhs(f)
+        u = torch.zeros_like(f)
+
+        def run():
+            u.zero_()
+            return F.solve(u, rtol=1e-10, max_cycles=60)
+
+        run()
+        out, t = _timed(run, 5)
+        cyc = out[-1][0]
+        res[name] = {"time_to_rtol_ms": t * 1e3, "cycles": cyc, "glups_per_cycle": cells * cyc / t / 1e9,
+                     "final_rel_residual": out[-1][1]}
+        F.close()
+    res["speedup_fp32_in_fp64"] = res["fp64"]["time_to_rtol_ms"] / res["fp32_in_fp64"]["time_to_rtol_ms"]
+    return res
+
+
+def _cfg_adjoint(dev):
+    """The differentiation workload: 4^3 roots of 32^3 refined twice around the sphere (448 + 512 blocks,
+    31,457,280 cells), log-normal k, bump f; forward FP32-in-FP64 solve to 1e-10, then the adjoint solve (transposed
+    V-cycles) giving dL/df and dL/dk for L = 1/2 ||u - u_t||^2."""
+    import synthetic as syn
+    from paper_2403_08063_gb300 import Forest
+    R, n, keys = syn.workload_forest("sphere_4x32")
+    k = syn.lognormal_k_rff(R, n, keys, seed=5, device=dev)
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=6, device=dev)
+    ut = syn.sin_target(R, n, keys, seed=7, device=dev)
+    cells = len(keys) * n ** 3
+    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=4)
+    t0 = time.perf_counter()
+    F.set_rhs(f, k)
+    torch.cuda.synchronize()
+    first_setup_s = time.perf_counter() - t0
+    u = torch.zeros_like(f)
+
+    def fwd():
+        u.zero_()
+        return F.solve(u, rtol=1e-10, max_cycles=60)
+
+    def adj():
+        return F.adjoint(u, u - ut, want_k=True, rtol=1e-10)
+
+    fwd()
+    adj()
+    fo, tf = _timed(fwd, 3)
+    _ao, ta = _timed(adj, 3)
+    _, ts = _timed(lambda: F.set_rhs(f, k), 3)
+    F.close()
+    return {"workload": "sphere_4x32 (448 + 512 blocks of 32^3, log-normal k, bump f, sin target)",
+            "cells": cells, "forward_ms": tf * 1e3, "forward_cycles": fo[-1][0], "adjoint_ms": ta * 1e3,
+            "forward_plus_adjoint_ms": (tf + ta) * 1e3, "setup_ms": ts * 1e3, "first_setup_s": first_setup_s,
+            "forward_glups_per_cycle": cells * fo[-1][0] / tf / 1e9,
+            "adjoint": "lambda = A^-T (u - u_t) to 1e-10 by defect correction with the transposed V-cycle, "
+                       "dL/df = lambda, dL/dk face by face"}
+
+
+def _cfg_batch(dev):
+    """256 independent single-root problems (block sizes 16..128, 0-2 refinement levels, log-normal k, U(-1, 1)
+    f), each solved to 1e-8 with FP32 cycles inside FP64 defect correction, one graph launch per step."""
+    import synthetic as syn
+    from paper_2403_08063_gb300 import Batch
+    t0 = time.perf_counter()
+    problems = syn.batch_problems(count=256, seed=0)
+    leaves, ns = syn.batch_leaves(problems)
+    f, k = syn.batch_fields(problems, seed=0, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    cells = f.numel()
+    t0 = time.perf_counter()
+    B = Batch(leaves, ns, coeff=True, inner_cycles=5)
+    B.set_rhs(f, k)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    u = torch.zeros_like(f)
+
+    def run():
+        u.zero_()
+        return B.solve(u, rtol=1e-8, max_cycles=60)
+
+    run()
+    out, t = _timed(run, 2)
+    cyc = max(out[-1][0])
+    info = B.info()
+    B.close()
+    del f, k, u
+    torch.cuda.empty_cache()
+    return {"workload": "batch_256", "problems": 256, "cells": cells, "groups": info["groups"], "rtol": 1e-8,
+            "solve_ms": t * 1e3, "cycles_max": cyc, "glups_per_cycle": cells * cyc / t / 1e9,
+            "worst_rel_residual": max(out[-1][1]), "inputs_s": gen_s, "create_and_first_setup_s": setup_s,
+            "timing": "2 solves after 1 warm-up, graph-launched"}
+
+
+def run_other_configs(dev):
+    out = {}
+    for name, fn in (("c1_uniform_2x16_fp64", _cfg_small), ("c2_sphere_2x32", _cfg_refined),
+                     ("c5_sphere_4x32_adjoint", _cfg_adjoint), ("c4_batch_256", _cfg_batch)):
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        w0 = time.perf_counter()
+        try:
+            rec = fn(dev)
+        except Exception as e:  # a failing extra configuration must not hide the headline line
+            rec = {"error": f"{type(e).__name__}: {e}"}
+        rec["wall_s"] = time.perf_counter() - w0
+        rec["clocks"] = sampler.stop()
+        out[name] = rec
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args):

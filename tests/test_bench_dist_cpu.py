@@ -138,7 +138,7 @@ def test_gpu_arm_json_contract_with_a_stand_in_library(monkeypatch, capsys):
     monkeypatch.setattr(bench, "ClockSampler", Sampler)
     monkeypatch.setattr(bench, "_inputs", inputs)
     args = types.SimpleNamespace(workload="uniform_8x64_k", inner_cycles=4, tail="auto", smoother_shape="",
-                                 warmup=3, steps=5, rtol=1e-10, no_cpu_baseline=True, gpus=1)
+                                 warmup=3, steps=5, rtol=1e-10, no_cpu_baseline=True, gpus=1, no_other_configs=True)
     bench.run_ours(args)
     lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -154,5 +154,19 @@ def test_gpu_arm_json_contract_with_a_stand_in_library(monkeypatch, capsys):
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
     assert d["smoother_finest"]["sweeps"] == 240
     cells = 8 * 8 ** 3  # the stand-in forest: 8 leaves of 8^3
+    # achieved = 8 algorithmic bytes per cell and one-colour launch over the family's mean launch time
+    assert abs(roof["achieved"] - 8.0 * cells * 480 / 0.1179 / 1e9) < 1e-9 * roof["achieved"]
+    assert roof["algorithmic_bytes_per_cell"] == 8.0 and roof["schedule_bytes_per_cell"] == 10.0
+    assert abs(roof["frac_schedule_bytes"] - 1.25 * roof["frac"]) < 1e-12
+    cyc = d["cycle_roofline"]
+    assert abs(cyc["achieved_gbs"] - d["value"] * 78.0) < 1e-9 and abs(cyc["frac"] * cyc["peak_gbs"] -
+                                                                     cyc["achieved_gbs"]) < 1e-9
     assert d["e2e"]["h2d_bytes_per_step"] == 2 * cells * 8 and d["e2e"]["d2h_bytes_per_step"] == cells * 8
     assert StandIn.set_rhs_calls == 4  # the timed forest's set-up, two set-up repeats, the FP64 forest's
+
+
+def test_host_cpu_description():
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench._host_cpu()
+    assert d["nproc"] == os.cpu_count() and isinstance(d["cpu_model"], str) and d["cpu_model"]
