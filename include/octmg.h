@@ -74,7 +74,9 @@ typedef struct {
  * Errors: MG_ERR_INVALID_ARG, MG_ERR_BLOCK_SIZE, MG_ERR_UNBALANCED, MG_ERR_OOM, MG_ERR_CUDA.  On error *out = NULL. */
 mg_status mg_forest_create(const mg_config *cfg, mg_forest **out);
 
-/* Free every device and host buffer of the forest (synchronises its stream).  NULL is a no-op. */
+/* Free every device and host buffer of the forest (synchronises its stream).  NULL is a no-op.  No counterpart in
+ * the paper, whose generated code keeps its blocks for the program's lifetime (Sec. 4); the lifetime call belongs to
+ * this library's C ABI. */
 void mg_forest_destroy(mg_forest *forest);
 
 /* Number of multigrid levels, and (optionally) per level the block count and block edge (host arrays of
@@ -256,7 +258,8 @@ mg_status mg_batch_profile(mg_batch *batch, int32_t enable);
 /* The multi-problem forest of group g (owned by the batch), e.g. for mg_profile_read; NULL if out of range. */
 mg_forest *mg_batch_group(mg_batch *batch, int32_t g);
 
-/* Thread-local description of the last error (empty string if none). */
+/* Thread-local description of the last error (empty string if none); the pointer stays valid until the next failing
+ * call on the same thread.  No counterpart in the paper: error reporting of this library's C ABI. */
 const char *mg_last_error(void);
 
 #ifdef __cplusplus

@@ -117,6 +117,9 @@ struct mg_forest {
     int coarse_runs = 0;                       // calls of assemble_coarse so far
     bool coarse_nograph = false;               // its recording failed: launched directly
     cudaStream_t cap_st = nullptr;             // private stream: graph recording, host-input copies
+    cudaGraphExec_t v64_graph = nullptr;       // one recorded FP64 V-cycle (vcycle64_step), replayed per cycle
+    int v64_runs = 0;                          // FP64 V-cycles run so far (recording starts at the second)
+    bool v64_nograph = false;                  // the recording failed or is not replayable: launched directly
     double *hst_f = nullptr, *hst_k = nullptr, *hst_u = nullptr;  // mg_solve_host staging buffers (user layout)
     cudaEvent_t hst_ev = nullptr;              // orders the staging copies against the forest's stream
     int8_t *pcol = nullptr;                    // colour probe (interface-free coarsest level): colour per unknown

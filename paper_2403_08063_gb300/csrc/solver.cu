@@ -101,9 +101,11 @@ void exchange(mg_forest *F, DevLevel &d, T *u, bool interface_only = false, bool
     const T *gb = nullptr;  // inhomogeneous Dirichlet data: FP64 finest level only
     if constexpr (sizeof(T) == 8)
         if (&d == &F->L[0]) gb = F->gb;
-    if (nitems && interface_only)  // C2F faces only: one thread per coarse source cell
-        k_exchange_c2f<T><<<grid_for(static_cast<int64_t>(nitems) * (d.g.n / 2) * (d.g.n / 2)), kThreads, 0, F->st>>>(
-            u, items, nitems, d.g, skip_of(F, d), F->cfg.c2f_variant);
+    if (nitems && interface_only) {  // C2F faces only: one CTA per fine face, shared intermediate extrapolations
+        const int w = d.g.n / 2 + 2, threads = d.g.n <= 8 ? 32 : (d.g.n <= 32 ? 128 : 256);
+        k_exchange_c2f_smem<T><<<nitems, threads, static_cast<size_t>(w) * w * sizeof(T), F->st>>>(
+            u, items, d.g, skip_of(F, d), F->cfg.c2f_variant);
+    }
     else if (nitems)
         k_exchange_faces<T, false><<<grid_for(static_cast<int64_t>(nitems) * d.g.n * d.g.n), kThreads, 0, F->st>>>(
             u, items, nitems, d.g, skip_of(F, d), F->cfg.c2f_variant, gb);
@@ -829,6 +831,52 @@ void vcycle64(mg_forest *F) {
     if (F->cfg.coeff) vcycle<double, 1>(F, 0, ENTRY_FULL);
     else vcycle<double, 0>(F, 0, ENTRY_FULL);
 }
+// One FP64 V-cycle on level 0, replayed from a recorded CUDA graph: the cycle's launch sequence depends only on the
+// forest, so it is recorded once, on the private stream (from the second cycle on: the first one loads the kernels,
+// which a capture does not allow), and each later cycle is one graph launch instead of one launch per step, which
+// is what small, launch-bound forests need.  Launched directly while profiling (per-family events), while the
+// caller's stream is being captured, and when the recorded cycle would not leave the damped-Jacobi ping-pong pools
+// as it found them (an odd number of sweeps per level) or the recording fails.  mg_set_boundary drops the graph.
+mg_status vcycle64_step(mg_forest *F) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MG_CUDA(cudaStreamIsCapturing(F->st, &cap));
+    if (F->prof || F->v64_nograph || cap != cudaStreamCaptureStatusNone || F->v64_runs++ == 0) {
+        vcycle64(F);
+        return MG_OK;
+    }
+    if (!F->v64_graph) {
+        std::vector<std::pair<double *, double *>> before;
+        for (const DevLevel &d : F->L) before.emplace_back(d.u64, d.u64b);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = F->cap_st ? cudaSuccess : cudaStreamCreateWithFlags(&F->cap_st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(F->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaStream_t own = F->st;
+            F->st = F->cap_st;
+            vcycle64(F);
+            F->st = own;
+            e = cudaStreamEndCapture(F->cap_st, &graph);
+        }
+        bool same = true;  // nothing ran during the recording: the iterate is still where it was
+        for (size_t i = 0; i < F->L.size(); ++i) {
+            same = same && F->L[i].u64 == before[i].first;
+            F->L[i].u64 = before[i].first;
+            F->L[i].u64b = before[i].second;
+        }
+        if (e == cudaSuccess && graph && same) e = cudaGraphInstantiate(&F->v64_graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || !same || !F->v64_graph) {
+            F->v64_graph = nullptr;
+            F->v64_nograph = true;
+            cudaGetLastError();
+            vcycle64(F);
+            return MG_OK;
+        }
+    }
+    MG_CUDA(cudaGraphLaunch(F->v64_graph, F->st));
+    return MG_OK;
+}
+
 // The FP32 correction on level 0 either was just zeroed with its face ghosts (k_residual_norm) or ends a previous
 // FP32 V-cycle whose last half-sweeps wrote its same-level and boundary ghosts through.
 void vcycle32(mg_forest *F) {
@@ -1018,7 +1066,7 @@ mg_status run_cycles(mg_forest *F, double *u_dev, double rtol, int max_cycles, i
     bool finite = true;
     if (F->cfg.precision == 0) {
         while (done < max_cycles) {
-            vcycle64(F);
+            MG_TRY(vcycle64_step(F));
             ++done;
             if (rtol >= 0.0 || done == max_cycles) {
                 MG_TRY(upload_scales(F, mult));
@@ -1405,6 +1453,7 @@ void mg_forest_destroy(mg_forest *F) {
     if (F->pinv_h) cudaFreeHost(F->pinv_h);
     if (F->pdone_h) cudaFreeHost(F->pdone_h);
     if (F->coarse_graph) cudaGraphExecDestroy(F->coarse_graph);
+    if (F->v64_graph) cudaGraphExecDestroy(F->v64_graph);
     if (F->cap_st) cudaStreamDestroy(F->cap_st);
     if (F->hst_ev) cudaEventDestroy(F->hst_ev);
     delete F;
@@ -1527,6 +1576,11 @@ mg_status mg_set_boundary(mg_forest *F, const double *g_dev) {
     if (!F) {
         set_error("null forest");
         return MG_ERR_INVALID_ARG;
+    }
+    if (F->v64_graph) {  // the recorded FP64 cycle holds the boundary-data pointer it was recorded with
+        MG_CUDA(cudaStreamSynchronize(F->st));
+        cudaGraphExecDestroy(F->v64_graph);
+        F->v64_graph = nullptr;
     }
     DevLevel &d = F->L[0];
     if (!g_dev) {
