@@ -61,6 +61,9 @@ struct DevLevel {
     std::array<int32_t, 5> s32{0, 0, 0, 0, 0};
     // adjoint work pools (allocated by the first adjoint call)
     double *a_ub = nullptr, *a_fb = nullptr, *a_z = nullptr, *a_tmp = nullptr;
+    // FP32 transposed cycles (forests with FP32 forward cycles): natural-layout pools and rounded coefficients
+    float *a32_ub = nullptr, *a32_fb = nullptr, *a32_z = nullptr, *a32_tmp = nullptr;
+    float *a32_tx = nullptr, *a32_ty = nullptr, *a32_tz = nullptr, *a32_dg = nullptr, *a32_dinv = nullptr;
     Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr}; }
     Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap}; }
     int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }

@@ -38,9 +38,12 @@ def test_apply_transpose_matches_oracle_and_dot_product(name, coeff, variant):
     assert abs(np.sum(x * Ay) - np.sum(got * y)) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(Ay)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,coeff,variant", CASES)
-def test_adjoint_solve_and_gradients_match_oracle(name, coeff, variant):
-    R, n, keys, k, f, F = _setup(name, coeff, variant)
+def test_adjoint_solve_and_gradients_match_oracle(name, coeff, variant, precision):
+    """lambda and dL/dk against the oracle's adjoint; precision 1 forests run FP32 transposed cycles inside FP64
+    defect correction, precision 0 forests FP64 ones: both reach the FP64 result."""
+    R, n, keys, k, f, F = _setup(name, coeff, variant, precision)
     ref = OracleMG(R, n, keys, k_user=None if k is None else k.numpy(), variant=variant)
     u_ref, _ = ref.solve(f.numpy(), rtol=1e-14, max_cycles=60)
     ut = syn.sin_target(R, n, keys, seed=64).numpy()
@@ -83,7 +86,8 @@ def test_gradients_match_finite_differences_on_refined_31m_cells():
     """Sphere-refined forest of 4^3 roots of 32^3 cells (448 + 512 blocks, 31,457,280 cells), log-normal k.
 
     Forward solves use FP32 cycles inside FP64 defect correction to 1e-11 (the FP64 rounding floor of f - A u for
-    this coefficient contrast is near 3e-12); the adjoint solve runs FP64 transposed cycles to 1e-11.  Central
+    this coefficient contrast is near 3e-12); the adjoint solve runs FP32 transposed cycles inside FP64 defect
+    correction to 1e-11.  Central
     differences on 10 seeded random cells and 10 seeded cells next to coarse-fine faces, evaluated through the
     difference solution delta = u+ - u- (exactly the central difference of L, without the cancellation of two
     nearly equal losses): step 1e-6 for f (L is quadratic in f); step 1e-4 relative for k, because at 1e-6 the
