@@ -267,7 +267,7 @@ class OracleMG:
     dtype = np.dtype(np.float64)  # working precision of the cycles (with_dtype makes an FP32 copy)
 
     def __init__(self, R, n, keys, k_user=None, variant="C", nu1=2, nu2=2, max_coarse=512, operator_only=False,
-                 bc=None, c2f_order=2, smoother="rbgs", omega=0.8, coarse_iters=None):
+                 bc=None, c2f_order=2, smoother="rbgs", omega=0.8, coarse_iters=None, coarse_coef="k"):
         """operator_only builds the finest level alone (for applying A, A^T and dA/dk; no solver).
 
         bc: None for homogeneous Dirichlet data, else a vectorised g(x, y, z) giving the Dirichlet value at
@@ -276,14 +276,19 @@ class OracleMG:
         smoother: 'rbgs' (red-black Gauss-Seidel) or 'jacobi' (damped by omega, the paper's own smoother, Sec. 5;
         one sweep per smoothing step).  coarse_iters: None for the dense direct coarsest solve, else that many damped
         Jacobi sweeps from zero on the coarsest level (the paper's coarsest solver, Sec. 5).
+        coarse_coef (variable k): 'k' rediscretises every coarse level from its k, the mean of the 8 children's
+        (the reading of Sec. 5's rediscretisation); 'faces' gives every coarse face the mean of the 2 x 2 finer
+        face coefficients it covers (an operator-aware coarsening the paper does not discuss; far fewer cycles for
+        rough k).  The finest level's coefficients are the harmonic means either way.
         """
         if n < 4 or n & (n - 1):
             raise ValueError("n must be a power of two >= 4")
         check_forest(R, list(keys))
         self.R, self.n, self.variant = R, n, variant
         self.nu1, self.nu2 = nu1, nu2
-        if c2f_order not in (0, 1, 2) or smoother not in ("rbgs", "jacobi"):
-            raise ValueError("c2f_order must be 0, 1 or 2 and smoother 'rbgs' or 'jacobi'")
+        if c2f_order not in (0, 1, 2) or smoother not in ("rbgs", "jacobi") or coarse_coef not in ("k", "faces"):
+            raise ValueError("c2f_order must be 0, 1 or 2, smoother 'rbgs' or 'jacobi', coarse_coef 'k' or 'faces'")
+        self.coarse_coef = coarse_coef
         self.c2f_order, self.smoother, self.omega, self.coarse_iters = c2f_order, smoother, omega, coarse_iters
         self.normal_w = normal_weights(c2f_order)
         self.levels = [Level(R, n, keys)]
@@ -316,7 +321,10 @@ class OracleMG:
                 self.levels[l + 1].kpad = kc
                 self.exchange_k(l + 1)
             for l in range(len(self.levels)):
-                self._cache_T(l)
+                if l == 0 or coarse_coef == "k":
+                    self._cache_T(l)
+                else:
+                    self._average_faces(l - 1)
         if not operator_only and coarse_iters is None:
             self._factor_coarsest()
 
@@ -380,7 +388,10 @@ class OracleMG:
             other.levels.append(M)
         if self.coeff:
             for l in range(len(other.levels)):
-                other._cache_T(l)
+                if l == 0 or self.coarse_coef == "k":
+                    other._cache_T(l)
+                else:  # averaged set-up data: the FP64 coefficients rounded
+                    other.levels[l].T = [t.astype(other.dtype) for t in self.levels[l].T]
         return other
 
     def _h2(self, l):
@@ -438,10 +449,8 @@ class OracleMG:
             u = Vf[1, 1:-1, 1:-1]
             uc = V[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2]
             if self.coeff:
-                Kf = face_view(L.kpad[fb], axis, 1 - side)
-                Tj = harmonic(Kf[1, 1:-1, 1:-1], Kf[0, 1:-1, 1:-1])
-                Kc = face_view(L.kpad[b], axis, side)
-                Tc = harmonic(Kc[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2], Kc[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2])
+                Tj = self._face_T(l, fb, axis, 1 - side)
+                Tc = self._face_T(l, b, axis, side)[o1:o1 + h2, o2:o2 + h2]
             else:
                 Tj = np.ones_like(g)
                 Tc = np.ones_like(uc)
@@ -482,6 +491,37 @@ class OracleMG:
         K = L.kpad
         kc = K[:, 1:-1, 1:-1, 1:-1]
         L.T = [harmonic(kc, nb) for nb in _neighbours(K)]
+
+    def _face_T(self, l, b, axis, side):
+        """Face coefficients of block b's face (axis, side) at its first interior layer, [t1, t2] (n x n)."""
+        return _interior_view(self.levels[l].T[2 * axis + side][b], axis, side)[0]
+
+    def _average_faces(self, l):
+        """Face coefficients of level l + 1 averaged from level l's (coarse_coef='faces'): a coarse cell's face is
+        covered by 2 x 2 faces of the finer level (the finer cells next to it on that side), and its coefficient is
+        their mean.  Blocks carried over unchanged keep their coefficients; merged octets are assembled first."""
+        Lf, Lc = self.levels[l], self.levels[l + 1]
+        out = [np.zeros((Lc.nb, Lc.n, Lc.n, Lc.n), dtype=self.dtype) for _ in range(6)]
+        for B, tr in enumerate(self.transfer[l]):
+            for q in range(6):
+                if tr[0] == "copy":
+                    out[q][B] = Lf.T[q][tr[1]]
+                    continue
+                fine = Lf.T[q][tr[1]] if tr[0] == "halve" else _assemble_octets([Lf.T[q][c] for c in tr[1]])
+                axis, side = q // 2, q % 2
+                sel = [slice(None)] * 3  # [z, y, x]
+                sel[2 - axis] = slice(side, None, 2)  # the finer cells on the face's side of each coarse cell
+                v = fine[tuple(sel)]
+                for d in range(3):
+                    if d == axis:
+                        continue
+                    a = 2 - d
+                    lo = [slice(None)] * 3
+                    hi = [slice(None)] * 3
+                    lo[a], hi[a] = slice(0, None, 2), slice(1, None, 2)
+                    v = 0.5 * (v[tuple(lo)] + v[tuple(hi)])
+                out[q][B] = v
+        Lc.T = out
 
     # -- stencil ---------------------------------------------------------------------------------------
     def _T(self, l):
@@ -704,11 +744,8 @@ class OracleMG:
                         o1, o2 = s1 * h2, s2 * h2
                         Gg = V[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2]
                         if self.coeff:
-                            Kf = face_view(L.kpad[fb], axis, 1 - side)
-                            Tj = harmonic(Kf[1, 1:-1, 1:-1], Kf[0, 1:-1, 1:-1])
-                            Kc = face_view(L.kpad[b], axis, side)
-                            Tc = harmonic(Kc[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2],
-                                          Kc[0, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2])
+                            Tj = self._face_T(l, fb, axis, 1 - side)
+                            Tc = self._face_T(l, b, axis, side)[o1:o1 + h2, o2:o2 + h2]
                         else:
                             Tj, Tc = np.ones((n, n)), np.ones((h2, h2))
                         V[1, 1 + o1:1 + o1 + h2, 1 + o2:1 + o2 + h2] += Gg
