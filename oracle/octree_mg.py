@@ -521,6 +521,18 @@ class OracleMG:
                     lo[a], hi[a] = slice(0, None, 2), slice(1, None, 2)
                     v = 0.5 * (v[tuple(lo)] + v[tuple(hi)])
                 out[q][B] = v
+            if tr[0] == "merge":
+                # Inside a merged block each face has one coefficient.  The two children meeting at a face between
+                # them each bring their own average, and these differ where that face was a refinement interface
+                # or lay between a copied and a merged block on the finer level: both sides take the mean of the two.
+                h = Lc.n // 2
+                for axis in range(3):
+                    up = [slice(None)] * 3
+                    dn = [slice(None)] * 3
+                    up[2 - axis], dn[2 - axis] = h - 1, h  # coarse cells below / above the children's shared face
+                    m = 0.5 * (out[2 * axis + 1][B][tuple(up)] + out[2 * axis][B][tuple(dn)])
+                    out[2 * axis + 1][B][tuple(up)] = m
+                    out[2 * axis][B][tuple(dn)] = m
         Lc.T = out
 
     # -- stencil ---------------------------------------------------------------------------------------

@@ -767,6 +767,56 @@ def test_face_averaged_coarse_operator_is_symmetric():
     assert np.abs(_level_operator(mg_k, 1) - _level_operator(mg, 1)).max() > 1e-3  # a different coarse operator
 
 
+def test_face_averaged_merged_blocks_hold_one_coefficient_per_face():
+    """On the refined sphere forest (8^3 blocks, interfaces on the finest levels, then a level of carried-over blocks
+    and merged octets, then merged roots) every level's face coefficients have one value per face inside a block:
+    the upper face of cell i equals the lower face of cell i + 1 along every axis, although the two children of a
+    merged octet bring different values of their shared face where it was an interface or lay between a carried-over
+    and a merged block.  On each merged block's mid-plane the two sides together keep a quarter of the sum of all the
+    finer values on that face, from both children (the mean of the two sides' 2 x 2 averages: an average of one side
+    only, or a missing 1/2, changes the sum).  The rediscretised coarse coefficients (coarse_coef='k') stay single
+    valued too."""
+    R, n, keys = syn.workload_forest("sphere_2x8")
+    k = syn.lognormal_k_rff(R, n, keys, seed=97).numpy()
+    mg = OracleMG(R, n, keys, k_user=k, coarse_coef="faces", operator_only=False, max_coarse=512)
+    assert [tr[0] for tr in mg.transfer[-1]].count("merge") == len(mg.transfer[-1])
+    merged_with_jump = 0
+    for l, L in enumerate(mg.levels):
+        for axis in range(3):
+            a = 3 - axis  # numpy axis of the face normal in [b, z, y, x]
+            up = np.take(L.T[2 * axis + 1], range(0, L.n - 1), axis=a)
+            lo = np.take(L.T[2 * axis], range(1, L.n), axis=a)
+            assert np.array_equal(up, lo), (l, axis)
+        if l == 0:
+            continue
+        Lf = mg.levels[l - 1]
+        h = L.n // 2
+        for B, tr in enumerate(mg.transfer[l - 1]):
+            if tr[0] != "merge":
+                continue
+            for axis in range(3):
+                a = 2 - axis  # axis of the face normal in one block's [z, y, x]
+                want = 0.0
+                jump = 0.0
+                for o, c in enumerate(tr[1]):
+                    if (o >> axis) & 1:  # upper child: its lower face on its first layer
+                        v = np.take(Lf.T[2 * axis][c], 0, axis=a)
+                    else:  # lower child: its upper face on its last layer
+                        v = np.take(Lf.T[2 * axis + 1][c], Lf.n - 1, axis=a)
+                    want += v.sum()
+                    jump += v.sum() * (1 if (o >> axis) & 1 else -1)
+                got = np.take(L.T[2 * axis + 1][B], h - 1, axis=a).sum() + np.take(L.T[2 * axis][B], h, axis=a).sum()
+                np.testing.assert_allclose(got, 0.25 * want, rtol=1e-13)
+                merged_with_jump += abs(jump) > 1e-6 * want
+    assert merged_with_jump > 0  # some merged faces really were two-valued on the finer level
+    mg_k = OracleMG(R, n, keys, k_user=k, coarse_coef="k", operator_only=False, max_coarse=512)
+    for L in mg_k.levels:
+        for axis in range(3):
+            up = np.take(L.T[2 * axis + 1], range(0, L.n - 1), axis=3 - axis)
+            lo = np.take(L.T[2 * axis], range(1, L.n), axis=3 - axis)
+            assert np.array_equal(up, lo)
+
+
 def test_face_averaged_coefficients_obey_the_parallel_conductor_law():
     """k constant on layers y = const (one value per fine row): an x-face of a coarse cell is covered by fine x-faces
     of the two fine layers it contains, which conduct in parallel, so its coefficient is the arithmetic mean of the
