@@ -67,6 +67,10 @@ typedef struct {
     int32_t smoother;         /* 0 red-black Gauss-Seidel; 1 damped Jacobi, one sweep per smoothing step (FP64) */
     double omega;             /* Jacobi damping (0.8 when <= 0) */
     int32_t coarse_iters;     /* 0: dense direct coarsest solve; > 0: that many damped Jacobi sweeps (FP64) */
+    int32_t coarse_coef;      /* coeff == 1, coarse levels: 0 rediscretised from k, the mean of the 8 children's
+                                 (default); 1 every coarse face takes the mean of the 2 x 2 finer face coefficients
+                                 it covers (an operator-aware coarsening not in the paper; far fewer V-cycles for
+                                 rough k).  The finest level's coefficients are the harmonic means either way. */
 } mg_config;
 
 /* Build the forest: validate the leaves, build neighbour and segment tables for every multigrid level, allocate

@@ -43,6 +43,7 @@ class MGConfig(ctypes.Structure):
         ("smoother", ctypes.c_int32),
         ("omega", ctypes.c_double),
         ("coarse_iters", ctypes.c_int32),
+        ("coarse_coef", ctypes.c_int32),
     ]
 
 

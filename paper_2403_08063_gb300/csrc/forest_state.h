@@ -64,8 +64,11 @@ struct DevLevel {
     // FP32 transposed cycles (forests with FP32 forward cycles): natural-layout pools and rounded coefficients
     float *a32_ub = nullptr, *a32_fb = nullptr, *a32_z = nullptr, *a32_tmp = nullptr;
     float *a32_tx = nullptr, *a32_ty = nullptr, *a32_tz = nullptr, *a32_dg = nullptr, *a32_dinv = nullptr;
-    Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr}; }
-    Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap}; }
+    // FP32 cycles on a face-averaged coarse level: its halved face coefficients (colour-split) and mode 3
+    float *ax32 = nullptr, *ay32 = nullptr, *az32 = nullptr;
+    bool face32 = false;
+    Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr, nullptr, nullptr, nullptr}; }
+    Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap, ax32, ay32, az32}; }
     int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }
     int64_t cells() const { return static_cast<int64_t>(g.nb) << (3 * g.lg); }
 };
@@ -81,6 +84,8 @@ struct TailLevel {
     const int32_t *nbr6, *bprob;
     int nfaces, nifaces, nsegs;
     int fast;  // the transfers to the next level use the specialised kernels (every block halves, edge 8..128)
+    const float *ax, *ay, *az;  // halved face coefficients of a face-averaged coarse level (mode 3)
+    int face32;                 // 1: this level's smoothing, ghosts and restriction use them
 };
 
 // One step of the tail's V-cycle; every step is followed by a grid barrier.

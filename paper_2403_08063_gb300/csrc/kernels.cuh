@@ -31,9 +31,13 @@ struct LevelGeom {
     int64_t bs;     // block stride in elements
 };
 
+// Coefficient modes: 0 constant (-Laplace); 1 FP64 scaled face coefficients T / h^2 (natural layout); 2 FP32 1/k per
+// cell, faces by harmonic means on the fly (colour-split); 3 FP32 halved face coefficients T / 2 per cell for its
+// lower x, y and z faces (colour-split; the face-averaged coarse levels of FP32 cycles).
 struct Coef {       // coefficient arrays of one level (unused members are null)
     const double *tx, *ty, *tz, *dg, *dinv;  // MODE 1
     const float *kap;                        // MODE 2
+    const float *ax, *ay, *az;               // MODE 3
 };
 
 // Problems of a multi-problem level that have met their tolerance in a batched solve: their blocks are skipped by
@@ -222,6 +226,10 @@ __device__ inline T face_coef(const Coef &c, int64_t loc, int64_t other, int axi
     if (MODE == 1) {
         const double *t = axis == 0 ? c.tx : (axis == 1 ? c.ty : c.tz);
         return T(t[loc]);
+    }
+    if (MODE == 3) {
+        const float *a = axis == 0 ? c.ax : (axis == 1 ? c.ay : c.az);
+        return T(2.0f * a[loc]);
     }
     return T(2.0f * frcp(c.kap[loc] + c.kap[other]));
 }
@@ -610,7 +618,9 @@ template <int MODE, int LG, int ZC, bool CG = false>
 __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const float *__restrict__ f,
                                                 const float *__restrict__ kap, const float *__restrict__ h2,
                                                 int64_t bs, int colour, const int32_t *__restrict__ nbr6,
-                                                Skip skip, int64_t t) {
+                                                Skip skip, int64_t t, const float *__restrict__ ax = nullptr,
+                                                const float *__restrict__ ay = nullptr,
+                                                const float *__restrict__ az = nullptr) {
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, HP = half_row(P), PL = P * HP, HALF = P * PL;
     constexpr int LZ = ZC == 1 ? 0 : (ZC == 2 ? 1 : (ZC == 4 ? 2 : 3));
     static_assert((1 << LZ) == ZC && ZC <= n, "column length");
@@ -659,6 +669,22 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
             k0[dz] = __ldg(kb + ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL);
         }
     }
+    // MODE 3: the stored halved face coefficients, a cell's lower faces at the cell, its upper ones at the upper
+    // neighbour (other half: x+ at the second of the x pair, y+ at the next row, z+ at the cell above)
+    float fx0[ZC], fx1[ZC], fy0[ZC], fy1[ZC], fz0[ZC], fz1[ZC];
+    if constexpr (MODE == 3) {
+#pragma unroll
+        for (int dz = 0; dz < ZC; ++dz) {
+            const int own = ((dz & 1) ? iw + 1 - 2 * c0 : iw) + dz * PL;
+            const int ic = (dz & 1) ? io + 1 - c0 : ioc;
+            fx0[dz] = __ldg(ax + base + own);
+            fx1[dz] = __ldg(ax + base + io + dz * PL + 1);
+            fy0[dz] = __ldg(ay + base + own);
+            fy1[dz] = __ldg(ay + base + ic + dz * PL + HP);
+            fz0[dz] = __ldg(az + base + own);
+            fz1[dz] = __ldg(az + base + io + (dz + 1) * PL + (c0 ^ (dz & 1)));
+        }
+    }
     const float hb = __ldg(h2 + b), hh = 0.5f * hb;  // T_f = 2 / (kap_i + kap_f): its 2 cancels against h^2 / 2
     // ---- updates -----------------------------------------------------------------------------------
     float val[ZC];
@@ -667,13 +693,26 @@ __device__ __forceinline__ void smooth32_column(float *__restrict__ u, const flo
         const int c = c0 ^ (dz & 1);
         const float zm = dz == 0 ? zlo : (c ? xr1[dz - 1] : xr0[dz - 1]);
         const float zp = dz == ZC - 1 ? zhi : (c ? xr1[dz + 1] : xr0[dz + 1]);
-        if constexpr (MODE == 2) {
-            const float kzm = dz == 0 ? kzlo : (c ? kx1[dz - 1] : kx0[dz - 1]);
-            const float kzp = dz == ZC - 1 ? kzhi : (c ? kx1[dz + 1] : kx0[dz + 1]);
-            const float kc = k0[dz];
-            const float a0 = frcp(kc + kx0[dz]), a1 = frcp(kc + kx1[dz]);
-            const float b0 = frcp(kc + kym[dz]), b1 = frcp(kc + kyp[dz]);
-            const float e0 = frcp(kc + kzm), e1 = frcp(kc + kzp);
+        if constexpr (MODE == 2 || MODE == 3) {
+            float a0, a1, b0, b1, e0, e1;
+            if constexpr (MODE == 2) {
+                const float kzm = dz == 0 ? kzlo : (c ? kx1[dz - 1] : kx0[dz - 1]);
+                const float kzp = dz == ZC - 1 ? kzhi : (c ? kx1[dz + 1] : kx0[dz + 1]);
+                const float kc = k0[dz];
+                a0 = frcp(kc + kx0[dz]);
+                a1 = frcp(kc + kx1[dz]);
+                b0 = frcp(kc + kym[dz]);
+                b1 = frcp(kc + kyp[dz]);
+                e0 = frcp(kc + kzm);
+                e1 = frcp(kc + kzp);
+            } else {
+                a0 = fx0[dz];
+                a1 = fx1[dz];
+                b0 = fy0[dz];
+                b1 = fy1[dz];
+                e0 = fz0[dz];
+                e1 = fz1[dz];
+            }
             float sacc = a0 * xr0[dz];
             sacc = fmaf(a1, xr1[dz], sacc);
             sacc = fmaf(b0, ym[dz], sacc);
@@ -730,9 +769,11 @@ template <int MODE, int LG, int ZC>
 static __global__ void __launch_bounds__(512) k_smooth32(float *__restrict__ u, const float *__restrict__ f,
                                                          const float *__restrict__ kap, const float *__restrict__ h2,
                                                          int64_t total, int64_t bs, int colour,
-                                                         const int32_t *__restrict__ nbr6, Skip skip) {
+                                                         const int32_t *__restrict__ nbr6, Skip skip,
+                                                         const float *__restrict__ ax, const float *__restrict__ ay,
+                                                         const float *__restrict__ az) {
     const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (t < total) smooth32_column<MODE, LG, ZC>(u, f, kap, h2, bs, colour, nbr6, skip, t);
+    if (t < total) smooth32_column<MODE, LG, ZC>(u, f, kap, h2, bs, colour, nbr6, skip, t, ax, ay, az);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -824,6 +865,7 @@ __host__ __device__ __forceinline__ uint32_t s32t_bytes(int off, int len) {
 // `array` (0 other-half u, 1 other-half kappa, 2 own-half f, 3 own-half kappa) to shared float `dst`, the wanted
 // segment starting `lead` floats into the copy.
 // First: other-half padded planes z0 and z0 + 1 (planes z0 - 1 and z0) into other slots 0 and 1.
+#pragma nv_exec_check_disable
 template <class Sink>
 __host__ __device__ __forceinline__ void s32t_issue_first(const S32tPlan &p, int z0, int y0, Sink &&sink) {
     const int o0 = s32t_off_other(p, z0, y0), o1 = s32t_off_other(p, z0 + 1, y0);
@@ -839,6 +881,7 @@ __host__ __device__ __forceinline__ void s32t_issue_first(const S32tPlan &p, int
 }
 // Group g: other-half padded plane z0 + g + 2 (plane z0 + g + 1) into other slot (g + 2) % RO, own-half padded
 // plane z0 + g + 1 (plane z0 + g) into own slot g % RW.
+#pragma nv_exec_check_disable
 template <class Sink>
 __host__ __device__ __forceinline__ void s32t_issue_group(const S32tPlan &p, int z0, int y0, int g, Sink &&sink) {
     const int bi = 1 + g % p.G;
@@ -902,6 +945,7 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
                                                           const float *__restrict__ kap, const float *__restrict__ h2,
                                                           int64_t bs, int colour, const int32_t *__restrict__ nbr6,
                                                           int TY, int TZ, int D, int *__restrict__ err, Skip skip) {
+    static_assert(MODE == 0 || MODE == 2, "the staged smoother stages 1/k (MODE 2) or nothing (MODE 0)");
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, H = half_row(P), PL = P * H, HALF = P * PL;
     constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1103,13 +1147,22 @@ __device__ inline T residual_xyz(const T *__restrict__ u, const T *__restrict__ 
                     (ldv<CG>(u + nb[4]) + ldv<CG>(u + nb[5]));
         return fma(fma(T(-6), u0, S), ih2, ldv<CG>(f + i0));
     } else {
-        const float k0 = cf.kap[i0];
         float S = 0.0f, D = 0.0f;
+        if constexpr (MODE == 3) {  // stored halved face coefficients: lower faces at the cell, upper at the neighbour
+            const float a6[6] = {cf.ax[i0], cf.ax[nb[1]], cf.ay[i0], cf.ay[nb[3]], cf.az[i0], cf.az[nb[5]]};
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const float a = frcp(k0 + cf.kap[nb[q]]);
-            S = fmaf(a, float(ldv<CG>(u + nb[q])), S);
-            D += a;
+            for (int q = 0; q < 6; ++q) {
+                S = fmaf(a6[q], float(ldv<CG>(u + nb[q])), S);
+                D += a6[q];
+            }
+        } else {
+            const float k0 = cf.kap[i0];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float a = frcp(k0 + cf.kap[nb[q]]);
+                S = fmaf(a, float(ldv<CG>(u + nb[q])), S);
+                D += a;
+            }
         }
         return T(fmaf(2.0f * fmaf(-D, float(u0), S), float(ih2), float(ldv<CG>(f + i0))));
     }
@@ -1207,7 +1260,9 @@ template <int MODE, int LG, bool CG = false>
 __device__ __forceinline__ void residual_restrict32_body(
         const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
         const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
-        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip, int64_t t0, int64_t ts) {
+        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip, int64_t t0, int64_t ts,
+        const float *__restrict__ ax = nullptr, const float *__restrict__ ay = nullptr,
+        const float *__restrict__ az = nullptr) {
     using Bx = Box32<LG>;
     constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), HALFc = Pc * Pc * HPc;
     const int64_t total = static_cast<int64_t>(nbc) << (3 * LC);
@@ -1231,6 +1286,20 @@ __device__ __forceinline__ void residual_restrict32_body(
                     U[k][j][i] = ldv<CG>(ub + Bx::off(i, j, k));
                     if constexpr (MODE == 2) K[k][j][i] = __ldg(kap + corner + Bx::off(i, j, k));
                 }
+        // MODE 3: the children's halved face coefficients, a face stored at the cell on its upper side
+        float AX[3][3][4], AY[3][4][3], AZ[4][3][3];
+        if constexpr (MODE == 3) {
+#pragma unroll
+            for (int k = 1; k < 3; ++k)
+#pragma unroll
+                for (int j = 1; j < 3; ++j)
+#pragma unroll
+                    for (int i = 1; i < 4; ++i) {
+                        AX[k][j][i] = __ldg(ax + corner + Bx::off(i, j, k));
+                        AY[k][i][j] = __ldg(ay + corner + Bx::off(j, i, k));
+                        AZ[i][k][j] = __ldg(az + corner + Bx::off(j, k, i));
+                    }
+        }
         const float ih2 = __ldg(ih2f + b);
         float sum = 0.0f;
 #pragma unroll
@@ -1246,6 +1315,16 @@ __device__ __forceinline__ void residual_restrict32_body(
                     if constexpr (MODE == 0) {
                         const float S = ((nbu[0] + nbu[1]) + (nbu[2] + nbu[3])) + (nbu[4] + nbu[5]);
                         sum += fmaf(fmaf(-6.0f, u0, S), ih2, fv);
+                    } else if constexpr (MODE == 3) {
+                        const float a6[6] = {AX[k][j][i], AX[k][j][i + 1], AY[k][j][i],
+                                             AY[k][j + 1][i], AZ[k][j][i], AZ[k + 1][j][i]};
+                        float S = 0.0f, D = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            S = fmaf(a6[q], nbu[q], S);
+                            D += a6[q];
+                        }
+                        sum += fmaf(2.0f * fmaf(-D, u0, S), ih2, fv);
                     } else {
                         const float k0 = K[k][j][i];
                         const float nbk[6] = {K[k][j][i - 1], K[k][j][i + 1], K[k][j - 1][i],
@@ -1285,10 +1364,11 @@ template <int MODE, int LG>
 static __global__ void __launch_bounds__(256) k_residual_restrict32(
         const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
         const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
-        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip) {
+        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip, const float *__restrict__ ax,
+        const float *__restrict__ ay, const float *__restrict__ az) {
     residual_restrict32_body<MODE, LG>(u, f, kap, ih2f, bsf, fc, uc, xf, nbc, bsc, skip,
                                        blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
-                                       static_cast<int64_t>(gridDim.x) * blockDim.x);
+                                       static_cast<int64_t>(gridDim.x) * blockDim.x, ax, ay, az);
 }
 
 // FP32 prolongation + correction for a level whose blocks all halve (fine edge 2^LG): one thread per coarse cell
@@ -1786,6 +1866,96 @@ static __global__ void k_face_coefs(const double *__restrict__ k, const double *
         const bool face_or_interior = (inX && inY) || (inX && inZ) || (inY && inZ);
         // 1/k for the FP32 cycles: FP32 accuracy suffices (binary32 conversion on exponent bits, FP32 division)
         if (kap && face_or_interior && kc > 0.0) kap[Lay<float>::at(g, b, X, Y, Z)] = 1.0f / f64_to_f32_pow2(kc, 0);
+    }
+}
+
+// Face coefficients of a coarse level averaged from the finer level's (face-averaged coarse coefficients): every
+// coarse face is covered by 2 x 2 faces of the finer level and takes their mean; the stored T / h^2 scales by
+// h_f^2 / h_c^2 = 1/4, so the coarse value is the sum of the four over 16 (halved blocks and merged octets; carried-over
+// blocks keep theirs).  Inside a merged octet the face between two children is held by both (their values differ where
+// it was a refinement interface, or lay between a carried-over and a merged block, on the finer level): the merged
+// block takes the mean of the two sides' eight values, so that each face inside a block has one coefficient.  One
+// thread per face position of every coarse block and axis: along the axis the lower face
+// of cell a (a = 0 .. n-1) and the block's upper face (a = n, stored at the ghost position), the two other
+// coordinates 0 .. n-1.  An operator-aware coarsening the paper does not discuss; its reading is this library's.
+static __global__ void k_average_faces64(const double *__restrict__ tfx, const double *__restrict__ tfy,
+                                         const double *__restrict__ tfz, LevelGeom gf, double *__restrict__ tcx,
+                                         double *__restrict__ tcy, double *__restrict__ tcz,
+                                         const XferItem *__restrict__ xf, LevelGeom gc) {
+    const int nc = gc.n, nf = gf.n;
+    const int64_t per = static_cast<int64_t>(nc + 1) * nc * nc;
+    const int64_t total = static_cast<int64_t>(gc.nb) * 3 * per;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t B = t / (3 * per);
+        const int64_t r = t - B * 3 * per;
+        const int axis = static_cast<int>(r / per);
+        const int q = static_cast<int>(r - axis * per);
+        const int a = q % (nc + 1), t1 = (q / (nc + 1)) % nc, t2 = q / ((nc + 1) * nc);
+        const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;  // the other two axes, increasing
+        int C[3];
+        C[axis] = a + 1;
+        C[o1] = t1 + 1;
+        C[o2] = t2 + 1;
+        const double *src = axis == 0 ? tfx : (axis == 1 ? tfy : tfz);
+        double *dst = axis == 0 ? tcx : (axis == 1 ? tcy : tcz);
+        const XferItem xi = xf[B];
+        const int64_t gcell = B * gc.bs + off3(C[0], C[1], C[2], gc.P);
+        if (xi.kind == XF_COPY) {
+            dst[gcell] = src[xi.src[0] * gf.bs + off3(C[0], C[1], C[2], gf.P)];
+            continue;
+        }
+        // a merged octet's face between two children: each child holds its own value of it (the lower child at its
+        // upper ghost position, the upper child at its first cell), and the merged block takes the mean of both
+        const bool shared = xi.kind == XF_MERGE && 2 * a == nf;
+        double s = 0.0;
+        for (int e2 = 0; e2 < 2; ++e2)
+            for (int e1 = 0; e1 < 2; ++e1) {
+                int F[3];  // finer interior coordinates of the cell on the face's upper side (2 n_c: the upper face)
+                F[axis] = 2 * a;
+                F[o1] = 2 * t1 + e1;
+                F[o2] = 2 * t2 + e2;
+                if (xi.kind == XF_HALVE) {
+                    s += src[xi.src[0] * gf.bs + off3(F[0] + 1, F[1] + 1, F[2] + 1, gf.P)];
+                    continue;
+                }
+                // merged octet: children of edge nf (= nc) assembled into a 2 nf block
+                int oc[3], L[3];
+                for (int d = 0; d < 3; ++d) {
+                    oc[d] = F[d] >= nf ? 1 : 0;
+                    L[d] = F[d] - oc[d] * nf + 1;
+                }
+                s += src[xi.src[oc[0] + 2 * oc[1] + 4 * oc[2]] * gf.bs + off3(L[0], L[1], L[2], gf.P)];
+                if (shared) {
+                    oc[axis] = 0;
+                    L[axis] = nf + 1;
+                    s += src[xi.src[oc[0] + 2 * oc[1] + 4 * oc[2]] * gf.bs + off3(L[0], L[1], L[2], gf.P)];
+                }
+            }
+        dst[gcell] = (shared ? 0.03125 : 0.0625) * s;
+    }
+}
+
+// FP32 halved face coefficients T / 2 = (T / h^2) h^2 / 2 of a face-averaged coarse level, from its FP64 scaled ones,
+// in the colour-split layout of the FP32 pools (a cell's lower x, y and z faces at the cell, the block's upper faces
+// at the ghost positions), for the FP32 cycles' coefficient mode 3.
+static __global__ void k_face_half32(const double *__restrict__ tx, const double *__restrict__ ty,
+                                     const double *__restrict__ tz, const double *__restrict__ h2, LevelGeom g,
+                                     float *__restrict__ ax, float *__restrict__ ay, float *__restrict__ az) {
+    const int P = g.P, n = g.n;
+    const int64_t per = static_cast<int64_t>(P) * P * P;
+    const int64_t total = static_cast<int64_t>(g.nb) * per;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t b = t / per;
+        const int r = static_cast<int>(t - b * per);
+        const int X = r % P, Y = (r / P) % P, Z = r / (P * P);
+        const bool inY = Y >= 1 && Y <= n, inZ = Z >= 1 && Z <= n, inX = X >= 1 && X <= n;
+        const int64_t gi = b * g.bs + r, gs = Lay<float>::at(g, b, X, Y, Z);
+        const double s = 0.5 * h2[b];
+        if (X >= 1 && inY && inZ) ax[gs] = static_cast<float>(tx[gi] * s);
+        if (Y >= 1 && inX && inZ) ay[gs] = static_cast<float>(ty[gi] * s);
+        if (Z >= 1 && inX && inY) az[gs] = static_cast<float>(tz[gi] * s);
     }
 }
 

@@ -144,13 +144,16 @@ void exchange_k(mg_forest *F, DevLevel &d) {
 // A shape only changes which thread updates a cell, never the arithmetic, so every shape gives identical bits.
 using Shape = std::array<int32_t, 5>;
 using Smooth32Fn = void (*)(float *, const float *, const float *, const float *, int64_t, int64_t, int,
-                            const int32_t *, Skip);
+                            const int32_t *, Skip, const float *, const float *, const float *);
 #define OCTMG_S32(K, M, L) {K<M, L, 1>, K<M, L, 2>, K<M, L, 4>}
-const Smooth32Fn kSmooth32[2][6][3] = {
+// [coefficient mode 0, 2, 3][block edge 2^2 .. 2^7][column length 1, 2, 4]
+const Smooth32Fn kSmooth32[3][6][3] = {
     {OCTMG_S32(k_smooth32, 0, 2), OCTMG_S32(k_smooth32, 0, 3), OCTMG_S32(k_smooth32, 0, 4),
      OCTMG_S32(k_smooth32, 0, 5), OCTMG_S32(k_smooth32, 0, 6), OCTMG_S32(k_smooth32, 0, 7)},
     {OCTMG_S32(k_smooth32, 2, 2), OCTMG_S32(k_smooth32, 2, 3), OCTMG_S32(k_smooth32, 2, 4),
-     OCTMG_S32(k_smooth32, 2, 5), OCTMG_S32(k_smooth32, 2, 6), OCTMG_S32(k_smooth32, 2, 7)}};
+     OCTMG_S32(k_smooth32, 2, 5), OCTMG_S32(k_smooth32, 2, 6), OCTMG_S32(k_smooth32, 2, 7)},
+    {OCTMG_S32(k_smooth32, 3, 2), OCTMG_S32(k_smooth32, 3, 3), OCTMG_S32(k_smooth32, 3, 4),
+     OCTMG_S32(k_smooth32, 3, 5), OCTMG_S32(k_smooth32, 3, 6), OCTMG_S32(k_smooth32, 3, 7)}};
 using Smooth32tFn = void (*)(float *, const float *, const float *, const float *, int64_t, int, const int32_t *, int,
                              int, int, int *, Skip);
 const Smooth32tFn kSmooth32t[2][3][3] = {
@@ -164,14 +167,21 @@ size_t smooth32t_smem(int lg, bool var, int TY, int D) { return s32t_smem_bytes(
 
 int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
 
-// The shapes a level may use (the tuner's candidates).
-std::vector<Shape> smooth32_shapes(const DevLevel &d, bool var) {
+// FP32 coefficient mode of a level: 0 constant k, 2 1/k with harmonic means on the fly, 3 stored halved face
+// coefficients (face-averaged coarse levels); and its index into the kernel tables.
+int mode32(const mg_forest *F, const DevLevel &d) { return !F->cfg.coeff ? 0 : (d.face32 ? 3 : 2); }
+int mode_index(int mode) { return mode == 3 ? 2 : (mode == 2 ? 1 : 0); }
+
+// The shapes a level may use (the tuner's candidates); the staged kernel stages 1/k, so a level with stored face
+// coefficients (mode 3) is offered the column kernel only.
+std::vector<Shape> smooth32_shapes(const DevLevel &d, int mode) {
     std::vector<Shape> v;
     const int n = d.g.n;
+    const bool var = mode == 2;
     for (int zc : {1, 2, 4})
         for (int th : {128, 256, 512})
             if (zc <= n) v.push_back({1, zc, th, 0, 0});
-    if (d.g.lg >= 5)
+    if (d.g.lg >= 5 && mode != 3)
         for (int R : {1, 2, 4})
             for (int th : {128, 256, 512})
                 for (int tz : {8, 16, 32, 64})
@@ -183,15 +193,15 @@ std::vector<Shape> smooth32_shapes(const DevLevel &d, bool var) {
     return v;
 }
 
-bool smooth32_shape_ok(const DevLevel &d, bool var, const Shape &sh) {
-    for (const auto &c : smooth32_shapes(d, var))
+bool smooth32_shape_ok(const DevLevel &d, int mode, const Shape &sh) {
+    for (const auto &c : smooth32_shapes(d, mode))
         if (c == sh) return true;
     return false;
 }
 
 void launch_smooth32(mg_forest *F, DevLevel &d, int colour, const Shape &sh, cudaStream_t st) {
-    const int mi = F->cfg.coeff ? 1 : 0;
-    if (sh[0] == 2) {
+    const int mode = mode32(F, d), mi = mode == 2 ? 1 : 0;
+    if (sh[0] == 2 && mode != 3) {
         const int TY = sh[1], TZ = sh[2], D = sh[3], R = sh[4], n = d.g.n;
         const size_t smem = smooth32t_smem(d.g.lg, mi == 1, TY, D);
         Smooth32tFn fn = kSmooth32t[mi][d.g.lg - 5][ridx(R)];
@@ -205,11 +215,11 @@ void launch_smooth32(mg_forest *F, DevLevel &d, int colour, const Shape &sh, cud
                                                                          d.nbr6, TY, TZ, D, F->kerr, skip_of(F, d));
         return;
     }
-    const int zc = sh[1], threads = sh[2];
+    const int zc = sh[0] == 1 ? sh[1] : 1, threads = sh[0] == 1 ? sh[2] : kThreads;
     const int64_t work = (d.cells() / 2) >> ridx(zc);  // one thread per column of zc cells
     const int64_t grid = (work + threads - 1) / threads;
-    kSmooth32[mi][d.g.lg - 2][ridx(zc)]<<<static_cast<unsigned>(grid), threads, 0, st>>>(
-        d.u32, d.f32, d.kap, d.h2_32, work, d.g.bs, colour, d.nbr6, skip_of(F, d));
+    kSmooth32[mode_index(mode)][d.g.lg - 2][ridx(zc)]<<<static_cast<unsigned>(grid), threads, 0, st>>>(
+        d.u32, d.f32, d.kap, d.h2_32, work, d.g.bs, colour, d.nbr6, skip_of(F, d), d.ax32, d.ay32, d.az32);
 }
 
 // Reads and clears the device error word of bounded waits.
@@ -239,14 +249,13 @@ mg_status tune_smooth32(mg_forest *F) {
     MG_CUDA(cudaGetDevice(&dev));
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     MG_CUDA(cudaStreamIsCapturing(F->st, &cap));
-    const bool var = F->cfg.coeff != 0;
     for (DevLevel &d : F->L) {
         if (!smooth32_specialised(d) || !d.u32 || d.s32[0]) continue;
         if (d.cells() < (int64_t(1) << 18) || cap != cudaStreamCaptureStatusNone) {
             d.s32 = {1, 1, kThreads, 0, 0};
             continue;
         }
-        const std::array<int64_t, 4> key{dev, F->cfg.coeff, d.g.n, d.g.nb};
+        const std::array<int64_t, 4> key{dev, mode32(F, d), d.g.n, d.g.nb};
         {
             std::lock_guard<std::mutex> lk(mu);
             auto it = cache.find(key);
@@ -262,7 +271,7 @@ mg_status tune_smooth32(mg_forest *F) {
         }
         float best = 0.0f;
         Shape pick{1, 1, kThreads, 0, 0};
-        for (const auto &sh : smooth32_shapes(d, var)) {
+        for (const auto &sh : smooth32_shapes(d, mode32(F, d))) {
             launch_smooth32(F, d, 0, sh, F->st);
             launch_smooth32(F, d, 1, sh, F->st);
             MG_CUDA(cudaEventRecord(e0, F->st));
@@ -293,12 +302,15 @@ mg_status tune_smooth32(mg_forest *F) {
 bool transfer32_specialised(const DevLevel &d) { return d.all_halve && d.g.lg >= 3 && d.g.lg <= 7; }
 
 using Restrict32Fn = void (*)(const float *, const float *, const float *, const float *, int64_t, float *, float *,
-                              const XferItem *, int32_t, int64_t, Skip);
-const Restrict32Fn kRestrict32[2][5] = {
+                              const XferItem *, int32_t, int64_t, Skip, const float *, const float *, const float *);
+// [coefficient mode 0, 2, 3][fine block edge 2^3 .. 2^7]
+const Restrict32Fn kRestrict32[3][5] = {
     {k_residual_restrict32<0, 3>, k_residual_restrict32<0, 4>, k_residual_restrict32<0, 5>,
      k_residual_restrict32<0, 6>, k_residual_restrict32<0, 7>},
     {k_residual_restrict32<2, 3>, k_residual_restrict32<2, 4>, k_residual_restrict32<2, 5>,
-     k_residual_restrict32<2, 6>, k_residual_restrict32<2, 7>}};
+     k_residual_restrict32<2, 6>, k_residual_restrict32<2, 7>},
+    {k_residual_restrict32<3, 3>, k_residual_restrict32<3, 4>, k_residual_restrict32<3, 5>,
+     k_residual_restrict32<3, 6>, k_residual_restrict32<3, 7>}};
 using Prolong32Fn = void (*)(float *, int64_t, const float *, const XferItem *, int32_t, int64_t,
                              const int32_t *, Skip);
 const Prolong32Fn kProlong32[5] = {k_prolong32<3>, k_prolong32<4>, k_prolong32<5>, k_prolong32<6>, k_prolong32<7>};
@@ -306,8 +318,9 @@ const Prolong32Fn kProlong32[5] = {k_prolong32<3>, k_prolong32<4>, k_prolong32<5
 void launch_residual_restrict32(mg_forest *F, DevLevel &d, DevLevel &c) {
     // one coarse cell per thread (no grid-stride loop): its load chain xf -> fine block -> 64 loads is latency-bound
     const auto grid = static_cast<unsigned>((c.cells() + kThreads - 1) / kThreads);
-    kRestrict32[F->cfg.coeff ? 1 : 0][d.g.lg - 3]<<<grid, kThreads, 0, F->st>>>(
-        d.u32, d.f32, d.kap, d.ih2_32, d.g.bs, c.f32, c.u32, d.xfer, c.g.nb, c.g.bs, skip_of(F, c));
+    kRestrict32[mode_index(mode32(F, d))][d.g.lg - 3]<<<grid, kThreads, 0, F->st>>>(
+        d.u32, d.f32, d.kap, d.ih2_32, d.g.bs, c.f32, c.u32, d.xfer, c.g.nb, c.g.bs, skip_of(F, c), d.ax32, d.ay32,
+        d.az32);
 }
 
 void launch_prolong32(mg_forest *F, DevLevel &d, DevLevel &c) {
@@ -403,7 +416,15 @@ struct LaunchExec {
         }
         return false;
     }
-    void exchange(int l, bool iface) { octmg::exchange<T, MODE>(F, F->L[l], ufield<T>(F->L[l]), iface); }
+    void exchange(int l, bool iface) {
+        if constexpr (sizeof(T) == 4 && MODE == 2) {
+            if (F->L[l].face32) {  // face-averaged coarse level: its conservative ghosts read the stored faces
+                octmg::exchange<float, 3>(F, F->L[l], F->L[l].u32, iface);
+                return;
+            }
+        }
+        octmg::exchange<T, MODE>(F, F->L[l], ufield<T>(F->L[l]), iface);
+    }
     void smooth(int l, int colour) { octmg::smooth<T, MODE>(F, F->L[l], colour); }
     void jacobi(int l, bool prof = true) {
         if constexpr (sizeof(T) == 8) {
@@ -435,6 +456,9 @@ struct LaunchExec {
         Prof p(F, cat_of<T>(P_RESTR64), 1);
         if (fast)
             launch_residual_restrict32(F, d, c);
+        else if (sizeof(T) == 4 && d.face32)
+            k_residual_restrict<float, 3><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
+                d.u32, d.f32, d.c32(), d.ih2_32, d.g, c.f32, c.u32, d.xfer, c.g, skip_of(F, c));
         else
             k_residual_restrict<T, MODE><<<grid_for(c.cells()), kThreads, 0, F->st>>>(
                 ufield<T>(d), ffield<T>(d), coef_of<T>(d), ih2_of<T>(d), d.g, ffield<T>(c), ufield<T>(c), d.xfer, c.g,
@@ -492,7 +516,8 @@ mg_status record_tail(mg_forest *F, int l) {
         for (size_t m = 0; m < F->L.size(); ++m) {
             const DevLevel &d = F->L[m];
             tl[m] = TailLevel{d.g, d.u32, d.f32, d.kap, d.h2_32, d.ih2_32, d.faces, d.ifaces, d.segs, d.xfer, d.nbr6,
-                              d.bprob, d.nfaces, d.nifaces, d.nsegs, transfer32_specialised(d) ? 1 : 0};
+                              d.bprob, d.nfaces, d.nifaces, d.nsegs, transfer32_specialised(d) ? 1 : 0,
+                              d.ax32, d.ay32, d.az32, d.face32 ? 1 : 0};
         }
         MG_TRY(upload(F, &F->tail_L, tl));
         MG_TRY(dalloc(F, &F->tail_bar, 2));
@@ -801,9 +826,20 @@ mg_status build_coefficients(mg_forest *F) {
             k_restrict_field<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(p.k64, p.g, d.k64, p.xfer, d.g);
         }
         exchange_k(F, d);
-        k_face_coefs<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.k64, d.ih2_64, d.g, d.tx, d.ty, d.tz,
-                                                                        d.kap);
+        const bool averaged = l > 0 && F->cfg.coarse_coef == 1 && d.tx;
+        // harmonic means of k on the finest level (and on every level when rediscretised); 1/k for the FP32 cycles
+        k_face_coefs<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.k64, d.ih2_64, d.g, averaged ? nullptr : d.tx,
+                                                                        averaged ? nullptr : d.ty,
+                                                                        averaged ? nullptr : d.tz, d.kap);
+        if (averaged) {
+            DevLevel &p = F->L[l - 1];
+            k_average_faces64<<<grid_for(static_cast<int64_t>(d.g.nb) * 3 * (d.g.n + 1) * d.g.n * d.g.n), kThreads, 0,
+                                F->st>>>(p.tx, p.ty, p.tz, p.g, d.tx, d.ty, d.tz, p.xfer, d.g);
+        }
         if (d.dg) k_diag<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.g, d.dg, d.dinv);
+        if (d.face32)
+            k_face_half32<<<grid_for(d.pool_elems()), kThreads, 0, F->st>>>(d.tx, d.ty, d.tz, d.h2_64, d.g, d.ax32,
+                                                                             d.ay32, d.az32);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;
@@ -1128,6 +1164,11 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         set_error("bad c2f_variant (0..2) / smoother (0, 1) / coarse_iters (>= 0) / omega (< 2)");
         return MG_ERR_INVALID_ARG;
     }
+    if (cfg->coarse_coef < 0 || cfg->coarse_coef > 1) {
+        set_error("bad coarse_coef (0 rediscretised from k, 1 face-averaged)");
+        return MG_ERR_INVALID_ARG;
+    }
+
     if ((cfg->smoother == 1 || cfg->coarse_iters > 0) && cfg->precision != 0) {
         set_error("the damped Jacobi smoother and coarsest solver run FP64 cycles (precision 0)");
         return MG_ERR_INVALID_ARG;
@@ -1229,7 +1270,7 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         }
         if (cfg->coeff) {
             if ((st = dalloc(F, &d.k64, pe)) != MG_OK) return fail(st);
-            if (fp64) {
+            if (fp64 || cfg->coarse_coef == 1) {  // face-averaged coarse levels derive from every level's FP64 faces
                 if ((st = dalloc(F, &d.tx, pe)) != MG_OK) return fail(st);
                 if ((st = dalloc(F, &d.ty, pe)) != MG_OK) return fail(st);
                 if ((st = dalloc(F, &d.tz, pe)) != MG_OK) return fail(st);
@@ -1237,6 +1278,12 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
             }
             if (!mixed && (st = dalloc(F, &d.dinv, pe)) != MG_OK) return fail(st);
             if (mixed && (st = dalloc(F, &d.kap, pe)) != MG_OK) return fail(st);
+            if (mixed && cfg->coarse_coef == 1 && l > 0) {  // FP32 cycles on face-averaged coarse levels: mode 3
+                if ((st = dalloc(F, &d.ax32, pe)) != MG_OK) return fail(st);
+                if ((st = dalloc(F, &d.ay32, pe)) != MG_OK) return fail(st);
+                if ((st = dalloc(F, &d.az32, pe)) != MG_OK) return fail(st);
+                d.face32 = true;
+            }
         }
     }
     if ((st = dalloc(F, &F->partial, 2 * kMaxGrid)) != MG_OK) return fail(st);
@@ -1564,7 +1611,7 @@ mg_status mg_set_smoother_shape(mg_forest *F, int32_t level, const int32_t *shap
         return MG_ERR_INVALID_ARG;
     }
     const Shape sh{shape[0], shape[1], shape[2], shape[3], shape[4]};
-    if (!smooth32_shape_ok(d, F->cfg.coeff != 0, sh)) {
+    if (!smooth32_shape_ok(d, mode32(F, d), sh)) {
         set_error("smoother shape not offered for this level (see mg_smoother_shapes)");
         return MG_ERR_INVALID_ARG;
     }
@@ -1653,7 +1700,7 @@ mg_status mg_smoother_shapes(const mg_forest *F, int32_t level, int32_t max_shap
     }
     const DevLevel &d = F->L[level];
     std::vector<Shape> v;
-    if (F->cfg.precision == 1 && smooth32_specialised(d)) v = smooth32_shapes(d, F->cfg.coeff != 0);
+    if (F->cfg.precision == 1 && smooth32_specialised(d)) v = smooth32_shapes(d, mode32(F, d));
     *n_shapes = static_cast<int32_t>(v.size());
     for (int i = 0; i < static_cast<int>(v.size()) && i < max_shapes && shapes; ++i)
         for (int k = 0; k < 5; ++k) shapes[5 * i + k] = v[i][k];
@@ -1673,7 +1720,7 @@ mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t
     d.g.lg = lg;
     d.g.P = d.g.n + 2;
     std::vector<Shape> staged;
-    for (const Shape &sh : smooth32_shapes(d, coeff != 0))
+    for (const Shape &sh : smooth32_shapes(d, coeff ? 2 : 0))
         if (sh[0] == 2) staged.push_back(sh);
     *n_shapes = static_cast<int32_t>(staged.size());
     *n_records = 0;

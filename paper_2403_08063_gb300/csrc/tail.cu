@@ -64,14 +64,59 @@ template <int MODE, int LG>
 __device__ __forceinline__ void tail_smooth(const TailLevel &d, int colour, Skip skip, int64_t t0, int64_t ts) {
     const int64_t work = d.g.nb * (int64_t(1) << (3 * LG - 1));
     for (int64_t t = t0; t < work; t += ts)
-        smooth32_column<MODE, LG, 1, true>(d.u, d.f, d.kap, d.h2, d.g.bs, colour, d.nbr6, skip, t);
+        smooth32_column<MODE, LG, 1, true>(d.u, d.f, d.kap, d.h2, d.g.bs, colour, d.nbr6, skip, t, d.ax, d.ay, d.az);
 }
 
 template <int MODE, int LG>
 __device__ __forceinline__ void tail_restrict(const TailLevel &d, const TailLevel &c, Skip skip, int64_t t0,
                                               int64_t ts) {
     residual_restrict32_body<MODE, LG, true>(d.u, d.f, d.kap, d.ih2, d.g.bs, c.f, c.u, d.xfer, c.g.nb, c.g.bs, skip,
-                                             t0, ts);
+                                             t0, ts, d.ax, d.ay, d.az);
+}
+
+// The phases that read the level's coefficients (smoothing, conservative fine-to-coarse ghosts, residual +
+// restriction), in coefficient mode M; the others do not depend on it.
+template <int M>
+__device__ __forceinline__ void tail_coef_phase(const TailArgs &a, const TailPhase &P, const TailLevel &d, Skip skip,
+                                                int64_t t0, int64_t ts) {
+    const Coef cf{nullptr, nullptr, nullptr, nullptr, nullptr, d.kap, d.ax, d.ay, d.az};
+    switch (P.op) {
+        case T_SMOOTH0:
+        case T_SMOOTH1: {
+            const int colour = P.op == T_SMOOTH1;
+            switch (d.g.lg) {
+                case 2: tail_smooth<M, 2>(d, colour, skip, t0, ts); break;
+                case 3: tail_smooth<M, 3>(d, colour, skip, t0, ts); break;
+                case 4: tail_smooth<M, 4>(d, colour, skip, t0, ts); break;
+                case 5: tail_smooth<M, 5>(d, colour, skip, t0, ts); break;
+                case 6: tail_smooth<M, 6>(d, colour, skip, t0, ts); break;
+                default: tail_smooth<M, 7>(d, colour, skip, t0, ts); break;
+            }
+            break;
+        }
+        case T_SEGS:
+            if (a.flux)
+                exchange_segs_body<float, M, true, true>(d.u, cf, d.segs, d.nsegs, d.g, skip, t0, ts);
+            else
+                exchange_segs_body<float, M, false, true>(d.u, cf, d.segs, d.nsegs, d.g, skip, t0, ts);
+            break;
+        default: {  // T_RESTRICT
+            const TailLevel &c = a.L[P.level + 1];
+            const Skip cs{c.bprob, a.done};
+            if (d.fast) {
+                switch (d.g.lg) {
+                    case 3: tail_restrict<M, 3>(d, c, cs, t0, ts); break;
+                    case 4: tail_restrict<M, 4>(d, c, cs, t0, ts); break;
+                    case 5: tail_restrict<M, 5>(d, c, cs, t0, ts); break;
+                    case 6: tail_restrict<M, 6>(d, c, cs, t0, ts); break;
+                    default: tail_restrict<M, 7>(d, c, cs, t0, ts); break;
+                }
+            } else {
+                residual_restrict_body<float, M, true>(d.u, d.f, cf, d.ih2, d.g, c.f, c.u, d.xfer, c.g, cs, t0, ts);
+            }
+            break;
+        }
+    }
 }
 
 template <int LG>
@@ -88,50 +133,20 @@ static __global__ void __launch_bounds__(kTailThreads) k_tail32(TailArgs a) {
         const TailPhase P = a.ph[p];
         const TailLevel &d = a.L[P.level];
         const Skip skip{d.bprob, a.done};
-        const Coef cf{nullptr, nullptr, nullptr, nullptr, nullptr, d.kap};
         switch (P.op) {
             case T_SMOOTH0:
-            case T_SMOOTH1: {
-                const int colour = P.op == T_SMOOTH1;
-                switch (d.g.lg) {
-                    case 2: tail_smooth<MODE, 2>(d, colour, skip, t0, ts); break;
-                    case 3: tail_smooth<MODE, 3>(d, colour, skip, t0, ts); break;
-                    case 4: tail_smooth<MODE, 4>(d, colour, skip, t0, ts); break;
-                    case 5: tail_smooth<MODE, 5>(d, colour, skip, t0, ts); break;
-                    case 6: tail_smooth<MODE, 6>(d, colour, skip, t0, ts); break;
-                    default: tail_smooth<MODE, 7>(d, colour, skip, t0, ts); break;
-                }
+            case T_SMOOTH1:
+            case T_SEGS:
+            case T_RESTRICT:
+                if (MODE == 2 && d.face32) tail_coef_phase<3>(a, P, d, skip, t0, ts);
+                else tail_coef_phase<MODE>(a, P, d, skip, t0, ts);
                 break;
-            }
             case T_FACES_IFACE:
                 exchange_faces_body<float, false, true>(d.u, d.ifaces, d.nifaces, d.g, skip, t0, ts);
                 break;
             case T_FACES_FULL:
                 exchange_faces_body<float, false, true>(d.u, d.faces, d.nfaces, d.g, skip, t0, ts);
                 break;
-            case T_SEGS:
-                if (a.flux)
-                    exchange_segs_body<float, MODE, true, true>(d.u, cf, d.segs, d.nsegs, d.g, skip, t0, ts);
-                else
-                    exchange_segs_body<float, MODE, false, true>(d.u, cf, d.segs, d.nsegs, d.g, skip, t0, ts);
-                break;
-            case T_RESTRICT: {
-                const TailLevel &c = a.L[P.level + 1];
-                const Skip cs{c.bprob, a.done};
-                if (d.fast) {
-                    switch (d.g.lg) {
-                        case 3: tail_restrict<MODE, 3>(d, c, cs, t0, ts); break;
-                        case 4: tail_restrict<MODE, 4>(d, c, cs, t0, ts); break;
-                        case 5: tail_restrict<MODE, 5>(d, c, cs, t0, ts); break;
-                        case 6: tail_restrict<MODE, 6>(d, c, cs, t0, ts); break;
-                        default: tail_restrict<MODE, 7>(d, c, cs, t0, ts); break;
-                    }
-                } else {
-                    residual_restrict_body<float, MODE, true>(d.u, d.f, cf, d.ih2, d.g, c.f, c.u, d.xfer, c.g, cs, t0,
-                                                              ts);
-                }
-                break;
-            }
             case T_PROLONG: {
                 const TailLevel &c = a.L[P.level + 1];
                 const Skip cs{c.bprob, a.done};

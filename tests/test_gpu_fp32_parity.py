@@ -35,8 +35,8 @@ def _problem(R, n, keys, coeff, seed):
     return k, f
 
 
-def _oracle_iterates(R, n, keys, k, f, variant):
-    mg = OracleMG(R, n, keys, k_user=None if k is None else k.cpu().numpy(), variant=variant)
+def _oracle_iterates(R, n, keys, k, f, variant, coarse_coef="k"):
+    mg = OracleMG(R, n, keys, k_user=None if k is None else k.cpu().numpy(), variant=variant, coarse_coef=coarse_coef)
     fn = f.cpu().numpy()
     u64, _ = mg.solve(fn, cycles=CYCLES)
     u32, _ = mixed_solve(mg, fn, steps=1, inner=CYCLES)
@@ -115,6 +115,24 @@ def test_fp32_step_refined_sphere_32(variant):
     F = _forest(R, n, keys, coeff=True, interface_flux=(variant == "C"), precision=1, inner_cycles=CYCLES)
     got = _fp32_step(F, f, k)
     _check(got, u64, u32, f"sphere_2x32 {variant}")
+    F.close()
+
+
+@pytest.mark.parametrize("name,variant", [("uniform_2x64", "C"), ("sphere_2x32", "C"), ("sphere_2x32", "P")])
+def test_fp32_step_face_averaged_coarse_coefficients(name, variant):
+    """Face-averaged coarse coefficients: the coarse levels' FP32 cycles read halved face coefficients T / 2 (the
+    column smoother, the fused residual + restriction, the interface exchanges), the finest level its kappa = 1 / k.
+    Against the oracle's FP64 and FP32 iterates with the same coarse operator."""
+    if name == "uniform_2x64":
+        R, n, keys = 2, 64, syn.uniform_leaves(2)
+    else:
+        R, n, keys = syn.workload_forest(name)
+    k, f = _problem(R, n, keys, True, seed=161)
+    u64, u32 = _oracle_iterates(R, n, keys, k, f, variant, coarse_coef="faces")
+    F = _forest(R, n, keys, coeff=True, interface_flux=(variant == "C"), precision=1, inner_cycles=CYCLES,
+                coarse_coef="faces")
+    got = _fp32_step(F, f, k)
+    _check(got, u64, u32, f"{name} {variant} face-averaged")
     F.close()
 
 

@@ -195,3 +195,36 @@ def test_mixed_precision_solve_error_vs_fp64_oracle(coeff, inner):
           f"rel L2 error vs FP64 oracle {err:.2e}")
     assert ref.rel_residual(got, f.numpy()) <= 1.05e-10
     assert err < 1e-8
+
+
+@pytest.mark.parametrize("name,variant", [("sphere_2x8", "C"), ("sphere_2x8", "P"), ("uniform_2x8", "C"),
+                                          ("mixed_coarsest", "C")])
+def test_face_averaged_coarse_coefficients_fp64_cycles_match_oracle(name, variant):
+    """Face-averaged coarse coefficients (coarse_coef 'faces'): three FP64 V(2,2) cycles match the oracle's iterate to
+    1e-10, on refined forests (both interface variants; merged octets below 4^3), a uniform one, and a coarsest
+    level that keeps refinement interfaces; the adjoint on the same operator hierarchy matches the oracle's."""
+    if name == "mixed_coarsest":
+        keys = [(1, i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1) if (i, j, k) != (0, 0, 0)]
+        keys += [(2, i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+        R, n, mc = 1, 8, 960
+    else:
+        R, n, keys = syn.workload_forest(name)
+        mc = 512
+    k = syn.lognormal_k_rff(R, n, keys, seed=151)
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=152)
+    F = _forest(R, n, keys, coeff=True, interface_flux=(variant == "C"), max_coarse=mc, coarse_coef="faces")
+    F.set_rhs(f.to(DEV), k.to(DEV))
+    u = torch.zeros_like(f, device=DEV)
+    F.vcycle(u, 3)
+    ref = OracleMG(R, n, keys, k_user=k.numpy(), variant=variant, max_coarse=mc, coarse_coef="faces")
+    u_ref, _ = ref.solve(f.numpy(), cycles=3)
+    got = u.cpu().numpy()
+    err = np.linalg.norm(got - u_ref) / np.linalg.norm(u_ref)
+    print(f"face-averaged coarse coefficients, {name} {variant}: 3 FP64 cycles, rel L2 to the oracle {err:.2e}")
+    assert err <= 1e-10
+    g = np.random.default_rng(153).normal(size=u_ref.shape)
+    lam, _ = F.adjoint(torch.from_numpy(u_ref).to(DEV), torch.from_numpy(g).to(DEV), want_k=False, rtol=1e-13,
+                       max_cycles=60)
+    lam_ref = ref.adjoint_solve(g, rtol=1e-13)
+    assert np.linalg.norm(lam.cpu().numpy() - lam_ref) <= 1e-10 * np.linalg.norm(lam_ref)
+    F.close()

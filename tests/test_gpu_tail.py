@@ -10,14 +10,17 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-@pytest.mark.parametrize("name,coeff", [("sphere_2x16", True), ("sphere_2x16", False), ("uniform_4x16", True)])
-def test_tail_reproduces_the_launched_vcycle(name, coeff):
+@pytest.mark.parametrize("name,coeff,coarse_coef", [("sphere_2x16", True, "k"), ("sphere_2x16", False, "k"),
+                                                    ("uniform_4x16", True, "k"), ("sphere_2x16", True, "faces"),
+                                                    ("uniform_4x16", True, "faces")])
+def test_tail_reproduces_the_launched_vcycle(name, coeff, coarse_coef):
+    """Also with face-averaged coarse coefficients, whose coarse levels run the halved-face coefficient mode."""
     from paper_2403_08063_gb300 import Forest
     R, n, keys = syn.workload_forest(name)
     dev = torch.device(DEV)
     f = syn.gaussian_bump_with_noise(R, n, keys, seed=51, device=dev)
     k = syn.lognormal_k_rff(R, n, keys, seed=52, device=dev) if coeff else None
-    F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=2)
+    F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=2, coarse_coef=coarse_coef)
     F.set_rhs(f, k)
     nlev = len(F.levels())
     F.set_tail(-1)
