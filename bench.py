@@ -111,8 +111,13 @@ _SCHEDULE_BYTES_HALF_SWEEP = {True: 10.0, False: 6.0}
 # the unfused model with one FP64 outer residual per cycle, and the minimum of one fused down- and up-pass per level.
 _CYCLE_BYTES_MIXED = 78.0
 _CYCLE_BYTES_ALG_MIN = 37.7
+# face-averaged coarse levels read three FP32 face arrays instead of one 1/k: +8 B per coarse cell in each of the four
+# smoother passes and in the residual + restriction, 40 B per coarse cell and cycle, 1/7 coarse cell per finest cell
+_CYCLE_BYTES_FACES_EXTRA = 40.0 / 7.0
 
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
+
+_COARSE_COEF_NAMES = {"faces": "face-averaged from the finer level", "k": "rediscretised from the children's mean k"}
 
 
 def _smoother_report(prof, cells):
@@ -322,7 +327,7 @@ def run_ours(args):
     R, n, keys, k, f = _inputs(args.workload, dev)
     coeff = k is not None
     cells = len(keys) * n ** 3
-    F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=args.inner_cycles)
+    F = Forest(R, n, keys, coeff=coeff, precision=1, inner_cycles=args.inner_cycles, coarse_coef=args.coarse_coef)
     F.set_rhs(f, k)
     if args.tail != "auto":
         F.set_tail(int(args.tail))
@@ -417,7 +422,7 @@ def run_ours(args):
     setup_ms = (time.perf_counter() - q0) * 1e3
 
     # plain FP64 V-cycles on the same problem (time to 1e-10)
-    F64 = Forest(R, n, keys, coeff=coeff, precision=0)
+    F64 = Forest(R, n, keys, coeff=coeff, precision=0, coarse_coef=args.coarse_coef)
     F64.set_rhs(f, k)
     step(F64)
     torch.cuda.synchronize()
@@ -432,6 +437,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     t64 = s0.elapsed_time(s1) / 1e3 / reps64
     F64.close()
+
+    # the other coarse operator on the same problem (time to rtol, both arms), for comparison
+    alt = None
+    if coeff:
+        other = "k" if args.coarse_coef == "faces" else "faces"
+        alt = {"coarse_coefficients": _COARSE_COEF_NAMES[other]}
+        for name, prec, inner in (("fp32_in_fp64", 1, args.inner_cycles), ("fp64", 0, 1)):
+            G = Forest(R, n, keys, coeff=True, precision=prec, inner_cycles=inner, coarse_coef=other)
+            G.set_rhs(f, k)
+            step(G)
+            res, tg = _timed(lambda: step(G), 2)
+            alt[name] = {"time_to_rtol_ms": tg * 1e3, "cycles": res[-1][0]}
+            G.close()
+            del G
+        alt["speedup_fp32_in_fp64"] = alt["fp64"]["time_to_rtol_ms"] / alt["fp32_in_fp64"]["time_to_rtol_ms"]
 
     # end to end through the C ABI with host buffers (mg_solve_host): H2D of f and k, the set-up, the solve from a zero
     # initial guess, D2H of u -- one library call per step, timed on the host around it
@@ -461,12 +481,14 @@ def run_ours(args):
                        "levels": levels, "coefficient": "log-normal k (sigma 1, ell 0.1)" if coeff else "1",
                        "rhs": WORKLOADS[args.workload][2], "rtol": args.rtol, "cycle": "V(2,2) red-black GS",
                        "inner_cycles": args.inner_cycles,
+                       "coarse_coefficients": _COARSE_COEF_NAMES[args.coarse_coef] if coeff else None,
                        "smoother_shapes": [list(F.smoother_shape(l)) for l in range(len(levels))],
                        "persistent_tail_from_level": F.tail_level(),
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"{ws} independent replicas"},
             "cycles_per_solve": cycles, "final_rel_residual": rels[-1],
             "time_to_rtol_s": {"fp32_in_fp64": tmix, "fp64": t64, "speedup": t64 / tmix},
             "fp64_cycles_per_solve": cyc64, "fp64_glups_per_cycle": cells * statistics.mean(cyc64) / t64 / 1e9,
+            "other_coarse_operator": alt,
             "roofline": roof,
             "cycle_roofline": {
                 "glups": value, "peak_gbs": hbm, "peak_source": src,
@@ -476,7 +498,10 @@ def run_ours(args):
                 "achieved_gbs_alg_min": value * _CYCLE_BYTES_ALG_MIN,
                 "frac_alg_min": value * _CYCLE_BYTES_ALG_MIN / hbm,
                 "models": "78 B: FP32 V(2,2) with four smoother passes, residual+restriction and prolongation per "
-                          "level plus one FP64 residual per cycle; 37.7 B: one fused down- and up-pass per level"},
+                          "level plus one FP64 residual per cycle; 37.7 B: one fused down- and up-pass per level",
+                **({"face_averaged_coarse_extra_bytes": _CYCLE_BYTES_FACES_EXTRA,
+                    "frac_with_face_coarse_bytes": value * (_CYCLE_BYTES_MIXED + _CYCLE_BYTES_FACES_EXTRA) / hbm}
+                   if coeff and args.coarse_coef == "faces" else {})},
             "setup_ms": {"mg_set_rhs": round(setup_ms, 3), "in_value": False},
             "smoother_finest": _smoother_report(prof, cells),
             "kernel_families_ms": {k_: round(v[0], 3) for k_, v in prof.items() if v[1]},
@@ -493,7 +518,7 @@ def run_ours(args):
     del F64
     if rank == 0 and ws == 1 and not getattr(args, "no_other_configs", False):
         torch.cuda.empty_cache()
-        out["other_configs"] = run_other_configs(dev)
+        out["other_configs"] = run_other_configs(dev, args.coarse_coef)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -516,7 +541,7 @@ def _timed(fn, reps):
     return out, e0.elapsed_time(e1) / 1e3 / reps
 
 
-def _cfg_small(dev):
+def _cfg_small(dev, cc):
     """2^3 roots of 16^3 (32,768 cells), -Laplace with the sin-product right-hand side, FP64 V(2,2), exactly 10
     cycles: launch-latency-bound, reported as microseconds per cycle."""
     import synthetic as syn
@@ -544,7 +569,7 @@ def _cfg_small(dev):
             "timing": "20 repetitions of 10 cycles from u = 0 (each ends with the residual and the copy of u)"}
 
 
-def _cfg_refined(dev):
+def _cfg_refined(dev, cc):
     """The refined 56 + 64 block forest of 32^3 blocks (3,932,160 cells), Gaussian bump plus noise, solved to
     1e-10 in FP64 (and with FP32 cycles inside FP64 defect correction for comparison)."""
     import synthetic as syn
@@ -572,7 +597,7 @@ def _cfg_refined(dev):
     return res
 
 
-def _cfg_adjoint(dev):
+def _cfg_adjoint(dev, cc):
     """The differentiation workload: 4^3 roots of 32^3 refined twice around the sphere (448 + 512 blocks,
     31,457,280 cells), log-normal k, bump f; forward FP32-in-FP64 solve to 1e-10, then the adjoint solve (transposed
     V-cycles) giving dL/df and dL/dk for L = 1/2 ||u - u_t||^2."""
@@ -583,7 +608,7 @@ def _cfg_adjoint(dev):
     f = syn.gaussian_bump_with_noise(R, n, keys, seed=6, device=dev)
     ut = syn.sin_target(R, n, keys, seed=7, device=dev)
     cells = len(keys) * n ** 3
-    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=4)
+    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=4, coarse_coef=cc)
     t0 = time.perf_counter()
     F.set_rhs(f, k)
     torch.cuda.synchronize()
@@ -604,14 +629,14 @@ def _cfg_adjoint(dev):
     _, ts = _timed(lambda: F.set_rhs(f, k), 3)
     F.close()
     return {"workload": "sphere_4x32 (448 + 512 blocks of 32^3, log-normal k, bump f, sin target)",
-            "cells": cells, "forward_ms": tf * 1e3, "forward_cycles": fo[-1][0], "adjoint_ms": ta * 1e3,
+            "cells": cells, "coarse_coefficients": _COARSE_COEF_NAMES[cc], "forward_ms": tf * 1e3, "forward_cycles": fo[-1][0], "adjoint_ms": ta * 1e3,
             "forward_plus_adjoint_ms": (tf + ta) * 1e3, "setup_ms": ts * 1e3, "first_setup_s": first_setup_s,
             "forward_glups_per_cycle": cells * fo[-1][0] / tf / 1e9,
             "adjoint": "lambda = A^-T (u - u_t) to 1e-10 by defect correction with the transposed V-cycle, "
                        "dL/df = lambda, dL/dk face by face"}
 
 
-def _cfg_batch(dev):
+def _cfg_batch(dev, cc):
     """256 independent single-root problems (block sizes 16..128, 0-2 refinement levels, log-normal k, U(-1, 1)
     f), each solved to 1e-8 with FP32 cycles inside FP64 defect correction, one graph launch per step."""
     import synthetic as syn
@@ -624,7 +649,7 @@ def _cfg_batch(dev):
     gen_s = time.perf_counter() - t0
     cells = f.numel()
     t0 = time.perf_counter()
-    B = Batch(leaves, ns, coeff=True, inner_cycles=5)
+    B = Batch(leaves, ns, coeff=True, inner_cycles=5, coarse_coef=cc)
     B.set_rhs(f, k)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -642,12 +667,13 @@ def _cfg_batch(dev):
     del f, k, u
     torch.cuda.empty_cache()
     return {"workload": "batch_256", "problems": 256, "cells": cells, "groups": info["groups"], "rtol": 1e-8,
+            "coarse_coefficients": _COARSE_COEF_NAMES[cc],
             "solve_ms": t * 1e3, "cycles_max": cyc, "glups_per_cycle": cells * cyc / t / 1e9,
             "worst_rel_residual": max(out[-1][1]), "inputs_s": gen_s, "create_and_first_setup_s": setup_s,
             "timing": "2 solves after 1 warm-up, graph-launched"}
 
 
-def run_other_configs(dev):
+def run_other_configs(dev, cc):
     out = {}
     for name, fn in (("c1_uniform_2x16_fp64", _cfg_small), ("c2_sphere_2x32", _cfg_refined),
                      ("c5_sphere_4x32_adjoint", _cfg_adjoint), ("c4_batch_256", _cfg_batch)):
@@ -655,7 +681,7 @@ def run_other_configs(dev):
         sampler.start()
         w0 = time.perf_counter()
         try:
-            rec = fn(dev)
+            rec = fn(dev, cc)
         except Exception as e:  # a failing extra configuration must not hide the headline line
             rec = {"error": f"{type(e).__name__}: {e}"}
         rec["wall_s"] = time.perf_counter() - w0
@@ -677,7 +703,7 @@ def run_batch(args):
     leaves, ns = syn.batch_leaves(problems)
     f, k = syn.batch_fields(problems, seed=0, device=dev)
     cells = f.numel()
-    B = Batch(leaves, ns, coeff=True, inner_cycles=args.inner_cycles)
+    B = Batch(leaves, ns, coeff=True, inner_cycles=args.inner_cycles, coarse_coef=args.coarse_coef)
     B.set_rhs(f, k)
     if args.tail == "-1":
         B.set_tail_off()
@@ -721,7 +747,9 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 outer",
             "data": "synthetic",
             "config": {"workload": args.workload, "problems": count, "cells": cells, "groups": B.info()["groups"],
-                       "rtol": rtol, "inner_cycles": args.inner_cycles, "persistent_tail_from_level": B.tail_levels(),
+                       "rtol": rtol, "inner_cycles": args.inner_cycles,
+                       "coarse_coefficients": _COARSE_COEF_NAMES[args.coarse_coef],
+                       "persistent_tail_from_level": B.tail_levels(),
                        "graphs": "one defect-correction step of "
                        "all groups per graph launch", "l2": "inputs larger than L2 (no flush)"},
             "cycles_per_solve_max": cyc_run, "cycles_per_problem_last": runs[-1][0],
@@ -870,12 +898,15 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform_8x64_k")
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--inner-cycles", type=int, default=0,
-                    help="FP32 V-cycles per FP64 defect-correction step (0: 4 for single solves to 1e-10, 5 for the "
-                         "batches solved to 1e-8, the fastest counts measured on a GB300)")
+                    help="FP32 V-cycles per FP64 defect-correction step (0: 5 for the batches solved to 1e-8 and "
+                         "for variable-k solves with face-averaged coarse levels, else 4)")
     ap.add_argument("--tail", default="auto",
                     help="level from which the persistent tail kernel runs the FP32 V-cycle (-1: off; auto: tuned)")
     ap.add_argument("--smoother-shape", default="",
                     help="FP32 smoother launch shape of the finest level, e.g. 2,16,16,2,4 (default: tuned)")
+    ap.add_argument("--coarse-coef", choices=sorted(_COARSE_COEF_NAMES), default="faces",
+                    help="coarse-level coefficients with variable k: faces (each coarse face the mean of the finer "
+                         "faces it covers) or k (rediscretised from the mean of the children's k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="skip the other configurations (small FP64 forest, refined forest, adjoint, batch)")
@@ -883,7 +914,10 @@ def main():
                     help="block sizes of the paper_table workload (256 needs about 130 GB on the device)")
     args = ap.parse_args()
     if args.inner_cycles <= 0:
-        args.inner_cycles = 5 if args.workload.startswith("batch") else 4
+        # the fastest counts measured on a GB300: 5 for the batches (to 1e-8) and for variable-k solves with
+        # face-averaged coarse levels (10 cycles to 1e-10 at 512^3, against 12 with 4 or 6), else 4
+        faces_k = args.coarse_coef == "faces" and WORKLOADS[args.workload][1]
+        args.inner_cycles = 5 if args.workload.startswith("batch") or faces_k else 4
     if args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith("batch"):

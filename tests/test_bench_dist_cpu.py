@@ -138,7 +138,8 @@ def test_gpu_arm_json_contract_with_a_stand_in_library(monkeypatch, capsys):
     monkeypatch.setattr(bench, "ClockSampler", Sampler)
     monkeypatch.setattr(bench, "_inputs", inputs)
     args = types.SimpleNamespace(workload="uniform_8x64_k", inner_cycles=4, tail="auto", smoother_shape="",
-                                 warmup=3, steps=5, rtol=1e-10, no_cpu_baseline=True, gpus=1, no_other_configs=True)
+                                 warmup=3, steps=5, rtol=1e-10, no_cpu_baseline=True, gpus=1, no_other_configs=True,
+                                 coarse_coef="faces")
     bench.run_ours(args)
     lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -162,7 +163,12 @@ def test_gpu_arm_json_contract_with_a_stand_in_library(monkeypatch, capsys):
     assert abs(cyc["achieved_gbs"] - d["value"] * 78.0) < 1e-9 and abs(cyc["frac"] * cyc["peak_gbs"] -
                                                                      cyc["achieved_gbs"]) < 1e-9
     assert d["e2e"]["h2d_bytes_per_step"] == 2 * cells * 8 and d["e2e"]["d2h_bytes_per_step"] == cells * 8
-    assert StandIn.set_rhs_calls == 4  # the timed forest's set-up, two set-up repeats, the FP64 forest's
+    assert d["config"]["coarse_coefficients"].startswith("face-averaged")
+    alt = d["other_coarse_operator"]
+    assert alt["coarse_coefficients"].startswith("rediscretised") and alt["fp64"]["cycles"] == 12
+    assert abs(cyc["frac_with_face_coarse_bytes"] * cyc["peak_gbs"] - d["value"] * (78.0 + 40.0 / 7.0)) < 1e-9
+    # the timed forest's set-up, two set-up repeats, the FP64 forest's, the two forests of the other coarse operator
+    assert StandIn.set_rhs_calls == 6
 
 
 def test_host_cpu_description():
