@@ -191,6 +191,14 @@ __device__ __forceinline__ float div6(float t) {
     return fmaf(t, hi, t * lo);
 }
 
+// Two lanes of frcp and div6 for the paired FP32 instructions (each component as the scalar function).
+__device__ __forceinline__ float2 frcp2(float2 x) { return float2{frcp(x.x), frcp(x.y)}; }
+__device__ __forceinline__ float2 div6x2(float2 t) {
+    constexpr float hi = 1.0f / 6.0f;
+    constexpr float lo = static_cast<float>(1.0 / 6.0 - static_cast<double>(1.0f / 6.0f));
+    return __ffma2_rn(t, float2{hi, hi}, __fmul2_rn(t, float2{lo, lo}));
+}
+
 // Conversions between binary64 and binary32 with an exact power-of-two scale, written on the IEEE 754 bit fields
 // (1 sign bit; 11 / 8 exponent bits with bias 1023 / 127; 52 / 23 fraction bits) so that they run on the integer
 // pipes: the hardware conversion instructions between the two formats issue on the FP64 pipe, the bottleneck of
@@ -960,9 +968,12 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
     uint64_t *bar = reinterpret_cast<uint64_t *>(ou + s32t_bar_floats(plan));
     uint64_t *ebar = bar + 1 + G, *ibar = ebar + G;
 
+    // the second colour walks the tiles in reverse: it starts where the first colour's launch ended, on the blocks
+    // whose u and 1/k that launch left in L2 (the updates of one colour are independent, so the order changes nothing)
+    const unsigned bid = colour ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int nty = n / TY;
-    const int ty = static_cast<int>(blockIdx.x % nty);
-    const int64_t rest = blockIdx.x / nty;
+    const int ty = static_cast<int>(bid % nty);
+    const int64_t rest = bid / nty;
     const int tz = static_cast<int>(rest % (n / TZ));
     const int64_t b = rest / (n / TZ);
     if (skip(b)) return;  // uniform over the CTA, before any barrier
@@ -1074,21 +1085,64 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
             const int qz = qo0 + k * PL;
             const auto plane = [&](auto Cc) {
                 constexpr int C = decltype(Cc)::value;
+                float pn0[R], pn1[R], val[R];
+                [[maybe_unused]] float qn0[R], qn1[R];  // kappa pair of plane z + 1 (MODE 2)
 #pragma unroll
                 for (int rr = 0; rr < R; ++rr) {
                     const int ro = ro0 + rr * rstep;
-                    const float pn0 = on[ro], pn1 = on[ro + 1];
+                    pn0[rr] = on[ro];
+                    pn1[rr] = on[ro + 1];
+                    if constexpr (MODE == 2) {
+                        qn0[rr] = kn[ro];
+                        qn1[rr] = kn[ro + 1];
+                    }
+                }
+                // rows in pairs on the paired FP32 instructions (each component rounds as the scalar operation, in
+                // the same order as the column smoother), an odd last row alone
+#pragma unroll
+                for (int rr = 0; rr + 1 < R; rr += 2) {
+                    const int ra = ro0 + rr * rstep, rb = ra + rstep;
+                    const float2 ym{oc[ra - H + C], oc[rb - H + C]}, yp{oc[ra + H + C], oc[rb + H + C]};
+                    const float2 fv{fw[ra - H + C], fw[rb - H + C]};
+                    const float2 x0{pc[rr][0], pc[rr + 1][0]}, x1{pc[rr][1], pc[rr + 1][1]};
+                    const float2 zm{zmu[rr], zmu[rr + 1]};
+                    const float2 zp = C ? float2{pn1[rr], pn1[rr + 1]} : float2{pn0[rr], pn0[rr + 1]};
+                    float2 v;
+                    if constexpr (MODE == 2) {
+                        const float2 kym{kc[ra - H + C], kc[rb - H + C]}, kyp{kc[ra + H + C], kc[rb + H + C]};
+                        const float2 k0{kw[ra - H + C], kw[rb - H + C]};
+                        const float2 kzp = C ? float2{qn1[rr], qn1[rr + 1]} : float2{qn0[rr], qn0[rr + 1]};
+                        const float2 a0 = frcp2(__fadd2_rn(k0, float2{qc[rr][0], qc[rr + 1][0]}));
+                        const float2 a1 = frcp2(__fadd2_rn(k0, float2{qc[rr][1], qc[rr + 1][1]}));
+                        const float2 b0 = frcp2(__fadd2_rn(k0, kym)), b1 = frcp2(__fadd2_rn(k0, kyp));
+                        const float2 e0 = frcp2(__fadd2_rn(k0, float2{zmk[rr], zmk[rr + 1]}));
+                        const float2 e1 = frcp2(__fadd2_rn(k0, kzp));
+                        float2 sacc = __fmul2_rn(a0, x0);
+                        sacc = __ffma2_rn(a1, x1, sacc);
+                        sacc = __ffma2_rn(b0, ym, sacc);
+                        sacc = __ffma2_rn(b1, yp, sacc);
+                        sacc = __ffma2_rn(e0, zm, sacc);
+                        sacc = __ffma2_rn(e1, zp, sacc);
+                        const float2 Dn =
+                            __fadd2_rn(__fadd2_rn(__fadd2_rn(a0, a1), __fadd2_rn(b0, b1)), __fadd2_rn(e0, e1));
+                        v = __fmul2_rn(__ffma2_rn(float2{hh, hh}, fv, sacc), frcp2(Dn));
+                    } else {
+                        const float2 S = __fadd2_rn(__fadd2_rn(__fadd2_rn(x0, x1), __fadd2_rn(ym, yp)), __fadd2_rn(zm, zp));
+                        v = div6x2(__ffma2_rn(float2{hb, hb}, fv, S));
+                    }
+                    val[rr] = v.x;
+                    val[rr + 1] = v.y;
+                }
+                if constexpr (R & 1) {
+                    constexpr int rr = R - 1;
+                    const int ro = ro0 + rr * rstep;
                     const float ym = oc[ro - H + C], yp = oc[ro + H + C];
                     const float fv = fw[ro - H + C];
-                    const float zp = C ? pn1 : pn0;
-                    float val;
-                    [[maybe_unused]] float qn0 = 0.f, qn1 = 0.f;  // kappa pair of plane z + 1 (MODE 2)
+                    const float zp = C ? pn1[rr] : pn0[rr];
                     if constexpr (MODE == 2) {
-                        qn0 = kn[ro];
-                        qn1 = kn[ro + 1];
                         const float kym = kc[ro - H + C], kyp = kc[ro + H + C];
                         const float k0 = kw[ro - H + C];
-                        const float kzp = C ? qn1 : qn0;
+                        const float kzp = C ? qn1[rr] : qn0[rr];
                         const float a0 = frcp(k0 + qc[rr][0]), a1 = frcp(k0 + qc[rr][1]);
                         const float b0 = frcp(k0 + kym), b1 = frcp(k0 + kyp);
                         const float e0 = frcp(k0 + zmk[rr]), e1 = frcp(k0 + kzp);
@@ -1099,23 +1153,26 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
                         sacc = fmaf(e0, zmu[rr], sacc);
                         sacc = fmaf(e1, zp, sacc);
                         const float Dn = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
-                        val = fmaf(hh, fv, sacc) * frcp(Dn);
+                        val[rr] = fmaf(hh, fv, sacc) * frcp(Dn);
                     } else {
                         const float S = ((pc[rr][0] + pc[rr][1]) + (ym + yp)) + (zmu[rr] + zp);
-                        val = div6(fmaf(hb, fv, S));
+                        val[rr] = div6(fmaf(hb, fv, S));
                     }
+                }
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
                     const int q = qz + rr * qstep + C;
-                    us[q] = val;
-                    if (xs == C && xw) xw[q] = xsg * val;
-                    if (yr == rr) yw[q] = ysg * val;
-                    if (zw) zw[q] = zsg * val;
+                    us[q] = val[rr];
+                    if (xs == C && xw) xw[q] = xsg * val[rr];
+                    if (yr == rr) yw[q] = ysg * val[rr];
+                    if (zw) zw[q] = zsg * val[rr];
                     zmu[rr] = pc[rr][1 - C];
-                    pc[rr][0] = pn0;
-                    pc[rr][1] = pn1;
+                    pc[rr][0] = pn0[rr];
+                    pc[rr][1] = pn1[rr];
                     if constexpr (MODE == 2) {
                         zmk[rr] = qc[rr][1 - C];
-                        qc[rr][0] = qn0;
-                        qc[rr][1] = qn1;
+                        qc[rr][0] = qn0[rr];
+                        qc[rr][1] = qn1[rr];
                     }
                 }
             };
