@@ -795,11 +795,11 @@ __device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
 }
 __device__ inline void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ inline void mbar_arm(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 // plain arrival (release) of one thread on `bar`
 __device__ inline void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // global -> shared bulk copy completing on `bar`; both addresses 16-byte aligned, bytes a multiple of 16
 __device__ inline void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -812,7 +812,7 @@ __device__ inline void bulk_load(void *dst, const void *src, uint32_t bytes, uin
 __device__ inline bool mbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
         : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
         : "memory");
@@ -1067,6 +1067,12 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
             zmk[rr] = qc[rr][0] = qc[rr][1] = 0.f;
         }
     }
+    // Slot 0 (plane z0 - 1) is refilled by a bulk copy once every warp has arrived on ibar, but its values are only
+    // used at the first plane, so nothing forces these loads to have read shared memory by the time of the arrival:
+    // without this fence the copy was seen to overwrite the slot under them (the z-minus 1/k of a warp's rows came
+    // from plane z0 + D + 1, mostly when other kernels shared the SMs).  The proxy fence orders this thread's
+    // generic-proxy reads of the slot before the async-proxy writes that follow the arrival.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(ibar);
     // ring positions: other-half slots of planes z + 1 and z, own-half slot and group barrier of plane z
@@ -1178,7 +1184,9 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
             };
             if ((cpar + k) & 1) plane(std::integral_constant<int, 1>{});
             else plane(std::integral_constant<int, 0>{});
-            // this warp is done with the slots of group k and other-half plane z: group k + G may refill them
+            // this warp is done with the slots of group k and other-half plane z: group k + G may refill them.  Every
+            // value read from those slots fed an update stored above, and the release arrival orders the stores (and
+            // so the reads they needed) before the refill; the first planes' slot 0 is the case that needs a fence
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&ebar[g_s]);
             oc_s = on_s;

@@ -63,3 +63,36 @@ def test_smoother_shape_arguments_are_checked():
     assert F64.smoother_shape(0) == (0, 0, 0, 0, 0) and F64.smoother_shapes(0) == []
     with pytest.raises(MGError):
         F64.set_smoother_shape(0, (1, 1, 256, 0, 0))
+
+
+@pytest.mark.parametrize("shape", [(2, 16, 16, 4, 4), (2, 16, 32, 4, 4)])
+def test_staged_smoother_is_bit_reproducible_next_to_other_kernels(shape):
+    """The staged smoother's shared-memory ring must not depend on how fast its warps run: with unrelated kernels
+    occupying the SMs from another stream, one FP32-in-FP64 step of 4^3 roots of 64^3 cells (variable k, the 512^3
+    workload's shapes) repeated eight times gives the same bits every time.  Before the first planes' loads were
+    fenced against the bulk copy that refills their slot, most repeats here differed."""
+    from paper_2403_08063_gb300 import Forest
+    R, n = 4, 64
+    keys = syn.uniform_leaves(R)
+    dev = torch.device(DEV)
+    k = syn.lognormal_k_rff(R, n, keys, seed=3, device=dev)
+    f = syn.uniform_rhs(len(keys), n, seed=4).to(dev)
+    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=2)
+    F.set_rhs(f, k)
+    F.set_smoother_shape(0, shape)
+    side = torch.cuda.Stream()
+    busy = torch.randn(64 * 1024 * 1024, device=dev)
+    outs = []
+    for rep in range(8):
+        u = torch.zeros_like(f)
+        torch.cuda.synchronize()
+        if rep % 2:
+            with torch.cuda.stream(side):
+                for _ in range(20):
+                    busy.mul_(1.0000001).add_(1e-7)
+        F.vcycle(u, 1)
+        torch.cuda.synchronize()
+        outs.append(u)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    F.close()
