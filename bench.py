@@ -663,11 +663,12 @@ def _cfg_batch(dev, cc):
     out, t = _timed(run, 2)
     cyc = max(out[-1][0])
     info = B.info()
+    mode, tails = B.tail_mode(), B.tail_levels()
     B.close()
     del f, k, u
     torch.cuda.empty_cache()
     return {"workload": "batch_256", "problems": 256, "cells": cells, "groups": info["groups"], "rtol": 1e-8,
-            "coarse_coefficients": _COARSE_COEF_NAMES[cc],
+            "coarse_coefficients": _COARSE_COEF_NAMES[cc], "tail_mode": mode, "persistent_tail_from_level": tails,
             "solve_ms": t * 1e3, "cycles_max": cyc, "glups_per_cycle": cells * cyc / t / 1e9,
             "worst_rel_residual": max(out[-1][1]), "inputs_s": gen_s, "create_and_first_setup_s": setup_s,
             "timing": "2 solves after 1 warm-up, graph-launched"}
@@ -750,6 +751,8 @@ def run_batch(args):
                        "rtol": rtol, "inner_cycles": args.inner_cycles,
                        "coarse_coefficients": _COARSE_COEF_NAMES[args.coarse_coef],
                        "persistent_tail_from_level": B.tail_levels(),
+                       "tail_mode": {0: "every level launched", 1: "each group's own persistent tail",
+                                     2: "one joint persistent tail per V-cycle"}[B.tail_mode()],
                        "graphs": "one defect-correction step of "
                        "all groups per graph launch", "l2": "inputs larger than L2 (no flush)"},
             "cycles_per_solve_max": cyc_run, "cycles_per_problem_last": runs[-1][0],

@@ -261,6 +261,20 @@ mg_status mg_batch_info(const mg_batch *batch, int32_t *n_groups, int64_t *total
 mg_status mg_batch_profile(mg_batch *batch, int32_t enable);
 /* The multi-problem forest of group g (owned by the batch), e.g. for mg_profile_read; NULL if out of range. */
 mg_forest *mg_batch_group(mg_batch *batch, int32_t g);
+/* How the coarse levels of the batch's FP32 V-cycles run (the batching extension; the paper launches one forest's
+ * cycle level by level, Sec. 4):
+ *   0  every level of every group as separate kernel launches (each group on its own stream);
+ *   1  each group's levels from its tuned tail level down (and back up) in one persistent cooperative launch of its
+ *      own, concurrently with the other groups' launches;
+ *   2  one joint persistent cooperative launch per V-cycle running the tails of all groups: each group first runs
+ *      its levels above the tail on its own stream, then every group waits for the joint tail, then each runs its
+ *      levels back up.  Between two grid barriers the joint tail runs one phase of every group.
+ * mg_batch_set_rhs picks the fastest of the three on first use (one timed defect-correction step of all groups
+ * each); mg_batch_set_tail_mode overrides it (MG_ERR_STATE before mg_batch_set_rhs, MG_ERR_INVALID_ARG for another
+ * mode).  All three give bit-identical iterates.  A grid barrier of the persistent launches that waits longer than
+ * about half a second makes the next call return MG_ERR_TIMEOUT. */
+mg_status mg_batch_set_tail_mode(mg_batch *batch, int32_t mode);
+mg_status mg_batch_get_tail_mode(const mg_batch *batch, int32_t *mode);
 
 /* Thread-local description of the last error (empty string if none); the pointer stays valid until the next failing
  * call on the same thread.  No counterpart in the paper: error reporting of this library's C ABI. */

@@ -86,6 +86,8 @@ SIGNATURES = {
     "mg_batch_info": (I32, [P, IP, _c.POINTER(_c.c_int64), IP, IP]),
     "mg_batch_profile": (I32, [P, I32]),
     "mg_batch_group": (P, [P, I32]),
+    "mg_batch_set_tail_mode": (I32, [P, I32]),
+    "mg_batch_get_tail_mode": (I32, [P, IP]),
     "mg_last_error": (_c.c_char_p, []),
 }
 

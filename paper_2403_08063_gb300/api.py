@@ -301,8 +301,17 @@ class Batch:
 
     def set_tail_off(self):
         """Runs every group's FP32 V-cycle as separate launches (no persistent tail)."""
-        for g in range(len(self.info()["groups"])):
-            _lib.check(self.lib.mg_set_tail(ctypes.c_void_p(self.lib.mg_batch_group(self.h, g)), -1))
+        self.set_tail_mode(0)
+
+    def tail_mode(self):
+        """0: every level launched; 1: each group's own persistent tail; 2: one joint persistent tail per V-cycle."""
+        m = ctypes.c_int32()
+        _lib.check(self.lib.mg_batch_get_tail_mode(self.h, ctypes.byref(m)))
+        return m.value
+
+    def set_tail_mode(self, mode):
+        """Overrides the tuned tail mode (see tail_mode); after set_rhs."""
+        _lib.check(self.lib.mg_batch_set_tail_mode(self.h, int(mode)))
 
     def profile(self, enable=True):
         _lib.check(self.lib.mg_batch_profile(self.h, int(bool(enable))))

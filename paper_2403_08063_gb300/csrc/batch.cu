@@ -29,9 +29,18 @@ struct mg_batch {
     int *flag = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_m = 0;
-    std::vector<int> graph_tails;  // the groups' tail levels when the graph was captured
+    std::vector<int> graph_tails;  // the groups' tail levels (and the tail mode, last) when the graph was captured
     bool rhs_set = false;
     bool tails_tuned = false;
+    // persistent tails: 0 every level launched, 1 each group's own tail, 2 one joint tail per V-cycle
+    int tail_mode = 0;
+    std::vector<int> tuned_tails;         // each group's tuned tail level (-1: none)
+    cudaEvent_t ev_joint = nullptr;       // the joint tail done (groups[0]'s stream), awaited by the other groups
+    octmg::TailArgs *jt_args = nullptr;   // device: every group's tail arguments
+    octmg::BatchEntry *jt_entries = nullptr;
+    int jt_ne = 0, jt_cap = 0;
+    unsigned *jt_bar = nullptr;
+    int64_t jt_need = 1;
 };
 
 namespace octmg {
@@ -55,6 +64,10 @@ void destroy_batch(mg_batch *B) {
     for (cudaEvent_t e : B->gev) cudaEventDestroy(e);
     for (cudaStream_t s : B->gst) cudaStreamDestroy(s);
     if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+    if (B->ev_joint) cudaEventDestroy(B->ev_joint);
+    if (B->jt_args) cudaFree(B->jt_args);
+    if (B->jt_entries) cudaFree(B->jt_entries);
+    if (B->jt_bar) cudaFree(B->jt_bar);
     if (B->flag) cudaFree(B->flag);
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
@@ -88,9 +101,84 @@ mg_status join(mg_batch *B) {
     return MG_OK;
 }
 
-// One FP32 defect-correction step of every group with unconverged problems is enqueued (no synchronisation).
+// The joint tail's entry list: phase i of every group that has one, then a grid barrier (groups with a recorded
+// tail only; their phase lists are aligned from the first phase).  Uploaded with the groups' tail arguments.
+mg_status build_joint_tail(mg_batch *B) {
+    std::vector<TailArgs> args;
+    std::vector<BatchEntry> e;
+    size_t longest = 0;
+    B->jt_need = 1;
+    for (mg_forest *F : B->groups) {
+        args.push_back(tail_args(F));
+        if (F->tail_level >= 0) {
+            longest = std::max(longest, F->tail_ph_host.size());
+            B->jt_need += tail_ctas(F);
+        }
+    }
+    for (size_t i = 0; i < longest; ++i) {
+        const size_t first = e.size();
+        for (size_t g = 0; g < B->groups.size(); ++g) {
+            const mg_forest *F = B->groups[g];
+            if (F->tail_level >= 0 && i < F->tail_ph_host.size())
+                e.push_back({static_cast<int32_t>(g), 0, F->tail_ph_host[i]});
+        }
+        if (e.size() > first) e.back().last = 1;
+    }
+    if (!B->jt_args) {
+        MG_CUDA(cudaMalloc(&B->jt_args, B->groups.size() * sizeof(TailArgs)));
+        MG_CUDA(cudaMalloc(&B->jt_bar, 2 * sizeof(unsigned)));
+    }
+    if (static_cast<int>(e.size()) > B->jt_cap) {
+        if (B->jt_entries) cudaFree(B->jt_entries);
+        B->jt_entries = nullptr;
+        MG_CUDA(cudaMalloc(&B->jt_entries, std::max<size_t>(1, e.size()) * sizeof(BatchEntry)));
+        B->jt_cap = static_cast<int>(e.size());
+    }
+    MG_CUDA(cudaMemcpyAsync(B->jt_args, args.data(), args.size() * sizeof(TailArgs), cudaMemcpyHostToDevice, B->st));
+    if (!e.empty())
+        MG_CUDA(cudaMemcpyAsync(B->jt_entries, e.data(), e.size() * sizeof(BatchEntry), cudaMemcpyHostToDevice, B->st));
+    MG_CUDA(cudaStreamSynchronize(B->st));
+    B->jt_ne = static_cast<int>(e.size());
+    return MG_OK;
+}
+
+// groups[0]'s stream waits for every other group's work so far; it then runs the joint tail, and the other groups'
+// streams wait for it.
+mg_status enqueue_joint_tail(mg_batch *B) {
+    mg_forest *F0 = B->groups[0];
+    for (size_t g = 1; g < B->groups.size(); ++g) {
+        MG_CUDA(cudaEventRecord(B->gev[g], B->gst[g]));
+        MG_CUDA(cudaStreamWaitEvent(B->gst[0], B->gev[g], 0));
+    }
+    if (B->jt_ne > 0) {
+        Prof p(F0, P_TAIL32, 1);
+        MG_TRY(launch_batch_tail32(B->groups.data(), B->jt_args, B->jt_entries, B->jt_ne, B->jt_bar, B->jt_need));
+    }
+    MG_CUDA(cudaEventRecord(B->ev_joint, B->gst[0]));
+    for (size_t g = 1; g < B->groups.size(); ++g) MG_CUDA(cudaStreamWaitEvent(B->gst[g], B->ev_joint, 0));
+    return MG_OK;
+}
+
+// One FP32 defect-correction step of every group with unconverged problems is enqueued (no synchronisation).  With
+// the joint tail every V-cycle is three stages: each group's steps down to its tail level (on its own stream), the
+// joint tail of all groups (one cooperative launch), each group's steps back up.
 mg_status enqueue_step(mg_batch *B, int m) {
     MG_TRY(fork(B));
+    if (B->tail_mode == 2) {
+        for (mg_forest *F : B->groups) MG_TRY(enqueue_done(F));
+        for (int c = 0; c < m; ++c) {
+            for (mg_forest *F : B->groups) vcycle32_part(F, 1);
+            MG_TRY(enqueue_joint_tail(B));
+            for (mg_forest *F : B->groups) vcycle32_part(F, 2);
+        }
+        for (mg_forest *F : B->groups) {
+            MG_TRY(enqueue_update_mixed(F));
+            MG_TRY(enqueue_scales(F));
+            MG_TRY(enqueue_residual(F));
+            MG_TRY(enqueue_problem_sums(F));
+        }
+        return join(B);
+    }
     for (mg_forest *F : B->groups) {
         MG_TRY(enqueue_done(F));
         MG_TRY(enqueue_fp32_step(F, m));
@@ -101,27 +189,40 @@ mg_status enqueue_step(mg_batch *B, int m) {
     return join(B);
 }
 
+// Tail mode 0 / 1 / 2 with the tuned tail levels (mode 0 turns every group's tail off).
+mg_status apply_tail_mode(mg_batch *B, int mode) {
+    for (size_t g = 0; g < B->groups.size(); ++g) {
+        mg_forest *F = B->groups[g];
+        const int lt = mode == 0 ? -1 : B->tuned_tails[g];
+        if (lt >= 0 && F->tail_for != lt) MG_TRY(record_tail(F, lt));
+        F->tail_level = lt;
+    }
+    B->tail_mode = mode;
+    if (mode == 2) MG_TRY(build_joint_tail(B));
+    return MG_OK;
+}
+
 // The groups' tail levels were tuned one group at a time; run concurrently, a cooperative tail launch may wait for
-// other groups' kernels to leave the SMs it needs.  So the batch times one defect-correction step of all groups
-// with the tuned tails and with every tail off (one untimed and two timed steps each, on the groups' pools, which
-// are dead between solves) and keeps the faster setting.
+// other groups' kernels to leave the SMs it needs.  So the batch times one defect-correction step of all groups in
+// each tail mode -- every level launched, each group's own tail, one joint tail per V-cycle -- (one untimed and two
+// timed steps each, on the groups' pools, which are dead between solves) and keeps the fastest.
 mg_status tune_batch_tails(mg_batch *B) {
-    std::vector<int> tuned;
+    B->tuned_tails.clear();
     bool any = false;
     for (mg_forest *F : B->groups) {
-        tuned.push_back(F->tail_level);
+        B->tuned_tails.push_back(F->tail_level);
         any = any || F->tail_level >= 0;
         set_scales_host(F, std::vector<double>(F->np, 1.0));
     }
-    if (!any) return MG_OK;
+    if (!any) return apply_tail_mode(B, 0);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MG_CUDA(cudaEventCreate(&e0));
     MG_CUDA(cudaEventCreate(&e1));
-    float ms[2] = {0.0f, 0.0f};
+    float ms[3] = {0.0f, 0.0f, 0.0f};
     const int m = std::max(1, B->cfg.inner_cycles);
     mg_status st = MG_OK;
-    for (int v = 0; v < 2 && st == MG_OK; ++v) {
-        for (size_t g = 0; g < B->groups.size(); ++g) B->groups[g]->tail_level = v ? tuned[g] : -1;
+    for (int v = 0; v < 3 && st == MG_OK; ++v) {
+        if ((st = apply_tail_mode(B, v)) != MG_OK) break;
         if ((st = enqueue_step(B, m)) != MG_OK) break;
         if (cudaEventRecord(e0, B->st) != cudaSuccess) st = MG_ERR_CUDA;
         for (int r = 0; r < 2 && st == MG_OK; ++r) st = enqueue_step(B, m);
@@ -135,7 +236,10 @@ mg_status tune_batch_tails(mg_batch *B) {
         if (st == MG_ERR_CUDA) set_error("timing the batch tails failed");
         return st;
     }
-    for (size_t g = 0; g < B->groups.size(); ++g) B->groups[g]->tail_level = ms[1] < ms[0] ? tuned[g] : -1;
+    int best = 0;
+    for (int v = 1; v < 3; ++v)
+        if (ms[v] < ms[best]) best = v;
+    MG_TRY(apply_tail_mode(B, best));
     for (mg_forest *F : B->groups) MG_TRY(check_kernel_waits(F));
     return MG_OK;
 }
@@ -213,6 +317,7 @@ mg_status batch_solve(mg_batch *B, double *u_dev, double rtol, int max_cycles, i
         if (m == inner && !profiling(B)) {
             std::vector<int> tails;
             for (mg_forest *F : B->groups) tails.push_back(F->tail_level);
+            tails.push_back(B->tail_mode);
             if (!B->graph || B->graph_m != m || B->graph_tails != tails) {
                 if (B->graph) cudaGraphExecDestroy(B->graph);
                 B->graph = nullptr;
@@ -306,6 +411,7 @@ mg_status mg_batch_create(const mg_config *cfg, const int32_t *problem_n, mg_bat
         cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_joint, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&B->flag, sizeof(int)) != cudaSuccess) {
         set_error("batch stream / event / flag allocation failed");
         return fail(MG_ERR_CUDA);
@@ -400,6 +506,8 @@ mg_status mg_batch_set_rhs(mg_batch *B, const double *f_dev, const double *k_dev
     if (!B->tails_tuned && B->cfg.precision == 1) {
         MG_TRY(tune_batch_tails(B));
         B->tails_tuned = true;
+    } else if (B->tail_mode == 2) {
+        MG_TRY(build_joint_tail(B));  // the groups' set-up may have moved what the tail arguments point to
     }
     B->rhs_set = true;
     MG_TRY(leave(B));
@@ -436,6 +544,29 @@ mg_status mg_batch_profile(mg_batch *B, int32_t enable) {
         return MG_ERR_INVALID_ARG;
     }
     for (mg_forest *F : B->groups) MG_TRY(mg_profile(F, enable));
+    return MG_OK;
+}
+
+mg_status mg_batch_set_tail_mode(mg_batch *B, int32_t mode) {
+    if (!B || mode < 0 || mode > 2) {
+        set_error("null batch or tail mode outside 0..2");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (!B->tails_tuned) {
+        set_error("mg_batch_set_rhs has not been called (the tail levels are tuned there)");
+        return MG_ERR_STATE;
+    }
+    MG_TRY(apply_tail_mode(B, mode));
+    for (mg_forest *F : B->groups) MG_TRY(check_kernel_waits(F));
+    return MG_OK;
+}
+
+mg_status mg_batch_get_tail_mode(const mg_batch *B, int32_t *mode) {
+    if (!B || !mode) {
+        set_error("null argument");
+        return MG_ERR_INVALID_ARG;
+    }
+    *mode = B->tail_mode;
     return MG_OK;
 }
 

@@ -96,6 +96,30 @@ struct TailPhase {
     int32_t op, level;
 };
 
+// Everything the tail kernel reads of one forest (its level descriptors, phase list, coarsest inverse, done-mask and
+// the barrier and error words of its launch).
+struct TailArgs {
+    const TailLevel *L;
+    const TailPhase *ph;
+    int nph;
+    int flux;  // conservative F2C ghosts
+    const double *Ainv;
+    const int64_t *cmap32;
+    const int32_t *uprob;
+    const int64_t *ustart, *moff;
+    int Nc;
+    const uint8_t *done;
+    unsigned *bar;  // [count, generation]
+    int *err;
+};
+
+// One entry of a batch's joint tail: phase P of group `group`'s recorded tail; a grid barrier follows the entry when
+// `last` is set (the entries between two barriers belong to different groups and are independent).
+struct BatchEntry {
+    int32_t group, last;
+    TailPhase P;
+};
+
 }  // namespace octmg
 
 struct mg_forest {
@@ -162,6 +186,7 @@ struct mg_forest {
     octmg::TailPhase *tail_ph = nullptr;  // device phase list
     int tail_nph = 0, tail_for = -2;      // phases recorded, and for which tail level
     unsigned *tail_bar = nullptr;          // grid-barrier counter and generation
+    std::vector<octmg::TailPhase> tail_ph_host;  // host copy of the phase list (merged into a batch's joint tail)
 };
 
 
@@ -217,6 +242,17 @@ mg_status forest_alloc(mg_forest *F, void **p, int64_t bytes);
 mg_status check_ready(mg_forest *F);
 mg_status check_kernel_waits(mg_forest *F);
 mg_status launch_tail32(mg_forest *F);  // tail.cu
+octmg::TailArgs tail_args(mg_forest *F);  // tail.cu: the forest's recorded tail as the kernel reads it
+// tail.cu: a batch's joint tail, one cooperative launch on groups[0]'s stream walking `ne` entries (device) over the
+// groups' tail arguments (device), with a grid of at most `need` CTAs
+mg_status launch_batch_tail32(mg_forest *const *groups, const octmg::TailArgs *args, const octmg::BatchEntry *entries,
+                              int ne, unsigned *bar, int64_t need);
+int64_t tail_ctas(mg_forest *F);  // tail.cu: CTAs the largest phase of F's tail can use
+// solver.cu: one FP32 V-cycle in two parts around a joint tail: part 1 the steps down to the tail level's entry,
+// part 2 the steps after the tail (0: the whole cycle, its tail launched as usual)
+void vcycle32_part(mg_forest *F, int part);
+mg_status enqueue_update_mixed(mg_forest *F);  // solver.cu: u64 += e32 / scale_p
+mg_status record_tail(mg_forest *F, int l);   // solver.cu
 mg_status launch_selftest_wait(mg_forest *F, int which);  // tail.cu (F->tail_bar allocated)
 void reset_done(mg_forest *F);
 mg_status enqueue_done(mg_forest *F);

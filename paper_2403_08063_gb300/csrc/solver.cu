@@ -497,6 +497,43 @@ void vcycle(mg_forest *F, int l, int entry) {
     vcycle_walk<T, MODE>(F, l, entry, ex);
 }
 
+// One part of an FP32 V-cycle around a tail that another launch runs (a batch's joint tail): the same schedule, with
+// the steps before the tail level's entry launched in part 1 and those after the tail in part 2.  A forest without a
+// recorded tail runs its whole cycle in part 1.
+template <int MODE>
+struct PartExec {
+    LaunchExec<float, MODE> in;
+    int part;
+    bool past = false;
+    bool on() const { return (part == 1) != past; }
+    bool tail(int l, int entry) {
+        mg_forest *F = in.F;
+        if (F->tail_level >= 0 && l == F->tail_level && F->tail_for == l && entry == entry32(F, l)) {
+            past = true;
+            return true;
+        }
+        return false;
+    }
+    void exchange(int l, bool iface) {
+        if (on()) in.exchange(l, iface);
+    }
+    void smooth(int l, int colour) {
+        if (on()) in.smooth(l, colour);
+    }
+    void jacobi(int l) {
+        if (on()) in.jacobi(l);
+    }
+    void coarse(int l) {
+        if (on()) in.coarse(l);
+    }
+    void restrict_to(int l, bool fast) {
+        if (on()) in.restrict_to(l, fast);
+    }
+    void prolong_from(int l, bool fast) {
+        if (on()) in.prolong_from(l, fast);
+    }
+};
+
 // Levels from which the tail kernel can run the rest of an FP32 V-cycle: every deeper level has a specialised
 // column smoother (edge 4..128).
 bool tail_possible(mg_forest *F, int l) {
@@ -527,6 +564,7 @@ mg_status record_tail(mg_forest *F, int l) {
                             F->st));
     MG_CUDA(cudaStreamSynchronize(F->st));
     F->tail_nph = static_cast<int>(rec.ph.size());
+    F->tail_ph_host = rec.ph;
     F->tail_for = l;
     return MG_OK;
 }
@@ -920,6 +958,18 @@ void vcycle32(mg_forest *F) {
     else vcycle<float, 0>(F, 0, ENTRY_INTERFACE);
 }
 
+void vcycle32_part(mg_forest *F, int part) {
+    if (part == 0) {
+        vcycle32(F);
+    } else if (F->cfg.coeff) {
+        PartExec<2> ex{{F}, part};
+        vcycle_walk<float, 2>(F, 0, ENTRY_INTERFACE, ex);
+    } else {
+        PartExec<0> ex{{F}, part};
+        vcycle_walk<float, 0>(F, 0, ENTRY_INTERFACE, ex);
+    }
+}
+
 // Picks the persistent tail's level: every level l whose own and deeper levels have at most 2^20 cells (and
 // specialised smoothers) is a candidate; each candidate and "off" is timed over five FP32 V-cycles (after two
 // untimed ones) on the FP32 pools, which are dead between solves, and the fastest is kept.  Skipped (off) while the
@@ -1010,13 +1060,17 @@ mg_status pack_initial_guess(mg_forest *F, const double *u_dev, bool *zero) {
 }
 
 // Second half: `cycles` FP32 V-cycles on the scaled residual, then u64 += e32 / scale_p (exact).
-mg_status finish_mixed_cycle(mg_forest *F, int cycles) {
+mg_status enqueue_update_mixed(mg_forest *F) {
     DevLevel &d = F->L[0];
-    for (int i = 0; i < cycles; ++i) vcycle32(F);
     Prof p(F, P_UPDATE, 1);
     k_update_mixed<<<grid_for(d.cells()), kThreads, 0, F->st>>>(d.u64, d.u32, F->pinv, d.bprob, d.g, skip_of(F, d));
     MG_CUDA(cudaGetLastError());
     return MG_OK;
+}
+
+mg_status finish_mixed_cycle(mg_forest *F, int cycles) {
+    for (int i = 0; i < cycles; ++i) vcycle32(F);
+    return enqueue_update_mixed(F);
 }
 
 // Level-0 FP64 scratch pools (operator application, gradients), allocated on first use.

@@ -45,21 +45,6 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err, unsigned 
     return ok != 0;
 }
 
-struct TailArgs {
-    const TailLevel *L;
-    const TailPhase *ph;
-    int nph;
-    int flux;  // conservative F2C ghosts
-    const double *Ainv;
-    const int64_t *cmap32;
-    const int32_t *uprob;
-    const int64_t *ustart, *moff;
-    int Nc;
-    const uint8_t *done;
-    unsigned *bar;  // [count, generation]
-    int *err;
-};
-
 template <int MODE, int LG>
 __device__ __forceinline__ void tail_smooth(const TailLevel &d, int colour, Skip skip, int64_t t0, int64_t ts) {
     const int64_t work = d.g.nb * (int64_t(1) << (3 * LG - 1));
@@ -125,78 +110,104 @@ __device__ __forceinline__ void tail_prolong(const TailLevel &d, const TailLevel
     prolong32_body<LG, true>(d.u, d.g.bs, c.u, d.xfer, c.g.nb, c.g.bs, d.nbr6, skip, t0, ts);
 }
 
+// One phase of a recorded tail, over every thread of the grid (thread t0 of ts).
+template <int MODE>
+__device__ __forceinline__ void tail_phase(const TailArgs &a, const TailPhase &P, int64_t t0, int64_t ts) {
+    const TailLevel &d = a.L[P.level];
+    const Skip skip{d.bprob, a.done};
+    switch (P.op) {
+        case T_SMOOTH0:
+        case T_SMOOTH1:
+        case T_SEGS:
+        case T_RESTRICT:
+            if (MODE == 2 && d.face32) tail_coef_phase<3>(a, P, d, skip, t0, ts);
+            else tail_coef_phase<MODE>(a, P, d, skip, t0, ts);
+            break;
+        case T_FACES_IFACE:
+            exchange_faces_body<float, false, true>(d.u, d.ifaces, d.nifaces, d.g, skip, t0, ts);
+            break;
+        case T_FACES_FULL:
+            exchange_faces_body<float, false, true>(d.u, d.faces, d.nfaces, d.g, skip, t0, ts);
+            break;
+        case T_PROLONG: {
+            const TailLevel &c = a.L[P.level + 1];
+            const Skip cs{c.bprob, a.done};
+            if (d.fast) {
+                switch (d.g.lg) {
+                    case 3: tail_prolong<3>(d, c, cs, t0, ts); break;
+                    case 4: tail_prolong<4>(d, c, cs, t0, ts); break;
+                    case 5: tail_prolong<5>(d, c, cs, t0, ts); break;
+                    case 6: tail_prolong<6>(d, c, cs, t0, ts); break;
+                    default: tail_prolong<7>(d, c, cs, t0, ts); break;
+                }
+            } else {
+                prolong_body<float, true>(d.u, d.g, c.u, d.xfer, c.g, cs, t0, ts);
+            }
+            break;
+        }
+        default: {  // T_COARSE: one warp per coarsest unknown
+            const int lane = threadIdx.x & 31;
+            const int64_t w0 = t0 >> 5, wn = ts >> 5;
+            for (int64_t w = w0; w < a.Nc; w += wn)
+                coarse_solve_row<float, true>(d.u, d.f, a.Ainv, a.cmap32, a.uprob, a.ustart, a.moff, a.done,
+                                              static_cast<int>(w), lane);
+            break;
+        }
+    }
+}
+
 template <int MODE>
 static __global__ void __launch_bounds__(kTailThreads) k_tail32(TailArgs a) {
     const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     const int64_t ts = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int p = 0; p < a.nph; ++p) {
-        const TailPhase P = a.ph[p];
-        const TailLevel &d = a.L[P.level];
-        const Skip skip{d.bprob, a.done};
-        switch (P.op) {
-            case T_SMOOTH0:
-            case T_SMOOTH1:
-            case T_SEGS:
-            case T_RESTRICT:
-                if (MODE == 2 && d.face32) tail_coef_phase<3>(a, P, d, skip, t0, ts);
-                else tail_coef_phase<MODE>(a, P, d, skip, t0, ts);
-                break;
-            case T_FACES_IFACE:
-                exchange_faces_body<float, false, true>(d.u, d.ifaces, d.nifaces, d.g, skip, t0, ts);
-                break;
-            case T_FACES_FULL:
-                exchange_faces_body<float, false, true>(d.u, d.faces, d.nfaces, d.g, skip, t0, ts);
-                break;
-            case T_PROLONG: {
-                const TailLevel &c = a.L[P.level + 1];
-                const Skip cs{c.bprob, a.done};
-                if (d.fast) {
-                    switch (d.g.lg) {
-                        case 3: tail_prolong<3>(d, c, cs, t0, ts); break;
-                        case 4: tail_prolong<4>(d, c, cs, t0, ts); break;
-                        case 5: tail_prolong<5>(d, c, cs, t0, ts); break;
-                        case 6: tail_prolong<6>(d, c, cs, t0, ts); break;
-                        default: tail_prolong<7>(d, c, cs, t0, ts); break;
-                    }
-                } else {
-                    prolong_body<float, true>(d.u, d.g, c.u, d.xfer, c.g, cs, t0, ts);
-                }
-                break;
-            }
-            default: {  // T_COARSE: one warp per coarsest unknown
-                const int lane = threadIdx.x & 31;
-                const int64_t w0 = t0 >> 5, wn = ts >> 5;
-                for (int64_t w = w0; w < a.Nc; w += wn)
-                    coarse_solve_row<float, true>(d.u, d.f, a.Ainv, a.cmap32, a.uprob, a.ustart, a.moff, a.done,
-                                                  static_cast<int>(w), lane);
-                break;
-            }
-        }
+        tail_phase<MODE>(a, a.ph[p], t0, ts);
         if (!grid_barrier(a.bar, a.bar + 1, a.err, gridDim.x)) return;
     }
 }
 
-// Enqueues the recorded tail on the forest's stream (capturable: a memset and a cooperative kernel launch).
-mg_status launch_tail32(mg_forest *F) {
-    const int mi = F->cfg.coeff ? 1 : 0;
-    const void *fn = mi ? reinterpret_cast<const void *>(k_tail32<2>) : reinterpret_cast<const void *>(k_tail32<0>);
-    static int per_sm[2] = {-1, -1}, sms = 0;
-    if (per_sm[mi] < 0) {
+// The joint tail of a batch: the recorded tails of several forests (one per block size) in one launch.  Entries
+// between two barriers are phases of different forests, which share no data, so the grid runs them back to back
+// and synchronises once; each forest's own phases keep their order, each followed by a barrier as in k_tail32.
+template <int MODE>
+static __global__ void __launch_bounds__(kTailThreads) k_batch_tail32(const TailArgs *__restrict__ ga,
+                                                                      const BatchEntry *__restrict__ e, int ne,
+                                                                      unsigned *bar, int *err) {
+    const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t ts = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int i = 0; i < ne; ++i) {
+        const BatchEntry E = e[i];
+        tail_phase<MODE>(ga[E.group], E.P, t0, ts);
+        if (E.last && !grid_barrier(bar, bar + 1, err, gridDim.x)) return;
+    }
+}
+
+TailArgs tail_args(mg_forest *F) {
+    return TailArgs{F->tail_L, F->tail_ph, F->tail_nph, F->cfg.interface_flux, F->Ainv, F->cmap32, F->uprob,
+                    F->ustart, F->moff, F->Nc, F->pdone, F->tail_bar, F->kerr};
+}
+
+// CTAs the largest phase of F's recorded tail can use (one thread per updated cell of a half-sweep).
+int64_t tail_ctas(mg_forest *F) {
+    int64_t need = 1;
+    for (int l = std::max(0, F->tail_level); l < static_cast<int>(F->L.size()); ++l)
+        need = std::max<int64_t>(need, (F->L[l].cells() / 2 + kTailThreads - 1) / kTailThreads);
+    return need;
+}
+
+// Cooperative launch of `fn` with one TailArgs-like argument list; grid: `need` CTAs, at most two per SM (all must
+// be resident together).
+static mg_status launch_cooperative(const void *fn, int slot, int64_t need, cudaStream_t st, void **args) {
+    static int per_sm[4] = {-1, -1, -1, -1}, sms = 0;
+    if (per_sm[slot] < 0) {
         int dev = 0, v = 0, sm = 0;
         MG_CUDA(cudaGetDevice(&dev));
         MG_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
         MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, kTailThreads, 0));
         sms = sm;
-        per_sm[mi] = std::max(1, std::min(v, 2));
+        per_sm[slot] = std::max(1, std::min(v, 2));
     }
-    // enough CTAs for the largest phase, at most two per SM (all must be resident together)
-    int64_t need = 1;
-    for (int l = F->tail_level; l < static_cast<int>(F->L.size()); ++l)
-        need = std::max<int64_t>(need, (F->L[l].cells() / 2 + kTailThreads - 1) / kTailThreads);
-    const int grid = static_cast<int>(std::min<int64_t>(need, static_cast<int64_t>(per_sm[mi]) * sms));
-    TailArgs a{F->tail_L, F->tail_ph, F->tail_nph, F->cfg.interface_flux, F->Ainv, F->cmap32, F->uprob, F->ustart,
-               F->moff, F->Nc, F->pdone, F->tail_bar, F->kerr};
-    MG_CUDA(cudaMemsetAsync(F->tail_bar, 0, 2 * sizeof(unsigned), F->st));
+    const int grid = static_cast<int>(std::min<int64_t>(need, static_cast<int64_t>(per_sm[slot]) * sms));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -204,12 +215,34 @@ mg_status launch_tail32(mg_forest *F) {
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kTailThreads);
     cfg.dynamicSmemBytes = 0;
-    cfg.stream = F->st;
+    cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void *args[] = {&a};
     MG_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
     return MG_OK;
+}
+
+// Enqueues the recorded tail on the forest's stream (capturable: a memset and a cooperative kernel launch).
+mg_status launch_tail32(mg_forest *F) {
+    const int mi = F->cfg.coeff ? 1 : 0;
+    const void *fn = mi ? reinterpret_cast<const void *>(k_tail32<2>) : reinterpret_cast<const void *>(k_tail32<0>);
+    TailArgs a = tail_args(F);
+    MG_CUDA(cudaMemsetAsync(F->tail_bar, 0, 2 * sizeof(unsigned), F->st));
+    void *args[] = {&a};
+    return launch_cooperative(fn, mi, tail_ctas(F), F->st, args);
+}
+
+// Enqueues a batch's joint tail on groups[0]'s stream (capturable), after that stream has waited for the others.
+mg_status launch_batch_tail32(mg_forest *const *groups, const TailArgs *args, const BatchEntry *entries, int ne,
+                              unsigned *bar, int64_t need) {
+    mg_forest *F = groups[0];
+    const int mi = F->cfg.coeff ? 1 : 0;
+    const void *fn =
+        mi ? reinterpret_cast<const void *>(k_batch_tail32<2>) : reinterpret_cast<const void *>(k_batch_tail32<0>);
+    MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), F->st));
+    int *err = F->kerr;
+    void *kargs[] = {&args, &entries, &ne, &bar, &err};
+    return launch_cooperative(fn, 2 + mi, need, F->st, kargs);
 }
 
 // Self-test of the bounded waits (mg_selftest_waits): one CTA waits for something that never happens and must give up

@@ -193,6 +193,8 @@ def test_batch_host_checks(lib):
     pn = np.ascontiguousarray([8, 6, 16], dtype=np.int32)
     st = lib.mg_batch_create(ctypes.byref(cfg), pn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h))
     assert st == 3 and "problem 1" in lib.mg_last_error().decode() and h.value is None
+    m = ctypes.c_int32()
+    assert lib.mg_batch_set_tail_mode(None, 0) == 1 and lib.mg_batch_get_tail_mode(None, ctypes.byref(m)) == 1
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

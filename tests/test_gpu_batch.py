@@ -80,6 +80,74 @@ def test_batch_with_mixed_block_sizes_matches_single_problem_oracle():
     B.close()
 
 
+def test_batch_tail_modes_give_identical_solves():
+    """The three ways of running the coarse levels of a batch -- every level launched, each block-size group's own
+    persistent tail, one joint persistent tail per V-cycle over all groups -- run the same device code per step, so
+    the solves are bit-identical (iterate, cycle counts and residuals).  Groups of block size 8, 16 and 32 with
+    refined problems (interface exchanges inside the tails), FP32 cycles in FP64 defect correction, graph-launched
+    steps."""
+    from paper_2403_08063_gb300 import Batch
+    problems = syn.batch_problems(count=9, seed=7, sizes=(8, 16, 32))
+    leaves, ns = syn.batch_leaves(problems)
+    rng = np.random.default_rng(8)
+    fs, ks = [], []
+    for p, (n, keys) in enumerate(problems):
+        fs.append(rng.uniform(-1, 1, size=len(keys) * n ** 3))
+        ks.append(syn.lognormal_k_rff(1, n, keys, seed=30 + p, sigma=0.5, ell=0.3).numpy().reshape(-1))
+    f = torch.from_numpy(np.concatenate(fs)).to(DEV)
+    k = torch.from_numpy(np.concatenate(ks)).to(DEV)
+    B = Batch(leaves, ns, coeff=True, inner_cycles=4, coarse_coef="faces")
+    B.set_rhs(f, k)
+    assert B.tail_mode() in (0, 1, 2)
+    assert any(lv >= 0 for lv in B.tail_levels()) or B.tail_mode() == 0
+    out = {}
+    for mode in (0, 1, 2):
+        B.set_tail_mode(mode)
+        assert B.tail_mode() == mode
+        u = torch.zeros_like(f)
+        cyc, rel = B.solve(u, rtol=1e-9, max_cycles=60)
+        assert max(rel) <= 1e-9
+        out[mode] = (u.cpu().numpy(), list(cyc), list(rel))
+    for mode in (1, 2):
+        assert np.array_equal(out[mode][0], out[0][0]), mode
+        assert out[mode][1] == out[0][1] and out[mode][2] == out[0][2], mode
+    B.set_tail_mode(2)  # the profiled (launched, not graph-replayed) path of the joint tail counts its launches
+    B.profile(True)
+    u = torch.zeros_like(f)
+    B.solve(u, rtol=1e-9, max_cycles=60)
+    prof = B.profile_read()
+    B.profile(False)
+    assert np.array_equal(u.cpu().numpy(), out[0][0])
+    tails = [lv for lv in B.tail_levels() if lv >= 0]
+    if tails:
+        assert prof.get("tail_f32", (0.0, 0))[1] > 0
+    with pytest.raises(Exception):
+        B.set_tail_mode(3)
+    B.close()
+
+
+def test_concurrent_groups_give_bit_reproducible_solves():
+    """Block-size groups run concurrently on their own streams, so the staged smoothers of one group share SMs with
+    the other groups' kernels.  Exactly 10 cycles of the same batch, repeated, must give bit-identical iterates: a
+    shared-memory slot refilled by a bulk copy before every read of it had landed made some problems differ at the
+    1e-12 level from one solve to the next (and in every problem's FP32 cycles)."""
+    from paper_2403_08063_gb300 import Batch, MGError
+    problems = [p for p in syn.batch_problems(count=256, seed=0) if p[0] in (16, 32, 64)][:120]
+    leaves, ns = syn.batch_leaves(problems)
+    f, k = syn.batch_fields(problems, seed=0, device=torch.device(DEV))
+    B = Batch(leaves, ns, coeff=True, inner_cycles=5)
+    B.set_rhs(f, k)
+    outs = []
+    for rep in range(3):
+        u = torch.zeros_like(f)
+        with pytest.raises(MGError):  # rtol 0 is never met: exactly max_cycles cycles
+            B.solve(u, rtol=0.0, max_cycles=10)
+        outs.append(u.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    B.close()
+
+
 def test_converged_problems_stop_where_they_would_stop_alone():
     """Per-problem done-mask: once a problem meets rtol its blocks are skipped by every kernel of the later
     defect-correction steps, so the batch returns, for each problem, the iterate and the cycle count of a solve of
