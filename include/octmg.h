@@ -269,8 +269,8 @@ mg_forest *mg_batch_group(mg_batch *batch, int32_t g);
  *   2  one joint persistent cooperative launch per V-cycle running the tails of all groups: each group first runs
  *      its levels above the tail on its own stream, then every group waits for the joint tail, then each runs its
  *      levels back up.  Between two grid barriers the joint tail runs one phase of every group.
- * mg_batch_set_rhs picks the fastest of the three on first use (one timed defect-correction step of all groups
- * each); mg_batch_set_tail_mode overrides it (MG_ERR_STATE before mg_batch_set_rhs, MG_ERR_INVALID_ARG for another
+ * mg_batch_set_rhs picks the fastest of the three on first use (two timed defect-correction steps of all groups
+ * each; a persistent mode when it is within 1 % of the fastest); mg_batch_set_tail_mode overrides it (MG_ERR_STATE before mg_batch_set_rhs, MG_ERR_INVALID_ARG for another
  * mode).  All three give bit-identical iterates.  A grid barrier of the persistent launches that waits longer than
  * about half a second makes the next call return MG_ERR_TIMEOUT. */
 mg_status mg_batch_set_tail_mode(mg_batch *batch, int32_t mode);
