@@ -23,7 +23,10 @@ What it computes
 * Multigrid (Sec. 5: block-local coarsening down to 4^3 cells per block): V(nu1, nu2) with red-black Gauss-Seidel,
   colour (x+y+z) mod 2 of the block-local cell index (blocks have even n, so this is the global parity), red
   first, an exchange before every half-sweep; residual restricted by the mean of the 8 children; prolongation
-  e_f = 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) with s_d towards the child's side; coarse levels rediscretised
+  e_f = 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) with s_d towards the child's side (or, optionally, the 8-point
+  trilinear interpolation, which reads the coarse correction's edge and corner ghosts: copies from a same-level
+  diagonal neighbour, else linear extrapolation from the neighbouring face (edge) ghosts, exact for trilinear data;
+  Sec. 8 names diagonal ghosts for wider stencils as future work); coarse levels rediscretised
   with homogeneous Dirichlet data and k averaged over the 8 children; when the 4^3 level has more than
   ``max_coarse`` unknowns, complete sibling octets at the deepest level are merged into their parent (a
   coarsening step the paper does not need, since it smooths on the coarsest level); the coarsest level is solved
@@ -49,6 +52,7 @@ from __future__ import annotations
 
 import copy
 import functools
+import itertools
 from fractions import Fraction
 
 import numpy as np
@@ -267,7 +271,8 @@ class OracleMG:
     dtype = np.dtype(np.float64)  # working precision of the cycles (with_dtype makes an FP32 copy)
 
     def __init__(self, R, n, keys, k_user=None, variant="C", nu1=2, nu2=2, max_coarse=512, operator_only=False,
-                 bc=None, c2f_order=2, smoother="rbgs", omega=0.8, coarse_iters=None, coarse_coef="k"):
+                 bc=None, c2f_order=2, smoother="rbgs", omega=0.8, coarse_iters=None, coarse_coef="k",
+                 prolongation="linear"):
         """operator_only builds the finest level alone (for applying A, A^T and dA/dk; no solver).
 
         bc: None for homogeneous Dirichlet data, else a vectorised g(x, y, z) giving the Dirichlet value at
@@ -280,6 +285,10 @@ class OracleMG:
         (the reading of Sec. 5's rediscretisation); 'faces' gives every coarse face the mean of the 2 x 2 finer
         face coefficients it covers (an operator-aware coarsening the paper does not discuss; far fewer cycles for
         rough k).  The finest level's coefficients are the harmonic means either way.
+        prolongation: 'linear' the face-neighbour linear interpolation (each fine cell from its coarse cell and the
+        three face neighbours towards it), 'trilinear' the 8-point tensor-product interpolation, which also needs the
+        coarse correction's edge and corner ghosts (exchange_diagonal; Sec. 8 lists such diagonal ghosts for wider
+        stencils as future work).
         """
         if n < 4 or n & (n - 1):
             raise ValueError("n must be a power of two >= 4")
@@ -289,6 +298,9 @@ class OracleMG:
         if c2f_order not in (0, 1, 2) or smoother not in ("rbgs", "jacobi") or coarse_coef not in ("k", "faces"):
             raise ValueError("c2f_order must be 0, 1 or 2, smoother 'rbgs' or 'jacobi', coarse_coef 'k' or 'faces'")
         self.coarse_coef = coarse_coef
+        if prolongation not in ("linear", "trilinear"):
+            raise ValueError("prolongation must be 'linear' or 'trilinear'")
+        self.prolongation = prolongation
         self.c2f_order, self.smoother, self.omega, self.coarse_iters = c2f_order, smoother, omega, coarse_iters
         self.normal_w = normal_weights(c2f_order)
         self.levels = [Level(R, n, keys)]
@@ -606,6 +618,54 @@ class OracleMG:
             fine = Xi[tr[1]] if tr[0] == "halve" else _assemble_octets([Xi[c] for c in tr[1]])
             Xc_pad[B, 1:-1, 1:-1, 1:-1] = fine.reshape(nc, 2, nc, 2, nc, 2).mean(axis=(1, 3, 5))
 
+    def exchange_diagonal(self, l, U):
+        """Edge and corner ghosts of level l, after the face exchange: the cells of a same-level block across the edge
+        or corner where there is one; else linear extrapolation, along each of the edge's (corner's) ghost axes in
+        turn, from the two ghosts next to it on that axis (face ghosts for an edge, edge ghosts for a corner), and the
+        mean of the two (three) results.  Data linear along each axis (trilinear data) is reproduced exactly.  Edges
+        first, then corners.  The paper defines no diagonal ghosts (Sec. 8 lists them as future work for wider
+        stencils); this is the reading used for the trilinear prolongation."""
+        L = self.levels[l]
+        n = L.n
+
+        def at(sel):  # sel: per axis (x, y, z) an index or a slice; array order [b, z, y, x]
+            return (sel[2], sel[1], sel[0])
+
+        def ghost(side):
+            return 0 if side < 0 else n + 1
+
+        def inner(side, depth):  # the interior index `depth` cells in from the ghost (depth 1 or 2)
+            return depth if side < 0 else n + 1 - depth
+
+        for b, key in enumerate(L.keys):
+            lev, idx = key[0], list(key[1:])
+            m = L.blocks_per_axis(lev)
+            V = U[b]
+            for corner in (False, True):
+                axes_sets = [(0, 1, 2)] if corner else [(0, 1), (0, 2), (1, 2)]
+                for axes in axes_sets:
+                    for signs in np.ndindex(*([2] * len(axes))):
+                        sg = [1 if q else -1 for q in signs]
+                        p = idx.copy()
+                        for a_, s_ in zip(axes, sg):
+                            p[a_] += s_
+                        nb = L.index.get((lev, *p)) if all(0 <= v < m for v in p) else None
+                        sel = [slice(1, n + 1)] * 3
+                        for a_, s_ in zip(axes, sg):
+                            sel[a_] = ghost(s_)
+                        if nb is not None:
+                            src = [slice(1, n + 1)] * 3
+                            for a_, s_ in zip(axes, sg):
+                                src[a_] = 1 if s_ > 0 else n  # the neighbour's cells next to the edge / corner
+                            V[at(sel)] = U[nb][at(src)]
+                            continue
+                        acc = 0.0
+                        for a_, s_ in zip(axes, sg):  # extrapolate along a_ from the two ghosts next to it
+                            s1, s2 = list(sel), list(sel)
+                            s1[a_], s2[a_] = inner(s_, 1), inner(s_, 2)
+                            acc = acc + (2.0 * V[at(s1)] - V[at(s2)])
+                        V[at(sel)] = acc / len(axes)
+
     def _prolong_add(self, l, Ec_pad, Uf):
         """u_f += P e_c, P the face-neighbour linear cell-centred interpolation; Ec_pad has its ghosts filled."""
         Lf, Lc = self.levels[l], self.levels[l + 1]
@@ -620,6 +680,17 @@ class OracleMG:
             for sz in (0, 1):
                 for sy in (0, 1):
                     for sx in (0, 1):
+                        if self.prolongation == "trilinear":
+                            # weights (3/4)^(3-d) (1/4)^d of the coarse cells d steps (0..3 axes) towards the fine cell
+                            acc = np.zeros_like(c)
+                            for dz in (0, 1):
+                                for dy in (0, 1):
+                                    for dx in (0, 1):
+                                        oz, oy, ox = (dz if sz else -dz), (dy if sy else -dy), (dx if sx else -dx)
+                                        w = 0.75 ** (3 - dx - dy - dz) * 0.25 ** (dx + dy + dz)
+                                        acc = acc + w * E[1 + oz:nc + 1 + oz, 1 + oy:nc + 1 + oy, 1 + ox:nc + 1 + ox]
+                            P[sz::2, sy::2, sx::2] = acc
+                            continue
                         ex = E[1:-1, 1:-1, 2:] if sx else E[1:-1, 1:-1, :-2]
                         ey = E[1:-1, 2:, 1:-1] if sy else E[1:-1, :-2, 1:-1]
                         ez = E[2:, 1:-1, 1:-1] if sz else E[:-2, 1:-1, 1:-1]
@@ -676,6 +747,8 @@ class OracleMG:
         Ec = self.levels[l + 1].zeros()
         self.vcycle(l + 1, Ec, Fc)
         self.exchange(l + 1, Ec)
+        if self.prolongation == "trilinear":
+            self.exchange_diagonal(l + 1, Ec)
         self._prolong_add(l, Ec, U)
         self.smooth(l, U, F, self.nu2)
 

@@ -861,3 +861,131 @@ def test_face_averaged_coarse_coefficients_converge_faster_and_to_the_same_solut
         A = _dense_operator(OracleMG(R, n, keys, k_user=k, variant=variant, operator_only=True))
         x = np.linalg.solve(A, f.reshape(-1))
         assert np.linalg.norm(u.reshape(-1) - x) <= 1e-10 * np.linalg.norm(x), variant
+
+
+# ---------------------------------------------------------------- edge / corner ghosts, trilinear prolongation
+
+
+def _scatter_global(L, G, R, n):
+    """Uniform level: the global array G [z, y, x] of (R n)^3 cells into padded blocks (interiors only)."""
+    U = L.zeros()
+    for b, (lev, i, j, k) in enumerate(L.keys):
+        U[b, 1:-1, 1:-1, 1:-1] = G[k * n:(k + 1) * n, j * n:(j + 1) * n, i * n:(i + 1) * n]
+    return U
+
+
+def _diag_ghost_cells(n):
+    """(z, y, x) padded indices of every edge and corner ghost cell of a block (two or three ghost coordinates)."""
+    out = []
+    for z in range(n + 2):
+        for y in range(n + 2):
+            for x in range(n + 2):
+                if sum(c in (0, n + 1) for c in (x, y, z)) >= 2:
+                    out.append((z, y, x))
+    return out
+
+
+def test_diagonal_ghosts_copy_same_level_blocks_and_are_exact_for_trilinear_data():
+    """Uniform 3^3 roots of 4^3: after the face exchange and exchange_diagonal every edge and corner ghost inside the
+    domain holds the global field's value there (the diagonal neighbour's cell; copying the wrong layer or the wrong
+    neighbour fails).  Refined forest (one root split, ghost-only interfaces): for trilinear data every edge and
+    corner ghost whose centre lies inside the domain equals the function there, for the copied ones and for those
+    extrapolated where the diagonal block is coarser or finer (a wrong sign or weight fails, and so does the
+    parallelogram rule g_a + g_b - u, which misses the cross terms)."""
+    R, n = 3, 4
+    keys = syn.uniform_leaves(R)
+    mg = OracleMG(R, n, keys, operator_only=True, prolongation="trilinear")
+    L = mg.levels[0]
+    G = np.random.default_rng(71).normal(size=(R * n,) * 3)
+    U = _scatter_global(L, G, R, n)
+    mg.exchange(0, U)
+    mg.exchange_diagonal(0, U)
+    checked = 0
+    for b, (lev, i, j, k) in enumerate(L.keys):
+        for (z, y, x) in _diag_ghost_cells(n):
+            gz, gy, gx = k * n + z - 1, j * n + y - 1, i * n + x - 1
+            if all(0 <= c < R * n for c in (gz, gy, gx)):
+                assert U[b, z, y, x] == G[gz, gy, gx], (b, z, y, x)
+                checked += 1
+    assert checked > 0
+    R, n = 2, 4
+    keys = one_refined_root(R)
+    coef = np.random.default_rng(72).normal(size=(2, 2, 2))
+    f = poly3(coef)
+    mg = OracleMG(R, n, keys, variant="P", operator_only=True, prolongation="trilinear")
+    L = mg.levels[0]
+    U = L.zeros()
+    for b, key in enumerate(L.keys):
+        x, y, z = padded_centres(R, n, key)
+        U[b, 1:-1, 1:-1, 1:-1] = f(x, y, z)[1:-1, 1:-1, 1:-1]
+    mg.exchange(0, U)
+    mg.exchange_diagonal(0, U)
+    kinds = {"copy": 0, "extrapolated": 0}
+    for b, key in enumerate(L.keys):
+        lev, i, j, k = key
+        x, y, z = padded_centres(R, n, key)
+        ref = f(x, y, z)
+        for (zz, yy, xx) in _diag_ghost_cells(n):
+            c = (x[zz, yy, xx], y[zz, yy, xx], z[zz, yy, xx])
+            if not all(0.0 < v < 1.0 for v in c):
+                continue
+            np.testing.assert_allclose(U[b, zz, yy, xx], ref[zz, yy, xx], rtol=0, atol=1e-12)
+            d = [0 if q in range(1, n + 1) else (1 if q == n + 1 else -1) for q in (xx, yy, zz)]
+            same = (lev, i + d[0], j + d[1], k + d[2]) in L.index
+            kinds["copy" if same else "extrapolated"] += 1
+    assert kinds["copy"] > 0 and kinds["extrapolated"] > 0, kinds
+
+
+@pytest.mark.parametrize("R,max_coarse,transfer", [(2, 4096, "halve"), (4, 512, "merge")])
+def test_trilinear_prolongation_is_exact_for_trilinear_corrections(R, max_coarse, transfer):
+    """A trilinear coarse correction (ghosts from the face and diagonal exchanges) prolongates to the function's
+    values at every fine cell whose coarse stencil stays inside the domain, across halving and octet-merging
+    transfers; the face-neighbour linear prolongation misses the cross terms (xy, xz, yz, xyz) there."""
+    n = 4 if transfer == "merge" else 8
+    keys = syn.uniform_leaves(R)
+    coef = np.random.default_rng(73).normal(size=(2, 2, 2))
+    coef[1, 1, 0] = 1.0  # a real xy term
+    f = poly3(coef)
+    errs = {}
+    for pr in ("trilinear", "linear"):
+        mg = OracleMG(R, n, keys, max_coarse=max_coarse, prolongation=pr)
+        assert any(t[0] == transfer for t in mg.transfer[0])
+        Lf, Lc = mg.levels[0], mg.levels[1]
+        Ec = Lc.zeros()
+        for B, key in enumerate(Lc.keys):
+            x, y, z = padded_centres(R, Lc.n, key)
+            Ec[B, 1:-1, 1:-1, 1:-1] = f(x, y, z)[1:-1, 1:-1, 1:-1]
+        mg.exchange(1, Ec)
+        if pr == "trilinear":
+            mg.exchange_diagonal(1, Ec)
+        Uf = Lf.zeros()
+        mg._prolong_add(0, Ec, Uf)
+        worst = 0.0
+        for b, key in enumerate(Lf.keys):
+            x, y, z = padded_centres(R, n, key)
+            hf = 1.0 / (R * 2 ** key[0] * n)
+            x, y, z = (c[1:-1, 1:-1, 1:-1] for c in (x, y, z))  # interior cells; at least two coarse cells inside
+            inner = np.ones_like(x, dtype=bool)
+            for c in (x, y, z):
+                inner &= (c > 4 * hf) & (c < 1 - 4 * hf)
+            diff = np.abs(Uf[b, 1:-1, 1:-1, 1:-1] - f(x, y, z))[inner]
+            worst = max(worst, float(diff.max()) if diff.size else 0.0)
+        errs[pr] = worst
+    assert errs["trilinear"] <= 1e-12, errs
+    assert errs["linear"] > 1e-3, errs
+
+
+@pytest.mark.parametrize("variant", ["C", "P"])
+def test_trilinear_prolongation_solves_to_the_dense_solution(variant):
+    """With the trilinear prolongation the cycle still solves the finest operator: on a refined forest with log-normal
+    k it reaches the dense solution (the prolongation changes the cycle, not the solution)."""
+    R, n = 2, 4
+    keys = one_refined_root(R)
+    k = syn.lognormal_k_rff(R, n, keys, seed=74).numpy()
+    f = np.random.default_rng(75).normal(size=(len(keys), n ** 3))
+    mg = OracleMG(R, n, keys, k_user=k, variant=variant, max_coarse=64, prolongation="trilinear")
+    u, hist = mg.solve(f, rtol=1e-13, max_cycles=80)
+    A = _dense_operator(OracleMG(R, n, keys, k_user=k, variant=variant, operator_only=True))
+    x = np.linalg.solve(A, f.reshape(-1))
+    assert np.linalg.norm(u.reshape(-1) - x) <= 1e-10 * np.linalg.norm(x)
+    assert len(hist) < 60
