@@ -71,6 +71,13 @@ typedef struct {
                                  (default); 1 every coarse face takes the mean of the 2 x 2 finer face coefficients
                                  it covers (an operator-aware coarsening not in the paper; far fewer V-cycles for
                                  rough k).  The finest level's coefficients are the harmonic means either way. */
+    int32_t prolongation;     /* 0 face-neighbour linear (each fine cell from its coarse cell and the three face
+                                 neighbours towards it; default); 1 trilinear (8 coarse cells), which reads the coarse
+                                 correction's edge and corner ghosts: copies from a same-level block across the edge
+                                 or corner, else linear extrapolation from the neighbouring face (edge) ghosts (the
+                                 diagonal ghosts of the paper's future work, Sec. 8).  With 1 the persistent tail is
+                                 off and mg_adjoint_solve returns MG_ERR_INVALID_ARG; mg_exchange_level also fills
+                                 the edge and corner ghosts. */
 } mg_config;
 
 /* Build the forest: validate the leaves, build neighbour and segment tables for every multigrid level, allocate

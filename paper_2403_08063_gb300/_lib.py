@@ -44,6 +44,7 @@ class MGConfig(ctypes.Structure):
         ("omega", ctypes.c_double),
         ("coarse_iters", ctypes.c_int32),
         ("coarse_coef", ctypes.c_int32),
+        ("prolongation", ctypes.c_int32),
     ]
 
 

@@ -40,7 +40,7 @@ class Forest:
 
     def __init__(self, R, n, leaves, coeff=False, interface_flux=True, precision=0, nu1=2, nu2=2, max_coarse=512,
                  inner_cycles=1, n_problems=None, stream=None, c2f_variant=0, smoother="rbgs", omega=0.8,
-                 coarse_iters=0, coarse_coef="k"):
+                 coarse_iters=0, coarse_coef="k", prolongation="linear"):
         self.lib = _lib.load()
         arr = np.asarray(leaves, dtype=np.int32)
         if arr.ndim == 2 and arr.shape[1] == 4:
@@ -61,6 +61,7 @@ class Forest:
         cfg.omega = float(omega)
         cfg.coarse_iters = int(coarse_iters)
         cfg.coarse_coef = {"k": 0, "faces": 1}[coarse_coef]
+        cfg.prolongation = {"linear": 0, "trilinear": 1}[prolongation]
         self.n_problems = int(n_problems) if n_problems else int(self._leaves[:, 0].max()) + 1
         cfg.n_problems = self.n_problems
         cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -233,7 +234,7 @@ class Batch:
     """
 
     def __init__(self, leaves, problem_n, R=1, coeff=True, interface_flux=True, inner_cycles=3, nu1=2, nu2=2,
-                 max_coarse=64, stream=None, coarse_coef="k"):
+                 max_coarse=64, stream=None, coarse_coef="k", prolongation="linear"):
         self.lib = _lib.load()
         self._leaves = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32))
         self._pn = np.ascontiguousarray(np.asarray(problem_n, dtype=np.int32))
@@ -246,6 +247,7 @@ class Batch:
         cfg.coeff, cfg.interface_flux, cfg.precision = int(coeff), int(interface_flux), 1
         cfg.nu1, cfg.nu2, cfg.max_coarse, cfg.inner_cycles = int(nu1), int(nu2), int(max_coarse), int(inner_cycles)
         cfg.coarse_coef = {"k": 0, "faces": 1}[coarse_coef]
+        cfg.prolongation = {"linear": 0, "trilinear": 1}[prolongation]
         cfg.n_problems = self.n_problems
         cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
         h = ctypes.c_void_p()

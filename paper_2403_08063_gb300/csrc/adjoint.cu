@@ -647,8 +647,9 @@ mg_status read_sum(mg_forest *F, int grid, double *out) {
 // The transposed operator and cycle are written for the quadratic coarse-to-fine scheme, red-black Gauss-Seidel, the
 // dense coarsest solve and homogeneous boundary data (the k-gradient of a boundary term would need g).
 mg_status adjoint_supported(const mg_forest *F) {
-    if (F->cfg.c2f_variant != 0 || F->cfg.smoother != 0 || F->cfg.coarse_iters != 0) {
-        set_error("the adjoint needs c2f_variant 0, the Gauss-Seidel smoother and the dense coarsest solve");
+    if (F->cfg.c2f_variant != 0 || F->cfg.smoother != 0 || F->cfg.coarse_iters != 0 || F->cfg.prolongation != 0) {
+        set_error("the adjoint needs c2f_variant 0, the Gauss-Seidel smoother, the dense coarsest solve and the "
+                  "face-neighbour linear prolongation");
         return MG_ERR_INVALID_ARG;
     }
     if (F->gb) {

@@ -235,6 +235,42 @@ bool merge_deepest(int32_t R, int32_t n_problems, int64_t max_coarse, const Host
 
 }  // namespace
 
+void build_diagonal(int32_t R, HostLevel &L) {
+    KeyMap idx;
+    idx.reserve(L.keys.size() * 2);
+    for (size_t b = 0; b < L.keys.size(); ++b) idx[L.keys[b]] = static_cast<int32_t>(b);
+    L.edges.clear();
+    L.corners.clear();
+    // the same-level block at offsets d[0..2] in {-1, 0, 1}, or -1
+    const auto across = [&](const Key &key, const int d[3]) -> int32_t {
+        int64_t m;
+        if (!blocks_per_axis(R, key.lev, m)) return -1;
+        Key k2 = key;
+        for (int a = 0; a < 3; ++a) {
+            const int v = coord(key, a) + d[a];
+            if (v < 0 || v >= m) return -1;
+            set_coord(k2, a, v);
+        }
+        const auto it = idx.find(k2);
+        return it == idx.end() ? -1 : it->second;
+    };
+    static const int kPair[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (size_t b = 0; b < L.keys.size(); ++b) {
+        const Key key = L.keys[b];
+        for (int q = 0; q < 3; ++q)
+            for (int bits = 0; bits < 4; ++bits) {
+                int d[3] = {0, 0, 0};
+                d[kPair[q][0]] = (bits & 1) ? 1 : -1;
+                d[kPair[q][1]] = (bits & 2) ? 1 : -1;
+                L.edges.push_back({static_cast<int32_t>(b), across(key, d), 4 * q + bits, 0});
+            }
+        for (int bits = 0; bits < 8; ++bits) {
+            const int d[3] = {(bits & 1) ? 1 : -1, (bits & 2) ? 1 : -1, (bits & 4) ? 1 : -1};
+            L.corners.push_back({static_cast<int32_t>(b), across(key, d), bits, 0});
+        }
+    }
+}
+
 mg_status build_hierarchy(int32_t R, int32_t n, int32_t n_problems, const std::vector<Key> &leaves,
                           int32_t max_coarse, HostHierarchy &out, std::string &err) {
     if (R < 1 || R > 4096) {

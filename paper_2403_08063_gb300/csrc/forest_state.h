@@ -67,6 +67,8 @@ struct DevLevel {
     // FP32 cycles on a face-averaged coarse level: its halved face coefficients (colour-split) and mode 3
     float *ax32 = nullptr, *ay32 = nullptr, *az32 = nullptr;
     bool face32 = false;
+    DiagItem *edges = nullptr, *corners = nullptr;  // trilinear prolongation: edge / corner items of every block
+    int nedges = 0, ncorners = 0;
     Coef c64() const { return Coef{tx, ty, tz, dg, dinv, nullptr, nullptr, nullptr, nullptr}; }
     Coef c32() const { return Coef{nullptr, nullptr, nullptr, nullptr, nullptr, kap, ax32, ay32, az32}; }
     int64_t pool_elems() const { return static_cast<int64_t>(g.nb) * g.bs; }

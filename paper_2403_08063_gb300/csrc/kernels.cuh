@@ -1582,6 +1582,121 @@ static __global__ void k_restrict_field(const T *__restrict__ xf_in, LevelGeom g
 // along axis d (face-neighbour linear interpolation, exact for linear functions; coarse ghosts exchanged).
 // One thread per coarse cell, writing its 8 children.
 // ------------------------------------------------------------------------------------------------------------
+// Edge (corners = false) or corner (corners = true) ghosts of a level, after its face exchange (the trilinear
+// prolongation reads them): the cells of the same-level block across the edge or corner where there is one (nbr >= 0),
+// else linear extrapolation along each of the item's ghost axes from the two ghosts next to it on that axis (face
+// ghosts for an edge, edge ghosts for a corner), averaged over the axes -- exact for trilinear data.  Edges: one
+// thread per ghost cell along the edge (n per item); corners: one thread per item.  Corners run after the edges.
+template <typename T>
+static __global__ void k_exchange_diag(T *__restrict__ u, const DiagItem *__restrict__ items, int nitems, LevelGeom g,
+                                       bool corners, Skip skip) {
+    const int n = g.n;
+    const int64_t total = corners ? static_cast<int64_t>(nitems) : static_cast<int64_t>(nitems) * n;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const DiagItem D = items[corners ? t : t / n];
+        if (skip(D.blk)) continue;
+        int nax = 3, ax[3] = {0, 1, 2}, sg[3];
+        int X[3];
+        if (corners) {
+            for (int a = 0; a < 3; ++a) sg[a] = (D.code >> a) & 1;
+        } else {
+            const int q = D.code >> 2;
+            nax = 2;
+            ax[0] = q == 2 ? 1 : 0;
+            ax[1] = q == 0 ? 1 : 2;
+            const int third = 3 - ax[0] - ax[1];
+            sg[0] = D.code & 1;
+            sg[1] = (D.code >> 1) & 1;
+            X[third] = static_cast<int>(t % n) + 1;
+        }
+        for (int i = 0; i < nax; ++i) X[ax[i]] = sg[i] ? n + 1 : 0;
+        const int64_t dst = Lay<T>::at(g, D.blk, X[0], X[1], X[2]);
+        if (D.nbr >= 0) {
+            int S[3] = {X[0], X[1], X[2]};
+            for (int i = 0; i < nax; ++i) S[ax[i]] = sg[i] ? 1 : n;  // the neighbour's cells next to it
+            u[dst] = u[Lay<T>::at(g, D.nbr, S[0], S[1], S[2])];
+            continue;
+        }
+        T acc = T(0);
+        for (int i = 0; i < nax; ++i) {
+            int A[3] = {X[0], X[1], X[2]}, B2[3] = {X[0], X[1], X[2]};
+            A[ax[i]] = sg[i] ? n : 1;       // first interior layer next to the ghost on that axis
+            B2[ax[i]] = sg[i] ? n - 1 : 2;  // second
+            acc = acc + (T(2) * u[Lay<T>::at(g, D.blk, A[0], A[1], A[2])] - u[Lay<T>::at(g, D.blk, B2[0], B2[1], B2[2])]);
+        }
+        u[dst] = acc / T(nax);
+    }
+}
+
+// Trilinear prolongation and correction, u_f += P e_c with P the 8-point tensor-product interpolation: a fine cell
+// takes (3/4)^(3-d) (1/4)^d of each of the 8 coarse cells that are d = 0 .. 3 steps (one per axis) from its coarse
+// cell towards it, edge and corner ghosts of e_c included (k_exchange_diag); carried-over blocks are injected.  One
+// thread per coarse cell, its 8 children (halved block or merged octet) written.  No ghost is written through.
+template <typename T>
+static __global__ void k_prolong_tri(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
+                                     const XferItem *__restrict__ xf, LevelGeom gc, Skip skip) {
+    const int lgc = gc.lg, nc = gc.n;
+    const int64_t total = static_cast<int64_t>(gc.nb) << (3 * lgc);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int X = static_cast<int>(t & (nc - 1));
+        const int Y = static_cast<int>((t >> lgc) & (nc - 1));
+        const int Z = static_cast<int>((t >> (2 * lgc)) & (nc - 1));
+        const int64_t B = t >> (3 * lgc);
+        if (skip(B)) continue;
+        const XferItem xi = xf[B];
+        if (xi.kind == XF_COPY) {
+            const int64_t gi = Lay<T>::at(gf, xi.src[0], X + 1, Y + 1, Z + 1);
+            uf[gi] = uf[gi] + ec[Lay<T>::at(gc, B, X + 1, Y + 1, Z + 1)];
+            continue;
+        }
+        T e[3][3][3];  // e[dz + 1][dy + 1][dx + 1]: the coarse cell and its 26 neighbours (ghosts included)
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx)
+                    e[dz + 1][dy + 1][dx + 1] = ec[Lay<T>::at(gc, B, X + 1 + dx, Y + 1 + dy, Z + 1 + dz)];
+        int64_t b;
+        int x0, y0, z0;
+        if (xi.kind == XF_HALVE) {
+            b = xi.src[0];
+            x0 = 2 * X;
+            y0 = 2 * Y;
+            z0 = 2 * Z;
+        } else {
+            const int hc = nc >> 1;
+            const int ox = X >= hc, oy = Y >= hc, oz = Z >= hc;
+            b = xi.src[ox + 2 * oy + 4 * oz];
+            x0 = 2 * X - ox * nc;
+            y0 = 2 * Y - oy * nc;
+            z0 = 2 * Z - oz * nc;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 2; ++dx) {
+                                const int d = dx + dy + dz;
+                                const T w = T(d == 0 ? 27.0 / 64.0 : (d == 1 ? 9.0 / 64.0 : (d == 2 ? 3.0 / 64.0 : 1.0 / 64.0)));
+                                acc = acc + w * e[1 + (c ? dz : -dz)][1 + (bb ? dy : -dy)][1 + (a ? dx : -dx)];
+                            }
+                    const int64_t gi = Lay<T>::at(gf, b, x0 + a + 1, y0 + bb + 1, z0 + c + 1);
+                    uf[gi] = uf[gi] + acc;
+                }
+    }
+}
+
 template <typename T, bool CG = false>
 __device__ __forceinline__ void prolong_body(T *__restrict__ uf, LevelGeom gf, const T *__restrict__ ec,
                                              const XferItem *__restrict__ xf, LevelGeom gc, Skip skip, int64_t t0,

@@ -48,6 +48,16 @@ struct Key {
     bool operator==(const Key &o) const { return p == o.p && lev == o.lev && i == o.i && j == o.j && k == o.k; }
 };
 
+// One edge (12 per block) or corner (8 per block) of a block's ghost layer, for the edge and corner ghosts the
+// trilinear prolongation reads.  Edges: code = 4 q + bits, q = 0 for the (x, y) edge, 1 for (x, z), 2 for (y, z),
+// bit 0 set for the plus side of the first axis, bit 1 for the second.  Corners: code = bits, bit a set for the plus
+// side of axis a.  nbr: the same-level block across the edge or corner (the same problem), -1 if there is none (the
+// ghosts are then extrapolated from the block's own face or edge ghosts).
+struct DiagItem {
+    int32_t blk, nbr, code, pad;
+};
+static_assert(sizeof(DiagItem) == 16, "DiagItem layout");
+
 struct HostLevel {
     int32_t n = 0;
     std::vector<Key> keys;
@@ -55,6 +65,7 @@ struct HostLevel {
     std::vector<FaceItem> faces;    // every block face that is not a coarse side of a refinement interface
     std::vector<SegItem> segs;      // coarse sides of refinement interfaces, 4 segments each
     std::vector<XferItem> to_next;  // per block of level l+1 (empty on the coarsest level)
+    std::vector<DiagItem> edges, corners;  // filled by build_diagonal (trilinear prolongation only)
 };
 
 struct HostHierarchy {
@@ -67,6 +78,9 @@ struct HostHierarchy {
 // the others carry their blocks over unchanged.
 mg_status build_hierarchy(int32_t R, int32_t n, int32_t n_problems, const std::vector<Key> &leaves,
                           int32_t max_coarse, HostHierarchy &out, std::string &err);
+
+// Edge and corner items of every block of a level (see DiagItem).
+void build_diagonal(int32_t R, HostLevel &L);
 
 void set_error(const std::string &msg);
 

@@ -382,8 +382,9 @@ void vcycle_walk(mg_forest *F, int l, int entry, E &ex) {
     ex.restrict_to(l, fast);
     vcycle_walk<T, MODE>(F, l + 1, fast ? ENTRY_NONE : ENTRY_FULL, ex);
     if (l + 1 != last) ex.exchange(l + 1, !jac);  // Jacobi sweeps write no ghosts through
-    ex.prolong_from(l, fast);
-    ex.exchange(l, fast);
+    const bool fast_p = fast && F->cfg.prolongation == 0;  // the trilinear prolongation writes no ghost through
+    ex.prolong_from(l, fast_p);
+    ex.exchange(l, fast_p);
     for (int i = 0; i < F->cfg.nu2; ++i) {
         if (jac) {
             if (i) ex.exchange(l, false);
@@ -401,6 +402,16 @@ void vcycle_walk(mg_forest *F, int l, int entry, E &ex) {
 int entry32(mg_forest *F, int l) {
     if (l == 0) return ENTRY_INTERFACE;
     return transfer32_specialised(F->L[l - 1]) ? ENTRY_NONE : ENTRY_FULL;
+}
+
+// Edge and corner ghosts of a level (trilinear prolongation; the face ghosts are current): edges, then corners.
+template <typename T>
+void exchange_diag(mg_forest *F, DevLevel &d, T *u) {
+    if (!d.nedges) return;
+    k_exchange_diag<T><<<grid_for(static_cast<int64_t>(d.nedges) * d.g.n), kThreads, 0, F->st>>>(
+        u, d.edges, d.nedges, d.g, false, skip_of(F, d));
+    k_exchange_diag<T><<<grid_for(d.ncorners), kThreads, 0, F->st>>>(u, d.corners, d.ncorners, d.g, true,
+                                                                     skip_of(F, d));
 }
 
 template <typename T, int MODE>
@@ -466,6 +477,13 @@ struct LaunchExec {
     }
     void prolong_from(int l, bool fast) {
         DevLevel &d = F->L[l], &c = F->L[l + 1];
+        if (F->cfg.prolongation == 1) {  // trilinear: the coarse correction's edge and corner ghosts first
+            Prof p(F, cat_of<T>(P_PROL64), 3);
+            exchange_diag<T>(F, c, ufield<T>(c));
+            k_prolong_tri<T><<<grid_for(c.cells()), kThreads, 0, F->st>>>(ufield<T>(d), d.g, ufield<T>(c), d.xfer,
+                                                                          c.g, skip_of(F, c));
+            return;
+        }
         Prof p(F, cat_of<T>(P_PROL64), 1);
         if (fast)
             launch_prolong32(F, d, c);
@@ -537,7 +555,8 @@ struct PartExec {
 // Levels from which the tail kernel can run the rest of an FP32 V-cycle: every deeper level has a specialised
 // column smoother (edge 4..128).
 bool tail_possible(mg_forest *F, int l) {
-    if (F->cfg.precision != 1 || l < 0 || l >= static_cast<int>(F->L.size())) return false;
+    if (F->cfg.precision != 1 || F->cfg.prolongation != 0 || l < 0 || l >= static_cast<int>(F->L.size()))
+        return false;
     for (int m = l; m < static_cast<int>(F->L.size()); ++m)
         if (F->L[m].g.lg < 2 || F->L[m].g.lg > 7) return false;
     return true;
@@ -1222,6 +1241,10 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         set_error("bad coarse_coef (0 rediscretised from k, 1 face-averaged)");
         return MG_ERR_INVALID_ARG;
     }
+    if (cfg->prolongation < 0 || cfg->prolongation > 1) {
+        set_error("bad prolongation (0 face-neighbour linear, 1 trilinear)");
+        return MG_ERR_INVALID_ARG;
+    }
 
     if ((cfg->smoother == 1 || cfg->coarse_iters > 0) && cfg->precision != 0) {
         set_error("the damped Jacobi smoother and coarsest solver run FP64 cycles (precision 0)");
@@ -1290,6 +1313,13 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
             if (!itf.empty() && (st = upload(F, &d.ifaces, itf)) != MG_OK) return fail(st);
         }
         if (!h.to_next.empty() && (st = upload(F, &d.xfer, h.to_next)) != MG_OK) return fail(st);
+        if (F->cfg.prolongation == 1) {  // edge and corner ghosts for the trilinear prolongation
+            build_diagonal(F->H.R, F->H.levels[l]);
+            d.nedges = static_cast<int>(h.edges.size());
+            d.ncorners = static_cast<int>(h.corners.size());
+            if ((st = upload(F, &d.edges, h.edges)) != MG_OK) return fail(st);
+            if ((st = upload(F, &d.corners, h.corners)) != MG_OK) return fail(st);
+        }
         d.all_halve = !h.to_next.empty() &&
                       std::all_of(h.to_next.begin(), h.to_next.end(), [](const XferItem &x) { return x.kind == XF_HALVE; });
         std::vector<double> h2(h.h.size()), ih2(h.h.size()), vol(h.h.size());
@@ -1631,6 +1661,7 @@ mg_status mg_exchange_level(mg_forest *F, int32_t level, const double *u_dev, do
     cudaMemsetAsync(pool, 0, d.pool_elems() * sizeof(double), F->st);
     k_pack<double><<<grid_for(d.cells()), kThreads, 0, F->st>>>(pool, u_dev, d.g);
     exchange_any64(F, d, pool);
+    if (F->cfg.prolongation == 1) exchange_diag<double>(F, d, pool);
     const size_t per = static_cast<size_t>(d.g.P) * d.g.P * d.g.P;
     cudaMemcpy2DAsync(padded_dev, per * sizeof(double), pool, d.g.bs * sizeof(double), per * sizeof(double), d.g.nb,
                       cudaMemcpyDeviceToDevice, F->st);

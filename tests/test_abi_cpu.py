@@ -166,6 +166,7 @@ _ROOTS = [(0, 0, i, j, k) for k in range(2) for j in range(2) for i in range(2)]
     (_ROOTS, {"omega": float("nan")}, 1, "omega"),
     (_ROOTS, {"coarse_iters": -1}, 1, "coarse_iters"),
     (_ROOTS, {"coarse_coef": 2}, 1, "coarse_coef"),
+    (_ROOTS, {"prolongation": 2}, 1, "prolongation"),
     (_ROOTS, {"smoother": 1, "precision": 1}, 1, "damped Jacobi"),
     (_ROOTS, {"roots": 0}, 1, "roots must be"),
     (_ROOTS, {"n": 2048}, 3, "4..1024"),

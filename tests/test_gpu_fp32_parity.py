@@ -35,8 +35,9 @@ def _problem(R, n, keys, coeff, seed):
     return k, f
 
 
-def _oracle_iterates(R, n, keys, k, f, variant, coarse_coef="k"):
-    mg = OracleMG(R, n, keys, k_user=None if k is None else k.cpu().numpy(), variant=variant, coarse_coef=coarse_coef)
+def _oracle_iterates(R, n, keys, k, f, variant, coarse_coef="k", prolongation="linear"):
+    mg = OracleMG(R, n, keys, k_user=None if k is None else k.cpu().numpy(), variant=variant, coarse_coef=coarse_coef,
+                  prolongation=prolongation)
     fn = f.cpu().numpy()
     u64, _ = mg.solve(fn, cycles=CYCLES)
     u32, _ = mixed_solve(mg, fn, steps=1, inner=CYCLES)
@@ -133,6 +134,23 @@ def test_fp32_step_face_averaged_coarse_coefficients(name, variant):
                 coarse_coef="faces")
     got = _fp32_step(F, f, k)
     _check(got, u64, u32, f"{name} {variant} face-averaged")
+    F.close()
+
+
+@pytest.mark.parametrize("name,variant", [("uniform_2x64", "C"), ("sphere_2x32", "C")])
+def test_fp32_step_trilinear_prolongation(name, variant):
+    """FP32 cycles with the trilinear prolongation (edge and corner ghosts, 8-point interpolation, full exchange
+    after it) and face-averaged coarse levels, against the oracle's FP64 and FP32 iterates of the same cycle."""
+    if name == "uniform_2x64":
+        R, n, keys = 2, 64, syn.uniform_leaves(2)
+    else:
+        R, n, keys = syn.workload_forest(name)
+    k, f = _problem(R, n, keys, True, seed=171)
+    u64, u32 = _oracle_iterates(R, n, keys, k, f, variant, coarse_coef="faces", prolongation="trilinear")
+    F = _forest(R, n, keys, coeff=True, interface_flux=(variant == "C"), precision=1, inner_cycles=CYCLES,
+                coarse_coef="faces", prolongation="trilinear")
+    got = _fp32_step(F, f, k)
+    _check(got, u64, u32, f"{name} {variant} trilinear")
     F.close()
 
 
