@@ -241,6 +241,13 @@ mg_status mg_set_tail(mg_forest *forest, int32_t level);
  * another `which`.  Synchronises the stream. */
 mg_status mg_selftest_waits(mg_forest *forest, int32_t which);
 
+/* Measured FMA throughput of the current device (TFLOP/s, 2 flop per FMA): eight independent FMA chains per thread on
+ * 8 CTAs of 256 threads per SM, one timed launch after a warm-up, on the legacy default stream; synchronises the
+ * device, so call it while nothing else is queued.  FP64 (about 0.06 s) and scalar FP32 (about 0.03 s); either output
+ * may be NULL, not both (MG_ERR_INVALID_ARG); MG_ERR_CUDA without a device.  The roof of the kernels bound by
+ * arithmetic rather than memory (the FP64 outer residual); no counterpart in the paper. */
+mg_status mg_alu_peaks(double *fp64_tflops, double *fp32_tflops);
+
 /* ---------------------------------------------------------------------------------------------------------------
  * Batches: many independent problems with different block sizes (uneven octree forests), solved together.
  * Every problem is its own forest over [0,1]^3 with cfg->roots root blocks per axis; its leaves are the rows of

@@ -3,4 +3,4 @@
 The solver lives in libocmg.so (include/octmg.h); this package is its thin Python front end.
 """
 from ._lib import MGError, load  # noqa: F401
-from .api import Batch, Forest, MGSolveFn  # noqa: F401
+from .api import Batch, Forest, MGSolveFn, alu_peaks  # noqa: F401

@@ -77,6 +77,7 @@ SIGNATURES = {
     "mg_get_tail": (I32, [P, IP]),
     "mg_set_tail": (I32, [P, I32]),
     "mg_selftest_waits": (I32, [P, I32]),
+    "mg_alu_peaks": (I32, [DP, DP]),
     "mg_get_smoother_shape": (I32, [P, I32, IP]),
     "mg_set_smoother_shape": (I32, [P, I32, IP]),
     "mg_profile_read": (I32, [P, I32, _c.c_char_p, DP, _c.POINTER(_c.c_int64), IP]),

@@ -330,6 +330,14 @@ class Batch:
         return out
 
 
+def alu_peaks():
+    """Measured FMA throughput of the current device, (FP64, FP32) in TFLOP/s (mg_alu_peaks; synchronises it)."""
+    lib = _lib.load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib.check(lib.mg_alu_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def _profile_read_handle(lib, h):
     nf = ctypes.c_int32()
     _lib.check(lib.mg_profile_read(h, 0, None, None, None, ctypes.byref(nf)))

@@ -196,6 +196,7 @@ def test_batch_host_checks(lib):
     assert st == 3 and "problem 1" in lib.mg_last_error().decode() and h.value is None
     m = ctypes.c_int32()
     assert lib.mg_batch_set_tail_mode(None, 0) == 1 and lib.mg_batch_get_tail_mode(None, ctypes.byref(m)) == 1
+    assert lib.mg_alu_peaks(None, None) == 1  # no output: refused before any CUDA call
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

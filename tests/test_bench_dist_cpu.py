@@ -129,6 +129,7 @@ def test_gpu_arm_json_contract_with_a_stand_in_library(monkeypatch, capsys):
         return R, n, keys, torch.ones_like(f), f
 
     monkeypatch.setattr(pkg, "Forest", StandIn)
+    monkeypatch.setattr(pkg, "alu_peaks", lambda: (1.2, 70.0))
     monkeypatch.setattr(torch.cuda, "Event", Event)
     for name in ("synchronize", "set_device", "current_stream"):
         monkeypatch.setattr(torch.cuda, name, lambda *a, **k: None)
@@ -163,6 +164,7 @@ def test_gpu_arm_json_contract_with_a_stand_in_library(monkeypatch, capsys):
     assert abs(cyc["achieved_gbs"] - d["value"] * 78.0) < 1e-9 and abs(cyc["frac"] * cyc["peak_gbs"] -
                                                                      cyc["achieved_gbs"]) < 1e-9
     assert d["e2e"]["h2d_bytes_per_step"] == 2 * cells * 8 and d["e2e"]["d2h_bytes_per_step"] == cells * 8
+    assert d["alu_peaks_tflops"]["fp64_fma"] == 1.2 and d["alu_peaks_tflops"]["fp32_fma"] == 70.0
     assert d["config"]["coarse_coefficients"].startswith("face-averaged")
     alt = d["other_coarse_operator"]
     assert alt["coarse_coefficients"].startswith("rediscretised") and alt["fp64"]["cycles"] == 12
