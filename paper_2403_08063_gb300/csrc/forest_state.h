@@ -161,7 +161,8 @@ struct mg_forest {
     // several independent problems: per-problem reductions, scales, block-diagonal coarsest inverse
     int np = 1;
     int32_t *pstart = nullptr, *pblk = nullptr;  // level-0 blocks of problem p: pblk[pstart[p] .. pstart[p+1])
-    double *bsum = nullptr;                      // per level-0 block sums of h^3 x^2
+    double *bsum = nullptr;                      // per-CTA partial sums of h^3 x^2 over level 0, bsum_cpb per block
+    int bsum_cpb = 1;
     double *psum = nullptr, *psum_h = nullptr;   // per-problem sums (device, pinned host)
     float *pscale = nullptr, *pscale_h = nullptr;  // per-problem power-of-two residual scale (device, pinned host)
     double *pinv = nullptr, *pinv_h = nullptr;     // its inverse in FP64

@@ -1436,11 +1436,68 @@ static __global__ void __launch_bounds__(256) k_residual_restrict32(
                                        static_cast<int64_t>(gridDim.x) * blockDim.x, ax, ay, az);
 }
 
+// The 8 children (2X + a, 2Y + b, 2Z + c), a, b, c in {1, 2}, of coarse cell (X, Y, Z) in fine block b of a halving
+// level (fine edge 2^LG) take the values val[c][b][a].  With nbr6 (the fine level's face table, as in k_smooth) every
+// child on a block face also writes its new value through to the same-level neighbour's mirroring ghost, or the
+// reflected value to its own boundary ghost, so that afterwards only refinement-interface ghosts need an exchange.
+template <int LG>
+__device__ __forceinline__ void prolong32_put(float *__restrict__ uf, int64_t bsf, int64_t b, int X, int Y, int Z,
+                                              const float (&val)[2][2][2], const int32_t *__restrict__ nbr6) {
+    using Bx = Box32<LG>;
+    constexpr int nc = (1 << LG) / 2;
+    const int corner = (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;  // in-block offset of the box corner
+    float *ub = uf + b * bsf + corner;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) ub[Bx::off(a + 1, bb + 1, c + 1)] = val[c][bb][a];
+    if (!nbr6) return;
+    constexpr int n = Bx::n, H = Bx::HP, PL = Bx::P * Bx::HP, HALF = Bx::HALF;
+    // x faces: one lane per coarse row (X = 0: children a = 0, X = nc - 1: children a = 1)
+    if (X == 0 || X == nc - 1) {
+        const int a = X == 0 ? 0 : 1;
+        const int nbv = nbr6[b * 6 + a];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb) {
+                const int hs = (a + bb + c + 1) & 1;  // half of the child (its padded coordinate sum's parity)
+                const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;  // offset inside its half
+                if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (a ? -n / 2 : n / 2)] = val[c][bb][a];
+                else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q] = -val[c][bb][a];
+            }
+    }
+    // y and z faces: whole coarse rows
+    if (Y == 0 || Y == nc - 1 || Z == 0 || Z == nc - 1) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int hs = (a + bb + c + 1) & 1;
+                    const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;
+                    const int cc[3] = {0, 2 * Y + bb, 2 * Z + c};
+#pragma unroll
+                    for (int axis = 1; axis < 3; ++axis) {
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            if (cc[axis] != (side ? n - 1 : 0)) continue;
+                            const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
+                            const int nbv = nbr6[b * 6 + 2 * axis + side];
+                            if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (side ? -Dm : Dm)] = val[c][bb][a];
+                            else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q + (side ? E : -E)] = -val[c][bb][a];
+                        }
+                    }
+                }
+    }
+}
+
 // FP32 prolongation + correction for a level whose blocks all halve (fine edge 2^LG): one thread per coarse cell
-// adds 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) to its 8 children, fine offsets as in Box32.  With nbr6 (the
-// fine level's face table, as in k_smooth) every child on a block face also writes its new value through to the
-// same-level neighbour's mirroring ghost, or the reflected value to its own boundary ghost, so that afterwards only
-// refinement-interface ghosts need an exchange.
+// adds 1/4 (e_C + e_{C+sx} + e_{C+sy} + e_{C+sz}) to its 8 children, fine offsets as in Box32, and writes them
+// through to the face ghosts (prolong32_put).
 template <int LG, bool CG = false>
 __device__ __forceinline__ void prolong32_body(float *__restrict__ uf, int64_t bsf, const float *__restrict__ ec,
                                                const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc,
@@ -1464,65 +1521,17 @@ __device__ __forceinline__ void prolong32_body(float *__restrict__ uf, int64_t b
         const float ezm = ldv<CG>(oth + ((Xc >> 1) - PLc)), ezp = ldv<CG>(oth + ((Xc >> 1) + PLc));
         const float ex[2] = {exm, exp_}, ey[2] = {eym, eyp}, ez[2] = {ezm, ezp};
         const int64_t b = xf[B].src[0];
-        float *ub = uf + b * bsf + (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;
-        float cur[2][2][2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-                for (int a = 0; a < 2; ++a) cur[c][bb][a] = ldv<CG>(ub + Bx::off(a + 1, bb + 1, c + 1));
-        const int corner = (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;  // in-block offset of the box corner
-        constexpr int n = Bx::n, H = Bx::HP, PL = Bx::P * Bx::HP, HALF = Bx::HALF;
+        const float *ub = uf + b * bsf + (2 * Z * Bx::P + 2 * Y) * Bx::HP + X;
         float val[2][2][2];
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    val[c][bb][a] = cur[c][bb][a] + 0.25f * ((e0 + ex[a]) + (ey[bb] + ez[c]));
-                    ub[Bx::off(a + 1, bb + 1, c + 1)] = val[c][bb][a];
-                }
-        if (!nbr6) continue;
-        // x faces: one lane per coarse row (X = 0: children a = 0, X = nc - 1: children a = 1)
-        if (X == 0 || X == nc - 1) {
-            const int a = X == 0 ? 0 : 1;
-            const int nbv = nbr6[b * 6 + a];
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int bb = 0; bb < 2; ++bb) {
-                    const int hs = (a + bb + c + 1) & 1;  // half of the child (its padded coordinate sum's parity)
-                    const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;  // offset inside its half
-                    if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (a ? -n / 2 : n / 2)] = val[c][bb][a];
-                    else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q] = -val[c][bb][a];
-                }
-        }
-        // y and z faces: whole coarse rows
-        if (Y == 0 || Y == nc - 1 || Z == 0 || Z == nc - 1) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        const int hs = (a + bb + c + 1) & 1;
-                        const int q = corner + Bx::off(a + 1, bb + 1, c + 1) - hs * HALF;
-                        const int cc[3] = {0, 2 * Y + bb, 2 * Z + c};
-#pragma unroll
-                        for (int axis = 1; axis < 3; ++axis) {
-#pragma unroll
-                            for (int side = 0; side < 2; ++side) {
-                                if (cc[axis] != (side ? n - 1 : 0)) continue;
-                                const int Dm = axis == 1 ? n * H : n * PL, E = axis == 1 ? H : PL;
-                                const int nbv = nbr6[b * 6 + 2 * axis + side];
-                                if (nbv >= 0) uf[nbv * bsf + hs * HALF + q + (side ? -Dm : Dm)] = val[c][bb][a];
-                                else if (nbv == -1) uf[b * bsf + (hs ^ 1) * HALF + q + (side ? E : -E)] = -val[c][bb][a];
-                            }
-                        }
-                    }
-        }
+                for (int a = 0; a < 2; ++a)
+                    val[c][bb][a] = ldv<CG>(ub + Bx::off(a + 1, bb + 1, c + 1)) +
+                                    0.25f * ((e0 + ex[a]) + (ey[bb] + ez[c]));
+        prolong32_put<LG>(uf, bsf, b, X, Y, Z, val, nbr6);
     }
 }
 
@@ -1534,6 +1543,86 @@ static __global__ void __launch_bounds__(256) k_prolong32(float *__restrict__ uf
     prolong32_body<LG>(uf, bsf, ec, xf, nbc, bsc, nbr6, skip,
                        blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
                        static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
+// The same prolongation with one thread per segment of ZC coarse cells of a z-column (X fastest across threads, then
+// Y, then the segment, then the block).  The thread loads the segment's coarse values once (the column's ZC + 2 and
+// the four lateral neighbours per cell) and the next cell's 8 children before it stores this cell's: loads touch
+// interior cells only, stores touch other interior cells and ghosts, so the early loads read the values the cell-by-cell
+// order would.  Each child takes the expression of prolong32_body, so the results are bit-identical to it.
+template <int LG, int ZC>
+static __global__ void __launch_bounds__(256) k_prolong32z(float *__restrict__ uf, int64_t bsf,
+                                                           const float *__restrict__ ec,
+                                                           const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc,
+                                                           const int32_t *__restrict__ nbr6, Skip skip) {
+    using Bx = Box32<LG>;
+    constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), PLc = Pc * HPc, HALFc = Pc * PLc;
+    static_assert(nc % ZC == 0 && (ZC & (ZC - 1)) == 0, "ZC: a power of two dividing the coarse edge");
+    constexpr int LS = LC - (ZC == 1 ? 0 : ZC == 2 ? 1 : ZC == 4 ? 2 : 3);  // log2 of the segments per column
+    static_assert(ZC <= 8, "ZC up to 8");
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t >= (static_cast<int64_t>(nbc) << (2 * LC + LS))) return;
+    const int X = static_cast<int>(t) & (nc - 1), Y = static_cast<int>(t >> LC) & (nc - 1);
+    const int seg = static_cast<int>(t >> (2 * LC)) & ((1 << LS) - 1);
+    const int64_t B = t >> (2 * LC + LS);
+    if (skip(B)) return;
+    const int Z0 = seg * ZC, Xc = X + 1, Yc = Y + 1;
+    const float *eb = ec + B * bsc;
+    // coarse padded cell (xc, yc, zc) in the split layout
+    const auto E = [&](int xc, int yc, int zc) {
+        return eb[((xc + yc + zc) & 1) * HALFc + (zc * Pc + yc) * HPc + (xc >> 1)];
+    };
+    float col[ZC + 2], exm[ZC], exp_[ZC], eym[ZC], eyp[ZC];
+#pragma unroll
+    for (int z = 0; z < ZC + 2; ++z) col[z] = E(Xc, Yc, Z0 + z);  // padded z = Z0 .. Z0 + ZC + 1
+#pragma unroll
+    for (int z = 0; z < ZC; ++z) {
+        const int Zc = Z0 + z + 1;
+        exm[z] = E(Xc - 1, Yc, Zc);
+        exp_[z] = E(Xc + 1, Yc, Zc);
+        eym[z] = E(Xc, Yc - 1, Zc);
+        eyp[z] = E(Xc, Yc + 1, Zc);
+    }
+    const int64_t b = xf[B].src[0];
+    const float *ub = uf + b * bsf + (2 * Z0 * Bx::P + 2 * Y) * Bx::HP + X;
+    constexpr int ZSTEP = 2 * Bx::P * Bx::HP;  // two fine planes
+    float cur[2][2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) cur[c][bb][a] = ub[Bx::off(a + 1, bb + 1, c + 1)];
+#pragma unroll
+    for (int z = 0; z < ZC; ++z) {
+        float nxt[2][2][2];
+        if (z + 1 < ZC) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) nxt[c][bb][a] = ub[(z + 1) * ZSTEP + Bx::off(a + 1, bb + 1, c + 1)];
+        }
+        const float e0 = col[z + 1];
+        const float ex[2] = {exm[z], exp_[z]}, ey[2] = {eym[z], eyp[z]}, ez[2] = {col[z], col[z + 2]};
+        float val[2][2][2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) val[c][bb][a] = cur[c][bb][a] + 0.25f * ((e0 + ex[a]) + (ey[bb] + ez[c]));
+        prolong32_put<LG>(uf, bsf, b, X, Y, Z0 + z, val, nbr6);
+        if (z + 1 < ZC) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) cur[c][bb][a] = nxt[c][bb][a];
+        }
+    }
 }
 
 // Restriction of a plain field (mean of the 8 children; copy for carried-over blocks), e.g. the coefficient k.
@@ -1796,20 +1885,21 @@ static __global__ void k_coarse_solve(T *__restrict__ u, const T *__restrict__ f
 // ------------------------------------------------------------------------------------------------------------
 // FP64 residual over the finest level, r = f - A u (Sec. 5, Eq. 1), written as FP32 r * scale_p (scale_p a power of two per
 // problem, so the scaling is exact), with the FP32 correction field zeroed, and per-block sums of h^3 (r scale_p)^2.
-// Grid: nb * cpb CTAs, CTA (b, c) covers the c-th of cpb contiguous chunks of block b, so each CTA adds one value
-// to its block's sum.  The squared norm is accumulated in FP32 per thread (it decides convergence and is reported
-// to ~1e-6 relative) and in FP64 across threads.  out / zero_out may be null.  ZU: u is known to be zero (a zero
+// Grid: nb * cpb CTAs, CTA (b, c) covers the c-th of cpb contiguous chunks of block b and writes its partial sum to
+// bpart[b cpb + c] (cleared before the launch, so 0 for a skipped block), which k_problem_sums adds up in a fixed
+// order, so the norm is the same from run to run.  The squared norm is accumulated in FP32 per thread (it decides convergence and is reported to
+// ~1e-6 relative) and in FP64 across threads.  out / zero_out may be null.  ZU: u is known to be zero (a zero
 // initial guess), so r = f without reading u or the operator.
 // ------------------------------------------------------------------------------------------------------------
 template <int MODE, bool ZU = false>
-static __global__ void k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
+static __global__ void __launch_bounds__(kThreads, 5) k_residual_norm(const double *__restrict__ u, const double *__restrict__ f, Coef cf,
                                        const double *__restrict__ ih2, const float *__restrict__ vol, LevelGeom g,
                                        int cpb, float *__restrict__ out, const float *__restrict__ pscale,
-                                       const int32_t *__restrict__ bprob, double *__restrict__ bsum,
+                                       const int32_t *__restrict__ bprob, double *__restrict__ bpart,
                                        float *__restrict__ zero_out, Skip skip = Skip{}) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t b = blockIdx.x / cpb;
-    if (skip(b)) return;  // the whole CTA: its block's sum stays 0
+    if (skip(b)) return;  // the whole CTA: its partial stays 0
     const int chunk = blockIdx.x - static_cast<int>(b * cpb);
     const int per = (1 << (3 * lg)) / cpb;
     const int sexp = static_cast<int>((__float_as_uint(pscale[bprob[b]]) >> 23) & 0xff) - 127;  // scale = 2^sexp
@@ -1843,13 +1933,14 @@ static __global__ void k_residual_norm(const double *__restrict__ u, const doubl
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) s += sm[w];
-        atomicAdd(&bsum[b], s);
+        bpart[blockIdx.x] = s;
     }
 }
 
-// Per-block sums of h^3 x^2 over the interior of an FP64 field (same grid shape as k_residual_norm).
+// Per-CTA partial sums of h^3 x^2 over the interior of an FP64 field (same grid shape and partials as
+// k_residual_norm).
 static __global__ void k_block_norm64(const double *__restrict__ x, const double *__restrict__ vol, LevelGeom g,
-                                      int cpb, double *__restrict__ bsum) {
+                                      int cpb, double *__restrict__ bpart) {
     const int lg = g.lg, n = g.n, P = g.P;
     const int64_t b = blockIdx.x / cpb;
     const int chunk = blockIdx.x - static_cast<int>(b * cpb);
@@ -1869,18 +1960,34 @@ static __global__ void k_block_norm64(const double *__restrict__ x, const double
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) s += sm[w];
-        atomicAdd(&bsum[b], s);
+        bpart[blockIdx.x] = s;
     }
 }
 
-// Per-problem sums of the per-block sums, blocks of problem p listed in pblk[pstart[p] .. pstart[p+1]).
-static __global__ void k_problem_sums(const double *__restrict__ bsum, const int32_t *__restrict__ pstart,
-                                      const int32_t *__restrict__ pblk, int np, double *__restrict__ psum) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// Per-problem sums of the per-CTA partials (cpb per block, blocks of problem p listed in pblk[pstart[p] ..
+// pstart[p+1])): one CTA of kThreads per problem, each thread adding a fixed strided subset, then a fixed tree, so
+// the sum does not depend on the order in which the partials were written.
+static __global__ void __launch_bounds__(kThreads) k_problem_sums(const double *__restrict__ bpart, int cpb,
+                                                                  const int32_t *__restrict__ pstart,
+                                                                  const int32_t *__restrict__ pblk, int np,
+                                                                  double *__restrict__ psum) {
+    const int p = blockIdx.x;
     if (p >= np) return;
+    const int first = pstart[p];
+    const int64_t cnt = static_cast<int64_t>(pstart[p + 1] - first) * cpb;
     double s = 0.0;
-    for (int i = pstart[p]; i < pstart[p + 1]; ++i) s += bsum[pblk[i]];
-    psum[p] = s;
+    for (int64_t i = threadIdx.x; i < cnt; i += kThreads)
+        s += bpart[static_cast<int64_t>(pblk[first + i / cpb]) * cpb + i % cpb];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double sm[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += sm[w];
+        psum[p] = t;
+    }
 }
 
 // A u over a whole level in FP64 (operator application; ghosts already exchanged).

@@ -314,6 +314,10 @@ const Restrict32Fn kRestrict32[3][5] = {
 using Prolong32Fn = void (*)(float *, int64_t, const float *, const XferItem *, int32_t, int64_t,
                              const int32_t *, Skip);
 const Prolong32Fn kProlong32[5] = {k_prolong32<3>, k_prolong32<4>, k_prolong32<5>, k_prolong32<6>, k_prolong32<7>};
+// fine block edges 32, 64, 128: one thread per segment of kProlongZC coarse cells of a z-column
+constexpr int kProlongZC = 2;
+const Prolong32Fn kProlong32z[3] = {k_prolong32z<5, kProlongZC>, k_prolong32z<6, kProlongZC>,
+                                    k_prolong32z<7, kProlongZC>};
 
 void launch_residual_restrict32(mg_forest *F, DevLevel &d, DevLevel &c) {
     // one coarse cell per thread (no grid-stride loop): its load chain xf -> fine block -> 64 loads is latency-bound
@@ -324,6 +328,12 @@ void launch_residual_restrict32(mg_forest *F, DevLevel &d, DevLevel &c) {
 }
 
 void launch_prolong32(mg_forest *F, DevLevel &d, DevLevel &c) {
+    if (d.g.lg >= 5) {
+        const auto grid = static_cast<unsigned>((c.cells() / kProlongZC + kThreads - 1) / kThreads);
+        kProlong32z[d.g.lg - 5]<<<grid, kThreads, 0, F->st>>>(d.u32, d.g.bs, c.u32, d.xfer, c.g.nb, c.g.bs, d.nbr6,
+                                                              skip_of(F, c));
+        return;
+    }
     kProlong32[d.g.lg - 3]<<<grid_for(c.cells()), kThreads, 0, F->st>>>(d.u32, d.g.bs, c.u32, d.xfer, c.g.nb, c.g.bs,
                                                                           d.nbr6, skip_of(F, c));
 }
@@ -593,7 +603,7 @@ int chunks_per_block(const DevLevel &d) { return std::max(1, static_cast<int>(d.
 
 // Per-problem sums of the per-block sums to the host (pinned psum_h), synchronising the stream.
 mg_status read_problem_sums(mg_forest *F) {
-    k_problem_sums<<<(F->np + 127) / 128, 128, 0, F->st>>>(F->bsum, F->pstart, F->pblk, F->np, F->psum);
+    k_problem_sums<<<F->np, kThreads, 0, F->st>>>(F->bsum, F->bsum_cpb, F->pstart, F->pblk, F->np, F->psum);
     MG_CUDA(cudaMemcpyAsync(F->psum_h, F->psum, F->np * sizeof(double), cudaMemcpyDeviceToHost, F->st));
     MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
@@ -632,7 +642,7 @@ mg_status upload_scales(mg_forest *F, const std::vector<double> &mult) {
 }
 
 mg_status enqueue_problem_sums(mg_forest *F) {
-    k_problem_sums<<<(F->np + 127) / 128, 128, 0, F->st>>>(F->bsum, F->pstart, F->pblk, F->np, F->psum);
+    k_problem_sums<<<F->np, kThreads, 0, F->st>>>(F->bsum, F->bsum_cpb, F->pstart, F->pblk, F->np, F->psum);
     MG_CUDA(cudaMemcpyAsync(F->psum_h, F->psum, F->np * sizeof(double), cudaMemcpyDeviceToHost, F->st));
     return MG_OK;
 }
@@ -646,7 +656,7 @@ mg_status residual64(mg_forest *F, double *u, const double *f, float *out, float
     DevLevel &d = F->L[0];
     if (!zero_u) exchange<double, MODE>(F, d, u);
     const int cpb = chunks_per_block(d);
-    MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
+    MG_CUDA(cudaMemsetAsync(F->bsum, 0, static_cast<size_t>(d.g.nb) * cpb * sizeof(double), F->st));
     {
         Prof p(F, P_RESID64, 1);
         if (zero_u)
@@ -1383,7 +1393,8 @@ mg_status create(const mg_config *cfg, mg_forest **out) {
         for (size_t b = 0; b < h0.keys.size(); ++b) pblk[fill[h0.keys[b].p]++] = static_cast<int32_t>(b);
         if ((st = upload(F, &F->pstart, pstart)) != MG_OK) return fail(st);
         if ((st = upload(F, &F->pblk, pblk)) != MG_OK) return fail(st);
-        if ((st = dalloc(F, &F->bsum, static_cast<int64_t>(h0.keys.size()))) != MG_OK) return fail(st);
+        F->bsum_cpb = chunks_per_block(F->L[0]);
+        if ((st = dalloc(F, &F->bsum, static_cast<int64_t>(h0.keys.size()) * F->bsum_cpb)) != MG_OK) return fail(st);
         if ((st = dalloc(F, &F->psum, np)) != MG_OK) return fail(st);
         if ((st = dalloc(F, &F->pscale, np)) != MG_OK) return fail(st);
         if ((st = dalloc(F, &F->pinv, np)) != MG_OK) return fail(st);
@@ -1422,7 +1433,6 @@ mg_status reference_norms(mg_forest *F) {
     std::vector<double> sums(F->np, 0.0);
     if (!F->gb) {
         const int cpb = chunks_per_block(d);
-        MG_CUDA(cudaMemsetAsync(F->bsum, 0, d.g.nb * sizeof(double), F->st));
         k_block_norm64<<<d.g.nb * cpb, kThreads, 0, F->st>>>(d.f64, d.vol_64, d.g, cpb, F->bsum);
         MG_TRY(read_problem_sums(F));
         for (int p = 0; p < F->np; ++p) sums[p] = F->psum_h[p];

@@ -12,9 +12,12 @@ DEV = "cuda:0"
 
 @pytest.mark.parametrize("name,coeff,coarse_coef", [("sphere_2x16", True, "k"), ("sphere_2x16", False, "k"),
                                                     ("uniform_4x16", True, "k"), ("sphere_2x16", True, "faces"),
-                                                    ("uniform_4x16", True, "faces")])
+                                                    ("uniform_4x16", True, "faces"), ("sphere_2x32", True, "faces"),
+                                                    ("uniform_4x64", True, "faces"), ("uniform_4x64", False, "k")])
 def test_tail_reproduces_the_launched_vcycle(name, coeff, coarse_coef):
-    """Also with face-averaged coarse coefficients, whose coarse levels run the halved-face coefficient mode."""
+    """Also with face-averaged coarse coefficients, whose coarse levels run the halved-face coefficient mode, and on
+    32^3 and 64^3 blocks, where the launched V-cycle's prolongation runs the z-column kernel and the tail the
+    cell-per-thread body."""
     from paper_2403_08063_gb300 import Forest
     R, n, keys = syn.workload_forest(name)
     dev = torch.device(DEV)
