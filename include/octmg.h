@@ -189,7 +189,9 @@ mg_status mg_profile_read(mg_forest *forest, int32_t max_families, char *names, 
 /* Launch shape of the FP32 smoother on one level (precision 1, block edges 4..128), five int32 {kind, p1..p4}:
  *   {1, zc, threads, 0, 0}: one thread per zc cells of a z-column (zc 1, 2 or 4), CTAs of 128, 256 or 512 threads;
  *   {2, TY, TZ, D, R}:      edges 32..128: a CTA per TY rows x TZ planes of a block, the other colour's planes
- *                           staged in shared memory by bulk copies D planes ahead, R rows per thread.
+ *                           staged in shared memory by bulk copies D planes ahead, R rows per thread (with
+ *                           variable k 1/k, on face-averaged coarse levels the three face arrays, of both colours,
+ *                           are staged too).
  * mg_smoother_shapes lists the shapes offered for a level (5 int32 each, up to max_shapes into shapes, which may
  * be NULL; *n_shapes receives the count).  The first mg_set_rhs of a forest picks each level's shape by timing
  * every offered shape on the level's own FP32 pools (levels under 2^18 cells take {1, 1, 256, 0, 0}); the choice
@@ -206,14 +208,16 @@ mg_status mg_set_smoother_shape(mg_forest *forest, int32_t level, const int32_t 
 /* Bulk-copy plan of the staged FP32 smoother (k_smooth32t), computed on the host by the same code the kernel's
  * producer thread runs; no GPU is needed.  No counterpart in the paper: it lets a test check every shared-memory copy
  * of the kernel against the rules of cp.async.bulk without running it.  For block edge 2^lg (lg 5..7), coefficient
- * mode coeff (0 constant, 1 variable k) and half-sweep colour `colour`, *n_shapes receives the number of staged
+ * mode coeff (0 constant, 1 variable k with 1/k staged, 2 stored halved face coefficients of a face-averaged coarse
+ * level, ax, ay, az staged) and half-sweep colour `colour`, *n_shapes receives the number of staged
  * shapes ({2, TY, TZ, D, R}) offered; for the one with index shape_index (none: *n_records = 0) shape receives it
  * (5 int32, may be NULL), *smem_bytes the dynamic shared memory a CTA is launched with and *block_bytes the block
  * stride of an FP32 pool (either may be NULL), and records (max_records x 10 int64, may be NULL) every mbarrier arm and
  * bulk copy that the CTAs of one block issue, in issue order per CTA:
  *   {tile (tz * n / TY + ty), kind (0 arm, 1 copy), barrier (0 first planes, 1 + g % (D + 1) group g),
  *    group g (-1: first planes), dst (bytes from the start of dynamic shared memory; -1 for an arm),
- *    array (0 other-half u, 1 other-half kappa, 2 own-half f, 3 own-half kappa; -1), src (bytes from the start of
+ *    array (0 other-half u, 1 other-half kappa or ax, 2 own-half f, 3 own-half kappa or ax, 4 / 5 other-half
+ *    ay / az, 6 / 7 own-half ay / az; -1), src (bytes from the start of
  *    the block in the pool; -1), bytes (armed or copied), lead (floats from the copy's start to the wanted plane
  *    segment; -1), len (floats of the wanted segment; -1)}.
  * *n_records receives the total (records beyond max_records are counted, not written).  MG_ERR_INVALID_ARG for a

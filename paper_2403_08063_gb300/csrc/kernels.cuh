@@ -830,20 +830,24 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // Copy plan of the staged half-sweep below (k_smooth32t), shared by the kernel's producer thread, the launch code
 // (dynamic shared-memory size) and the host-side enumerator that checks every copy against the bulk-copy rules.
 //
-// Shared memory, in floats from the start: RO = D + 2 other-half slots of so floats (u; with variable k, kappa
-// after it), then RW = D + 1 own-half slots of sw floats (f; kappa after it), then 2 G + 2 mbarriers (G = D + 1).
-// A plane segment of len floats starting at float off of its half is copied from off & ~3 (the 16-byte boundary
-// at or below it), (off & 3) + len floats rounded up to a multiple of 4, so it lands off & 3 floats into its slot.
+// Shared memory, in floats from the start: RO = D + 2 other-half slots of NA so floats, then RW = D + 1 own-half
+// slots of NA sw floats, then 2 G + 2 mbarriers (G = D + 1).  NA arrays per half: 1 (constant k: u; f), 2 (1/k: u,
+// kappa; f, kappa) or 4 (stored halved face coefficients: u, ax, ay, az; f, ax, ay, az), each NA-th part of a slot
+// one array's plane segment.  A plane segment of len floats starting at float off of its half is copied from
+// off & ~3 (the 16-byte boundary at or below it), (off & 3) + len floats rounded up to a multiple of 4, so it lands
+// off & 3 floats into its slot.
 // ------------------------------------------------------------------------------------------------------------
 struct S32tPlan {
     int P, H, NA, RO, RW, G;  // padded edge, half-row length, staged arrays per half, ring sizes, group barriers
     int lo, lw, so, sw;       // other / own segment lengths and slot strides (floats)
 };
-__host__ __device__ __forceinline__ S32tPlan s32t_plan(int lg, bool var, int TY, int D) {
+// staged arrays per half of coefficient mode 0, 2 or 3
+__host__ __device__ constexpr int s32t_arrays(int mode) { return mode == 3 ? 4 : (mode == 2 ? 2 : 1); }
+__host__ __device__ __forceinline__ S32tPlan s32t_plan(int lg, int na, int TY, int D) {
     S32tPlan p;
     p.P = (1 << lg) + 2;
     p.H = half_row(p.P);
-    p.NA = var ? 2 : 1;
+    p.NA = na;
     p.RO = 2 + D;
     p.RW = 1 + D;
     p.G = 1 + D;
@@ -868,10 +872,13 @@ __host__ __device__ __forceinline__ int s32t_off_own(const S32tPlan &p, int Zp, 
 __host__ __device__ __forceinline__ uint32_t s32t_bytes(int off, int len) {
     return static_cast<uint32_t>(((off & 3) + len + 3) & ~3) * 4;
 }
+// Array numbers of the a-th staged array of the other and of the own half: 0 other-half u, 1 other-half kappa or
+// ax, 2 own-half f, 3 own-half kappa or ax, 4 / 5 other-half ay / az, 6 / 7 own-half ay / az.
+__host__ __device__ __forceinline__ int s32t_other_array(int a) { return a < 2 ? a : a + 2; }
+__host__ __device__ __forceinline__ int s32t_own_array(int a) { return a < 2 ? a + 2 : a + 4; }
 // The copies of one CTA.  sink.arm(bar, bytes) arms barrier `bar` (0: the first planes; 1 + g % G: group g) with
 // the bytes that will complete it; sink.copy(dst, array, src, lead, bytes, bar) copies `bytes` from float `src` of
-// `array` (0 other-half u, 1 other-half kappa, 2 own-half f, 3 own-half kappa) to shared float `dst`, the wanted
-// segment starting `lead` floats into the copy.
+// `array` (numbered as above) to shared float `dst`, the wanted segment starting `lead` floats into the copy.
 // First: other-half padded planes z0 and z0 + 1 (planes z0 - 1 and z0) into other slots 0 and 1.
 #pragma nv_exec_check_disable
 template <class Sink>
@@ -883,8 +890,7 @@ __host__ __device__ __forceinline__ void s32t_issue_first(const S32tPlan &p, int
         const int off = io ? o1 : o0;
         const uint32_t bb = io ? b1 : b0;
         const int d = s32t_other_slot(p, io);
-        sink.copy(d, 0, off & ~3, off & 3, bb, 0);
-        if (p.NA == 2) sink.copy(d + p.so, 1, off & ~3, off & 3, bb, 0);
+        for (int a = 0; a < p.NA; ++a) sink.copy(d + a * p.so, s32t_other_array(a), off & ~3, off & 3, bb, 0);
     }
 }
 // Group g: other-half padded plane z0 + g + 2 (plane z0 + g + 1) into other slot (g + 2) % RO, own-half padded
@@ -897,20 +903,17 @@ __host__ __device__ __forceinline__ void s32t_issue_group(const S32tPlan &p, int
     const uint32_t bo = s32t_bytes(oo, p.lo), bw = s32t_bytes(ow, p.lw);
     sink.arm(bi, p.NA * (bo + bw));
     const int d0 = s32t_other_slot(p, (g + 2) % p.RO), d1 = s32t_own_slot(p, g % p.RW);
-    sink.copy(d0, 0, oo & ~3, oo & 3, bo, bi);
-    if (p.NA == 2) sink.copy(d0 + p.so, 1, oo & ~3, oo & 3, bo, bi);
-    sink.copy(d1, 2, ow & ~3, ow & 3, bw, bi);
-    if (p.NA == 2) sink.copy(d1 + p.sw, 3, ow & ~3, ow & 3, bw, bi);
+    for (int a = 0; a < p.NA; ++a) sink.copy(d0 + a * p.so, s32t_other_array(a), oo & ~3, oo & 3, bo, bi);
+    for (int a = 0; a < p.NA; ++a) sink.copy(d1 + a * p.sw, s32t_own_array(a), ow & ~3, ow & 3, bw, bi);
 }
 // The kernel's sink: arms the CTA's mbarriers and issues the bulk copies.
 struct S32tDeviceSink {
     float *smem;
-    const float *ou, *ok, *wf, *wk;  // other-half u, kappa; own-half f, kappa (the block's halves)
+    const float *src[8];  // the block's halves of the arrays, numbered as above (null where not staged)
     uint64_t *bar;
     __device__ __forceinline__ void arm(int bi, uint32_t bytes) const { mbar_arm(&bar[bi], bytes); }
     __device__ __forceinline__ void copy(int dst, int array, int off, int, uint32_t bytes, int bi) const {
-        const float *src = array == 0 ? ou : (array == 1 ? ok : (array == 2 ? wf : wk));
-        bulk_load(smem + dst, src + off, bytes, &bar[bi]);
+        bulk_load(smem + dst, src[array] + off, bytes, &bar[bi]);
     }
 };
 
@@ -952,15 +955,18 @@ template <int MODE, int LG, int R>
 static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u, const float *__restrict__ f,
                                                           const float *__restrict__ kap, const float *__restrict__ h2,
                                                           int64_t bs, int colour, const int32_t *__restrict__ nbr6,
-                                                          int TY, int TZ, int D, int *__restrict__ err, Skip skip) {
-    static_assert(MODE == 0 || MODE == 2, "the staged smoother stages 1/k (MODE 2) or nothing (MODE 0)");
+                                                          int TY, int TZ, int D, int *__restrict__ err, Skip skip,
+                                                          const float *__restrict__ ax, const float *__restrict__ ay,
+                                                          const float *__restrict__ az) {
+    static_assert(MODE == 0 || MODE == 2 || MODE == 3, "coefficient modes 0, 2, 3");
     constexpr int n = 1 << LG, NH = n / 2, P = n + 2, H = half_row(P), PL = P * H, HALF = P * PL;
-    constexpr int NA = MODE == 2 ? 2 : 1;  // staged arrays per half
+    constexpr int NA = s32t_arrays(MODE);  // staged arrays per half
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const S32tPlan plan = s32t_plan(LG, MODE == 2, TY, D);
+    const S32tPlan plan = s32t_plan(LG, NA, TY, D);
     const int RO = plan.RO, RW = plan.RW, G = plan.G;
     const int so = plan.so, sw = plan.sw;
-    // other-half slot i: u at ou + i NA so, kappa after it; own-half slot i: f at wf + i NA sw, kappa after it
+    // other-half slot i: u at ou + i NA so, then kappa (MODE 2) or ax, ay, az (MODE 3) so floats apart; own-half
+    // slot i: f at wf + i NA sw, then kappa or ax, ay, az sw floats apart
     float *ou = reinterpret_cast<float *>(smem_raw);
     float *wf = ou + s32t_own_slot(plan, 0);
     // full barriers: bar[0] planes z0 - 1, z0; bar[1 + g % G] group g.  Empty barriers (all consumer warps are done
@@ -985,13 +991,18 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
     int yl0 = tid >> (LG - 1);
     if constexpr (NH < 32) yl0 = (yl0 & ~3) | ((yl0 & 1) << 1) | ((yl0 >> 1) & 1);  // a warp's two rows: same parity
     const int64_t base = b * bs;
-    const float *gou = u + base + (s ^ 1) * HALF, *gok = kap + base + (s ^ 1) * HALF;
-    const float *gwf = f + base + s * HALF, *gwk = kap + base + s * HALF;
+    // the block's halves of the staged arrays, numbered as in s32t_other_array / s32t_own_array
+    const float *c1 = MODE == 3 ? ax : kap;
+    const int64_t ho = base + (s ^ 1) * HALF, hw = base + s * HALF;
 
     const auto off_o = [&](int Zp) { return s32t_off_other(plan, Zp, y0); };
     const auto off_w = [&](int Zp) { return s32t_off_own(plan, Zp, y0); };
     // the producer's copies, as planned by s32t_issue_first / s32t_issue_group
-    const S32tDeviceSink sink{ou, gou, gok, gwf, gwk, bar};
+    const S32tDeviceSink sink{ou,
+                              {u + ho, MODE ? c1 + ho : nullptr, f + hw, MODE ? c1 + hw : nullptr,
+                               MODE == 3 ? ay + ho : nullptr, MODE == 3 ? az + ho : nullptr,
+                               MODE == 3 ? ay + hw : nullptr, MODE == 3 ? az + hw : nullptr},
+                              bar};
     const auto issue_first = [&]() { s32t_issue_first(plan, z0, y0, sink); };
     const auto issue_group = [&](int g) { s32t_issue_group(plan, z0, y0, g, sink); };
     const int nthc = blockDim.x - 32, ncw = nthc >> 5;  // consumer threads and warps; the last warp produces
@@ -1132,6 +1143,24 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
                         const float2 Dn =
                             __fadd2_rn(__fadd2_rn(__fadd2_rn(a0, a1), __fadd2_rn(b0, b1)), __fadd2_rn(e0, e1));
                         v = __fmul2_rn(__ffma2_rn(float2{hh, hh}, fv, sacc), frcp2(Dn));
+                    } else if constexpr (MODE == 3) {
+                        // stored halved faces: the lower ones at the cell (own slot), the upper ones at the x+ and
+                        // y+ neighbours of this plane and the z+ neighbour of the next (other slots)
+                        const int wa = ra - H + C, wb = rb - H + C;
+                        const float2 a0{fw[sw + wa], fw[sw + wb]}, b0{fw[2 * sw + wa], fw[2 * sw + wb]};
+                        const float2 e0{fw[3 * sw + wa], fw[3 * sw + wb]};
+                        const float2 a1{oc[so + ra + 1], oc[so + rb + 1]};
+                        const float2 b1{oc[2 * so + ra + H + C], oc[2 * so + rb + H + C]};
+                        const float2 e1{on[3 * so + ra + C], on[3 * so + rb + C]};
+                        float2 sacc = __fmul2_rn(a0, x0);
+                        sacc = __ffma2_rn(a1, x1, sacc);
+                        sacc = __ffma2_rn(b0, ym, sacc);
+                        sacc = __ffma2_rn(b1, yp, sacc);
+                        sacc = __ffma2_rn(e0, zm, sacc);
+                        sacc = __ffma2_rn(e1, zp, sacc);
+                        const float2 Dn =
+                            __fadd2_rn(__fadd2_rn(__fadd2_rn(a0, a1), __fadd2_rn(b0, b1)), __fadd2_rn(e0, e1));
+                        v = __fmul2_rn(__ffma2_rn(float2{hh, hh}, fv, sacc), frcp2(Dn));
                     } else {
                         const float2 S = __fadd2_rn(__fadd2_rn(__fadd2_rn(x0, x1), __fadd2_rn(ym, yp)), __fadd2_rn(zm, zp));
                         v = div6x2(__ffma2_rn(float2{hb, hb}, fv, S));
@@ -1152,6 +1181,19 @@ static __global__ void __launch_bounds__(544) k_smooth32t(float *__restrict__ u,
                         const float a0 = frcp(k0 + qc[rr][0]), a1 = frcp(k0 + qc[rr][1]);
                         const float b0 = frcp(k0 + kym), b1 = frcp(k0 + kyp);
                         const float e0 = frcp(k0 + zmk[rr]), e1 = frcp(k0 + kzp);
+                        float sacc = a0 * pc[rr][0];
+                        sacc = fmaf(a1, pc[rr][1], sacc);
+                        sacc = fmaf(b0, ym, sacc);
+                        sacc = fmaf(b1, yp, sacc);
+                        sacc = fmaf(e0, zmu[rr], sacc);
+                        sacc = fmaf(e1, zp, sacc);
+                        const float Dn = ((a0 + a1) + (b0 + b1)) + (e0 + e1);
+                        val[rr] = fmaf(hh, fv, sacc) * frcp(Dn);
+                    } else if constexpr (MODE == 3) {
+                        const int w = ro - H + C;
+                        const float a0 = fw[sw + w], a1 = oc[so + ro + 1];
+                        const float b0 = fw[2 * sw + w], b1 = oc[2 * so + ro + H + C];
+                        const float e0 = fw[3 * sw + w], e1 = on[3 * so + ro + C];
                         float sacc = a0 * pc[rr][0];
                         sacc = fmaf(a1, pc[rr][1], sacc);
                         sacc = fmaf(b0, ym, sacc);

@@ -155,15 +155,19 @@ const Smooth32Fn kSmooth32[3][6][3] = {
     {OCTMG_S32(k_smooth32, 3, 2), OCTMG_S32(k_smooth32, 3, 3), OCTMG_S32(k_smooth32, 3, 4),
      OCTMG_S32(k_smooth32, 3, 5), OCTMG_S32(k_smooth32, 3, 6), OCTMG_S32(k_smooth32, 3, 7)}};
 using Smooth32tFn = void (*)(float *, const float *, const float *, const float *, int64_t, int, const int32_t *, int,
-                             int, int, int *, Skip);
-const Smooth32tFn kSmooth32t[2][3][3] = {
+                             int, int, int *, Skip, const float *, const float *, const float *);
+// [coefficient mode 0, 2, 3][block edge 2^5 .. 2^7][rows per thread 1, 2, 4]
+const Smooth32tFn kSmooth32t[3][3][3] = {
     {OCTMG_S32(k_smooth32t, 0, 5), OCTMG_S32(k_smooth32t, 0, 6), OCTMG_S32(k_smooth32t, 0, 7)},
-    {OCTMG_S32(k_smooth32t, 2, 5), OCTMG_S32(k_smooth32t, 2, 6), OCTMG_S32(k_smooth32t, 2, 7)}};
+    {OCTMG_S32(k_smooth32t, 2, 5), OCTMG_S32(k_smooth32t, 2, 6), OCTMG_S32(k_smooth32t, 2, 7)},
+    {OCTMG_S32(k_smooth32t, 3, 5), OCTMG_S32(k_smooth32t, 3, 6), OCTMG_S32(k_smooth32t, 3, 7)}};
 #undef OCTMG_S32
 
 bool smooth32_specialised(const DevLevel &d) { return d.g.lg >= 2 && d.g.lg <= 7; }
 
-size_t smooth32t_smem(int lg, bool var, int TY, int D) { return s32t_smem_bytes(s32t_plan(lg, var, TY, D)); }
+size_t smooth32t_smem(int lg, int mode, int TY, int D) {
+    return s32t_smem_bytes(s32t_plan(lg, s32t_arrays(mode), TY, D));
+}
 
 int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
 
@@ -172,22 +176,21 @@ int ridx(int v) { return v == 4 ? 2 : (v == 2 ? 1 : 0); }
 int mode32(const mg_forest *F, const DevLevel &d) { return !F->cfg.coeff ? 0 : (d.face32 ? 3 : 2); }
 int mode_index(int mode) { return mode == 3 ? 2 : (mode == 2 ? 1 : 0); }
 
-// The shapes a level may use (the tuner's candidates); the staged kernel stages 1/k, so a level with stored face
-// coefficients (mode 3) is offered the column kernel only.
+// The shapes a level may use (the tuner's candidates): column kernels, and for edges 32..128 the staged kernel
+// (1/k, or the three stored face arrays of mode 3, staged with u and f).
 std::vector<Shape> smooth32_shapes(const DevLevel &d, int mode) {
     std::vector<Shape> v;
     const int n = d.g.n;
-    const bool var = mode == 2;
     for (int zc : {1, 2, 4})
         for (int th : {128, 256, 512})
             if (zc <= n) v.push_back({1, zc, th, 0, 0});
-    if (d.g.lg >= 5 && mode != 3)
+    if (d.g.lg >= 5)
         for (int R : {1, 2, 4})
             for (int th : {128, 256, 512})
                 for (int tz : {8, 16, 32, 64})
                     for (int D : {2, 4}) {
                         const int TY = th * R / (n / 2);
-                        if (TY >= R && TY <= n && tz <= n && smooth32t_smem(d.g.lg, var, TY, D) <= 200 * 1024)
+                        if (TY >= R && TY <= n && tz <= n && smooth32t_smem(d.g.lg, mode, TY, D) <= 200 * 1024)
                             v.push_back({2, TY, tz, D, R});
                     }
     return v;
@@ -200,19 +203,20 @@ bool smooth32_shape_ok(const DevLevel &d, int mode, const Shape &sh) {
 }
 
 void launch_smooth32(mg_forest *F, DevLevel &d, int colour, const Shape &sh, cudaStream_t st) {
-    const int mode = mode32(F, d), mi = mode == 2 ? 1 : 0;
-    if (sh[0] == 2 && mode != 3) {
+    const int mode = mode32(F, d), mi = mode_index(mode);
+    if (sh[0] == 2) {
         const int TY = sh[1], TZ = sh[2], D = sh[3], R = sh[4], n = d.g.n;
-        const size_t smem = smooth32t_smem(d.g.lg, mi == 1, TY, D);
+        const size_t smem = smooth32t_smem(d.g.lg, mode, TY, D);
         Smooth32tFn fn = kSmooth32t[mi][d.g.lg - 5][ridx(R)];
-        static std::once_flag once[2][3][3];
+        static std::once_flag once[3][3][3];
         std::call_once(once[mi][d.g.lg - 5][ridx(R)], [&] {
             cudaFuncSetAttribute(reinterpret_cast<const void *>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024);
         });
         const int64_t grid = static_cast<int64_t>(d.g.nb) * (n / TY) * (n / TZ);
         fn<<<static_cast<unsigned>(grid), (n / 2) * TY / R + 32, smem, st>>>(d.u32, d.f32, d.kap, d.h2_32, d.g.bs, colour,
-                                                                         d.nbr6, TY, TZ, D, F->kerr, skip_of(F, d));
+                                                                         d.nbr6, TY, TZ, D, F->kerr, skip_of(F, d),
+                                                                         d.ax32, d.ay32, d.az32);
         return;
     }
     const int zc = sh[0] == 1 ? sh[1] : 1, threads = sh[0] == 1 ? sh[2] : kThreads;
@@ -1805,17 +1809,18 @@ mg_status mg_smoother_shapes(const mg_forest *F, int32_t level, int32_t max_shap
 mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t shape_index, int32_t *shape,
                               int32_t *n_shapes, int64_t *smem_bytes, int64_t *block_bytes, int64_t max_records,
                               int64_t *records, int64_t *n_records) {
-    if (lg < 5 || lg > 7 || coeff < 0 || coeff > 1 || colour < 0 || colour > 1 || shape_index < 0 || !n_shapes ||
+    if (lg < 5 || lg > 7 || coeff < 0 || coeff > 2 || colour < 0 || colour > 1 || shape_index < 0 || !n_shapes ||
         !n_records || max_records < 0) {
-        set_error("mg_staged_copy_plan: lg 5..7, coeff and colour 0 or 1, shape_index >= 0, outputs not null");
+        set_error("mg_staged_copy_plan: lg 5..7, coeff 0..2, colour 0 or 1, shape_index >= 0, outputs not null");
         return MG_ERR_INVALID_ARG;
     }
+    const int mode = coeff == 2 ? 3 : (coeff ? 2 : 0);
     DevLevel d;
     d.g.n = 1 << lg;
     d.g.lg = lg;
     d.g.P = d.g.n + 2;
     std::vector<Shape> staged;
-    for (const Shape &sh : smooth32_shapes(d, coeff ? 2 : 0))
+    for (const Shape &sh : smooth32_shapes(d, mode))
         if (sh[0] == 2) staged.push_back(sh);
     *n_shapes = static_cast<int32_t>(staged.size());
     *n_records = 0;
@@ -1824,10 +1829,10 @@ mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t
     if (shape)
         for (int k = 0; k < 5; ++k) shape[k] = sh[k];
     const int TY = sh[1], TZ = sh[2], D = sh[3], n = d.g.n;
-    const S32tPlan plan = s32t_plan(lg, coeff != 0, TY, D);
+    const S32tPlan plan = s32t_plan(lg, s32t_arrays(mode), TY, D);
     const int64_t half = static_cast<int64_t>(plan.P) * plan.P * plan.H;
     const int64_t bs = block_stride(d.g.P);
-    if (smem_bytes) *smem_bytes = static_cast<int64_t>(smooth32t_smem(lg, coeff != 0, TY, D));
+    if (smem_bytes) *smem_bytes = static_cast<int64_t>(smooth32t_smem(lg, mode, TY, D));
     if (block_bytes) *block_bytes = 4 * bs;
     // the kernel's halves: the colour being updated is stored in half s = colour ^ 1, the other one in half colour
     const int64_t own = (colour ^ 1) * half, other = static_cast<int64_t>(colour) * half;
@@ -1841,8 +1846,9 @@ mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t
         }
         void arm(int bi, uint32_t bytes) { put({tile, 0, bi, group, -1, -1, -1, static_cast<int64_t>(bytes), -1, -1}); }
         void copy(int dst, int array, int off, int lead, uint32_t bytes, int bi) {
-            const int64_t src = (array < 2 ? other : own) + off;
-            const int len = array < 2 ? p->lo : p->lw;
+            const bool oth = array < 2 || array == 4 || array == 5;
+            const int64_t src = (oth ? other : own) + off;
+            const int len = oth ? p->lo : p->lw;
             put({tile, 1, bi, group, 4 * static_cast<int64_t>(dst), array, 4 * src, static_cast<int64_t>(bytes), lead,
                  len});
         }

@@ -47,6 +47,42 @@ def test_every_smoother_shape_gives_identical_bits(coeff, workload):
             assert torch.equal(u, ref), [shapes[l][i % len(shapes[l])] for l in range(nlev)]
 
 
+@pytest.mark.parametrize("refined", [False, True])
+def test_stored_face_levels_run_the_staged_smoother_with_identical_bits(refined):
+    """Face-averaged coarse levels keep three halved face arrays (coefficient mode 3); with 32^3 blocks they are
+    offered the staged kernel too, which stages the three arrays of both colours with u and f.  Every shape of such a
+    level gives the bits of the column kernel.  64^3 leaf blocks, 4^3 uniform roots or 2^3 roots refined twice
+    around a ball (interface ghosts on the 32^3 level)."""
+    from paper_2403_08063_gb300 import Forest
+    n = 64
+    if refined:
+        R = 2
+        keys = syn.balance_2to1(syn.refine_ball(R, (0.5, 0.5, 0.5), 0.25, 2, open_ball=True), R, "26")
+    else:
+        R = 4
+        keys = syn.uniform_leaves(R)
+    dev = torch.device(DEV)
+    f = syn.gaussian_bump_with_noise(R, n, keys, seed=33, device=dev)
+    k = syn.lognormal_k_rff(R, n, keys, seed=34, device=dev)
+    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=2, coarse_coef="faces")
+    F.set_rhs(f, k)
+    lev = [l for l in range(len(F.levels())) if l > 0 and F.smoother_shapes(l)
+           and {s[0] for s in F.smoother_shapes(l)} == {1, 2}]
+    assert lev, "no face-averaged level with staged shapes"
+    ref = None
+    for l in lev:
+        for sh in F.smoother_shapes(l):
+            F.set_smoother_shape(l, sh)
+            u = torch.zeros_like(f)
+            F.vcycle(u, 2)
+            if ref is None:
+                ref = u.clone()
+                assert torch.isfinite(ref).all() and ref.abs().max() > 0
+            else:
+                assert torch.equal(u, ref), (l, sh)
+        F.set_smoother_shape(l, (1, 1, 256, 0, 0))
+
+
 def test_smoother_shape_arguments_are_checked():
     from paper_2403_08063_gb300 import Forest, MGError
     R, n, keys = syn.workload_forest("uniform_2x4")

@@ -2,7 +2,8 @@
 
 mg_staged_copy_plan runs the kernel's own copy planner (the code its producer thread executes) on the host and
 returns every mbarrier arm and bulk copy of one block's CTAs.  For every staged shape offered at block edges 32, 64
-and 128, both coefficient modes and both colours this test checks:
+and 128, the three coefficient modes (constant k: u and f staged; 1/k: with kappa; stored halved face coefficients:
+with ax, ay, az) and both colours this test checks:
   * the size rule and 16-byte alignment of both addresses (global: the block stride keeps every block and half on a
     16-byte boundary; shared: the slots);
   * that each barrier is armed with exactly the bytes of the copies that complete it, below the 2^20 tx limit;
@@ -54,7 +55,10 @@ def _check(lg, coeff, colour, shape, smem, blk, rec):
     bar0 = smem - 8 * (2 * G + 2)
     assert bar0 % 8 == 0 and smem <= 200 * 1024
     assert blk % 16 == 0 and blk >= 4 * 2 * HALF
-    half_start = {0: colour * HALF, 1: colour * HALF, 2: (colour ^ 1) * HALF, 3: (colour ^ 1) * HALF}
+    other_arrays = {0: [0], 1: [0, 1], 2: [0, 1, 4, 5]}[coeff]
+    own_arrays = {0: [2], 1: [2, 3], 2: [2, 3, 6, 7]}[coeff]
+    half_start = {a: colour * HALF for a in (0, 1, 4, 5)}
+    half_start.update({a: (colour ^ 1) * HALF for a in (2, 3, 6, 7)})
     tiles = (n // TY) * (n // TZ)
     assert set(rec[:, 0]) == set(range(tiles))
     for tile in range(tiles):
@@ -73,7 +77,7 @@ def _check(lg, coeff, colour, shape, smem, blk, rec):
             armed = int(rg[0, 7])
             copies = rg[1:]
             assert armed == copies[:, 7].sum() and 0 < armed < (1 << 20)
-            want_arrays = ([0, 1] if coeff else [0]) * (2 if g < 0 else 1) + ([] if g < 0 else ([2, 3] if coeff else [2]))
+            want_arrays = other_arrays * (2 if g < 0 else 1) + ([] if g < 0 else own_arrays)
             assert sorted(copies[:, 5].tolist()) == sorted(want_arrays)
             new = []
             for c in copies:
@@ -84,15 +88,15 @@ def _check(lg, coeff, colour, shape, smem, blk, rec):
                 assert 0 <= lead <= 3 and lead + ln <= nbytes // 4  # the wanted segment is copied whole
                 seg = src // 4 + lead - half_start[arr]
                 assert 0 <= seg and seg + ln <= HALF
-                if arr < 2:  # other colour: rows y0 - 1 .. y0 + TY of one padded plane
+                if arr in other_arrays:  # other colour: rows y0 - 1 .. y0 + TY of one padded plane
                     assert ln == (TY + 2) * H and seg % (P * H) == y0 * H
                     zp = seg // (P * H)
                 else:        # own colour: rows y0 .. y0 + TY - 1 of one padded plane
                     assert ln == TY * H and seg % (P * H) == (y0 + 1) * H
                     zp = seg // (P * H)
                 new.append((arr, zp, (dst, dst + nbytes)))
-            o_planes = sorted({zp for arr, zp, _ in new if arr < 2})
-            w_planes = sorted({zp for arr, zp, _ in new if arr >= 2})
+            o_planes = sorted({zp for arr, zp, _ in new if arr in other_arrays})
+            w_planes = sorted({zp for arr, zp, _ in new if arr in own_arrays})
             if g < 0:
                 assert o_planes == [z0, z0 + 1] and not w_planes
             else:
@@ -113,7 +117,7 @@ def _check(lg, coeff, colour, shape, smem, blk, rec):
                         for r2 in own_slot[p]:
                             assert not _overlap(rg_, r2), (shape, tile, g, p)
             for arr, zp, rg_ in new:
-                (other_slot if arr < 2 else own_slot).setdefault(zp, []).append(rg_)
+                (other_slot if arr in other_arrays else own_slot).setdefault(zp, []).append(rg_)
             # copies of one group never overlap each other
             for i in range(len(new)):
                 for k in range(i + 1, len(new)):
@@ -121,7 +125,7 @@ def _check(lg, coeff, colour, shape, smem, blk, rec):
 
 
 @pytest.mark.parametrize("lg", [5, 6, 7])
-@pytest.mark.parametrize("coeff", [0, 1])
+@pytest.mark.parametrize("coeff", [0, 1, 2])
 def test_every_staged_copy_follows_the_bulk_copy_rules(lg, coeff):
     lib = _lib.load()
     ns, *_ = _plan(lib, lg, coeff, 0, 1 << 30)
@@ -135,5 +139,5 @@ def test_every_staged_copy_follows_the_bulk_copy_rules(lg, coeff):
 def test_copy_plan_rejects_bad_arguments():
     lib = _lib.load()
     ns, nrec = ctypes.c_int32(), I64()
-    for args in ((4, 0, 0), (8, 0, 0), (6, 2, 0), (6, 0, 2)):
+    for args in ((4, 0, 0), (8, 0, 0), (6, 3, 0), (6, 0, 2)):
         assert lib.mg_staged_copy_plan(*args, 0, None, ctypes.byref(ns), None, None, 0, None, ctypes.byref(nrec)) == 1
