@@ -96,7 +96,7 @@ def _family_work(fam, levels, nu1, nu2, coeff, cycles_total, outer_total, launch
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the level's cells), scaled here to the launch's cells
 # (the traffic grows in proportion to the cells).
 _NCU_TRAFFIC_PER_CELL = {
-    "smooth_f32_finest": (165.026048e6 / 16777216, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+    "smooth_f32_finest": (164.37632e6 / 16777216, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                           "k_smooth32t<2,6,4> launch (rows in pairs, colour-reversed tile order), shape {2,16,16,4,4}, "
                           "on 4^3 roots of 64^3 cells (16,777,216 cells, log-normal k), scaled by cells"),
 }

@@ -2007,27 +2007,37 @@ static __global__ void k_block_norm64(const double *__restrict__ x, const double
 }
 
 // Per-problem sums of the per-CTA partials (cpb per block, blocks of problem p listed in pblk[pstart[p] ..
-// pstart[p+1])): one CTA of kThreads per problem, each thread adding a fixed strided subset, then a fixed tree, so
-// the sum does not depend on the order in which the partials were written.
-static __global__ void __launch_bounds__(kThreads) k_problem_sums(const double *__restrict__ bpart, int cpb,
-                                                                  const int32_t *__restrict__ pstart,
-                                                                  const int32_t *__restrict__ pblk, int np,
-                                                                  double *__restrict__ psum) {
+// pstart[p+1])): one CTA of 1024 threads per problem, thread t adding partials t, t + 1024, ... of the problem's list
+// (block-major), then a fixed tree, so the sum does not depend on the order in which the partials were written.
+constexpr int kSumThreads = 1024;
+static __global__ void __launch_bounds__(kSumThreads) k_problem_sums(const double *__restrict__ bpart, int cpb,
+                                                                     const int32_t *__restrict__ pstart,
+                                                                     const int32_t *__restrict__ pblk, int np,
+                                                                     double *__restrict__ psum) {
     const int p = blockIdx.x;
     if (p >= np) return;
-    const int first = pstart[p];
-    const int64_t cnt = static_cast<int64_t>(pstart[p + 1] - first) * cpb;
+    const int first = pstart[p], nblk = pstart[p + 1] - first;
+    // (block, chunk) of list entry t, advanced by kSumThreads entries per step without a division
+    const int step_b = kSumThreads / cpb, step_c = kSumThreads % cpb;
+    int bq = threadIdx.x / cpb, c = threadIdx.x % cpb;
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < cnt; i += kThreads)
-        s += bpart[static_cast<int64_t>(pblk[first + i / cpb]) * cpb + i % cpb];
+#pragma unroll 4
+    for (; bq < nblk; bq += step_b) {
+        s += bpart[static_cast<int64_t>(pblk[first + bq]) * cpb + c];
+        c += step_c;
+        if (c >= cpb) {
+            c -= cpb;
+            ++bq;
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double sm[kThreads / 32];
+    __shared__ double sm[kSumThreads / 32];
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += sm[w];
+        for (int w = 0; w < kSumThreads / 32; ++w) t += sm[w];
         psum[p] = t;
     }
 }

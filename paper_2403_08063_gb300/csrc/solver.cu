@@ -607,7 +607,7 @@ int chunks_per_block(const DevLevel &d) { return std::max(1, static_cast<int>(d.
 
 // Per-problem sums of the per-block sums to the host (pinned psum_h), synchronising the stream.
 mg_status read_problem_sums(mg_forest *F) {
-    k_problem_sums<<<F->np, kThreads, 0, F->st>>>(F->bsum, F->bsum_cpb, F->pstart, F->pblk, F->np, F->psum);
+    k_problem_sums<<<F->np, kSumThreads, 0, F->st>>>(F->bsum, F->bsum_cpb, F->pstart, F->pblk, F->np, F->psum);
     MG_CUDA(cudaMemcpyAsync(F->psum_h, F->psum, F->np * sizeof(double), cudaMemcpyDeviceToHost, F->st));
     MG_CUDA(cudaStreamSynchronize(F->st));
     return MG_OK;
@@ -646,7 +646,7 @@ mg_status upload_scales(mg_forest *F, const std::vector<double> &mult) {
 }
 
 mg_status enqueue_problem_sums(mg_forest *F) {
-    k_problem_sums<<<F->np, kThreads, 0, F->st>>>(F->bsum, F->bsum_cpb, F->pstart, F->pblk, F->np, F->psum);
+    k_problem_sums<<<F->np, kSumThreads, 0, F->st>>>(F->bsum, F->bsum_cpb, F->pstart, F->pblk, F->np, F->psum);
     MG_CUDA(cudaMemcpyAsync(F->psum_h, F->psum, F->np * sizeof(double), cudaMemcpyDeviceToHost, F->st));
     return MG_OK;
 }
