@@ -226,6 +226,24 @@ mg_status mg_staged_copy_plan(int32_t lg, int32_t coeff, int32_t colour, int32_t
                               int32_t *n_shapes, int64_t *smem_bytes, int64_t *block_bytes, int64_t max_records,
                               int64_t *records, int64_t *n_records);
 
+/* Bulk-copy plan of the staged FP32 residual + restriction (k_residual_restrict32t, fine block edges 64 and 128),
+ * computed on the host by the same code the kernel's producer thread runs; no GPU is needed.  No counterpart in the
+ * paper: it lets a test check every shared-memory copy against the rules of cp.async.bulk without running the kernel.
+ * For fine block edge 2^lg (lg 6 or 7) and coefficient mode coeff (0 constant, 1 variable k, 2 stored halved face
+ * coefficients), shape (3 int32, in and out) = {TY, TZ, D}: fine rows and planes per CTA and planes staged beyond the
+ * four a coarse plane reads; {0, ...} on input selects the tile the library launches, written back.  *smem_bytes
+ * receives the dynamic shared memory of a CTA and *block_bytes the block stride of an FP32 pool (either may be NULL);
+ * records (max_records x 11 int64, may be NULL) every mbarrier arm and bulk copy the CTAs of one block issue, in issue
+ * order per CTA:
+ *   {tile (tz * n / TY + ty), kind (0 arm, 1 copy), ring slot, plane q (padded plane z0 + q), dst (bytes from the
+ *    start of dynamic shared memory; -1), array (0 u, then kappa (coeff 1) or ax, ay, az (coeff 2), then f; -1),
+ *    half (-1), src (bytes from the start of the block in the pool; -1), bytes (armed or copied), lead (floats from
+ *    the copy's start to the wanted segment; -1), len (floats of the wanted segment; -1)}.
+ * *n_records receives the total (records beyond max_records are counted, not written).  MG_ERR_INVALID_ARG for a bad
+ * lg, coeff or tile, or a null shape or count pointer. */
+mg_status mg_restrict_copy_plan(int32_t lg, int32_t coeff, int32_t *shape, int64_t *smem_bytes, int64_t *block_bytes,
+                                int64_t max_records, int64_t *records, int64_t *n_records);
+
 /* Persistent tail of the FP32 V-cycle (precision 1): from level `level` down to the coarsest and back, every step
  * (half-sweeps, exchanges, restriction, prolongation, coarsest solve) runs inside one cooperative kernel launch
  * whose CTAs stay resident and meet at grid barriers, instead of one launch per step.  Results are bit-identical

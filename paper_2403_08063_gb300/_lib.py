@@ -74,6 +74,8 @@ SIGNATURES = {
     "mg_smoother_shapes": (I32, [P, I32, I32, IP, IP]),
     "mg_staged_copy_plan": (I32, [I32, I32, I32, I32, IP, IP, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64),
                                   _c.c_int64, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
+    "mg_restrict_copy_plan": (I32, [I32, I32, IP, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64), _c.c_int64,
+                                    _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
     "mg_get_tail": (I32, [P, IP]),
     "mg_set_tail": (I32, [P, I32]),
     "mg_selftest_waits": (I32, [P, I32]),

@@ -1363,6 +1363,80 @@ struct Box32 {
     }
 };
 
+// The sum of the 8 children's residuals from the box values (U, and K for MODE 2, AX / AY / AZ for MODE 3, as
+// loaded by residual_restrict32_body or staged by k_residual_restrict32t) and f of child (i, j, k) from fv(i, j, k),
+// children in (k, j, i) order, so both kernels give the same bits.
+template <int MODE, class FV>
+__device__ __forceinline__ float rr32_sum(const float (&U)[4][4][4], const float (&K)[4][4][4],
+                                          const float (&AX)[3][3][4], const float (&AY)[3][4][3],
+                                          const float (&AZ)[4][3][3], float ih2, FV &&fv_at) {
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 1; k < 3; ++k)
+#pragma unroll
+        for (int j = 1; j < 3; ++j)
+#pragma unroll
+            for (int i = 1; i < 3; ++i) {
+                const float u0 = U[k][j][i];
+                const float fv = fv_at(i, j, k);
+                const float nbu[6] = {U[k][j][i - 1], U[k][j][i + 1], U[k][j - 1][i],
+                                      U[k][j + 1][i], U[k - 1][j][i], U[k + 1][j][i]};
+                if constexpr (MODE == 0) {
+                    const float S = ((nbu[0] + nbu[1]) + (nbu[2] + nbu[3])) + (nbu[4] + nbu[5]);
+                    sum += fmaf(fmaf(-6.0f, u0, S), ih2, fv);
+                } else if constexpr (MODE == 3) {
+                    const float a6[6] = {AX[k][j][i], AX[k][j][i + 1], AY[k][j][i],
+                                         AY[k][j + 1][i], AZ[k][j][i], AZ[k + 1][j][i]};
+                    float S = 0.0f, D = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        S = fmaf(a6[q], nbu[q], S);
+                        D += a6[q];
+                    }
+                    sum += fmaf(2.0f * fmaf(-D, u0, S), ih2, fv);
+                } else {
+                    const float k0 = K[k][j][i];
+                    const float nbk[6] = {K[k][j][i - 1], K[k][j][i + 1], K[k][j - 1][i],
+                                          K[k][j + 1][i], K[k - 1][j][i], K[k + 1][j][i]};
+                    float S = 0.0f, D = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        // operands in a fixed order per face (the lower neighbour first), so the two children
+                        // of an interior face evaluate the same expression and it is computed once; the sum
+                        // is the same either way
+                        const float a = (q & 1) ? frcp(k0 + nbk[q]) : frcp(nbk[q] + k0);
+                        S = fmaf(a, nbu[q], S);
+                        D += a;
+                    }
+                    sum += fmaf(2.0f * fmaf(-D, u0, S), ih2, fv);
+                }
+            }
+    return sum;
+}
+
+// The coarse right-hand side (1/8 of the children's residual sum) and a zero coarse correction, with its face
+// ghosts, at coarse cell (X, Y, Z) of coarse block B (coarse edge nc, colour-split pool).
+template <int LG>
+__device__ __forceinline__ void rr32_store(float *__restrict__ fc, float *__restrict__ uc, int64_t B, int64_t bsc,
+                                           int X, int Y, int Z, float sum) {
+    constexpr int nc = (1 << LG) / 2, Pc = nc + 2, HPc = half_row(Pc), HALFc = Pc * Pc * HPc;
+    const int Xc = X + 1, Yc = Y + 1, Zc = Z + 1;
+    const auto at = [&](int xx, int yy, int zz) {
+        return B * bsc + ((xx + yy + zz) & 1) * HALFc + (zz * Pc + yy) * HPc + (xx >> 1);
+    };
+    const int64_t gc = at(Xc, Yc, Zc);
+    fc[gc] = 0.125f * sum;
+    uc[gc] = 0.0f;
+    // the coarse correction starts from zero: its face ghosts are zero too, so the level needs no exchange
+    // before its first half-sweep
+    if (X == 0) uc[at(0, Yc, Zc)] = 0.0f;
+    if (X == nc - 1) uc[at(nc + 1, Yc, Zc)] = 0.0f;
+    if (Y == 0) uc[at(Xc, 0, Zc)] = 0.0f;
+    if (Y == nc - 1) uc[at(Xc, nc + 1, Zc)] = 0.0f;
+    if (Z == 0) uc[at(Xc, Yc, 0)] = 0.0f;
+    if (Z == nc - 1) uc[at(Xc, Yc, nc + 1)] = 0.0f;
+}
+
 template <int MODE, int LG, bool CG = false>
 __device__ __forceinline__ void residual_restrict32_body(
         const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
@@ -1371,7 +1445,7 @@ __device__ __forceinline__ void residual_restrict32_body(
         const float *__restrict__ ax = nullptr, const float *__restrict__ ay = nullptr,
         const float *__restrict__ az = nullptr) {
     using Bx = Box32<LG>;
-    constexpr int nc = (1 << LG) / 2, LC = LG - 1, Pc = nc + 2, HPc = half_row(Pc), HALFc = Pc * Pc * HPc;
+    constexpr int nc = (1 << LG) / 2, LC = LG - 1;
     const int64_t total = static_cast<int64_t>(nbc) << (3 * LC);
     for (int64_t t = t0; t < total; t += ts) {
         const int r = static_cast<int>(t) & ((1 << (3 * LC)) - 1);
@@ -1408,62 +1482,10 @@ __device__ __forceinline__ void residual_restrict32_body(
                     }
         }
         const float ih2 = __ldg(ih2f + b);
-        float sum = 0.0f;
-#pragma unroll
-        for (int k = 1; k < 3; ++k)
-#pragma unroll
-            for (int j = 1; j < 3; ++j)
-#pragma unroll
-                for (int i = 1; i < 3; ++i) {
-                    const float u0 = U[k][j][i];
-                    const float fv = ldr<CG>(f + corner + Bx::off(i, j, k));
-                    const float nbu[6] = {U[k][j][i - 1], U[k][j][i + 1], U[k][j - 1][i],
-                                          U[k][j + 1][i], U[k - 1][j][i], U[k + 1][j][i]};
-                    if constexpr (MODE == 0) {
-                        const float S = ((nbu[0] + nbu[1]) + (nbu[2] + nbu[3])) + (nbu[4] + nbu[5]);
-                        sum += fmaf(fmaf(-6.0f, u0, S), ih2, fv);
-                    } else if constexpr (MODE == 3) {
-                        const float a6[6] = {AX[k][j][i], AX[k][j][i + 1], AY[k][j][i],
-                                             AY[k][j + 1][i], AZ[k][j][i], AZ[k + 1][j][i]};
-                        float S = 0.0f, D = 0.0f;
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) {
-                            S = fmaf(a6[q], nbu[q], S);
-                            D += a6[q];
-                        }
-                        sum += fmaf(2.0f * fmaf(-D, u0, S), ih2, fv);
-                    } else {
-                        const float k0 = K[k][j][i];
-                        const float nbk[6] = {K[k][j][i - 1], K[k][j][i + 1], K[k][j - 1][i],
-                                              K[k][j + 1][i], K[k - 1][j][i], K[k + 1][j][i]};
-                        float S = 0.0f, D = 0.0f;
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) {
-                            // operands in a fixed order per face (the lower neighbour first), so the two children
-                            // of an interior face evaluate the same expression and it is computed once; the sum
-                            // is the same either way
-                            const float a = (q & 1) ? frcp(k0 + nbk[q]) : frcp(nbk[q] + k0);
-                            S = fmaf(a, nbu[q], S);
-                            D += a;
-                        }
-                        sum += fmaf(2.0f * fmaf(-D, u0, S), ih2, fv);
-                    }
-                }
-        const int Xc = X + 1, Yc = Y + 1, Zc = Z + 1;
-        const auto at = [&](int xx, int yy, int zz) {
-            return B * bsc + ((xx + yy + zz) & 1) * HALFc + (zz * Pc + yy) * HPc + (xx >> 1);
-        };
-        const int64_t gc = at(Xc, Yc, Zc);
-        fc[gc] = 0.125f * sum;
-        uc[gc] = 0.0f;
-        // the coarse correction starts from zero: its face ghosts are zero too, so the level needs no exchange
-        // before its first half-sweep
-        if (X == 0) uc[at(0, Yc, Zc)] = 0.0f;
-        if (X == nc - 1) uc[at(nc + 1, Yc, Zc)] = 0.0f;
-        if (Y == 0) uc[at(Xc, 0, Zc)] = 0.0f;
-        if (Y == nc - 1) uc[at(Xc, nc + 1, Zc)] = 0.0f;
-        if (Z == 0) uc[at(Xc, Yc, 0)] = 0.0f;
-        if (Z == nc - 1) uc[at(Xc, Yc, nc + 1)] = 0.0f;
+        const float sum = rr32_sum<MODE>(U, K, AX, AY, AZ, ih2, [&](int i, int j, int k) {
+            return ldr<CG>(f + corner + Bx::off(i, j, k));
+        });
+        rr32_store<LG>(fc, uc, B, bsc, X, Y, Z, sum);
     }
 }
 
@@ -1476,6 +1498,194 @@ static __global__ void __launch_bounds__(256) k_residual_restrict32(
     residual_restrict32_body<MODE, LG>(u, f, kap, ih2f, bsf, fc, uc, xf, nbc, bsc, skip,
                                        blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
                                        static_cast<int64_t>(gridDim.x) * blockDim.x, ax, ay, az);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Copy plan of the staged residual + restriction below (k_residual_restrict32t), shared by the kernel's producer
+// thread, the launch code and the host-side enumerator that checks every copy against the bulk-copy rules.
+//
+// A CTA owns fine block b, interior rows y0 .. y0 + TY - 1 and planes z0 .. z0 + TZ - 1 (TY, TZ, y0, z0 even): the
+// coarse cells of TY / 2 coarse rows and TZ / 2 coarse planes.  It stages the fine padded planes z0 .. z0 + TZ + 1
+// (q = 0 .. TZ + 1 relative to z0), one by one, into a ring of RS = 4 + 2 D plane slots.  A slot holds, of both
+// halves, the segment of padded rows y0 .. y0 + TY + 1 of each of the NU arrays the residual reads around a cell (u;
+// u and kappa; u, ax, ay, az) and, for q = 1 .. TZ, the segment of rows y0 + 1 .. y0 + TY of f; each widened to
+// 16-byte bounds as in the staged smoother (a segment never ends past its half: the half length is a multiple of 4
+// floats).  Coarse plane step g reads planes 2g .. 2g + 3 and then releases planes 2g and 2g + 1; plane q reuses the
+// slot of plane q - RS once that plane is released, and the planes a step reads are RS-consecutive or fewer, so they
+// sit in distinct slots.  Shared memory: RS slots of ss floats, then RS "full" and RS "empty" mbarriers.
+// ------------------------------------------------------------------------------------------------------------
+struct R32tPlan {
+    int P, H, NU, RS, TZ;
+    int lo, lw, so, sw, ss;  // segment lengths, segment strides and the slot stride (floats)
+};
+__host__ __device__ __forceinline__ R32tPlan r32t_plan(int lg, int mode, int TY, int TZ, int D) {
+    R32tPlan p;
+    p.P = (1 << lg) + 2;
+    p.H = half_row(p.P);
+    p.NU = mode == 3 ? 4 : (mode == 2 ? 2 : 1);
+    p.RS = 4 + 2 * D;
+    p.TZ = TZ;
+    p.lo = (TY + 2) * p.H;
+    p.lw = TY * p.H;
+    p.so = (p.lo + 6) & ~3;
+    p.sw = (p.lw + 6) & ~3;
+    p.ss = 2 * p.NU * p.so + 2 * p.sw;
+    return p;
+}
+__host__ __device__ __forceinline__ size_t r32t_smem_bytes(const R32tPlan &p) {
+    return static_cast<size_t>(4) * p.RS * p.ss + static_cast<size_t>(8) * 2 * p.RS;
+}
+// start (floats, within a half) of padded plane Zp's segment of the stencil arrays and of f
+__host__ __device__ __forceinline__ int r32t_off_lo(const R32tPlan &p, int Zp, int y0) { return (Zp * p.P + y0) * p.H; }
+__host__ __device__ __forceinline__ int r32t_off_f(const R32tPlan &p, int Zp, int y0) { return (Zp * p.P + y0 + 1) * p.H; }
+// shared float offset, within its slot, of array a's (a = NU: f's) segment of half h
+__host__ __device__ __forceinline__ int r32t_seg(const R32tPlan &p, int a, int h) {
+    return a < p.NU ? (2 * a + h) * p.so : 2 * p.NU * p.so + h * p.sw;
+}
+// The copies of plane q of one CTA: sink.arm(slot, bytes) arms the slot's full barrier with the bytes that complete
+// it; sink.copy(dst, array, half, src, lead, bytes, slot) copies `bytes` from float `src` of half `half` of `array`
+// (0 .. NU - 1: u, then kappa or ax, ay, az; NU: f) to shared float `dst`, the wanted segment `lead` floats in.
+#pragma nv_exec_check_disable
+template <class Sink>
+__host__ __device__ __forceinline__ void r32t_issue_plane(const R32tPlan &p, int z0, int y0, int q, Sink &&sink) {
+    const int slot = q % p.RS, base = slot * p.ss;
+    const int ol = r32t_off_lo(p, z0 + q, y0), of = r32t_off_f(p, z0 + q, y0);
+    const uint32_t bl = s32t_bytes(ol, p.lo), bf = s32t_bytes(of, p.lw);
+    const bool withf = q >= 1 && q <= p.TZ;
+    sink.arm(slot, 2 * p.NU * bl + (withf ? 2 * bf : 0));
+    for (int a = 0; a < p.NU; ++a)
+        for (int h = 0; h < 2; ++h) sink.copy(base + r32t_seg(p, a, h), a, h, ol & ~3, ol & 3, bl, slot);
+    if (withf)
+        for (int h = 0; h < 2; ++h) sink.copy(base + r32t_seg(p, p.NU, h), p.NU, h, of & ~3, of & 3, bf, slot);
+}
+struct R32tDeviceSink {
+    float *smem;
+    const float *src[5][2];  // [plan array (u, kappa or ax, ay, az, then f)][half] of the block
+    uint64_t *full;
+    __device__ __forceinline__ void arm(int slot, uint32_t bytes) const { mbar_arm(&full[slot], bytes); }
+    __device__ __forceinline__ void copy(int dst, int array, int half, int off, int, uint32_t bytes, int slot) const {
+        bulk_load(smem + dst, src[array][half] + off, bytes, &full[slot]);
+    }
+};
+
+// FP32 residual + restriction of a halving level (fine edge 2^LG) with the fine planes staged in shared memory by
+// bulk copies (plan above): consumer thread (X, Yl) owns coarse cell (X, y0 / 2 + Yl) of every coarse plane of the
+// tile and reads its box of u (and kappa / face coefficients) and f from the staged planes, with the arithmetic of
+// residual_restrict32_body (rr32_sum, rr32_store), so the results are bit-identical to k_residual_restrict32.
+// Warps of one coarse row each (nc >= 32); the CTA's last warp produces.  Every wait is bounded: a consumer warp
+// whose wait runs out sets bit 4 of *err and stops; the producer stops when a slot is not released in time, sets the
+// bit and waits, again bounded, for the copies it issued before it exits.
+template <int MODE, int LG>
+static __global__ void __launch_bounds__(544) k_residual_restrict32t(
+        const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
+        const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
+        const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip, const float *__restrict__ ax,
+        const float *__restrict__ ay, const float *__restrict__ az, int TY, int TZ, int D, int *__restrict__ err) {
+    constexpr int n = 1 << LG, nc = n / 2, P = n + 2, H = half_row(P), HALF = P * P * H;
+    static_assert(nc >= 32, "a warp per coarse row");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const R32tPlan plan = r32t_plan(LG, MODE, TY, TZ, D);
+    const int RS = plan.RS, ss = plan.ss;
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + RS * ss), *empty = full + RS;
+    const int nty = n / TY, ntz = n / TZ;
+    const int ty = static_cast<int>(blockIdx.x % nty);
+    const int tz = static_cast<int>((blockIdx.x / nty) % ntz);
+    const int64_t B = blockIdx.x / (nty * ntz);
+    if (B >= nbc || skip(B)) return;  // uniform over the CTA, before any barrier
+    const int64_t b = xf[B].src[0];
+    const int y0 = ty * TY, z0 = tz * TZ;
+    const int tid = threadIdx.x, nthc = blockDim.x - 32, ncw = nthc >> 5;
+    if (tid == 0) {
+        for (int i = 0; i < RS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], ncw);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid >= nthc) {
+        if (tid == nthc) {
+            const int64_t h0 = b * bsf, h1 = h0 + HALF;
+            // the plan's arrays: u, then kappa (MODE 2) or ax, ay, az (MODE 3), then f
+            constexpr int NU = MODE == 3 ? 4 : (MODE == 2 ? 2 : 1);
+            const float *arr[5] = {u, MODE == 3 ? ax : kap, ay, az, f};
+            if constexpr (NU < 4) arr[NU] = f;
+            R32tDeviceSink sink{sm, {}, full};
+#pragma unroll
+            for (int a = 0; a <= NU; ++a) {
+                sink.src[a][0] = arr[a] + h0;
+                sink.src[a][1] = arr[a] + h1;
+            }
+            const int NP = TZ + 2;
+            bool ok = true;
+            int q = 0;
+            for (; q < NP; ++q) {
+                if (q >= RS && !mbar_wait(&empty[q % RS], ((q / RS) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                r32t_issue_plane(plan, z0, y0, q, sink);
+            }
+            if (!ok) atomicOr(err, 4);
+            // the copies still in flight land before the CTA's shared memory can be released
+            for (int r = q > RS ? q - RS : 0; r < q; ++r) mbar_wait(&full[r % RS], (r / RS) & 1);
+        }
+        return;
+    }
+    const int X = tid & (nc - 1), Yl = tid >> (LG - 1);
+    const float ih2 = __ldg(ih2f + b);
+    int bad = 0;
+    for (int g = 0; g < TZ / 2; ++g) {
+        for (int q = g ? 2 * g + 2 : 0; q <= 2 * g + 3; ++q)
+            bad |= __any_sync(0xffffffffu, !mbar_wait(&full[q % RS], (q / RS) & 1));
+        if (bad) break;
+        // box cell (i, j, k) of array a: plane q = 2g + k, half (i + j + k) & 1, slot row 2 Yl + j, position X + i / 2
+        const auto at = [&](int a, int i, int j, int k) {
+            const int q = 2 * g + k;
+            return sm[(q % RS) * ss + r32t_seg(plan, a, (i + j + k) & 1) + (r32t_off_lo(plan, z0 + q, y0) & 3) +
+                      (2 * Yl + j) * H + X + (i >> 1)];
+        };
+        float U[4][4][4], K[4][4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int out = (i == 0 || i == 3) + (j == 0 || j == 3) + (k == 0 || k == 3);
+                    if (out > 1) continue;
+                    U[k][j][i] = at(0, i, j, k);
+                    if constexpr (MODE == 2) K[k][j][i] = at(1, i, j, k);
+                }
+        float AX[3][3][4], AY[3][4][3], AZ[4][3][3];
+        if constexpr (MODE == 3) {
+#pragma unroll
+            for (int k = 1; k < 3; ++k)
+#pragma unroll
+                for (int j = 1; j < 3; ++j)
+#pragma unroll
+                    for (int i = 1; i < 4; ++i) {
+                        AX[k][j][i] = at(1, i, j, k);
+                        AY[k][i][j] = at(2, j, i, k);
+                        AZ[i][k][j] = at(3, j, k, i);
+                    }
+        }
+        const float sum = rr32_sum<MODE>(U, K, AX, AY, AZ, ih2, [&](int i, int j, int k) {
+            const int q = 2 * g + k;
+            return sm[(q % RS) * ss + r32t_seg(plan, plan.NU, (i + j + k) & 1) + (r32t_off_f(plan, z0 + q, y0) & 3) +
+                      (2 * Yl + j - 1) * H + X + (i >> 1)];
+        });
+        rr32_store<LG>(fc, uc, B, bsc, X, y0 / 2 + Yl, z0 / 2 + g, sum);
+        // planes 2g and 2g + 1 are done: every value read from them fed the store above
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if ((tid & 31) == 0) {
+            mbar_arrive(&empty[(2 * g) % RS]);
+            mbar_arrive(&empty[(2 * g + 1) % RS]);
+        }
+    }
+    if (bad && (tid & 31) == 0) atomicOr(err, 4);
 }
 
 // The 8 children (2X + a, 2Y + b, 2Z + c), a, b, c in {1, 2}, of coarse cell (X, Y, Z) in fine block b of a halving
