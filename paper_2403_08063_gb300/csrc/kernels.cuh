@@ -2157,6 +2157,8 @@ static __global__ void __launch_bounds__(kThreads, 5) k_residual_norm(const doub
     const int sexp = static_cast<int>((__float_as_uint(pscale[bprob[b]]) >> 23) & 0xff) - 127;  // scale = 2^sexp
     const double ihb = MODE == 1 ? 0.0 : ih2[b];
     float acc = 0.0f;
+    // the zero-guess form is a stream (f in, r and the zeroed correction out): four cells in flight per thread
+#pragma unroll(ZU ? 4 : 1)
     for (int c = chunk * per + threadIdx.x; c < (chunk + 1) * per; c += blockDim.x) {
         const int x = c & (n - 1), y = (c >> lg) & (n - 1), z = c >> (2 * lg);
         const int64_t gi = b * g.bs + off3(x + 1, y + 1, z + 1, P);
@@ -2321,6 +2323,7 @@ static __global__ void k_pack(T *__restrict__ pool, const double *__restrict__ u
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
     bool any = false;
+#pragma unroll 4  // several cells' loads in flight per thread
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int x = static_cast<int>(t & (n - 1));
@@ -2340,6 +2343,7 @@ static __global__ void k_unpack(double *__restrict__ user, const T *__restrict__
                                 const int64_t *__restrict__ off = nullptr) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+#pragma unroll 4  // several cells' loads in flight per thread
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int x = static_cast<int>(t & (n - 1));
@@ -2358,6 +2362,7 @@ static __global__ void k_update_mixed(double *__restrict__ u, const float *__res
                                       LevelGeom g, Skip skip = Skip{}) {
     const int lg = g.lg, n = g.n;
     const int64_t total = static_cast<int64_t>(g.nb) << (3 * lg);
+#pragma unroll 4  // several cells' loads in flight per thread
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int x = static_cast<int>(t & (n - 1));
