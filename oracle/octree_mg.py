@@ -157,6 +157,35 @@ def harmonic(a, b):
     return 2.0 * a * b / (a + b)
 
 
+def residual_from_stencil(u7, k7, bnd, f, h, g=0.0):
+    """r = f - A u at cells taken one by one, each from its own 7-point stencil (Sec. 5, Eq. 1-2, in the point form
+    of this module's header), for cells whose six face neighbours lie on the same refinement level or on the domain
+    boundary: large problems can be checked at sampled cells without building the forest.
+
+    u7, k7: (m, 7) FP64 arrays, column 0 the cell, columns 1..6 its x-, x+, y-, y+, z-, z+ neighbours (ignored where
+    ``bnd`` is set); bnd: (m, 6) bool, the face lies on the domain boundary, whose Dirichlet reflection ghost is
+    2 g - u_i with the cell's own k (harmonic(k_i, k_i) = k_i), g a scalar or (m, 6) per face; f: (m,); h: cell
+    width (scalar or (m,)).
+    Returns (A u, r, s), s = sum_f T_f (|u_i| + |u_f|) / h^2 the size of the terms, for rounding bounds."""
+    u7 = np.asarray(u7, dtype=np.float64)
+    k7 = np.asarray(k7, dtype=np.float64)
+    bnd = np.asarray(bnd, dtype=bool)
+    uc, kc = u7[:, 0], k7[:, 0]
+    h2 = np.asarray(h, dtype=np.float64) ** 2
+    au = np.zeros_like(uc)
+    s = np.zeros_like(uc)
+    for face in range(6):
+        b = bnd[:, face]
+        gf = np.asarray(g, dtype=np.float64)[:, face] if np.ndim(g) == 2 else g
+        uf = np.where(b, 2.0 * gf - uc, u7[:, 1 + face])
+        kf = np.where(b, kc, k7[:, 1 + face])
+        T = harmonic(kc, kf)
+        au += T * (uc - uf)
+        s += T * (np.abs(uc) + np.abs(uf))
+    au = au / h2
+    return au, np.asarray(f, dtype=np.float64) - au, s / h2
+
+
 # ----------------------------------------------------------------------------------------------------------
 # Forest geometry and neighbour tables (Sec. 2, Sec. 3.1: N_neigh = 4 finer neighbours per face in 3D)
 # ----------------------------------------------------------------------------------------------------------

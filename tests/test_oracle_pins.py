@@ -15,7 +15,7 @@ import pytest
 import scipy.fft
 
 import synthetic as syn
-from oracle.octree_mg import OracleMG, face_view
+from oracle.octree_mg import OracleMG, face_view, residual_from_stencil
 from tests.helpers import (padded_centres, one_refined_root, poly3, neg_laplace_poly3, vw_norm, leaf_h)
 
 
@@ -1030,3 +1030,85 @@ def test_rbgs_leaves_zero_residual_on_second_colour_away_from_boundary_and_inter
     assert seen["bnd"] > 1e-3 * scale and seen["iface"] > 1e-3 * scale, (seen, scale)
     # and the first colour's residual is not zero anywhere near as often
     assert np.abs(r[:, ~black]).max() > 1e-3 * scale
+
+
+# ---------------------------------------------------------------- per-cell residual (sampled checks of large solves)
+
+
+def _grid_stencils(N, ufun, kfun):
+    """Every cell of the uniform N^3 grid on [0, 1]^3 as a 7-point stencil (cell, x-, x+, y-, y+, z-, z+): values of
+    ufun / kfun at the cell centres (a boundary neighbour gets a placeholder), the boundary flags, and g = ufun at
+    each boundary face's centre."""
+    h = 1.0 / N
+    t = (np.arange(N) + 0.5) * h
+    z, y, x = np.meshgrid(t, t, t, indexing="ij")
+    pts = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    idx = np.stack(np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")[::-1], axis=-1).reshape(-1, 3)
+    u7 = np.empty((len(pts), 7))
+    k7 = np.empty((len(pts), 7))
+    bnd = np.zeros((len(pts), 6), dtype=bool)
+    g = np.zeros((len(pts), 6))
+    u7[:, 0] = ufun(*pts.T)
+    k7[:, 0] = kfun(*pts.T)
+    for face in range(6):
+        axis, side = face // 2, face % 2
+        d = np.zeros(3)
+        d[axis] = h if side else -h
+        q = pts + d
+        bnd[:, face] = idx[:, axis] == (N - 1 if side else 0)
+        u7[:, 1 + face] = np.where(bnd[:, face], 0.0, ufun(*q.T))
+        k7[:, 1 + face] = np.where(bnd[:, face], 0.0, kfun(*q.T))
+        fc = pts + d / 2
+        g[:, face] = ufun(*fc.T)
+    return u7, k7, bnd, g, h, idx
+
+
+def test_stencil_residual_linear_and_quadratic():
+    """k = 1: a linear u with its own boundary values is reproduced exactly by the operator, reflection ghosts
+    included (A u = 0 at every cell); u = x^2 + y^2 - 3 z^2 / 2 gives A u = -lap u = -1 at every interior cell.  A sign
+    error in the reflection, the neighbour's k on a boundary face or a missing 1/h^2 fails one of them."""
+    one = lambda x, y, z: np.ones_like(x)
+    lin = lambda x, y, z: 1.0 + 2.0 * x - 3.0 * y + 0.5 * z
+    u7, k7, bnd, g, h, idx = _grid_stencils(8, lin, one)
+    au, r, s = residual_from_stencil(u7, k7, bnd, np.zeros(len(u7)), h, g)
+    np.testing.assert_allclose(au, 0.0, atol=1e-12 * s.max())
+    quad = lambda x, y, z: x ** 2 + y ** 2 - 1.5 * z ** 2
+    u7, k7, bnd, g, h, idx = _grid_stencils(8, quad, one)
+    au, r, s = residual_from_stencil(u7, k7, bnd, np.full(len(u7), -1.0), h, g)
+    inner = ~bnd.any(axis=1)
+    np.testing.assert_allclose(au[inner], -1.0, rtol=0, atol=1e-11 * s.max())
+    np.testing.assert_allclose(r[inner], 0.0, rtol=0, atol=1e-11 * s.max())
+
+
+def test_stencil_residual_material_jump_is_exact():
+    """k jumps from 1 to 10 across the plane x = 1/2 (a cell face); u is linear on each side with continuous flux
+    (k u' equal).  The harmonic face mean makes the discrete flux exact, so A u = 0 at every cell; an arithmetic face
+    mean, or the neighbour's k on a boundary face, fails it."""
+    k1, k2, a1 = 1.0, 10.0, 3.0
+    a2 = k1 * a1 / k2
+    kfun = lambda x, y, z: np.where(x < 0.5, k1, k2)
+    ufun = lambda x, y, z: np.where(x < 0.5, a1 * x, a1 * 0.5 + a2 * (x - 0.5))
+    u7, k7, bnd, g, h, idx = _grid_stencils(8, ufun, kfun)
+    au, r, s = residual_from_stencil(u7, k7, bnd, np.zeros(len(u7)), h, g)
+    np.testing.assert_allclose(au, 0.0, atol=1e-12 * s.max())
+
+
+def test_stencil_residual_agrees_with_the_forest_operator():
+    """Random u and k on 2^3 roots of 4^3 cells: the per-cell residual equals the forest operator's (OracleMG.apply_A)
+    at every cell."""
+    R, n = 2, 4
+    N = R * n
+    keys = syn.uniform_leaves(R)
+    rng = np.random.default_rng(84)
+    Ug = rng.normal(size=(N, N, N))
+    Kg = np.exp(rng.normal(size=(N, N, N)))
+    blocks = lambda G: np.stack([G[c * n:(c + 1) * n, b * n:(b + 1) * n, a * n:(a + 1) * n].reshape(-1)
+                                 for (_, a, b, c) in keys])
+    mg = OracleMG(R, n, keys, k_user=blocks(Kg))
+    want = mg.apply_A(blocks(Ug))
+    at = lambda G: (lambda x, y, z: G[np.minimum((z * N).astype(int), N - 1), np.minimum((y * N).astype(int), N - 1),
+                                      np.minimum((x * N).astype(int), N - 1)])
+    u7, k7, bnd, _, h, idx = _grid_stencils(N, at(Ug), at(Kg))
+    au, _, s = residual_from_stencil(u7, k7, bnd, np.zeros(len(u7)), h, 0.0)
+    got = blocks(au.reshape(N, N, N))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * s.max())
