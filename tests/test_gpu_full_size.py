@@ -1,8 +1,8 @@
 """The 512^3 workload at full size, in the launch configuration the benchmark times, checked at sampled cells.
 
 8^3 roots of 64^3 cells (134,217,728 cells), log-normal k (sigma 1, correlation length 0.1), f uniform in (-1, 1):
-the benchmark's inputs from the same seeded generators, FP32 V(2,2) cycles inside FP64 defect correction (the
-library's default count per step), face-averaged coarse levels, tuned smoother shapes and tail.  The oracle cannot
+the benchmark's inputs from the same seeded generators, FP32 V(2,2) cycles inside FP64 defect correction (five per
+step, the count the benchmark runs), face-averaged coarse levels, tuned smoother shapes and tail.  The oracle cannot
 build a forest of this size, so the check goes cell by cell: ``residual_from_stencil`` computes A u and
 r = f - A u in FP64 from each sampled cell's 7-point stencil of the GPU's solution and the input k.
 """
@@ -48,11 +48,18 @@ def test_512_cubed_solve_at_sampled_cells():
     assert N == 512 and len(keys) == 512
     k = syn.lognormal_k_rff(R, n, keys, seed=0, device=dev)
     f = syn.uniform_rhs(len(keys), n, seed=1).to(dev)
-    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=0, coarse_coef="faces")
+    F = Forest(R, n, keys, coeff=True, precision=1, inner_cycles=5, coarse_coef="faces")
     F.set_rhs(f, k)
     u = torch.zeros_like(f)
     cyc, rel = F.solve(u, rtol=1e-10, max_cycles=60)
     assert rel <= 1e-10 and cyc <= 20, (cyc, rel)
+    # a second solve from zero on the same forest repeats the first bit for bit (no state carries over)
+    u2 = torch.zeros_like(f)
+    cyc2, rel2 = F.solve(u2, rtol=1e-10, max_cycles=60)
+    print(f"512^3: tail from level {F.tail_level()}, shapes {F.smoother_shape(0)} / {F.smoother_shape(1)}, "
+          f"solves {cyc} / {cyc2} cycles, rel {rel:.6e} / {rel2:.6e}, max |u - u2| {(u - u2).abs().max().item():.3e}")
+    assert cyc2 == cyc and rel2 == rel and torch.equal(u2, u)
+    del u2
     au = F.apply(u)
     torch.cuda.synchronize()
     F.close()
