@@ -171,7 +171,8 @@ mg_status mg_exchange_level(mg_forest *forest, int32_t level, const double *u_de
  * cycles (precision 1) and conservative interfaces, the FP64 face coefficients that the fine-to-coarse ghosts
  * need are created by the first mg_exchange_level, mg_apply or mg_adjoint_solve call; before that, a level with
  * fine-to-coarse ghosts returns MG_ERR_STATE.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it.  All calls share the array and it keeps the last call's contents (each
+ * (cudaGetSymbolAddress) and caches it; make that first call before any CUDA stream capture starts in the process.
+ * All calls share the array and it keeps the last call's contents (each
  * call clears the part it uses): calls whose work overlaps on the GPU (other streams, other threads, other
  * forests) race on it.  The call enqueues its work on the forest's stream and synchronises that stream before
  * returning. */
