@@ -12,6 +12,7 @@ import torch
 
 import synthetic as syn
 from oracle.octree_mg import residual_from_stencil
+from tests.helpers import batch_stencils
 
 pytestmark = pytest.mark.gpu
 
@@ -94,49 +95,6 @@ def test_512_cubed_solve_at_sampled_cells():
           f"max |A u| error {(err / s).max() / eps:.2f} eps of the terms")
 
 
-def _batch_stencils(problems, rng, per_problem=64):
-    """Sampled cells of a batch whose six face neighbours are in the same block, in a same-level leaf or on the
-    domain boundary (cells next to a refinement interface are drawn and dropped): flat indices (m, 7) into the
-    batch layout (a boundary face's column repeats the cell), boundary flags (m, 6), problem ids and cell widths."""
-    idx, bnds, pids, hs = [], [], [], []
-    off = 0
-    for p, (n, keys) in enumerate(problems):
-        where = {key: b for b, key in enumerate(keys)}
-        for _ in range(per_problem):
-            b = int(rng.integers(0, len(keys)))
-            lev, bi, bj, bk = keys[b]
-            c = rng.integers(0, n, size=3)
-            row, flags, ok = [off + b * n ** 3 + int(c[0] + n * (c[1] + n * c[2]))], [], True
-            for face in range(6):
-                axis, side = face // 2, face % 2
-                q = c.copy()
-                q[axis] += 1 if side else -1
-                if 0 <= q[axis] < n:
-                    row.append(off + b * n ** 3 + int(q[0] + n * (q[1] + n * q[2])))
-                    flags.append(False)
-                    continue
-                nb = [bi, bj, bk]
-                nb[axis] += 1 if side else -1
-                if not 0 <= nb[axis] < 2 ** lev:
-                    row.append(row[0])
-                    flags.append(True)
-                    continue
-                key = (lev, *nb)
-                if key not in where:
-                    ok = False  # a refinement interface: not a same-level stencil
-                    break
-                q[axis] %= n
-                row.append(off + where[key] * n ** 3 + int(q[0] + n * (q[1] + n * q[2])))
-                flags.append(False)
-            if ok:
-                idx.append(row)
-                bnds.append(flags)
-                pids.append(p)
-                hs.append(1.0 / (n * 2 ** lev))
-        off += len(keys) * n ** 3
-    return np.array(idx), np.array(bnds), np.array(pids), np.array(hs)
-
-
 def test_batch_256_at_sampled_cells():
     """The 256-problem batch (block sizes 16..128, 0-2 refinement levels, 1.886e9 cells), built and solved to 1e-8 as
     the benchmark's batch configuration solves it (five FP32 cycles per step, face-averaged coarse levels, the tail
@@ -154,7 +112,7 @@ def test_batch_256_at_sampled_cells():
     cyc, rel = B.solve(u, rtol=1e-8, max_cycles=60)
     assert max(rel) <= 1e-8, max(rel)
     B.close()
-    idx, bnd, pid, h = _batch_stencils(problems, np.random.default_rng(86))
+    idx, bnd, pid, h = batch_stencils(problems, np.random.default_rng(86))
     assert len(idx) > 8000 and bnd.any()
     I = torch.from_numpy(idx).to(dev)
     u7 = u[I].cpu().numpy()

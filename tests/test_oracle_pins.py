@@ -1112,3 +1112,26 @@ def test_stencil_residual_agrees_with_the_forest_operator():
     au, _, s = residual_from_stencil(u7, k7, bnd, np.zeros(len(u7)), h, 0.0)
     got = blocks(au.reshape(N, N, N))
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * s.max())
+
+
+def test_batch_stencil_sampler_matches_the_forest_operator():
+    """The sampler behind the full-size batch check (tests.helpers.batch_stencils) on a small batch of refined
+    problems: at every sampled cell, the per-cell operator built from the sampled stencil equals the forest
+    operator of that problem (OracleMG.apply_A).  So the flat offsets, the neighbour blocks across block faces and
+    the boundary flags it returns are right, and cells next to refinement interfaces are left out."""
+    from tests.helpers import batch_stencils
+    problems = syn.batch_problems(count=6, seed=3, sizes=(4, 8), max_depth=2, box=(0.2, 0.5))
+    assert any(len(keys) > 1 for _, keys in problems)
+    rng = np.random.default_rng(87)
+    us, ks, want = [], [], []
+    for n, keys in problems:
+        k = np.exp(rng.normal(size=(len(keys), n ** 3)))
+        u = rng.normal(size=(len(keys), n ** 3))
+        want.append(OracleMG(1, n, keys, k_user=k).apply_A(u).reshape(-1))
+        us.append(u.reshape(-1))
+        ks.append(k.reshape(-1))
+    u, k, want = np.concatenate(us), np.concatenate(ks), np.concatenate(want)
+    idx, bnd, pid, h = batch_stencils(problems, np.random.default_rng(88), per_problem=200)
+    assert len(idx) > 600 and bnd.any() and len(np.unique(pid)) == len(problems)
+    au, _, s = residual_from_stencil(u[idx], k[idx], bnd, np.zeros(len(idx)), h, 0.0)
+    np.testing.assert_allclose(au, want[idx[:, 0]], rtol=0, atol=1e-12 * s.max())
