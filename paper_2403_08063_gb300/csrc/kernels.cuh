@@ -1580,7 +1580,13 @@ static __global__ void __launch_bounds__(544) k_residual_restrict32t(
         const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
         const float *__restrict__ ih2f, int64_t bsf, float *__restrict__ fc, float *__restrict__ uc,
         const XferItem *__restrict__ xf, int32_t nbc, int64_t bsc, Skip skip, const float *__restrict__ ax,
-        const float *__restrict__ ay, const float *__restrict__ az, int TY, int TZ, int D, int *__restrict__ err) {
+        const float *__restrict__ ay, const float *__restrict__ az, int TYr, int TZr, int Dr, int *__restrict__ err) {
+    // the tile the launch code uses, as constants: ring slots, segment offsets and plane strides fold into immediates
+    constexpr int TY = 8, TZ = 32, D = 1;
+    if (TYr != TY || TZr != TZ || Dr != D) {
+        if (threadIdx.x == 0) atomicOr(err, 4);
+        return;
+    }
     constexpr int n = 1 << LG, nc = n / 2, P = n + 2, H = half_row(P), HALF = P * P * H;
     static_assert(nc >= 32, "a warp per coarse row");
     extern __shared__ __align__(128) unsigned char smem_raw[];
