@@ -1572,9 +1572,11 @@ struct R32tDeviceSink {
 // bulk copies (plan above): consumer thread (X, Yl) owns coarse cell (X, y0 / 2 + Yl) of every coarse plane of the
 // tile and reads its box of u (and kappa / face coefficients) and f from the staged planes, with the arithmetic of
 // residual_restrict32_body (rr32_sum, rr32_store), so the results are bit-identical to k_residual_restrict32.
-// Warps of one coarse row each (nc >= 32); the CTA's last warp produces.  Every wait is bounded: a consumer warp
-// whose wait runs out sets bit 4 of *err and stops; the producer stops when a slot is not released in time, sets the
-// bit and waits, again bounded, for the copies it issued before it exits.
+// Warps of one coarse row each (nc >= 32); the CTA's last warp produces.  The tile is compiled in ({8, 32, 1}, the
+// one restrict32t_shape launches); a launch with another tile sets bit 4 of *err and returns before any barrier is
+// initialised.  Every wait is bounded: a consumer warp whose wait runs out sets bit 4 of *err and stops; the producer
+// stops when a slot is not released in time, sets the bit and waits, again bounded, for the copies it issued before
+// it exits.
 template <int MODE, int LG>
 static __global__ void __launch_bounds__(544) k_residual_restrict32t(
         const float *__restrict__ u, const float *__restrict__ f, const float *__restrict__ kap,
